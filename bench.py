@@ -1,0 +1,390 @@
+"""Benchmark: RTM shots of the layered 2 km x 2 km x 1 km model on GB300.
+
+Workload (one "step" = one complete RTM shot): ~1.9e5 tetrahedra, N = 4, FP32, three multi-rate
+levels, 10 Hz Ricker source at (1000, 1000, 8) m, 201 receivers, 1.5 s record, transparent
+boundaries; forward source run with boundary-trace recording, then the backward source and
+receiver runs in lockstep with both images (FP64 accumulation).  Metric: DOF updates per second
+(elements updated x 4 fields x Np per local step, both wavefields counted in the backward phase).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ridg|reference]
+
+Prints one JSON line.  With --gpus N > 1 (launched by torch.distributed.run) each rank migrates
+its own shot (shots are independent: weak scaling) and the images are summed over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "DOF-updates/s & RTM shots/s at stated error vs FP64; p50/p99 shot latency"
+UNIT = "DOF-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _workload():
+    from synth import config2_layered_rtm
+
+    return config2_layered_rtm()
+
+
+def _config(w, extra=None):
+    cfg = {
+        "workload": "layered 2x2x1 km RTM shot: 190608 tets, N=4, FP32, 3 LTS levels, 201 receivers, 1.5 s record",
+        "elements": int(w.K),
+        "order": w.N,
+        "record_s": w.t_final,
+        "receivers": int(len(w.receivers)),
+        "l2_policy": "inputs larger than L2 (fields+history+traces of two wavefields are ~GBs)",
+    }
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.path = os.path.join("/tmp", f"ridg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _rejected(clocks):
+    bad = {"hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown"}
+    if any(r in bad for r in clocks.get("reasons", [])):
+        return True
+    sm, smax = clocks.get("sm_mhz"), clocks.get("sm_max_mhz")
+    if sm and smax and sm < 0.6 * smax and not clocks.get("reasons"):
+        return True
+    return False
+
+
+# --------------------------------------------------------------------------- roofline helpers
+def step_bytes_per_element(Np, Nfp, W, real_bytes=4):
+    """Algorithmic bytes one element moves in one fused step with W wavefields.
+
+    Per wavefield: q read + write (8 Np), two older right-hand sides read and the new one written
+    (12 Np), neighbour traces read and own traces written (2 x 8 Nfp), injection range (8 B).
+    Per element: FP64 geometry (25 doubles), material and penalties (11 words), connectivity and
+    flags (4 neighbour slots + 4 face bytes + boundary index + flags = 28 B); with W = 2 the two
+    FP64 images are read and written (32 Np B)."""
+    per_wave = (20 * Np + 16 * Nfp) * real_bytes + 8
+    per_elem = 25 * 8 + 11 * real_bytes + 28
+    img = 32 * Np if W == 2 else 0
+    return W * per_wave + per_elem + img
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def _traffic():
+    path = os.path.join(ROOT, "profiles", "dg_step_traffic.json")
+    try:
+        d = json.load(open(path))
+        return d
+    except (OSError, ValueError):
+        return None
+
+
+# --------------------------------------------------------------------------- CPU oracle leg
+ORACLE_SAMPLE = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+from synth import config2_layered_rtm
+from oracle.rtm import make_problem
+from oracle.mrab import MRAB
+from oracle.wavelet import ricker
+w = config2_layered_rtm()
+prob = make_problem(w.xyz, w.tets, w.c, w.rho, w.N, default_bc=w.default_bc, cfl=w.cfl, n_levels_max=w.n_levels_max)
+g = prob.geo
+ks, rs = g.locate(w.source_xyz)
+S = MRAB(g, prob.levels, prob.n_levels, prob.dt_local, +1)
+S.injections = [(ks, g.source_weights(ks, rs), lambda tau: float(ricker(tau * prob.dt_local, w.f0, w.t_peak)))]
+steps = {steps}
+out = []
+for i in range(steps):
+    d0 = S.dof_updates
+    t0 = time.perf_counter()
+    S.global_step()
+    out.append((S.dof_updates - d0, time.perf_counter() - t0))
+print(json.dumps(out))
+"""
+
+
+def run_oracle_steps(steps, timeout=1800):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[v] = "1"
+    r = subprocess.run([sys.executable, "-c", ORACLE_SAMPLE.format(root=ROOT, steps=steps)], capture_output=True,
+                       text=True, env=env, timeout=timeout)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_line():
+    res = run_oracle_steps(1)
+    dof, sec = res[-1]
+    return {"value": dof / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"1 global MRAB step (4 steps of the finest level, source on) of the same 190608-tet N=4 "
+                      f"mesh in the FP64 numpy oracle, 1 thread: {dof} DOF updates in {sec:.2f} s"}
+
+
+# --------------------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    w = _workload()
+    res = run_oracle_steps(args.warmup + args.steps)
+    timed = res[args.warmup:]
+    dof = sum(d for d, _ in timed)
+    sec = sum(s for _, s in timed)
+    value = dof / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(w, {"reference_step": "one global MRAB step of the forward source run"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} global MRAB steps after {args.warmup} warm-up steps, FP64 numpy, 1 thread"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+def run_ridg(args):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    # the oracle CPU baseline runs in its own process; start it before the GPU work (rank 0, N = 1)
+    cpu_future = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import concurrent.futures as cf
+
+        cpu_pool = cf.ThreadPoolExecutor(max_workers=1)
+        cpu_future = cpu_pool.submit(cpu_baseline_line)
+
+    from paper_1506_00907_gb300 import ridg
+
+    w = _workload()
+    dev = torch.device("cuda", local)
+    torch.cuda.synchronize()
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max,
+                    stream=torch.cuda.current_stream(dev).cuda_stream)
+    info = s.info
+    nrec = len(w.receivers)
+    n_t = s.trace_len(w.t_final)
+    src_x = tuple(float(v) for v in w.source_xyz)
+    # shots differ per rank by a lateral source shift (independent shots of a survey line)
+    src_x = (src_x[0] + 50.0 * rank, src_x[1], src_x[2])
+    traces = torch.zeros((nrec, n_t), dtype=torch.float64, device=dev)
+    observed = torch.zeros_like(traces)
+    img_p = torch.zeros((w.K, info.Np), dtype=torch.float64, device=dev)
+    img_q = torch.zeros_like(img_p)
+
+    def shot(obs):
+        s.rtm_shot_device(src_x, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start, observed=obs,
+                          traces=traces, image_p=img_p, image_q=img_q)
+        if dist is not None:
+            dist.all_reduce(img_p)
+            dist.all_reduce(img_q)
+
+    # warm-up: the first shot models the data that later shots migrate
+    s.set_profiling(16)
+    for i in range(args.warmup):
+        shot(None if i == 0 else observed)
+        if i == 0:
+            torch.cuda.synchronize()
+            observed.copy_(traces)
+    torch.cuda.synchronize()
+
+    def timed_region():
+        clock = ClockSampler(local)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clock.start()
+        st = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        wall0 = time.perf_counter()
+        e0.record(st)
+        launches = 0
+        for _ in range(args.steps):
+            shot(observed)
+            launches += s.shot_stats().kernel_launches
+        e1.record(st)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if dist is not None:
+            dist.barrier()
+        clocks = clock.stop()
+        return e0.elapsed_time(e1) / 1e3, wall, launches, clocks
+
+    sec, wall, launches, clocks = timed_region()
+    if _rejected(clocks):
+        sec, wall, launches, clocks = timed_region()
+    stats = s.shot_stats()
+    dof_shot = stats.dof_updates_forward + stats.dof_updates_backward
+    if dist is not None:
+        t = torch.tensor([sec], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sec = float(t.item())
+    value = world * dof_shot * args.steps / sec
+
+    # roofline of the dominant kernel: the fused backward step over every element (two wavefields)
+    Np, Nfp = info.Np, info.Nfp
+    bw_ms = stats.prof_backward_ms / max(stats.prof_backward_launches, 1)
+    fw_ms = stats.prof_forward_ms / max(stats.prof_forward_launches, 1)
+    bytes_bw = w.K * step_bytes_per_element(Np, Nfp, 2) + info.n_half_step * 2 * 8 * Nfp * 4
+    bytes_fw = w.K * step_bytes_per_element(Np, Nfp, 1) + info.n_half_step * 8 * Nfp * 4
+    peak, peak_kind = _peaks()
+    ach_bw = bytes_bw / (bw_ms * 1e-3) / 1e9
+    ach_fw = bytes_fw / (fw_ms * 1e-3) / 1e9
+    tr = _traffic()
+    traffic = None
+    if tr and tr.get("kernel") == "dg_step_kernel<4,float,2>" and tr.get("source_hash") == _kernel_hash():
+        traffic = tr.get("bytes_per_launch_full_mesh")
+    roofline = {"bound": "hbm", "achieved": ach_bw, "peak": peak, "unit": "GB/s", "frac": ach_bw / peak,
+                "traffic": traffic, "kernel": "dg_step_kernel<4,float,2> (backward S+R+images, all levels)",
+                "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_bw, "avg_launch_ms": bw_ms,
+                "forward_kernel": {"achieved": ach_fw, "frac": ach_fw / peak, "avg_launch_ms": fw_ms,
+                                   "algorithmic_bytes_per_launch": bytes_fw}}
+
+    # end to end through the host-buffer call: H2D of the observed traces, D2H of traces and images
+    obs_host = observed.cpu().numpy()
+    t0 = time.perf_counter()
+    tr_h, ip_h, iq_h = s.rtm_shot(src_x, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start,
+                                  observed=obs_host)
+    e2e_sec = time.perf_counter() - t0
+    e2e = {"value": world * dof_shot / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": int(obs_host.nbytes),
+           "d2h_bytes_per_step": int(tr_h.nbytes + ip_h.nbytes + iq_h.nbytes), "shots_per_s": world / e2e_sec}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(w, {"levels": [int(x) for x in info.level_count[:info.n_levels]],
+                                  "dt_local_s": info.dt_local, "global_steps": int(stats.n_global),
+                                  "boundary_trace_bytes": int(stats.boundary_trace_bytes),
+                                  "parallelism": f"shots x{world} (replicas, image all-reduce)"}),
+            "shots_per_s": world * args.steps / sec,
+            "dof_updates_per_shot": int(dof_shot),
+            "wall_s": wall,
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+        if cpu_future is not None:
+            try:
+                line["cpu_baseline"] = cpu_future.result(timeout=1800)
+            except Exception as exc:  # noqa: BLE001
+                line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                        "sample": f"failed: {exc}"}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _kernel_hash():
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in ("step_kernel.cuh",):
+        h.update(open(os.path.join(ROOT, "paper_1506_00907_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ridg", choices=["ridg", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    from paper_1506_00907_gb300.build import build
+
+    build()
+    return run_ridg(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,203 @@
+/*
+ * ridg.h -- C ABI of the GB300 nodal discontinuous-Galerkin RTM library.
+ *
+ * The library solves the first-order acoustic pressure-velocity system
+ *     dp/dt + rho c^2 div v = f(t) delta(x - x0),      rho dv/dt + grad p = 0
+ * (Sec. 2, Eqs. waveSyst1-2) on unstructured tetrahedra with the nodal DG scheme of
+ * Sec. 3.1 (Eqs. dgLocalSchemeP/U), the multi-rate Adams-Bashforth local time stepping of
+ * Sec. 3.2 (Eqs. updateAB, updateABcoarse, Algorithm 1), and accumulates the classical
+ * (Eq. imageP) and characteristic (Eqs. imageQ, charact) imaging conditions of one RTM shot
+ * with the AB3-exact increments of Sec. 3.3 (Eq. updateABcorr).  Every step of the time loop
+ * runs in CUDA kernels for sm_103a; the host only prepares the mesh and schedules launches.
+ *
+ * Conventions
+ *  - Every function returns an int status: RIDG_OK (0) or a negative RIDG_E_* code.  The
+ *    message of the last failure of the calling thread is returned by ridg_last_error().
+ *    No C++ exception crosses this interface.
+ *  - Arrays are C-contiguous.  "host" pointers are read or written by the CPU; "device"
+ *    pointers must be CUDA device memory of the current device.  The library copies every
+ *    input it keeps; the caller keeps ownership of all buffers it passes.
+ *  - Element fields are laid out [K][4][Np] with the fields (p, vx, vy, vz) and the nodes in
+ *    the reference order: equidistant lattice order (t slowest, then s, r fastest) of the
+ *    warp-and-blend nodes of Sec. 3.1.  Np = (N+1)(N+2)(N+3)/6.
+ *  - Local face f of tetrahedron (v0,v1,v2,v3) is spanned by the vertices
+ *    f=0:(v0,v1,v2), f=1:(v0,v1,v3), f=2:(v1,v2,v3), f=3:(v0,v2,v3).
+ *  - Handles are not thread safe; use one solver per host thread and stream.
+ */
+#ifndef RIDG_H
+#define RIDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+#define RIDG_OK 0
+#define RIDG_E_INVALID_ARG -1 /* a size, pointer or option is out of range */
+#define RIDG_E_BAD_MESH -2    /* degenerate/inverted element, non-manifold face, boundary code on an interior face */
+#define RIDG_E_OOM -3         /* device or host memory could not be allocated */
+#define RIDG_E_CUDA -4        /* a CUDA call failed (message holds cudaGetErrorString) */
+#define RIDG_E_UNSTABLE -5    /* a non-finite value or energy growth was detected */
+#define RIDG_E_TIMEOUT -6     /* a bounded device-side wait gave up */
+#define RIDG_E_NOT_FOUND -7   /* a source or receiver lies outside the mesh */
+
+/* boundary-condition codes per local face (Sec. 2): 0 = automatic (interior where a neighbour
+ * exists, else the default code), 1 = free surface p = 0, 2 = transparent p - rho c n.v = 0
+ * (Eq. ABC), 3 = rigid wall n.v = 0. */
+#define RIDG_BC_AUTO 0
+#define RIDG_BC_FREE 1
+#define RIDG_BC_TRANSPARENT 2
+#define RIDG_BC_RIGID 3
+
+/* working precision of the fields and kernels */
+#define RIDG_F32 0
+#define RIDG_F64 1
+
+typedef struct ridg_mesh ridg_mesh;
+typedef struct ridg_solver ridg_solver;
+
+/* Returns the message of the last failing call of this thread ("" if none). */
+const char* ridg_last_error(void);
+
+/* Library version string. */
+const char* ridg_version(void);
+
+/* ------------------------------------------------------------------ mesh (host only)
+ * Creates a tetrahedral mesh (Sec. 3.1: Omega = union of the cells D_k).
+ *   xyz      host double [n_vert][3]  vertex coordinates
+ *   tet      host int64  [K][4]       vertex indices; every element must have positive
+ *                                      orientation det[v1-v0, v2-v0, v3-v0] > 0
+ *   face_bc  host int8   [K][4] or NULL  boundary code per local face (RIDG_BC_*); a non-zero
+ *                                      code on a face shared by two elements is RIDG_E_BAD_MESH
+ *   default_bc                          code of unmatched faces whose face_bc is 0
+ * Faces are matched by their vertex triples.  Errors: RIDG_E_INVALID_ARG, RIDG_E_BAD_MESH. */
+int ridg_mesh_create(const double* xyz, int64_t n_vert, const int64_t* tet, int64_t K, const int8_t* face_bc,
+                     int8_t default_bc, ridg_mesh** out);
+void ridg_mesh_destroy(ridg_mesh* mesh);
+/* Number of boundary faces, interior faces of the mesh (host only). */
+int ridg_mesh_counts(const ridg_mesh* mesh, int64_t* n_boundary_faces, int64_t* n_interior_faces);
+
+/* ------------------------------------------------------------------ reference element (host only)
+ * Operators of the reference tetrahedron of order N (Sec. 3.1 and the appendix), computed by the
+ * library's own setup code.  Any output pointer may be NULL.
+ *   rst   [Np][3]   node coordinates          D     [3][Np][Np]  D_r, D_s, D_t
+ *   M     [Np][Np]  mass matrix               LIFT  [Np][4*Nfp]  M^{-1} E (face masses on a
+ *   fmask [4][Nfp]  face node indices                            2-D reference triangle of area 2) */
+int ridg_reference_operators(int N, double* rst, double* D, double* M, double* LIFT, int32_t* fmask);
+
+/* ------------------------------------------------------------------ solver */
+typedef struct ridg_options {
+  int32_t dtype;        /* RIDG_F32 (default) or RIDG_F64 */
+  double cfl;           /* C in Delta t_k = C l_k / ((N+1)^2 c_k) (Sec. 5.1); <= 0 selects 0.15 */
+  int32_t n_levels_max; /* maximum number of multi-rate levels (Sec. 3.2); <= 0 selects 3 */
+  int32_t reserved[5];
+} ridg_options;
+
+typedef struct ridg_info {
+  int32_t N, Np, Nfp, n_levels;
+  int64_t K;
+  double dt_local, dt_global;  /* Delta t_local and Delta t_global = 2^(n_levels-1) Delta t_local */
+  int64_t level_count[8];      /* elements per level, level 1 (coarsest) first */
+  int64_t n_boundary_faces;
+  int64_t device_bytes;        /* device memory held by the solver (fields, history, traces, tables) */
+  int64_t n_half_step;         /* elements with a finer neighbour (they also write half-step traces) */
+} ridg_info;
+
+/* Creates a solver for order N (1..6) with piecewise-constant c, rho per element (host double
+ * [K] each, positive).  Sets up the reference operators, geometric factors (inverse Jacobian,
+ * normals, J_f/J), face connectivity, multi-rate levels (coarsest level each element's bound
+ * allows, then moved finer until neighbours differ by at most one level) and uploads them.
+ * cuda_stream: a cudaStream_t cast to uintptr_t (0 = default stream); every kernel of this
+ * solver runs on it.  The state starts at rest at t = 0.
+ * Errors: RIDG_E_INVALID_ARG, RIDG_E_BAD_MESH, RIDG_E_OOM, RIDG_E_CUDA. */
+int ridg_solver_create(const ridg_mesh* mesh, int N, const double* c, const double* rho, const ridg_options* opt,
+                       uintptr_t cuda_stream, ridg_solver** out);
+void ridg_solver_destroy(ridg_solver* s);
+int ridg_solver_info(const ridg_solver* s, ridg_info* info);
+/* Level (1 = coarsest) of every element, host int32 [K]. */
+int ridg_solver_levels(const ridg_solver* s, int32_t* levels);
+/* Physical node coordinates, host double [K][Np][3]. */
+int ridg_solver_nodes(const ridg_solver* s, double* xyz);
+
+/* ------------------------------------------------------------------ state access
+ * ridg_set_state: q host double [K][4][Np]; sets the fields, recomputes the traces, resets the
+ *   time to t = 0 and the right-hand-side history to zero.
+ * ridg_set_history: host double [K][4][Np] each (may be NULL = zero): the right-hand sides one
+ *   and two level steps before the current time (each element at its own level's step), the
+ *   values Eq. updateAB needs before the first step.
+ * ridg_eval_rhs: host double in [K][4][Np] -> out [K][4][Np]: the right-hand side of Eqs.
+ *   dgLocalSchemeP/U (forward tau, no source) of the given fields, evaluated by the CUDA kernel.
+ *   Does not change the solver's state.
+ * ridg_step: advances n_global global steps (Algorithm 1; one fused kernel launch per step of the
+ *   finest level), asynchronously on the solver's stream.
+ * ridg_get_state: copies the fields to host double [K][4][Np] (synchronises the stream). */
+int ridg_set_state(ridg_solver* s, const double* q);
+int ridg_set_history(ridg_solver* s, const double* rhs_prev1, const double* rhs_prev2);
+int ridg_eval_rhs(ridg_solver* s, const double* q, double* rhs_out);
+int ridg_step(ridg_solver* s, int64_t n_global);
+int ridg_get_state(ridg_solver* s, double* q_out);
+/* Discrete energy sum_k J_k/2 (p^T M p/(rho c^2) + rho v^T M v), accumulated in FP64 on the device. */
+int ridg_energy(ridg_solver* s, double* energy);
+
+/* ------------------------------------------------------------------ one RTM shot (Sec. 2, Sec. 4.3)
+ * Source: Ricker pulse f(t) = amplitude (1 - 2 pi^2 f0^2 tau^2) exp(-pi^2 f0^2 tau^2), tau = t - t_peak,
+ * at source_xyz (Eq. waveSyst1, L2-projected Dirac of Eq. sourceTerm).
+ * Receivers: rec_xyz host double [nrec][3]; traces are sampled at t_n = n Delta t_global for
+ * n = 0 .. n_t-1 with n_t = ridg_trace_len(s, t_final) = ceil(t_final / Delta t_global) + 1.
+ *
+ * ridg_rtm_shot runs (i) the forward source run with receiver sampling and the recording of the
+ * traces (p, n.v) on every boundary face at every evaluation time of its element, two global steps
+ * past t_final; (ii) the backward source run from the saved final state, whose boundary faces take
+ * the recorded traces as their exterior state; (iii) the backward receiver run that re-injects the
+ * observed traces (cubic Lagrange interpolation in time); (ii) and (iii) run in lockstep in one
+ * fused kernel per step, which also accumulates the two images over [t_image_start, t_final].
+ *   observed   host double [nrec][n_t] or NULL (= re-inject the modelled traces)
+ *   traces_out host double [nrec][n_t] or NULL
+ *   image_p    host double [K][Np] or NULL: classical image int p_S p_R dt (Eq. imageP)
+ *   image_q    host double [K][Np] or NULL: characteristic image int q^-_S q^+_R dt (Eq. imageQ),
+ *              q^{+/-} = p +/- c rho (e_up . v)
+ *   e_up       host double [3] or NULL (= (0,0,-1): z is depth)
+ * The images are accumulated in FP64.  The call synchronises the stream before returning.
+ * Errors: RIDG_E_INVALID_ARG, RIDG_E_NOT_FOUND, RIDG_E_OOM (boundary-trace arena), RIDG_E_CUDA,
+ * RIDG_E_UNSTABLE. */
+typedef struct ridg_source {
+  double xyz[3];
+  double f0, t_peak, amplitude;
+} ridg_source;
+
+int64_t ridg_trace_len(const ridg_solver* s, double t_final);
+int ridg_rtm_shot(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                  double t_image_start, const double* observed, double* traces_out, double* image_p,
+                  double* image_q, const double* e_up);
+/* Same shot with device buffers: observed, traces_out (double [nrec][n_t]) and image_p, image_q
+ * (double [K][Np]) are device pointers (observed/traces_out/images may be NULL).  Nothing is
+ * copied between host and device except the small per-shot tables; the call returns after the
+ * work is enqueued (synchronise the solver's stream before reading the outputs). */
+int ridg_rtm_shot_device(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec,
+                         double t_final, double t_image_start, const double* observed_dev, double* traces_dev,
+                         double* image_p_dev, double* image_q_dev, const double* e_up);
+
+/* Counters of the last shot: DOF updates (elements updated x 4 x Np, both wavefields counted in
+ * the backward phase), fused-kernel launches and total kernel launches. */
+typedef struct ridg_shot_stats {
+  int64_t dof_updates_forward, dof_updates_backward;
+  int64_t fused_launches, kernel_launches;
+  int64_t n_global, boundary_trace_bytes;
+  /* with profiling on: CUDA-event time (ms) and count of the sampled fused launches that cover
+   * every element (all levels active), forward (one wavefield) and backward (two wavefields) */
+  double prof_forward_ms, prof_backward_ms;
+  int64_t prof_forward_launches, prof_backward_launches;
+} ridg_shot_stats;
+/* Synchronises the solver's stream, then returns the counters of the last shot. */
+int ridg_last_shot_stats(const ridg_solver* s, ridg_shot_stats* stats);
+
+/* Profiling: when every > 0, every every-th global step the fused launch that covers all elements
+ * is bracketed by CUDA events on the solver's stream; 0 turns it off (default). */
+int ridg_set_profiling(ridg_solver* s, int32_t every);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RIDG_H */

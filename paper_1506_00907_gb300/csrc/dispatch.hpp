@@ -1,0 +1,21 @@
+// Per-order launch entry points, instantiated in kernels_n<N>.cu.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "step_kernel.cuh"
+
+namespace ridg {
+
+template <int N, typename real>
+struct Launch {
+  static cudaError_t step(const StepArgs<real>& a, int W, cudaStream_t st);
+  static cudaError_t init_traces(const real* q, real* trace, int slot, int64_t n_slots, const double* geo,
+                                 const int* meta, const int* fmask, cudaStream_t st);
+  static cudaError_t sample(const real* q, const int64_t* rec_slot, const real* rec_row, int nrec, double* out,
+                            int64_t n_time, int64_t col, cudaStream_t st);
+  static cudaError_t energy(const real* q, int64_t n_slots, const double* J, const real* mat, const int* meta,
+                            const double* M, double* out, cudaStream_t st);
+  static cudaError_t image_out(const double* img, const int64_t* slot_of, int64_t K, double* out, cudaStream_t st);
+};
+
+}  // namespace ridg

@@ -1,0 +1,572 @@
+// Host setup of the nodal DG discretisation (Sec. 3.1, Sec. 3.2 and the appendix).
+//
+// The reference element spans P_N with products of Legendre polynomials L_a(r) L_b(s) L_c(t),
+// a+b+c <= N, and integrates with a collapsed-coordinate Gauss-Legendre rule that is exact for
+// the degrees involved.  Nodes are the warp-and-blend nodes (Warburton 2006, cited in Sec. 3.1),
+// without the optimisation constant.  Face-node correspondences come from the nodes' lattice
+// barycentrics and the vertex correspondence of the shared triangle; normals and J_f/J from
+// Nanson's formula.
+#include "setup.hpp"
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "../../include/ridg.h"
+
+namespace ridg {
+
+// ------------------------------------------------------------------ dense helpers
+Mat matmul(const Mat& A, const Mat& B) {
+  Mat C(A.r, B.c);
+  for (int i = 0; i < A.r; ++i)
+    for (int k = 0; k < A.c; ++k) {
+      double a = A(i, k);
+      if (a == 0.0) continue;
+      for (int j = 0; j < B.c; ++j) C(i, j) += a * B(k, j);
+    }
+  return C;
+}
+
+Mat transpose(const Mat& A) {
+  Mat T(A.c, A.r);
+  for (int i = 0; i < A.r; ++i)
+    for (int j = 0; j < A.c; ++j) T(j, i) = A(i, j);
+  return T;
+}
+
+Mat inverse(const Mat& A) {
+  int n = A.r;
+  Mat LU = A, inv(n, n);
+  std::vector<int> piv(n);
+  std::iota(piv.begin(), piv.end(), 0);
+  for (int k = 0; k < n; ++k) {
+    int p = k;
+    for (int i = k + 1; i < n; ++i)
+      if (std::fabs(LU(i, k)) > std::fabs(LU(p, k))) p = i;
+    if (LU(p, k) == 0.0) throw Error{RIDG_E_INVALID_ARG, "singular matrix in reference-element setup"};
+    if (p != k) {
+      for (int j = 0; j < n; ++j) std::swap(LU(p, j), LU(k, j));
+      std::swap(piv[p], piv[k]);
+    }
+    for (int i = k + 1; i < n; ++i) {
+      LU(i, k) /= LU(k, k);
+      for (int j = k + 1; j < n; ++j) LU(i, j) -= LU(i, k) * LU(k, j);
+    }
+  }
+  for (int col = 0; col < n; ++col) {
+    std::vector<double> x(n);
+    for (int i = 0; i < n; ++i) x[i] = (piv[i] == col) ? 1.0 : 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < i; ++j) x[i] -= LU(i, j) * x[j];
+    for (int i = n - 1; i >= 0; --i) {
+      for (int j = i + 1; j < n; ++j) x[i] -= LU(i, j) * x[j];
+      x[i] /= LU(i, i);
+    }
+    for (int i = 0; i < n; ++i) inv(i, col) = x[i];
+  }
+  return inv;
+}
+
+// ------------------------------------------------------------------ 1-D polynomials
+// Legendre P_n(x) and P_n'(x) by the three-term recurrence.
+static void legendre(int n, double x, double& p, double& dp) {
+  double p0 = 1.0, p1 = x;
+  if (n == 0) {
+    p = 1.0;
+    dp = 0.0;
+    return;
+  }
+  for (int k = 2; k <= n; ++k) {
+    double pk = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+    p0 = p1;
+    p1 = pk;
+  }
+  p = p1;
+  // derivative from n (P_{n-1} - x P_n) = (1 - x^2) P_n'; at x = +-1 use P_n'(+-1) = (+-1)^{n-1} n(n+1)/2
+  if (std::fabs(1.0 - x * x) < 1e-14) {
+    dp = (x > 0 ? 1.0 : ((n % 2) ? 1.0 : -1.0)) * n * (n + 1) / 2.0;
+  } else {
+    dp = n * (p0 - x * p1) / (1.0 - x * x);
+  }
+}
+
+std::vector<double> gauss_lobatto(int N) {
+  std::vector<double> x(N + 1);
+  x[0] = -1.0;
+  x[N] = 1.0;
+  for (int j = 1; j < N; ++j) {
+    double z = -std::cos(M_PI * j / N);
+    for (int it = 0; it < 100; ++it) {
+      double p, dp;
+      legendre(N, z, p, dp);
+      // second derivative from the Legendre equation
+      double d2p = (2.0 * z * dp - N * (N + 1.0) * p) / (1.0 - z * z);
+      double dz = dp / d2p;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    x[j] = z;
+  }
+  return x;
+}
+
+static void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n);
+  w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double p = 0, dp = 0;
+    for (int it = 0; it < 100; ++it) {
+      legendre(n, z, p, dp);
+      double dz = p / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) break;
+    }
+    legendre(n, z, p, dp);
+    x[i] = z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// blend-divided 1-D warp: (GLL - equidistant displacement interpolant)(r) / (1 - r^2)
+static double warp_factor(int N, double r) {
+  if (std::fabs(r) >= 1.0 - 1e-10) return 0.0;
+  std::vector<double> gll = gauss_lobatto(N);
+  double w = 0.0;
+  for (int i = 0; i <= N; ++i) {
+    double ri = -1.0 + 2.0 * i / N;
+    double li = 1.0;
+    for (int j = 0; j <= N; ++j) {
+      if (j == i) continue;
+      double rj = -1.0 + 2.0 * j / N;
+      li *= (r - rj) / (ri - rj);
+    }
+    w += (gll[i] - ri) * li;
+  }
+  return w / (1.0 - r * r);
+}
+
+// ------------------------------------------------------------------ nodes
+static std::vector<std::array<double, 3>> warp_blend_nodes(int N, std::vector<std::array<int, 4>>& lattice) {
+  // vertices of an equilateral tetrahedron, in the order of the reference vertices v0..v3
+  const double s3 = std::sqrt(3.0), s6 = std::sqrt(6.0);
+  const double E[4][3] = {{-1.0, -1.0 / s3, -1.0 / s6}, {1.0, -1.0 / s3, -1.0 / s6}, {0.0, 2.0 / s3, -1.0 / s6},
+                          {0.0, 0.0, 3.0 / s6}};
+  std::vector<std::array<double, 3>> out;
+  lattice.clear();
+  for (int kt = 0; kt <= N; ++kt)
+    for (int js = 0; js <= N - kt; ++js)
+      for (int ir = 0; ir <= N - js - kt; ++ir) {
+        // barycentrics of the lattice point: lambda_1 ~ r, lambda_2 ~ s, lambda_3 ~ t
+        int l1 = ir, l2 = js, l3 = kt, l0 = N - ir - js - kt;
+        lattice.push_back({l0, l1, l2, l3});
+        double lam[4] = {double(l0) / N, double(l1) / N, double(l2) / N, double(l3) / N};
+        double X[3] = {0, 0, 0};
+        for (int v = 0; v < 4; ++v)
+          for (int d = 0; d < 3; ++d) X[d] += lam[v] * E[v][d];
+        double shift[3] = {0, 0, 0};
+        int npos = 0;
+        for (int v = 0; v < 4; ++v) npos += (lam[v] > 1e-10);
+        bool edge = (npos == 2);
+        if (N > 1) {
+          for (int f = 0; f < 4; ++f) {
+            const int* fv = kFaceVerts[f];
+            int o = kFaceOpp[f];
+            double warp[3] = {0, 0, 0};
+            int pairs[3][2] = {{fv[0], fv[1]}, {fv[1], fv[2]}, {fv[2], fv[0]}};
+            for (auto& pr : pairs) {
+              int a = pr[0], b = pr[1];
+              double t[3], nt = 0;
+              for (int d = 0; d < 3; ++d) {
+                t[d] = E[b][d] - E[a][d];
+                nt += t[d] * t[d];
+              }
+              nt = std::sqrt(nt);
+              double amt = 4.0 * lam[a] * lam[b] * warp_factor(N, lam[b] - lam[a]);
+              for (int d = 0; d < 3; ++d) warp[d] += amt * t[d] / nt;
+            }
+            if (edge) {
+              if (lam[o] < 1e-10)
+                for (int d = 0; d < 3; ++d) shift[d] = warp[d];  // unblended edge warp (set, not added)
+              continue;
+            }
+            double num = lam[fv[0]] * lam[fv[1]] * lam[fv[2]];
+            double den = (lam[fv[0]] + 0.5 * lam[o]) * (lam[fv[1]] + 0.5 * lam[o]) * (lam[fv[2]] + 0.5 * lam[o]);
+            double blend = den > 1e-10 ? num / den : 0.0;
+            for (int d = 0; d < 3; ++d) shift[d] += blend * warp[d];
+          }
+        }
+        double Xw[3] = {X[0] + shift[0], X[1] + shift[1], X[2] + shift[2]};
+        // invert X = (E1+E2+E3-E0)/2 + (r (E1-E0) + s (E2-E0) + t (E3-E0))/2
+        Mat A(3, 3);
+        double rhs[3];
+        for (int d = 0; d < 3; ++d) {
+          A(d, 0) = 0.5 * (E[1][d] - E[0][d]);
+          A(d, 1) = 0.5 * (E[2][d] - E[0][d]);
+          A(d, 2) = 0.5 * (E[3][d] - E[0][d]);
+          rhs[d] = Xw[d] - 0.5 * (E[1][d] + E[2][d] + E[3][d] - E[0][d]);
+        }
+        Mat Ai = inverse(A);
+        std::array<double, 3> p{};
+        for (int i = 0; i < 3; ++i) p[i] = Ai(i, 0) * rhs[0] + Ai(i, 1) * rhs[1] + Ai(i, 2) * rhs[2];
+        out.push_back(p);
+      }
+  return out;
+}
+
+// ------------------------------------------------------------------ basis
+static std::vector<std::array<int, 3>> basis_indices(int N) {
+  std::vector<std::array<int, 3>> idx;
+  for (int a = 0; a <= N; ++a)
+    for (int b = 0; b <= N - a; ++b)
+      for (int c = 0; c <= N - a - b; ++c) idx.push_back({a, b, c});
+  return idx;
+}
+
+static void basis_eval(int N, const std::array<double, 3>& p, std::vector<double>& phi, std::vector<double>* grad) {
+  auto idx = basis_indices(N);
+  double L[3][8], dL[3][8];
+  for (int d = 0; d < 3; ++d)
+    for (int n = 0; n <= N; ++n) legendre(n, p[d], L[d][n], dL[d][n]);
+  phi.resize(idx.size());
+  if (grad) grad->assign(3 * idx.size(), 0.0);
+  for (size_t q = 0; q < idx.size(); ++q) {
+    int a = idx[q][0], b = idx[q][1], c = idx[q][2];
+    phi[q] = L[0][a] * L[1][b] * L[2][c];
+    if (grad) {
+      (*grad)[0 * idx.size() + q] = dL[0][a] * L[1][b] * L[2][c];
+      (*grad)[1 * idx.size() + q] = L[0][a] * dL[1][b] * L[2][c];
+      (*grad)[2 * idx.size() + q] = L[0][a] * L[1][b] * dL[2][c];
+    }
+  }
+}
+
+std::vector<double> RefElem::basis_at(const std::array<double, 3>& p) const {
+  std::vector<double> phi;
+  basis_eval(N, p, phi, nullptr);
+  return phi;
+}
+
+std::vector<double> RefElem::lagrange_at(const std::array<double, 3>& p) const {
+  // l(p) = V^{-T} phi(p)
+  std::vector<double> phi = basis_at(p), l(Np, 0.0);
+  for (int i = 0; i < Np; ++i)
+    for (int q = 0; q < Np; ++q) l[i] += Vinv(q, i) * phi[q];
+  return l;
+}
+
+const int kTriPerm[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+RefElem build_reference(int N) {
+  if (N < 1 || N > 6) throw Error{RIDG_E_INVALID_ARG, "order N must be in 1..6"};
+  RefElem re;
+  re.N = N;
+  re.Np = n_nodes(N);
+  re.Nfp = n_face_nodes(N);
+  re.rst = warp_blend_nodes(N, re.lattice);
+  const int Np = re.Np, Nfp = re.Nfp;
+  re.V = Mat(Np, Np);
+  Mat Vd[3] = {Mat(Np, Np), Mat(Np, Np), Mat(Np, Np)};
+  for (int i = 0; i < Np; ++i) {
+    std::vector<double> phi, grad;
+    basis_eval(N, re.rst[i], phi, &grad);
+    for (int q = 0; q < Np; ++q) {
+      re.V(i, q) = phi[q];
+      for (int d = 0; d < 3; ++d) Vd[d](i, q) = grad[d * Np + q];
+    }
+  }
+  re.Vinv = inverse(re.V);
+  for (int d = 0; d < 3; ++d) re.D[d] = matmul(Vd[d], re.Vinv);
+  // mass matrix by collapsed Gauss-Legendre quadrature (exact for degree 2N)
+  std::vector<double> gx, gw;
+  gauss_legendre(N + 3, gx, gw);
+  re.M = Mat(Np, Np);
+  for (size_t i = 0; i < gx.size(); ++i)
+    for (size_t j = 0; j < gx.size(); ++j)
+      for (size_t k = 0; k < gx.size(); ++k) {
+        double a = gx[i], b = gx[j], c = gx[k];
+        std::array<double, 3> p = {(1 + a) * (1 - b) * (1 - c) / 4 - 1, (1 + b) * (1 - c) / 2 - 1, c};
+        double w = gw[i] * gw[j] * gw[k] * (1 - b) / 2 * (1 - c) / 2 * (1 - c) / 2;
+        std::vector<double> l = re.lagrange_at(p);
+        for (int m = 0; m < Np; ++m)
+          for (int n = 0; n < Np; ++n) re.M(m, n) += w * l[m] * l[n];
+      }
+  re.Minv = inverse(re.M);
+  // face nodes: the opposite vertex's lattice barycentric is zero
+  re.fmask.assign(4, {});
+  for (int f = 0; f < 4; ++f) {
+    int cnt = 0;
+    for (int n = 0; n < Np; ++n)
+      if (re.lattice[n][kFaceOpp[f]] == 0) re.fmask[f][cnt++] = n;
+    if (cnt != Nfp) throw Error{RIDG_E_INVALID_ARG, "face node count mismatch"};
+  }
+  // face mass matrices on the 2-D reference triangle {u, v >= -1, u + v <= 0} (area 2)
+  Mat E(Np, 4 * Nfp);
+  const double Vref[4][3] = {{-1, -1, -1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+  for (int f = 0; f < 4; ++f) {
+    Mat Mf(Nfp, Nfp);
+    for (size_t i = 0; i < gx.size(); ++i)
+      for (size_t j = 0; j < gx.size(); ++j) {
+        double a = gx[i], b = gx[j];
+        double u = (1 + a) * (1 - b) / 2 - 1, v = b;
+        double w = gw[i] * gw[j] * (1 - b) / 2;
+        const double* A = Vref[kFaceVerts[f][0]];
+        const double* B = Vref[kFaceVerts[f][1]];
+        const double* C = Vref[kFaceVerts[f][2]];
+        std::array<double, 3> p;
+        for (int d = 0; d < 3; ++d) p[d] = -(u + v) / 2 * A[d] + (1 + u) / 2 * B[d] + (1 + v) / 2 * C[d];
+        std::vector<double> l = re.lagrange_at(p);
+        for (int m = 0; m < Nfp; ++m)
+          for (int n = 0; n < Nfp; ++n) Mf(m, n) += w * l[re.fmask[f][m]] * l[re.fmask[f][n]];
+      }
+    for (int m = 0; m < Nfp; ++m)
+      for (int n = 0; n < Nfp; ++n) E(re.fmask[f][m], f * Nfp + n) = Mf(m, n);
+  }
+  re.LIFT = matmul(re.Minv, E);
+  // face-node correspondences from lattice barycentrics
+  re.perm.assign(6, {});
+  for (int code = 0; code < 6; ++code) {
+    // face nodes of the reference face 0 (vertices 0,1,2) as barycentric triples
+    for (int j = 0; j < Nfp; ++j) {
+      const auto& lj = re.lattice[re.fmask[0][j]];
+      int tri[3] = {lj[0], lj[1], lj[2]};
+      int want[3];
+      for (int x = 0; x < 3; ++x) want[x] = tri[kTriPerm[code][x]];
+      int found = -1;
+      for (int jj = 0; jj < Nfp; ++jj) {
+        const auto& lk = re.lattice[re.fmask[0][jj]];
+        if (lk[0] == want[0] && lk[1] == want[1] && lk[2] == want[2]) found = jj;
+      }
+      if (found < 0) throw Error{RIDG_E_INVALID_ARG, "face permutation not found"};
+      re.perm[code][j] = found;
+    }
+  }
+  return re;
+}
+
+// ------------------------------------------------------------------ mesh and connectivity
+MeshData build_mesh(const double* xyz, int64_t n_vert, const int64_t* tet, int64_t K, const int8_t* face_bc,
+                    int8_t default_bc) {
+  if (!xyz || !tet || n_vert < 4 || K < 1) throw Error{RIDG_E_INVALID_ARG, "mesh: empty or null input"};
+  if (default_bc < 1 || default_bc > 3) throw Error{RIDG_E_INVALID_ARG, "mesh: default_bc must be 1, 2 or 3"};
+  MeshData m;
+  m.K = K;
+  m.n_vert = n_vert;
+  m.xyz.assign(xyz, xyz + 3 * n_vert);
+  m.tet.assign(tet, tet + 4 * K);
+  for (int64_t i = 0; i < 4 * K; ++i)
+    if (m.tet[i] < 0 || m.tet[i] >= n_vert) throw Error{RIDG_E_BAD_MESH, "mesh: vertex index out of range"};
+  if (face_bc)
+    for (int64_t i = 0; i < 4 * K; ++i)
+      if (face_bc[i] < 0 || face_bc[i] > 3) throw Error{RIDG_E_INVALID_ARG, "mesh: face_bc code out of range"};
+  // faces keyed by their sorted vertex triple
+  struct FaceKey {
+    int64_t v[3];
+    int64_t elem;
+    int face;
+  };
+  std::vector<FaceKey> faces(4 * K);
+  for (int64_t k = 0; k < K; ++k)
+    for (int f = 0; f < 4; ++f) {
+      FaceKey fk;
+      for (int x = 0; x < 3; ++x) fk.v[x] = m.tet[4 * k + kFaceVerts[f][x]];
+      std::sort(fk.v, fk.v + 3);
+      fk.elem = k;
+      fk.face = f;
+      faces[4 * k + f] = fk;
+    }
+  std::sort(faces.begin(), faces.end(), [](const FaceKey& a, const FaceKey& b) {
+    if (a.v[0] != b.v[0]) return a.v[0] < b.v[0];
+    if (a.v[1] != b.v[1]) return a.v[1] < b.v[1];
+    if (a.v[2] != b.v[2]) return a.v[2] < b.v[2];
+    if (a.elem != b.elem) return a.elem < b.elem;
+    return a.face < b.face;
+  });
+  m.nbr.assign(4 * K, -1);
+  m.nbr_face.assign(4 * K, -1);
+  m.perm_code.assign(4 * K, 0);
+  m.bc.assign(4 * K, 0);
+  auto same = [](const FaceKey& a, const FaceKey& b) {
+    return a.v[0] == b.v[0] && a.v[1] == b.v[1] && a.v[2] == b.v[2];
+  };
+  for (size_t i = 0; i < faces.size();) {
+    size_t j = i + 1;
+    while (j < faces.size() && same(faces[i], faces[j])) ++j;
+    if (j - i > 2) throw Error{RIDG_E_BAD_MESH, "mesh: a face is shared by more than two elements"};
+    if (j - i == 2) {
+      const FaceKey& a = faces[i];
+      const FaceKey& b = faces[i + 1];
+      if (a.elem == b.elem) throw Error{RIDG_E_BAD_MESH, "mesh: degenerate element (repeated face)"};
+      m.nbr[4 * a.elem + a.face] = b.elem;
+      m.nbr_face[4 * a.elem + a.face] = int8_t(b.face);
+      m.nbr[4 * b.elem + b.face] = a.elem;
+      m.nbr_face[4 * b.elem + b.face] = int8_t(a.face);
+    }
+    i = j;
+  }
+  // vertex correspondence of each shared face: the neighbour lists vertex x of its face as our
+  // local vertex kTriPerm[code][x]
+  for (int64_t k = 0; k < K; ++k)
+    for (int f = 0; f < 4; ++f) {
+      int64_t k2 = m.nbr[4 * k + f];
+      if (k2 < 0) {
+        int8_t code = face_bc ? face_bc[4 * k + f] : 0;
+        m.bc[4 * k + f] = code ? code : default_bc;
+        ++m.n_boundary;
+        continue;
+      }
+      if (face_bc && face_bc[4 * k + f] != 0) throw Error{RIDG_E_BAD_MESH, "mesh: boundary code on an interior face"};
+      ++m.n_interior;
+      int f2 = m.nbr_face[4 * k + f];
+      int64_t mine[3], theirs[3];
+      for (int x = 0; x < 3; ++x) {
+        mine[x] = m.tet[4 * k + kFaceVerts[f][x]];
+        theirs[x] = m.tet[4 * k2 + kFaceVerts[f2][x]];
+      }
+      int code = -1;
+      for (int c = 0; c < 6 && code < 0; ++c) {
+        bool ok = true;
+        for (int x = 0; x < 3; ++x) ok = ok && (theirs[x] == mine[kTriPerm[c][x]]);
+        if (ok) code = c;
+      }
+      if (code < 0) throw Error{RIDG_E_BAD_MESH, "mesh: shared face vertices do not correspond"};
+      m.perm_code[4 * k + f] = int8_t(code);
+    }
+  m.n_interior /= 2;
+  return m;
+}
+
+// ------------------------------------------------------------------ geometry
+static void inv3(const double A[3][3], double Ai[3][3], double& det) {
+  det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+        A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+  double id = 1.0 / det;
+  Ai[0][0] = (A[1][1] * A[2][2] - A[1][2] * A[2][1]) * id;
+  Ai[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * id;
+  Ai[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * id;
+  Ai[1][0] = (A[1][2] * A[2][0] - A[1][0] * A[2][2]) * id;
+  Ai[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * id;
+  Ai[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id;
+  Ai[2][0] = (A[1][0] * A[2][1] - A[1][1] * A[2][0]) * id;
+  Ai[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * id;
+  Ai[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id;
+}
+
+static void element_jacobian(const MeshData& m, int64_t k, double A[3][3]) {
+  const double* P0 = &m.xyz[3 * m.tet[4 * k + 0]];
+  for (int col = 0; col < 3; ++col) {
+    const double* Pc = &m.xyz[3 * m.tet[4 * k + 1 + col]];
+    for (int d = 0; d < 3; ++d) A[d][col] = 0.5 * (Pc[d] - P0[d]);  // dx_d / dr_col
+  }
+}
+
+Geometry build_geometry(const MeshData& m) {
+  Geometry g;
+  const int64_t K = m.K;
+  g.rx.resize(9 * K);
+  g.normal.resize(12 * K);
+  g.fscale.resize(4 * K);
+  g.J.resize(K);
+  g.lmin.resize(K);
+  // reference outward normals scaled by (reference face area)/2
+  const double nref[4][3] = {{0, 0, -1}, {0, -1, 0}, {1, 1, 1}, {-1, 0, 0}};
+  for (int64_t k = 0; k < K; ++k) {
+    double A[3][3], Ai[3][3], det;
+    element_jacobian(m, k, A);
+    inv3(A, Ai, det);
+    if (!(det > 0.0) || !std::isfinite(det))
+      throw Error{RIDG_E_BAD_MESH, "mesh: element " + std::to_string(k) + " has a non-positive Jacobian"};
+    g.J[k] = det;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) g.rx[9 * k + 3 * i + j] = Ai[j][i];  // d r_j / d x_i
+    double fmax = 0.0;
+    for (int f = 0; f < 4; ++f) {
+      double n[3];
+      for (int i = 0; i < 3; ++i) n[i] = Ai[0][i] * nref[f][0] + Ai[1][i] * nref[f][1] + Ai[2][i] * nref[f][2];
+      double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+      g.fscale[4 * k + f] = nn;  // Nanson: (face area / 2) / J
+      for (int i = 0; i < 3; ++i) g.normal[12 * k + 3 * f + i] = n[i] / nn;
+      fmax = std::max(fmax, nn);
+    }
+    g.lmin[k] = 2.0 / fmax;  // 3 V / (largest face area) with V = 4J/3 and area = 2 J fscale
+  }
+  return g;
+}
+
+// ------------------------------------------------------------------ levels (Sec. 3.2)
+Levels assign_levels(const MeshData& m, const Geometry& g, int N, const double* c, double cfl, int n_levels_max) {
+  Levels lv;
+  const int64_t K = m.K;
+  std::vector<double> dtk(K);
+  double dtmin = 1e300;
+  for (int64_t k = 0; k < K; ++k) {
+    if (!(c[k] > 0.0)) throw Error{RIDG_E_INVALID_ARG, "velocity must be positive"};
+    dtk[k] = cfl * g.lmin[k] / ((N + 1.0) * (N + 1.0) * c[k]);
+    dtmin = std::min(dtmin, dtk[k]);
+  }
+  lv.dt_local = dtmin;
+  std::vector<int> L(K);
+  int Lmax = 0;
+  for (int64_t k = 0; k < K; ++k) {
+    L[k] = int(std::floor(std::log2(dtk[k] / dtmin) * (1.0 + 1e-12)));
+    Lmax = std::max(Lmax, L[k]);
+  }
+  lv.n_levels = std::min(n_levels_max, 1 + Lmax);
+  lv.level.resize(K);
+  for (int64_t k = 0; k < K; ++k) lv.level[k] = lv.n_levels - std::min(L[k], lv.n_levels - 1);
+  // move elements to finer levels until neighbours differ by at most one level (the smallest
+  // such assignment; it does not depend on the sweep order)
+  bool changed = true;
+  while (changed) {
+    changed = false;
+    for (int64_t k = 0; k < K; ++k)
+      for (int f = 0; f < 4; ++f) {
+        int64_t k2 = m.nbr[4 * k + f];
+        if (k2 >= 0 && lv.level[k] < lv.level[k2] - 1) {
+          lv.level[k] = lv.level[k2] - 1;
+          changed = true;
+        }
+      }
+  }
+  return lv;
+}
+
+Ordering build_ordering(const Levels& lv, int64_t K) {
+  Ordering o;
+  o.slot_of.assign(K, -1);
+  o.level_begin.assign(lv.n_levels + 1, 0);
+  int64_t slot = 0;
+  for (int l = 1; l <= lv.n_levels; ++l) {
+    o.level_begin[l - 1] = slot;
+    for (int64_t k = 0; k < K; ++k)
+      if (lv.level[k] == l) o.slot_of[k] = slot++;
+    slot = (slot + 31) / 32 * 32;
+  }
+  o.level_begin[lv.n_levels] = slot;
+  o.n_slots = slot;
+  o.elem_of.assign(slot, -1);
+  for (int64_t k = 0; k < K; ++k) o.elem_of[o.slot_of[k]] = k;
+  return o;
+}
+
+int64_t locate_point(const MeshData& m, const Geometry& g, const double x[3], double rst[3]) {
+  (void)g;
+  for (int64_t k = 0; k < m.K; ++k) {
+    double A[3][3], Ai[3][3], det;
+    element_jacobian(m, k, A);
+    inv3(A, Ai, det);
+    const double* P0 = &m.xyz[3 * m.tet[4 * k]];
+    double d[3] = {x[0] - P0[0], x[1] - P0[1], x[2] - P0[2]};
+    double r1[3];  // r + 1
+    for (int i = 0; i < 3; ++i) r1[i] = Ai[i][0] * d[0] + Ai[i][1] * d[1] + Ai[i][2] * d[2];
+    double lam[4] = {1.0 - 0.5 * (r1[0] + r1[1] + r1[2]), 0.5 * r1[0], 0.5 * r1[1], 0.5 * r1[2]};
+    if (lam[0] >= -1e-12 && lam[1] >= -1e-12 && lam[2] >= -1e-12 && lam[3] >= -1e-12) {
+      for (int i = 0; i < 3; ++i) rst[i] = r1[i] - 1.0;
+      return k;
+    }
+  }
+  return -1;
+}
+
+}  // namespace ridg

@@ -1,0 +1,1028 @@
+// Host engine and C ABI: uploads the discretisation, schedules the fused step kernel per step of
+// the finest level (Algorithm 1), and drives one RTM shot (Sec. 2, Sec. 4.3).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <stdexcept>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "../../include/ridg.h"
+#include "dispatch.hpp"
+#include "setup.hpp"
+
+namespace ridg {
+
+static thread_local std::string g_last_error;
+
+static void set_error(const std::string& s) { g_last_error = s; }
+
+#define RIDG_CUDA(call)                                                                                   \
+  do {                                                                                                    \
+    cudaError_t e_ = (call);                                                                              \
+    if (e_ != cudaSuccess) throw Error{RIDG_E_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)}; \
+  } while (0)
+
+template <typename F>
+static auto dispatch_order(int N, F&& f) {
+  switch (N) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 5: return f(std::integral_constant<int, 5>{});
+    default: return f(std::integral_constant<int, 6>{});
+  }
+}
+
+// Owning device allocation.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DBuf() = default;
+  DBuf(const DBuf&) = delete;
+  DBuf& operator=(const DBuf&) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t n) {
+    if (n == bytes && p) return;
+    release();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&p, n);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Error{RIDG_E_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e)};
+    }
+    bytes = n;
+  }
+};
+
+template <typename T>
+static T* dptr(const DBuf& b) {
+  return static_cast<T*>(b.p);
+}
+
+template <typename T>
+static void upload(DBuf& b, const std::vector<T>& v, cudaStream_t st) {
+  b.alloc(v.size() * sizeof(T));
+  if (!v.empty()) RIDG_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+}
+
+static int mod3(int64_t x) { return int(((x % 3) + 3) % 3); }
+
+static double ricker(double t, double f0, double tp, double amp) {
+  double a = M_PI * f0 * (t - tp);
+  a *= a;
+  return amp * (1.0 - 2.0 * a) * std::exp(-a);
+}
+
+}  // namespace ridg
+
+struct ridg_mesh {
+  ridg::MeshData m;
+};
+
+struct ridg_solver {
+  virtual ~ridg_solver() = default;
+  virtual void info(ridg_info* out) const = 0;
+  virtual void levels(int32_t* out) const = 0;
+  virtual void nodes(double* out) const = 0;
+  virtual void set_state(const double* q) = 0;
+  virtual void set_history(const double* r1, const double* r2) = 0;
+  virtual void eval_rhs(const double* q, double* out) = 0;
+  virtual void step(int64_t n) = 0;
+  virtual void get_state(double* q) = 0;
+  virtual double energy() = 0;
+  virtual int64_t trace_len(double t_final) const = 0;
+  virtual void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i,
+                    const double* obs_dev, double* traces_dev, double* imgp_dev, double* imgq_dev,
+                    const double* e_up) = 0;
+  virtual cudaStream_t stream() const = 0;
+  virtual const ridg_shot_stats& stats() = 0;
+  virtual void set_profiling(int every) = 0;
+};
+
+namespace ridg {
+
+template <typename real>
+struct Wave {
+  DBuf q, ring, trace;
+  DBuf inj_range, inj_w, inj_row;
+};
+
+template <typename real>
+class Engine final : public ridg_solver {
+ public:
+  Engine(const MeshData& mesh, int N, const double* c, const double* rho, const ridg_options& opt, cudaStream_t st)
+      : mesh_(mesh), N_(N), st_(st) {
+    ref_ = build_reference(N);
+    Np_ = ref_.Np;
+    Nfp_ = ref_.Nfp;
+    NFPP_ = Nfp_ <= 16 ? 16 : 32;
+    NPa_ = 2 * ((Np_ + 1) / 2);
+    geo_ = build_geometry(mesh_);
+    c_.assign(c, c + mesh_.K);
+    rho_.assign(rho, rho + mesh_.K);
+    for (int64_t k = 0; k < mesh_.K; ++k)
+      if (!(rho_[k] > 0.0) || !(c_[k] > 0.0) || !std::isfinite(rho_[k]) || !std::isfinite(c_[k]))
+        throw Error{RIDG_E_INVALID_ARG, "c and rho must be positive and finite"};
+    double cfl = opt.cfl > 0 ? opt.cfl : 0.15;
+    int nlm = opt.n_levels_max > 0 ? opt.n_levels_max : 3;
+    if (nlm > kMaxLevels) throw Error{RIDG_E_INVALID_ARG, "n_levels_max too large"};
+    lv_ = assign_levels(mesh_, geo_, N, c_.data(), cfl, nlm);
+    ord_ = build_ordering(lv_, mesh_.K);
+    n_slots_ = ord_.n_slots;
+    L_ = lv_.n_levels;
+    NL_ = int64_t(1) << (L_ - 1);
+    check_shared_memory();
+    build_nodes();
+    check_face_nodes();
+    build_tables();
+    alloc_wave(w_[0]);
+    reset_time();
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+  }
+
+  cudaStream_t stream() const override { return st_; }
+  const ridg_shot_stats& stats() override {
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    double fw = 0.0, bw = 0.0;
+    int64_t nf = 0, nb = 0;
+    for (size_t i = 0; i < prof_used_; ++i) {
+      float ms = 0.f;
+      RIDG_CUDA(cudaEventElapsedTime(&ms, prof_ev_[2 * i], prof_ev_[2 * i + 1]));
+      if (prof_w_[i] == 1) {
+        fw += ms;
+        ++nf;
+      } else {
+        bw += ms;
+        ++nb;
+      }
+    }
+    stats_.prof_forward_ms = fw;
+    stats_.prof_backward_ms = bw;
+    stats_.prof_forward_launches = nf;
+    stats_.prof_backward_launches = nb;
+    return stats_;
+  }
+  void set_profiling(int every) override { prof_every_ = std::max(0, every); }
+
+  ~Engine() override {
+    for (auto e : prof_ev_) cudaEventDestroy(e);
+  }
+
+  void info(ridg_info* out) const override {
+    std::memset(out, 0, sizeof(*out));
+    out->N = N_;
+    out->Np = Np_;
+    out->Nfp = Nfp_;
+    out->n_levels = L_;
+    out->K = mesh_.K;
+    out->dt_local = lv_.dt_local;
+    out->dt_global = lv_.dt_local * double(NL_);
+    for (int l = 1; l <= L_ && l <= 8; ++l)
+      out->level_count[l - 1] = std::count(lv_.level.begin(), lv_.level.end(), l);
+    out->n_boundary_faces = n_bfaces_;
+    out->device_bytes = int64_t(device_bytes());
+    out->n_half_step = n_half_;
+  }
+  void levels(int32_t* out) const override {
+    for (int64_t k = 0; k < mesh_.K; ++k) out[k] = lv_.level[k];
+  }
+  void nodes(double* out) const override { std::memcpy(out, xnodes_.data(), xnodes_.size() * sizeof(double)); }
+
+  // ------------------------------------------------------------------ state
+  void set_state(const double* q) override {
+    std::vector<real> h = to_slots(q);
+    RIDG_CUDA(cudaMemcpyAsync(w_[0].q.p, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice, st_));
+    RIDG_CUDA(cudaMemsetAsync(w_[0].ring.p, 0, w_[0].ring.bytes, st_));
+    reset_time();
+    init_traces(w_[0], mod3(tau_));
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+  }
+  void set_history(const double* r1, const double* r2) override {
+    size_t qb = qsize() * sizeof(real);
+    // with every level counter at 0 the two older ring slots are 2 (one step back) and 1
+    const double* src[2] = {r1, r2};
+    const int slot[2] = {2, 1};
+    for (int i = 0; i < 2; ++i) {
+      char* dst = static_cast<char*>(w_[0].ring.p) + slot[i] * qb;
+      if (!src[i]) {
+        RIDG_CUDA(cudaMemsetAsync(dst, 0, qb, st_));
+      } else {
+        std::vector<real> h = to_slots(src[i]);
+        RIDG_CUDA(cudaMemcpyAsync(dst, h.data(), qb, cudaMemcpyHostToDevice, st_));
+      }
+    }
+    std::fill(ring_count_.begin(), ring_count_.end(), 0);
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+  }
+  void eval_rhs(const double* q, double* out) override {
+    Wave<real> tmp;
+    tmp.q.alloc(qsize() * sizeof(real));
+    tmp.trace.alloc(trace_slot_elems() * sizeof(real));
+    DBuf rout;
+    rout.alloc(qsize() * sizeof(real));
+    RIDG_CUDA(cudaMemsetAsync(rout.p, 0, rout.bytes, st_));
+    std::vector<real> h = to_slots(q);
+    RIDG_CUDA(cudaMemcpyAsync(tmp.q.p, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice, st_));
+    init_traces_into(dptr<real>(tmp.q), dptr<real>(tmp.trace), 0);
+    StepArgs<real> a = base_args();
+    a.wave[0] = wave_args(tmp);
+    a.wave[0].amp_mode = 0;
+    a.slot_lo = 0;
+    a.slot_hi = n_slots_;
+    a.trace_read = 0;
+    a.tau_sign = real(1);
+    a.mode = kModeRhsOnly;
+    a.rhs_out = dptr<real>(rout);
+    launch(a, 1);
+    std::vector<real> r(qsize());
+    RIDG_CUDA(cudaMemcpyAsync(r.data(), rout.p, rout.bytes, cudaMemcpyDeviceToHost, st_));
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    from_slots(r, out);
+  }
+  void step(int64_t n) override {
+    if (n < 0) throw Error{RIDG_E_INVALID_ARG, "n_global must be >= 0"};
+    for (int64_t g = 0; g < n; ++g)
+      for (int64_t s = 0; s < NL_; ++s) {
+        StepArgs<real> a = fine_args(+1, 1, 0);
+        a.wave[0] = wave_args(w_[0]);
+        a.wave[0].amp_mode = 0;
+        launch_fine(a, +1, 1);
+      }
+    RIDG_CUDA(cudaGetLastError());
+  }
+  void get_state(double* q) override {
+    std::vector<real> h(qsize());
+    RIDG_CUDA(cudaMemcpyAsync(h.data(), w_[0].q.p, h.size() * sizeof(real), cudaMemcpyDeviceToHost, st_));
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    from_slots(h, q);
+  }
+  double energy() override { return energy_of(dptr<real>(w_[0].q)); }
+  int64_t trace_len(double t_final) const override {
+    double dtg = lv_.dt_local * double(NL_);
+    return int64_t(std::ceil(t_final / dtg - 1e-9)) + 1;
+  }
+
+  // ------------------------------------------------------------------ one shot
+  void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i, const double* obs_dev,
+            double* traces_dev, double* imgp_dev, double* imgq_dev, const double* e_up) override {
+    if (!(t_final > 0.0) || !(t_i >= 0.0) || t_i > t_final) throw Error{RIDG_E_INVALID_ARG, "bad time span"};
+    if (nrec < 0 || (nrec > 0 && !rec)) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
+    std::memset(&stats_, 0, sizeof(stats_));
+    prof_used_ = 0;
+    const double dtl = lv_.dt_local, dtg = dtl * double(NL_);
+    const int64_t n_global = int64_t(std::ceil(t_final / dtg - 1e-9));
+    const int64_t n_t = n_global + 1;
+    int64_t n_i = int64_t(std::floor(t_i / dtg + 1e-9));
+    n_i = std::min(n_i, n_global);
+    const int64_t tau_f = n_global * NL_, tau_i = n_i * NL_;
+    stats_.n_global = n_global;
+    // ---- source and receivers
+    double rst[3];
+    int64_t ks = locate_point(mesh_, geo_, src.xyz, rst);
+    if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
+    std::vector<real> w_src = projected_dirac(ks, rst);
+    struct Rec {
+      int64_t slot;
+      std::vector<real> row, w;
+      int idx;
+    };
+    std::vector<Rec> recs(nrec);
+    for (int64_t r = 0; r < nrec; ++r) {
+      int64_t kr = locate_point(mesh_, geo_, rec + 3 * r, rst);
+      if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
+      recs[r].slot = ord_.slot_of[kr];
+      std::array<double, 3> p = {rst[0], rst[1], rst[2]};
+      std::vector<double> l = ref_.lagrange_at(p);
+      recs[r].row.assign(l.begin(), l.end());
+      recs[r].w = projected_dirac(kr, rst);
+      recs[r].idx = int(r);
+    }
+    // source injection table (wavefield 0)
+    {
+      std::vector<int2> range(n_slots_, make_int2(0, 0));
+      range[ord_.slot_of[ks]] = make_int2(0, 1);
+      upload(w_[0].inj_range, range, st_);
+      upload(w_[0].inj_w, w_src, st_);
+      upload(w_[0].inj_row, std::vector<int>{0}, st_);
+    }
+    alloc_wave(w_[1]);
+    {
+      // receiver injections grouped by slot (wavefield 1)
+      std::vector<Rec> sorted = recs;
+      std::stable_sort(sorted.begin(), sorted.end(), [](const Rec& a, const Rec& b) { return a.slot < b.slot; });
+      std::vector<int2> range(n_slots_, make_int2(0, 0));
+      std::vector<real> wv;
+      std::vector<int> rows;
+      for (size_t i = 0; i < sorted.size(); ++i) {
+        int2& rg = range[sorted[i].slot];
+        if (rg.y == 0) rg.x = int(i);
+        rg.y += 1;
+        wv.insert(wv.end(), sorted[i].w.begin(), sorted[i].w.end());
+        rows.push_back(sorted[i].idx);
+      }
+      if (rows.empty()) {
+        rows.push_back(0);
+        wv.assign(Np_, real(0));
+      }
+      upload(w_[1].inj_range, range, st_);
+      upload(w_[1].inj_w, wv, st_);
+      upload(w_[1].inj_row, rows, st_);
+      std::vector<int64_t> rslot(std::max<int64_t>(nrec, 1), 0);
+      std::vector<real> rrow(std::max<int64_t>(nrec, 1) * Np_, real(0));
+      for (int64_t r = 0; r < nrec; ++r) {
+        rslot[r] = recs[r].slot;
+        for (int m = 0; m < Np_; ++m) rrow[r * Np_ + m] = recs[r].row[m];
+      }
+      upload(rec_slot_, rslot, st_);
+      upload(rec_row_, rrow, st_);
+    }
+    double* traces = traces_dev;
+    if (!traces) {
+      traces_tmp_.alloc(size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double));
+      traces = dptr<double>(traces_tmp_);
+    }
+    // ---- boundary-trace arena: one record per boundary face of every active element per step
+    std::vector<int64_t> arena_base(tau_f + 2, 0);
+    for (int64_t t = 0; t <= tau_f; ++t) arena_base[t + 1] = arena_base[t] + (n_bfaces_ - bface_first(slot_lo(t)));
+    size_t arena_bytes = size_t(arena_base[tau_f + 1]) * 2 * NFPP_ * sizeof(real);
+    arena_.alloc(std::max<size_t>(arena_bytes, 16));
+    stats_.boundary_trace_bytes = int64_t(arena_bytes);
+    q_snap_.alloc(qsize() * sizeof(real));
+    ring_snap_.alloc(3 * qsize() * sizeof(real));
+    img_p_.alloc(size_t(n_slots_) * Np_ * sizeof(double));
+    img_q_.alloc(size_t(n_slots_) * Np_ * sizeof(double));
+
+    // ---- forward source run
+    zero_wave(w_[0]);
+    reset_time();
+    RIDG_CUDA(cudaMemsetAsync(traces, 0, size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double), st_));
+    sample(traces, n_t, 0, nrec);
+    auto forward_step = [&](int mode) {
+      StepArgs<real> a = fine_args(+1, 1, mode);
+      a.wave[0] = wave_args(w_[0]);
+      a.wave[0].amp_mode = 1;
+      a.wave[0].amp = real(ricker(double(tau_) * dtl, src.f0, src.t_peak, src.amplitude));
+      a.arena_write = dptr<real>(arena_);
+      a.arena_offset = arena_base[std::min<int64_t>(tau_, tau_f)] - bface_first(a.slot_lo);
+      launch_fine(a, +1, 1);
+    };
+    for (int64_t g = 0; g < n_global; ++g) {
+      for (int64_t s = 0; s < NL_; ++s) forward_step(kModeRecord);
+      sample(traces, n_t, g + 1, nrec);
+    }
+    stats_.dof_updates_forward = dof_;
+    RIDG_CUDA(cudaMemcpyAsync(q_snap_.p, w_[0].q.p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
+    // two more global steps (and the first right-hand side of a third) give, per level l, the
+    // right-hand sides at t_f + Delta t_l and t_f + 2 Delta t_l that start the backward run
+    for (int64_t i = 0; i <= 2 * NL_; ++i) {
+      int64_t t_now = tau_;
+      std::vector<int> before = ring_count_;
+      forward_step(t_now == tau_f ? kModeRecord : 0);
+      for (int l = 1; l <= L_; ++l) {
+        int64_t d = int64_t(1) << (L_ - l);
+        if (t_now == tau_f + 2 * d) snapshot_history(l, before[l - 1]);
+      }
+    }
+    // ---- backward: source (replayed boundary) and receiver wavefields in lockstep
+    RIDG_CUDA(cudaMemcpyAsync(w_[0].q.p, q_snap_.p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
+    RIDG_CUDA(cudaMemcpyAsync(w_[0].ring.p, ring_snap_.p, 3 * qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
+    zero_wave(w_[1]);
+    RIDG_CUDA(cudaMemsetAsync(img_p_.p, 0, img_p_.bytes, st_));
+    RIDG_CUDA(cudaMemsetAsync(img_q_.p, 0, img_q_.bytes, st_));
+    std::fill(ring_count_.begin(), ring_count_.end(), 0);
+    tau_ = tau_f;
+    RIDG_CUDA(cudaMemsetAsync(w_[0].trace.p, 0, w_[0].trace.bytes, st_));
+    init_traces(w_[0], mod3(tau_));
+    const double* data = obs_dev ? obs_dev : traces;
+    int64_t dof_before = dof_;
+    while (tau_ > tau_i) {
+      StepArgs<real> a = fine_args(-1, 2, kModeReplay | kModeImage);
+      a.wave[0] = wave_args(w_[0]);
+      a.wave[0].amp_mode = 1;
+      a.wave[0].amp = real(ricker(double(tau_) * dtl, src.f0, src.t_peak, src.amplitude));
+      a.wave[1] = wave_args(w_[1]);
+      a.wave[1].amp_mode = nrec > 0 ? 2 : 0;
+      a.wave[1].data = data;
+      a.wave[1].n_time = int(n_t);
+      int64_t n_lo = tau_ / NL_;
+      double u = double(tau_ - n_lo * NL_) / double(NL_);
+      a.interp_n0 = int(n_lo - 1);
+      const double xs[4] = {-1.0, 0.0, 1.0, 2.0};
+      for (int i = 0; i < 4; ++i) {
+        double li = 1.0;
+        for (int j = 0; j < 4; ++j)
+          if (j != i) li *= (u - xs[j]) / (xs[i] - xs[j]);
+        a.interp_w[i] = li;
+      }
+      a.arena_read = dptr<real>(arena_);
+      a.arena_offset = arena_base[tau_] - bface_first(a.slot_lo);
+      a.image_p = dptr<double>(img_p_);
+      a.image_q = dptr<double>(img_q_);
+      double eu[3] = {0.0, 0.0, -1.0};
+      if (e_up) std::memcpy(eu, e_up, sizeof(eu));
+      for (int d = 0; d < 3; ++d) a.e_up[d] = real(eu[d]);
+      launch_fine(a, -1, 2);
+    }
+    stats_.dof_updates_backward = dof_ - dof_before;
+    if (imgp_dev) image_out(dptr<double>(img_p_), imgp_dev);
+    if (imgq_dev) image_out(dptr<double>(img_q_), imgq_dev);
+    RIDG_CUDA(cudaGetLastError());
+  }
+
+ private:
+  // ------------------------------------------------------------------ helpers
+  size_t qsize() const { return size_t(n_slots_) * 4 * Np_; }
+  size_t trace_slot_elems() const { return size_t(n_slots_) * 8 * NFPP_; }
+  size_t device_bytes() const {
+    size_t b = 0;
+    const DBuf* all[] = {&geo_d_, &J_d_, &mat_d_, &nbr_d_, &finfo_d_, &bface_d_, &meta_d_, &Dt_d_, &Lt_d_,
+                         &fmask_d_, &perm_d_, &M_d_, &slot_of_d_, &q_snap_, &ring_snap_, &img_p_, &img_q_, &arena_};
+    for (auto* x : all) b += x->bytes;
+    for (auto& w : w_) b += w.q.bytes + w.ring.bytes + w.trace.bytes;
+    return b;
+  }
+  int64_t bface_first(int64_t slot) const { return slot >= n_slots_ ? n_bfaces_ : bface_host_[slot]; }
+  int first_active_level(int64_t tau) const {
+    // level l (1..L) is active iff tau is a multiple of 2^(L-l); the active set is a suffix
+    for (int l = 1; l <= L_; ++l)
+      if (tau % (int64_t(1) << (L_ - l)) == 0) return l;
+    return L_;
+  }
+  int64_t slot_lo(int64_t tau) const { return ord_.level_begin[first_active_level(tau) - 1]; }
+
+  void reset_time() {
+    tau_ = 0;
+    ring_count_.assign(L_, 0);
+    dof_ = 0;
+  }
+
+  std::vector<real> to_slots(const double* q) const {
+    std::vector<real> h(qsize(), real(0));
+    for (int64_t k = 0; k < mesh_.K; ++k) {
+      int64_t s = ord_.slot_of[k];
+      for (int f = 0; f < 4; ++f)
+        for (int n = 0; n < Np_; ++n) h[(((s >> 5) * 4 + f) * Np_ + n) * 32 + (s & 31)] = real(q[(k * 4 + f) * Np_ + n]);
+    }
+    return h;
+  }
+  void from_slots(const std::vector<real>& h, double* q) const {
+    for (int64_t k = 0; k < mesh_.K; ++k) {
+      int64_t s = ord_.slot_of[k];
+      for (int f = 0; f < 4; ++f)
+        for (int n = 0; n < Np_; ++n) q[(k * 4 + f) * Np_ + n] = double(h[(((s >> 5) * 4 + f) * Np_ + n) * 32 + (s & 31)]);
+    }
+  }
+
+  void check_shared_memory() const {
+    int dev = 0, optin = 0;
+    RIDG_CUDA(cudaGetDevice(&dev));
+    RIDG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    size_t need = dispatch_order(N_, [&](auto NC) {
+      constexpr int NN = decltype(NC)::value;
+      return std::max(step_smem_bytes<NN, real, 1>(), step_smem_bytes<NN, real, 2>());
+    });
+    if (need > size_t(optin))
+      throw Error{RIDG_E_INVALID_ARG, "order " + std::to_string(N_) + " in this precision needs " +
+                                          std::to_string(need) + " bytes of shared memory per block (device allows " +
+                                          std::to_string(optin) + ")"};
+  }
+
+  void build_nodes() {
+    xnodes_.assign(size_t(mesh_.K) * Np_ * 3, 0.0);
+    for (int64_t k = 0; k < mesh_.K; ++k)
+      for (int n = 0; n < Np_; ++n) {
+        const auto& r = ref_.rst[n];
+        double lam[4] = {-(1 + r[0] + r[1] + r[2]) / 2, (1 + r[0]) / 2, (1 + r[1]) / 2, (1 + r[2]) / 2};
+        for (int v = 0; v < 4; ++v)
+          for (int d = 0; d < 3; ++d) xnodes_[(k * Np_ + n) * 3 + d] += lam[v] * mesh_.xyz[3 * mesh_.tet[4 * k + v] + d];
+      }
+  }
+
+  void check_face_nodes() {
+    for (int64_t k = 0; k < mesh_.K; ++k)
+      for (int f = 0; f < 4; ++f) {
+        int64_t k2 = mesh_.nbr[4 * k + f];
+        if (k2 < 0) continue;
+        int f2 = mesh_.nbr_face[4 * k + f], code = mesh_.perm_code[4 * k + f];
+        double tol = 1e-8 * std::max(geo_.lmin[k], 1e-300);
+        for (int j = 0; j < Nfp_; ++j) {
+          const double* xa = &xnodes_[(k * Np_ + ref_.fmask[f][j]) * 3];
+          const double* xb = &xnodes_[(k2 * Np_ + ref_.fmask[f2][ref_.perm[code][j]]) * 3];
+          double d = std::fabs(xa[0] - xb[0]) + std::fabs(xa[1] - xb[1]) + std::fabs(xa[2] - xb[2]);
+          if (d > tol) throw Error{RIDG_E_BAD_MESH, "face nodes of neighbouring elements do not coincide"};
+        }
+      }
+  }
+
+  void build_tables() {
+    const int64_t S = n_slots_;
+    std::vector<double> geo(S * kGeo, 0.0), J(S, 0.0);
+    std::vector<real> mat(S * kMat, real(0));
+    std::vector<int> nbr(S * 4, -1), bface(S, 0), meta(S, 0);
+    std::vector<uint8_t> finfo(S * 4, 0);
+    int64_t nb = 0;
+    for (int64_t s = 0; s < S; ++s) {
+      bface[s] = int(nb);
+      int64_t k = ord_.elem_of[s];
+      if (k < 0) continue;
+      meta[s] = kMetaValid;
+      for (int i = 0; i < 9; ++i) geo[s * kGeo + i] = geo_.rx[9 * k + i];
+      for (int i = 0; i < 12; ++i) geo[s * kGeo + 9 + i] = geo_.normal[12 * k + i];
+      for (int f = 0; f < 4; ++f) geo[s * kGeo + 21 + f] = geo_.fscale[4 * k + f];
+      J[s] = geo_.J[k];
+      double Zk = rho_[k] * c_[k];
+      mat[s * kMat + 0] = real(rho_[k] * c_[k] * c_[k]);
+      mat[s * kMat + 1] = real(1.0 / rho_[k]);
+      mat[s * kMat + 2] = real(Zk);
+      for (int f = 0; f < 4; ++f) {
+        int64_t k2 = mesh_.nbr[4 * k + f];
+        double Zb = k2 >= 0 ? 0.5 * (Zk + rho_[k2] * c_[k2]) : Zk;
+        mat[s * kMat + 3 + f] = real(1.0 / Zb);
+        mat[s * kMat + 7 + f] = real(Zb);
+        int bc = k2 >= 0 ? 0 : mesh_.bc[4 * k + f];
+        int nf = k2 >= 0 ? mesh_.nbr_face[4 * k + f] : 0;
+        int pc = k2 >= 0 ? mesh_.perm_code[4 * k + f] : 0;
+        finfo[s * 4 + f] = uint8_t(nf | (pc << 2) | (bc << 5));
+        nbr[s * 4 + f] = k2 >= 0 ? int(ord_.slot_of[k2]) : -1;
+        if (k2 < 0) ++nb;
+        if (k2 >= 0 && lv_.level[k2] > lv_.level[k]) meta[s] |= kMetaHalf;
+      }
+      if (meta[s] & kMetaHalf) ++n_half_;
+    }
+    n_bfaces_ = nb;
+    bface_host_ = bface;
+    upload(geo_d_, geo, st_);
+    upload(J_d_, J, st_);
+    upload(mat_d_, mat, st_);
+    upload(nbr_d_, nbr, st_);
+    upload(finfo_d_, finfo, st_);
+    upload(bface_d_, bface, st_);
+    upload(meta_d_, meta, st_);
+    std::vector<real> Dt(3 * Np_ * NPa_, real(0)), Lt(4 * Nfp_ * NPa_, real(0));
+    for (int j = 0; j < 3; ++j)
+      for (int m = 0; m < Np_; ++m)
+        for (int n = 0; n < Np_; ++n) Dt[(j * Np_ + m) * NPa_ + n] = real(ref_.D[j](n, m));
+    for (int fm = 0; fm < 4 * Nfp_; ++fm)
+      for (int n = 0; n < Np_; ++n) Lt[fm * NPa_ + n] = real(ref_.LIFT(n, fm));
+    upload(Dt_d_, Dt, st_);
+    upload(Lt_d_, Lt, st_);
+    std::vector<int> fm(128, 0), pm(192, 0);
+    for (int f = 0; f < 4; ++f)
+      for (int j = 0; j < Nfp_; ++j) fm[f * 32 + j] = ref_.fmask[f][j];
+    for (int c = 0; c < 6; ++c)
+      for (int j = 0; j < Nfp_; ++j) pm[c * 32 + j] = ref_.perm[c][j];
+    upload(fmask_d_, fm, st_);
+    upload(perm_d_, pm, st_);
+    upload(M_d_, ref_.M.a, st_);
+    upload(slot_of_d_, ord_.slot_of, st_);
+    level_count_.assign(L_, 0);
+    for (int64_t k = 0; k < mesh_.K; ++k) level_count_[lv_.level[k] - 1]++;
+  }
+
+  void alloc_wave(Wave<real>& w) {
+    if (w.q.p) return;
+    w.q.alloc(qsize() * sizeof(real));
+    w.ring.alloc(3 * qsize() * sizeof(real));
+    w.trace.alloc(3 * trace_slot_elems() * sizeof(real));
+    zero_wave(w);
+    if (!w.inj_range.p) {
+      upload(w.inj_range, std::vector<int2>(n_slots_, make_int2(0, 0)), st_);
+      upload(w.inj_w, std::vector<real>(Np_, real(0)), st_);
+      upload(w.inj_row, std::vector<int>{0}, st_);
+    }
+  }
+  void zero_wave(Wave<real>& w) {
+    RIDG_CUDA(cudaMemsetAsync(w.q.p, 0, w.q.bytes, st_));
+    RIDG_CUDA(cudaMemsetAsync(w.ring.p, 0, w.ring.bytes, st_));
+    RIDG_CUDA(cudaMemsetAsync(w.trace.p, 0, w.trace.bytes, st_));
+  }
+
+  std::vector<real> projected_dirac(int64_t k, const double rst[3]) const {
+    // Eq. sourceTerm: M_k w = l(x0), M_k = J_k M
+    std::array<double, 3> p = {rst[0], rst[1], rst[2]};
+    std::vector<double> l = ref_.lagrange_at(p);
+    std::vector<real> w(Np_, real(0));
+    for (int i = 0; i < Np_; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < Np_; ++j) acc += ref_.Minv(i, j) * l[j];
+      w[i] = real(acc / geo_.J[k]);
+    }
+    return w;
+  }
+
+  WaveArgs<real> wave_args(Wave<real>& w) {
+    WaveArgs<real> a{};
+    a.q = dptr<real>(w.q);
+    a.ring = dptr<real>(w.ring);
+    a.trace = dptr<real>(w.trace);
+    a.inj_range = dptr<const int2>(w.inj_range);
+    a.inj_w = dptr<const real>(w.inj_w);
+    a.inj_row = dptr<const int>(w.inj_row);
+    return a;
+  }
+
+  StepArgs<real> base_args() const {
+    StepArgs<real> a{};
+    a.n_slots = n_slots_;
+    a.n_levels = L_;
+    for (int l = 0; l <= L_; ++l) a.level_begin[l] = ord_.level_begin[l];
+    for (int l = L_ + 1; l <= kMaxLevels; ++l) a.level_begin[l] = n_slots_;
+    a.geo = dptr<const double>(geo_d_);
+    a.mat = dptr<const real>(mat_d_);
+    a.nbr = dptr<const int>(nbr_d_);
+    a.finfo = dptr<const uint8_t>(finfo_d_);
+    a.bface = dptr<const int>(bface_d_);
+    a.meta = dptr<const int>(meta_d_);
+    a.Dt = dptr<const real>(Dt_d_);
+    a.Lt = dptr<const real>(Lt_d_);
+    a.fmask = dptr<const int>(fmask_d_);
+    a.perm = dptr<const int>(perm_d_);
+    a.e_up[2] = real(-1);
+    return a;
+  }
+
+  // arguments of one step of the finest level at the current time tau_ (direction sigma)
+  StepArgs<real> fine_args(int sigma, int W, int mode) const {
+    (void)W;
+    StepArgs<real> a = base_args();
+    int l0 = first_active_level(tau_);
+    a.slot_lo = ord_.level_begin[l0 - 1];
+    a.slot_hi = n_slots_;
+    a.trace_read = mod3(tau_);
+    for (int l = 1; l <= L_; ++l) {
+      int64_t d = int64_t(1) << (L_ - l);
+      int c = ring_count_[l - 1];
+      a.ring_new[l - 1] = c % 3;
+      a.ring_old1[l - 1] = (c + 2) % 3;
+      a.ring_old2[l - 1] = (c + 1) % 3;
+      a.h[l - 1] = real(double(sigma) * double(d) * lv_.dt_local);
+      a.trace_write[l - 1] = mod3(tau_ + sigma * d);
+      a.trace_half[l - 1] = d >= 2 ? mod3(tau_ + sigma * (d / 2)) : mod3(tau_ + 2 * sigma);
+    }
+    a.tau_sign = real(sigma);
+    a.mode = mode;
+    return a;
+  }
+
+  void launch(const StepArgs<real>& a, int W) {
+    cudaError_t e = dispatch_order(N_, [&](auto NC) { return Launch<decltype(NC)::value, real>::step(a, W, st_); });
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("step kernel launch: ") + cudaGetErrorString(e)};
+    ++stats_.kernel_launches;
+    ++stats_.fused_launches;
+  }
+
+  void launch_fine(const StepArgs<real>& a, int sigma, int W) {
+    int l0 = first_active_level(tau_);
+    bool prof = prof_every_ > 0 && l0 == 1 && ((tau_ / NL_) % prof_every_) == 0;
+    if (prof) {
+      if (prof_used_ >= prof_w_.size()) {
+        cudaEvent_t e0, e1;
+        RIDG_CUDA(cudaEventCreate(&e0));
+        RIDG_CUDA(cudaEventCreate(&e1));
+        prof_ev_.push_back(e0);
+        prof_ev_.push_back(e1);
+        prof_w_.push_back(0);
+      }
+      prof_w_[prof_used_] = W;
+      RIDG_CUDA(cudaEventRecord(prof_ev_[2 * prof_used_], st_));
+    }
+    launch(a, W);
+    if (prof) {
+      RIDG_CUDA(cudaEventRecord(prof_ev_[2 * prof_used_ + 1], st_));
+      ++prof_used_;
+    }
+    for (int l = l0; l <= L_; ++l) {
+      ring_count_[l - 1] += 1;
+      dof_ += level_count_[l - 1] * 4 * Np_ * W;
+    }
+    tau_ += sigma;
+  }
+
+  void init_traces_into(const real* q, real* trace, int slot) {
+    cudaError_t e = dispatch_order(N_, [&](auto NC) {
+      return Launch<decltype(NC)::value, real>::init_traces(q, trace, slot, n_slots_, dptr<const double>(geo_d_),
+                                                             dptr<const int>(meta_d_), dptr<const int>(fmask_d_), st_);
+    });
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
+    ++stats_.kernel_launches;
+  }
+  void init_traces(Wave<real>& w, int slot) { init_traces_into(dptr<real>(w.q), dptr<real>(w.trace), slot); }
+
+  void sample(double* traces, int64_t n_t, int64_t col, int64_t nrec) {
+    if (nrec <= 0) return;
+    cudaError_t e = dispatch_order(N_, [&](auto NC) {
+      return Launch<decltype(NC)::value, real>::sample(dptr<real>(w_[0].q), dptr<const int64_t>(rec_slot_),
+                                                        dptr<const real>(rec_row_), int(nrec), traces, n_t, col, st_);
+    });
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
+    ++stats_.kernel_launches;
+  }
+
+  void snapshot_history(int l, int count_before) {
+    // the step that just ran wrote r(t_f + 2 dt_l) into ring slot count_before % 3; the one before
+    // it, r(t_f + dt_l), sits in (count_before + 2) % 3.  The backward run starts with counter 0,
+    // whose older slots are 2 (one step back: t_f + dt_l) and 1 (two steps back: t_f + 2 dt_l).
+    size_t per = 4 * size_t(Np_) * 32;
+    size_t off = size_t(ord_.level_begin[l - 1] / 32) * per;
+    size_t len = size_t((ord_.level_begin[l] - ord_.level_begin[l - 1]) / 32) * per * sizeof(real);
+    if (len == 0) return;
+    const char* ring = static_cast<const char*>(w_[0].ring.p);
+    char* snap = static_cast<char*>(ring_snap_.p);
+    size_t qb = qsize() * sizeof(real);
+    int newest = count_before % 3, prev = (count_before + 2) % 3;
+    RIDG_CUDA(cudaMemcpyAsync(snap + 1 * qb + off * sizeof(real), ring + newest * qb + off * sizeof(real), len,
+                              cudaMemcpyDeviceToDevice, st_));
+    RIDG_CUDA(cudaMemcpyAsync(snap + 2 * qb + off * sizeof(real), ring + prev * qb + off * sizeof(real), len,
+                              cudaMemcpyDeviceToDevice, st_));
+  }
+
+  void image_out(const double* img, double* out) {
+    cudaError_t e = dispatch_order(N_, [&](auto NC) {
+      return Launch<decltype(NC)::value, real>::image_out(img, dptr<const int64_t>(slot_of_d_), mesh_.K, out, st_);
+    });
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
+    ++stats_.kernel_launches;
+  }
+
+  double energy_of(const real* q) {
+    DBuf out;
+    out.alloc(sizeof(double));
+    RIDG_CUDA(cudaMemsetAsync(out.p, 0, sizeof(double), st_));
+    cudaError_t e = dispatch_order(N_, [&](auto NC) {
+      return Launch<decltype(NC)::value, real>::energy(q, n_slots_, dptr<const double>(J_d_), dptr<const real>(mat_d_),
+                                                        dptr<const int>(meta_d_), dptr<const double>(M_d_),
+                                                        dptr<double>(out), st_);
+    });
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
+    double v = 0.0;
+    RIDG_CUDA(cudaMemcpyAsync(&v, out.p, sizeof(double), cudaMemcpyDeviceToHost, st_));
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    return v;
+  }
+
+  MeshData mesh_;
+  int N_, Np_ = 0, Nfp_ = 0, NFPP_ = 16, NPa_ = 0;
+  cudaStream_t st_;
+  RefElem ref_;
+  Geometry geo_;
+  Levels lv_;
+  Ordering ord_;
+  std::vector<double> c_, rho_, xnodes_;
+  int64_t n_slots_ = 0, NL_ = 1, n_bfaces_ = 0;
+  int L_ = 1;
+  std::vector<int> bface_host_;
+  std::vector<int64_t> level_count_;
+  DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
+  DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_;
+  Wave<real> w_[2];
+  int64_t tau_ = 0, dof_ = 0;
+  std::vector<int> ring_count_;
+  ridg_shot_stats stats_{};
+  int prof_every_ = 0;
+  size_t prof_used_ = 0;
+  std::vector<cudaEvent_t> prof_ev_;
+  std::vector<int> prof_w_;
+  int64_t n_half_ = 0;
+};
+
+}  // namespace ridg
+
+// ==================================================================== C ABI
+using ridg::Error;
+
+template <typename F>
+static int guarded(F&& f) {
+  try {
+    f();
+    ridg::g_last_error.clear();
+    return RIDG_OK;
+  } catch (const Error& e) {
+    ridg::set_error(e.msg);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    ridg::set_error("host allocation failed");
+    return RIDG_E_OOM;
+  } catch (const std::exception& e) {
+    ridg::set_error(e.what());
+    return RIDG_E_INVALID_ARG;
+  } catch (...) {
+    ridg::set_error("unknown error");
+    return RIDG_E_INVALID_ARG;
+  }
+}
+
+extern "C" {
+
+const char* ridg_last_error(void) { return ridg::g_last_error.c_str(); }
+const char* ridg_version(void) { return "ridg-gb300 0.1 (sm_103a)"; }
+
+int ridg_mesh_create(const double* xyz, int64_t n_vert, const int64_t* tet, int64_t K, const int8_t* face_bc,
+                     int8_t default_bc, ridg_mesh** out) {
+  return guarded([&] {
+    if (!out) throw Error{RIDG_E_INVALID_ARG, "out is null"};
+    *out = nullptr;
+    auto m = std::make_unique<ridg_mesh>();
+    m->m = ridg::build_mesh(xyz, n_vert, tet, K, face_bc, default_bc);
+    // reject inverted or degenerate elements here already
+    ridg::build_geometry(m->m);
+    *out = m.release();
+  });
+}
+
+void ridg_mesh_destroy(ridg_mesh* mesh) { delete mesh; }
+
+int ridg_mesh_counts(const ridg_mesh* mesh, int64_t* nb, int64_t* ni) {
+  return guarded([&] {
+    if (!mesh) throw Error{RIDG_E_INVALID_ARG, "mesh is null"};
+    if (nb) *nb = mesh->m.n_boundary;
+    if (ni) *ni = mesh->m.n_interior;
+  });
+}
+
+int ridg_reference_operators(int N, double* rst, double* D, double* M, double* LIFT, int32_t* fmask) {
+  return guarded([&] {
+    ridg::RefElem re = ridg::build_reference(N);
+    int Np = re.Np, Nfp = re.Nfp;
+    if (rst)
+      for (int n = 0; n < Np; ++n)
+        for (int d = 0; d < 3; ++d) rst[3 * n + d] = re.rst[n][d];
+    if (D)
+      for (int j = 0; j < 3; ++j)
+        for (int a = 0; a < Np; ++a)
+          for (int b = 0; b < Np; ++b) D[(j * Np + a) * Np + b] = re.D[j](a, b);
+    if (M) std::memcpy(M, re.M.a.data(), sizeof(double) * Np * Np);
+    if (LIFT) std::memcpy(LIFT, re.LIFT.a.data(), sizeof(double) * Np * 4 * Nfp);
+    if (fmask)
+      for (int f = 0; f < 4; ++f)
+        for (int j = 0; j < Nfp; ++j) fmask[f * Nfp + j] = re.fmask[f][j];
+  });
+}
+
+int ridg_solver_create(const ridg_mesh* mesh, int N, const double* c, const double* rho, const ridg_options* opt,
+                       uintptr_t cuda_stream, ridg_solver** out) {
+  return guarded([&] {
+    if (!out) throw Error{RIDG_E_INVALID_ARG, "out is null"};
+    *out = nullptr;
+    if (!mesh || !c || !rho) throw Error{RIDG_E_INVALID_ARG, "null mesh, c or rho"};
+    ridg_options o{};
+    if (opt) o = *opt;
+    if (o.dtype != RIDG_F32 && o.dtype != RIDG_F64) throw Error{RIDG_E_INVALID_ARG, "dtype must be RIDG_F32 or RIDG_F64"};
+    if (N < 1 || N > 6) throw Error{RIDG_E_INVALID_ARG, "order N must be in 1..6"};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e)};
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(cuda_stream);
+    if (o.dtype == RIDG_F32)
+      *out = new ridg::Engine<float>(mesh->m, N, c, rho, o, st);
+    else
+      *out = new ridg::Engine<double>(mesh->m, N, c, rho, o, st);
+  });
+}
+
+void ridg_solver_destroy(ridg_solver* s) {
+  if (s) {
+    cudaStreamSynchronize(s->stream());
+    delete s;
+  }
+}
+
+#define RIDG_NEED(s)                                                      \
+  if (!(s)) throw Error{RIDG_E_INVALID_ARG, "solver handle is null"};
+
+int ridg_solver_info(const ridg_solver* s, ridg_info* info) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!info) throw Error{RIDG_E_INVALID_ARG, "info is null"};
+    s->info(info);
+  });
+}
+int ridg_solver_levels(const ridg_solver* s, int32_t* levels) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!levels) throw Error{RIDG_E_INVALID_ARG, "levels is null"};
+    s->levels(levels);
+  });
+}
+int ridg_solver_nodes(const ridg_solver* s, double* xyz) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!xyz) throw Error{RIDG_E_INVALID_ARG, "xyz is null"};
+    s->nodes(xyz);
+  });
+}
+int ridg_set_state(ridg_solver* s, const double* q) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!q) throw Error{RIDG_E_INVALID_ARG, "q is null"};
+    s->set_state(q);
+  });
+}
+int ridg_set_history(ridg_solver* s, const double* r1, const double* r2) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->set_history(r1, r2);
+  });
+}
+int ridg_eval_rhs(ridg_solver* s, const double* q, double* out) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!q || !out) throw Error{RIDG_E_INVALID_ARG, "null buffer"};
+    s->eval_rhs(q, out);
+  });
+}
+int ridg_step(ridg_solver* s, int64_t n) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->step(n);
+  });
+}
+int ridg_get_state(ridg_solver* s, double* q) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!q) throw Error{RIDG_E_INVALID_ARG, "q is null"};
+    s->get_state(q);
+  });
+}
+int ridg_energy(ridg_solver* s, double* e) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!e) throw Error{RIDG_E_INVALID_ARG, "energy is null"};
+    *e = s->energy();
+  });
+}
+int64_t ridg_trace_len(const ridg_solver* s, double t_final) {
+  if (!s || !(t_final > 0.0)) return 0;
+  return s->trace_len(t_final);
+}
+
+int ridg_rtm_shot_device(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                         double t_image_start, const double* observed_dev, double* traces_dev, double* image_p_dev,
+                         double* image_q_dev, const double* e_up) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!src) throw Error{RIDG_E_INVALID_ARG, "source is null"};
+    s->shot(*src, rec_xyz, nrec, t_final, t_image_start, observed_dev, traces_dev, image_p_dev, image_q_dev, e_up);
+  });
+}
+
+int ridg_rtm_shot(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                  double t_image_start, const double* observed, double* traces_out, double* image_p, double* image_q,
+                  const double* e_up) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!src) throw Error{RIDG_E_INVALID_ARG, "source is null"};
+    ridg_info inf;
+    s->info(&inf);
+    int64_t n_t = s->trace_len(t_final);
+    size_t tb = size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double);
+    size_t ib = size_t(inf.K) * inf.Np * sizeof(double);
+    cudaStream_t st = s->stream();
+    ridg::DBuf obs, tr, ip, iq;
+    if (observed) {
+      obs.alloc(tb);
+      RIDG_CUDA(cudaMemcpyAsync(obs.p, observed, size_t(nrec) * n_t * sizeof(double), cudaMemcpyHostToDevice, st));
+    }
+    tr.alloc(tb);
+    if (image_p) ip.alloc(ib);
+    if (image_q) iq.alloc(ib);
+    s->shot(*src, rec_xyz, nrec, t_final, t_image_start, observed ? ridg::dptr<double>(obs) : nullptr, ridg::dptr<double>(tr),
+            ridg::dptr<double>(ip), ridg::dptr<double>(iq), e_up);
+    if (traces_out && nrec > 0)
+      RIDG_CUDA(cudaMemcpyAsync(traces_out, tr.p, size_t(nrec) * n_t * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (image_p) RIDG_CUDA(cudaMemcpyAsync(image_p, ip.p, ib, cudaMemcpyDeviceToHost, st));
+    if (image_q) RIDG_CUDA(cudaMemcpyAsync(image_q, iq.p, ib, cudaMemcpyDeviceToHost, st));
+    RIDG_CUDA(cudaStreamSynchronize(st));
+    if (image_p)
+      for (size_t i = 0; i < ib / sizeof(double); ++i)
+        if (!std::isfinite(image_p[i])) throw Error{RIDG_E_UNSTABLE, "non-finite image value"};
+  });
+}
+
+int ridg_last_shot_stats(const ridg_solver* s, ridg_shot_stats* stats) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!stats) throw Error{RIDG_E_INVALID_ARG, "stats is null"};
+    *stats = const_cast<ridg_solver*>(s)->stats();
+  });
+}
+
+int ridg_set_profiling(ridg_solver* s, int32_t every) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->set_profiling(every);
+  });
+}
+
+}  // extern "C"

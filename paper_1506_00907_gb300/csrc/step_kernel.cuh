@@ -1,0 +1,659 @@
+// Fused multi-rate DG step kernel for sm_103a.
+//
+// One launch processes every element whose unknowns sit at the current fine time t_start
+// (Algorithm 1: the active elements form a suffix of the level-ordered slots) and, per element:
+//   * the volume term (Eqs. dgLocalSchemeP/U, volume part): r_p = sum_j D_j (-rho c^2 sum_i rx_ij v_i),
+//     r_vi = -(1/rho) sum_j rx_ij (D_j p);
+//   * the surface term with the penalty fluxes of Eqs. weakFormP/V (factor 1/2, tau from the mean
+//     impedance, negated backward in time) and the boundary conditions of Sec. 2 through ghost
+//     states; r -= sum_f (J_f/J) L_f P_f, with the velocity lift taken per face and combined
+//     with the normals afterwards (L_f (n_f s_f) = n_f (L_f s_f));
+//   * the point injections of Eq. sourceTerm (source wavelet or re-injected receiver traces);
+//   * the Adams-Bashforth update of its level (Eq. updateAB) -- done right away, since it only
+//     needs the history -- and its traces at t_start + Delta t_l, written to a trace slot chosen
+//     by time modulo 3 so that neighbours still read the traces at t_start;
+//   * the half-step traces at t_start + Delta t_l / 2 (Eq. updateABcoarse) when it has finer
+//     neighbours;
+//   * forward runs: the traces of its domain-boundary faces into the boundary-trace arena;
+//     backward source runs: those recorded traces as the exterior state of its boundary faces;
+//   * backward runs with two wavefields (source S, receivers R): the AB3-exact increments of the
+//     classical and characteristic images (Eq. updateABcorr), accumulated in FP64.
+//
+// A CTA owns 32 "columns": 32 elements of one wavefield (W = 1) or 16 elements x 2 wavefields
+// (W = 2).  All per-element matrix products are done as small GEMMs out of shared memory: each
+// thread owns a register tile of 2 nodes x 4 columns and accumulates, per node and column, the
+// pressure right-hand side, the three reference derivatives of p and the four per-face velocity
+// lifts (64 FP32 accumulators).  The reference matrices are read through the read-only data path
+// (they stay resident in L1); field columns are read as 16-byte vectors.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ridg {
+
+constexpr int kMaxLevels = 8;
+
+// finfo byte per (element, face): bits 0-1 neighbour face, bits 2-4 correspondence code,
+// bits 5-6 boundary code (0 = interior)
+__host__ __device__ inline int finfo_face(uint8_t x) { return x & 3; }
+__host__ __device__ inline int finfo_perm(uint8_t x) { return (x >> 2) & 7; }
+__host__ __device__ inline int finfo_bc(uint8_t x) { return (x >> 5) & 3; }
+
+// meta flags per slot
+constexpr int kMetaValid = 1;
+constexpr int kMetaHalf = 2;
+
+// kernel modes
+constexpr int kModeRecord = 1;   // forward: record boundary-face traces
+constexpr int kModeReplay = 2;   // wavefield 0 takes recorded traces as exterior state on boundary faces
+constexpr int kModeImage = 4;    // accumulate the images (W == 2)
+constexpr int kModeRhsOnly = 8;  // only write the right-hand side to rhs_out
+
+// per-element geometry (double): rx[9], normal[12], fscale[4]
+constexpr int kGeo = 25;
+// per-element material (working precision): rho c^2, 1/rho, rho c, tau_p[4], tau_v[4]
+constexpr int kMat = 11;
+
+template <typename real>
+struct WaveArgs {
+  real* q;           // [n_slots/32][4][Np][32]
+  real* ring;        // 3 x q-sized
+  real* trace;       // 3 slots x [n_slots][4][2][NFPP]
+  const int2* inj_range;  // [n_slots] (first, count) or null
+  const real* inj_w;      // [n_inj][Np]
+  const int* inj_row;     // [n_inj] data row
+  int amp_mode;           // 0 none, 1 constant amplitude, 2 interpolated data rows
+  real amp;               // amp_mode 1
+  const double* data;     // amp_mode 2: [rows][n_time]
+  int n_time;
+};
+
+template <typename real>
+struct StepArgs {
+  WaveArgs<real> wave[2];
+  // interpolation of data rows at this time: samples interp_n0 .. interp_n0+3 with weights
+  int interp_n0;
+  double interp_w[4];
+  int64_t slot_lo, slot_hi;  // active slots [slot_lo, slot_hi), multiples of 32
+  int64_t level_begin[kMaxLevels + 1];
+  int n_levels;
+  int ring_new[kMaxLevels], ring_old1[kMaxLevels], ring_old2[kMaxLevels];
+  real h[kMaxLevels];  // signed local step of each level
+  int trace_read;
+  int trace_write[kMaxLevels], trace_half[kMaxLevels];
+  real tau_sign;
+  int mode;
+  int64_t n_slots;
+  // boundary-trace arena: records of face index b (global boundary-face numbering) at this step
+  // live at arena + (arena_offset + b) * 2 * NFPP
+  real* arena_write;
+  const real* arena_read;
+  int64_t arena_offset;
+  // images [n_slots/32][Np][32] (double)
+  double* image_p;
+  double* image_q;
+  real e_up[3];
+  // static tables
+  const double* geo;     // [n_slots][kGeo]
+  const real* mat;       // [n_slots][kMat]
+  const int* nbr;        // [n_slots][4] neighbour slot or -1
+  const uint8_t* finfo;  // [n_slots][4]
+  const int* bface;      // [n_slots] index of the first boundary face of the slot
+  const int* meta;       // [n_slots]
+  const real* Dt;        // [3][Np][NPa]  Dt[j][m][n] = D_j[n][m]
+  const real* Lt;        // [4*Nfp][NPa]  Lt[fm][n] = LIFT[n][fm]
+  const int* fmask;      // [4][32]
+  const int* perm;       // [6][32]
+  real* rhs_out;         // kModeRhsOnly: q-sized
+};
+
+template <int N>
+struct Order {
+  static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;
+  static constexpr int Nfp = (N + 1) * (N + 2) / 2;
+  static constexpr int NPP = (Np + 1) / 2;
+  static constexpr int NPa = 2 * NPP;
+  static constexpr int NT = ((8 * NPP + 31) / 32) * 32;
+  static constexpr int NFPP = Nfp <= 16 ? 16 : 32;
+};
+
+template <typename real>
+struct ColStride {
+  static constexpr int value = 36;
+};
+template <>
+struct ColStride<double> {
+  static constexpr int value = 34;
+};
+
+// AB3 (Eq. updateAB), half-step (Eq. updateABcoarse) and image (Eq. updateABcorr) coefficients
+struct AB {
+  static constexpr double a1 = 23.0 / 12.0, a2 = -16.0 / 12.0, a3 = 5.0 / 12.0;
+  static constexpr double b1 = 17.0 / 24.0, b2 = -7.0 / 24.0, b3 = 2.0 / 24.0;
+  static constexpr double c1 = 19.0 / 24.0, c2 = -5.0 / 12.0, c3 = 1.0 / 8.0;
+};
+
+template <typename real>
+__device__ __forceinline__ real fmaf_t(real a, real b, real c) {
+  return fma(a, b, c);
+}
+
+template <typename real>
+__device__ __forceinline__ void ld4(const real* p, real v[4]) {
+  if constexpr (sizeof(real) == 4) {
+    float4 x = *reinterpret_cast<const float4*>(p);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = x.z;
+    v[3] = x.w;
+  } else {
+    double2 x = *reinterpret_cast<const double2*>(p);
+    double2 y = *reinterpret_cast<const double2*>(p + 2);
+    v[0] = x.x;
+    v[1] = x.y;
+    v[2] = y.x;
+    v[3] = y.y;
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ void ld2g(const real* p, real v[2]) {
+  if constexpr (sizeof(real) == 4) {
+    float2 x = __ldg(reinterpret_cast<const float2*>(p));
+    v[0] = x.x;
+    v[1] = x.y;
+  } else {
+    double2 x = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = x.x;
+    v[1] = x.y;
+  }
+}
+
+// Load/store the 4 columns (c0..c0+3) of one (field,node) row from/to the global q-layout of the
+// two wavefields.  W == 1: 4 consecutive slots of one array.  W == 2: columns alternate S, R.
+template <typename real, int W>
+__device__ __forceinline__ void gload_cols(real* const base[2], int64_t off, real v[4]) {
+  if constexpr (W == 1) {
+    ld4<real>(base[0] + off, v);
+  } else {
+    // off points at the first of 2 consecutive elements
+    real a0 = base[0][off], a1 = base[0][off + 1];
+    real b0 = base[1][off], b1 = base[1][off + 1];
+    v[0] = a0;
+    v[1] = b0;
+    v[2] = a1;
+    v[3] = b1;
+  }
+}
+
+template <typename real, int W>
+__device__ __forceinline__ void gstore_cols(real* const base[2], int64_t off, const real v[4], const bool ok[4]) {
+  if constexpr (W == 1) {
+    if (ok[0] && ok[1] && ok[2] && ok[3]) {
+      if constexpr (sizeof(real) == 4) {
+        *reinterpret_cast<float4*>(base[0] + off) = make_float4(v[0], v[1], v[2], v[3]);
+      } else {
+        *reinterpret_cast<double2*>(base[0] + off) = make_double2(v[0], v[1]);
+        *reinterpret_cast<double2*>(base[0] + off + 2) = make_double2(v[2], v[3]);
+      }
+    } else {
+      for (int k = 0; k < 4; ++k)
+        if (ok[k]) base[0][off + k] = v[k];
+    }
+  } else {
+    if (ok[0]) base[0][off] = v[0];
+    if (ok[1]) base[1][off] = v[1];
+    if (ok[2]) base[0][off + 1] = v[2];
+    if (ok[3]) base[1][off + 1] = v[3];
+  }
+}
+
+template <int N, typename real, int W>
+__global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<real> A) {
+  using O = Order<N>;
+  constexpr int Np = O::Np, Nfp = O::Nfp, NPa = O::NPa, NT = O::NT, NFPP = O::NFPP;
+  constexpr int CS = ColStride<real>::value;  // column-row stride in shared memory
+  constexpr int EPB = 32 / W;                 // elements per CTA
+  constexpr int XS = 33;                      // stride of the exterior-trace staging rows
+  constexpr int NG = 48;                      // per-element coefficient block
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  real* sQ = reinterpret_cast<real*>(smem_raw);          // [4][Np][CS]
+  real* sS = sQ + 4 * Np * CS;                           // [4*Nfp][CS] velocity penalty scalars
+  real* sT = sS + 4 * Nfp * CS;                          // [4*Nfp][CS] pressure penalties
+  constexpr int UX = (3 * Np * CS > 8 * Nfp * XS) ? 3 * Np * CS : 8 * Nfp * XS;
+  real* sU = sT + 4 * Nfp * CS;                          // [3][Np][CS]   (aliases sX)
+  real* sX = sU;                                         // [4][Nfp][2][XS] exterior traces
+  real* sG = sU + UX;                                    // [EPB][NG] per-element coefficients
+  int* sI = reinterpret_cast<int*>(sG + EPB * NG);       // per-element ints
+  int* sNbr = sI;                                        // [EPB][4]
+  int* sInfo = sNbr + 4 * EPB;                           // [EPB][4]
+  int* sBf = sInfo + 4 * EPB;                            // [EPB]
+  int* sMeta = sBf + EPB;                                // [EPB]
+  int* sFm = sMeta + EPB;                                // [4][32]
+  int* sPerm = sFm + 128;                                // [6][32]
+  real* sH = sS;  // half-step fields [4][Np][CS] reuse sS/sT/sU after the products
+
+  const int tid = threadIdx.x;
+  const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * EPB;
+  if (slot0 >= A.slot_hi) return;
+  const int64_t blk = slot0 >> 5;        // 32-slot block of the q layout
+  const int lane0 = int(slot0 & 31);     // first element's lane in that block (0 or 16)
+  // level of this CTA (all its slots share one level)
+  int lev = 0;
+  for (int l = 0; l < A.n_levels; ++l)
+    if (slot0 >= A.level_begin[l]) lev = l;
+  const real h = A.h[lev];
+
+  // ---------------------------------------------------------------- phase 0: tables
+  for (int i = tid; i < 128; i += NT) sFm[i] = A.fmask[i];
+  for (int i = tid; i < 192; i += NT) sPerm[i] = A.perm[i];
+  for (int i = tid; i < EPB * 4; i += NT) {
+    int e = i >> 2, f = i & 3;
+    int64_t s = slot0 + e;
+    sNbr[i] = A.nbr[s * 4 + f];
+    sInfo[i] = A.finfo[s * 4 + f];
+  }
+  for (int e = tid; e < EPB; e += NT) {
+    int64_t s = slot0 + e;
+    sBf[e] = A.bface[s];
+    sMeta[e] = A.meta[s];
+    const double* g = A.geo + s * kGeo;
+    const real* m = A.mat + s * kMat;
+    real* G = sG + e * NG;
+    real rc2 = m[0], irho = m[1];
+    // G[0..8]: -rho c^2 rx_ij (volume p equation), G[9..17]: -rx_ij / rho (volume v equation)
+    for (int ij = 0; ij < 9; ++ij) {
+      real rxij = real(g[ij]);
+      G[ij] = -rc2 * rxij;
+      G[9 + ij] = -irho * rxij;
+    }
+    // G[18..29]: outward normals
+    for (int k = 0; k < 12; ++k) G[18 + k] = real(g[9 + k]);
+    // G[30..45]: penalty coefficients per face: t = A_f [nv] + B_f [p], s = C_f [p] + D_f [nv]
+    for (int f = 0; f < 4; ++f) {
+      real fs = real(g[21 + f]);
+      real taup = A.tau_sign * m[3 + f], tauv = A.tau_sign * m[7 + f];
+      G[30 + 4 * f + 0] = -real(0.5) * fs * rc2;
+      G[30 + 4 * f + 1] = real(0.5) * fs * rc2 * taup;
+      G[30 + 4 * f + 2] = real(0.5) * fs * irho;
+      G[30 + 4 * f + 3] = -real(0.5) * fs * irho * tauv;
+    }
+    G[46] = m[2];  // rho c
+    G[47] = 0;
+  }
+  // ---------------------------------------------------------------- phase 1: fields -> smem
+  for (int i = tid; i < 4 * Np * 32; i += NT) {
+    int c = i & 31, row = i >> 5;  // row = field*Np + node
+    int e = c / W, w = c % W;
+    int64_t off = ((blk * 4) * Np + row) * 32 + lane0 + e;
+    sQ[row * CS + c] = A.wave[w].q[off];
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- phase 2a: exterior traces
+  // half-warp per (column, face), lanes over face nodes: coalesced reads of the neighbour's face
+  // block, permuted by the face correspondence
+  {
+    const int hw = tid >> 4, j = tid & 15;
+    for (int item = hw; item < 32 * 4; item += NT / 16) {
+      int c = item >> 2, f = item & 3;
+      int e = c / W, w = c % W;
+      if (!(sMeta[e] & kMetaValid)) continue;
+      int info = sInfo[e * 4 + f];
+      int bc = finfo_bc(uint8_t(info));
+      for (int jj = j; jj < Nfp; jj += 16) {
+        real xp = 0, xv = 0;
+        bool have = false;
+        if (bc == 0) {
+          int64_t s2 = sNbr[e * 4 + f];
+          int f2 = finfo_face(uint8_t(info));
+          int j2 = sPerm[finfo_perm(uint8_t(info)) * 32 + jj];
+          const real* tb = A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + s2) * (8 * NFPP) + f2 * 2 * NFPP;
+          xp = tb[j2];
+          xv = -tb[NFPP + j2];  // neighbour's n.v with our normal
+          have = true;
+        } else {
+          // own traces of the boundary face at t_start
+          int n = sFm[f * 32 + jj];
+          const real* G = sG + e * NG;
+          real p = sQ[(0 * Np + n) * CS + c];
+          real vn = G[18 + 3 * f] * sQ[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sQ[(2 * Np + n) * CS + c] +
+                    G[20 + 3 * f] * sQ[(3 * Np + n) * CS + c];
+          int b = sBf[e];
+          for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
+          if ((A.mode & kModeRecord) && w == 0) {
+            real* rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
+            rec[jj] = p;
+            rec[NFPP + jj] = vn;
+          }
+          if ((A.mode & kModeReplay) && w == 0) {
+            const real* rec = A.arena_read + (A.arena_offset + b) * (2 * NFPP);
+            xp = rec[jj];
+            xv = rec[NFPP + jj];
+            have = true;
+          }
+        }
+        if (have) {
+          sX[((f * Nfp + jj) * 2 + 0) * XS + c] = xp;
+          sX[((f * Nfp + jj) * 2 + 1) * XS + c] = xv;
+        }
+      }
+    }
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- phase 2b: penalties
+  for (int i = tid; i < 4 * Nfp * 32; i += NT) {
+    int c = i & 31, fj = i >> 5;
+    int f = fj / Nfp, jj = fj - f * Nfp;
+    int e = c / W, w = c % W;
+    const real* G = sG + e * NG;
+    int n = sFm[f * 32 + jj];
+    real p = sQ[(0 * Np + n) * CS + c];
+    real vn = G[18 + 3 * f] * sQ[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sQ[(2 * Np + n) * CS + c] +
+              G[20 + 3 * f] * sQ[(3 * Np + n) * CS + c];
+    int info = sInfo[e * 4 + f];
+    int bc = finfo_bc(uint8_t(info));
+    real jp, jv;
+    bool replay = (A.mode & kModeReplay) && w == 0 && bc != 0;
+    if (bc == 0 || replay) {
+      jp = sX[((f * Nfp + jj) * 2 + 0) * XS + c] - p;
+      jv = sX[((f * Nfp + jj) * 2 + 1) * XS + c] - vn;
+    } else if (bc == 1) {  // free surface: p+ = -p-, n.v+ = n.v-
+      jp = -2 * p;
+      jv = 0;
+    } else if (bc == 2) {  // transparent: p+ = 0, v+ = 0
+      jp = -p;
+      jv = -vn;
+    } else {  // rigid: p+ = p-, n.v+ = -n.v-
+      jp = 0;
+      jv = -2 * vn;
+    }
+    const real* pc = G + 30 + 4 * f;
+    real t = pc[0] * jv + pc[1] * jp;
+    real sv = pc[2] * jp + pc[3] * jv;
+    if (!(sMeta[e] & kMetaValid)) {
+      t = 0;
+      sv = 0;
+    }
+    sT[fj * CS + c] = t;
+    sS[fj * CS + c] = sv;
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- phase 2c: U_j = G_p * v
+  for (int i = tid; i < Np * 32; i += NT) {
+    int c = i & 31, m = i >> 5;
+    int e = c / W;
+    const real* G = sG + e * NG;
+    real vx = sQ[(1 * Np + m) * CS + c], vy = sQ[(2 * Np + m) * CS + c], vz = sQ[(3 * Np + m) * CS + c];
+    for (int j = 0; j < 3; ++j) sU[(j * Np + m) * CS + c] = G[0 + j] * vx + G[3 + j] * vy + G[6 + j] * vz;
+  }
+  __syncthreads();
+
+  // ---------------------------------------------------------------- phase 3: element products
+  const int np = tid >> 3;      // node pair
+  const int cq = tid & 7;       // column quad
+  const bool gemm = np < O::NPP;
+  const int c0 = cq * 4;
+  real rp[2][4], dp[3][2][4], ls[4][2][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      rp[i][k] = 0;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) dp[j][i][k] = 0;
+#pragma unroll
+      for (int f = 0; f < 4; ++f) ls[f][i][k] = 0;
+    }
+  if (gemm) {
+    const real* Dt = A.Dt + 2 * np;
+#pragma unroll 5
+    for (int m = 0; m < Np; ++m) {
+      real bp[4], bu[3][4], a[3][2];
+      ld4<real>(sQ + m * CS + c0, bp);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        ld4<real>(sU + (j * Np + m) * CS + c0, bu[j]);
+        ld2g<real>(Dt + (j * Np + m) * NPa, a[j]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            dp[j][i][k] = fmaf_t(a[j][i], bp[k], dp[j][i][k]);
+            rp[i][k] = fmaf_t(a[j][i], bu[j][k], rp[i][k]);
+          }
+        }
+    }
+    const real* Lt = A.Lt + 2 * np;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+#pragma unroll 5
+      for (int jj = 0; jj < Nfp; ++jj) {
+        const int fm = f * Nfp + jj;
+        real bt[4], bs[4], a[2];
+        ld4<real>(sT + fm * CS + c0, bt);
+        ld4<real>(sS + fm * CS + c0, bs);
+        ld2g<real>(Lt + fm * NPa, a);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            rp[i][k] = fmaf_t(a[i], bt[k], rp[i][k]);
+            ls[f][i][k] = fmaf_t(a[i], bs[k], ls[f][i][k]);
+          }
+      }
+    }
+  }
+  __syncthreads();  // all reads of sS/sT/sU are done: sH may now reuse them
+
+  // ---------------------------------------------------------------- phase 4: update
+  if (gemm) {
+    const int rn = A.ring_new[lev], r1i = A.ring_old1[lev], r2i = A.ring_old2[lev];
+    const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
+    real* qb[2] = {A.wave[0].q, W == 2 ? A.wave[1].q : nullptr};
+    real* rnew[2] = {A.wave[0].ring + rn * qsize, W == 2 ? A.wave[1].ring + rn * qsize : nullptr};
+    real* rold1[2] = {A.wave[0].ring + r1i * qsize, W == 2 ? A.wave[1].ring + r1i * qsize : nullptr};
+    real* rold2[2] = {A.wave[0].ring + r2i * qsize, W == 2 ? A.wave[1].ring + r2i * qsize : nullptr};
+    real* rout[2] = {A.rhs_out, nullptr};
+    bool ok[4];
+    int eidx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      eidx[k] = (c0 + k) / W;
+      ok[k] = (sMeta[eidx[k]] & kMetaValid) != 0;
+    }
+    const int64_t col_off = (W == 1) ? (lane0 + c0) : (lane0 + c0 / 2);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const int n = 2 * np + i;
+      if (n >= Np) continue;
+      real r[4][4];  // [field][column]
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const real* G = sG + eidx[k] * NG;
+        r[0][k] = rp[i][k];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          real v = G[9 + 3 * d + 0] * dp[0][i][k] + G[9 + 3 * d + 1] * dp[1][i][k] + G[9 + 3 * d + 2] * dp[2][i][k];
+#pragma unroll
+          for (int f = 0; f < 4; ++f) v -= G[18 + 3 * f + d] * ls[f][i][k];
+          r[1 + d][k] = v;
+        }
+      }
+      // point injections (source wavelet or receiver traces)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int w = (c0 + k) % W;
+        const WaveArgs<real>& wa = A.wave[w];
+        if (wa.amp_mode == 0 || !ok[k]) continue;
+        int2 ir = wa.inj_range[slot0 + eidx[k]];
+        for (int q = ir.x; q < ir.x + ir.y; ++q) {
+          real amp;
+          if (wa.amp_mode == 1) {
+            amp = wa.amp;
+          } else {
+            double acc = 0.0;
+            int row = wa.inj_row[q];
+            for (int t = 0; t < 4; ++t) {
+              int nt = A.interp_n0 + t;
+              if (nt >= 0 && nt < wa.n_time) acc += A.interp_w[t] * wa.data[int64_t(row) * wa.n_time + nt];
+            }
+            amp = real(acc);
+          }
+          r[0][k] += amp * wa.inj_w[int64_t(q) * Np + n];
+        }
+      }
+      if (A.mode & kModeRhsOnly) {
+#pragma unroll
+        for (int fld = 0; fld < 4; ++fld) {
+          const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + col_off;
+          gstore_cols<real, W>(rout, off, r[fld], ok);
+        }
+        continue;
+      }
+      real qn[4][4], r1[4][4], r2[4][4];
+#pragma unroll
+      for (int fld = 0; fld < 4; ++fld) {
+        const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + col_off;
+        gload_cols<real, W>(rold1, off, r1[fld]);
+        gload_cols<real, W>(rold2, off, r2[fld]);
+      }
+      // images from the fields and histories at t_start, before the update
+      if ((A.mode & kModeImage) && W == 2) {
+#pragma unroll
+        for (int pr = 0; pr < 2; ++pr) {
+          const int kS = 2 * pr, kR = 2 * pr + 1;
+          if (!ok[kS]) continue;
+          const real* G = sG + eidx[kS] * NG;
+          const real Z = G[46];
+          real xS = sQ[(0 * Np + n) * CS + c0 + kS], xR = sQ[(0 * Np + n) * CS + c0 + kR];
+          real vS = A.e_up[0] * sQ[(1 * Np + n) * CS + c0 + kS] + A.e_up[1] * sQ[(2 * Np + n) * CS + c0 + kS] +
+                    A.e_up[2] * sQ[(3 * Np + n) * CS + c0 + kS];
+          real vR = A.e_up[0] * sQ[(1 * Np + n) * CS + c0 + kR] + A.e_up[1] * sQ[(2 * Np + n) * CS + c0 + kR] +
+                    A.e_up[2] * sQ[(3 * Np + n) * CS + c0 + kR];
+          real rS[3] = {r[0][kS], r1[0][kS], r2[0][kS]};
+          real rR[3] = {r[0][kR], r1[0][kR], r2[0][kR]};
+          real rvS[3], rvR[3];
+          {
+            rvS[0] = A.e_up[0] * r[1][kS] + A.e_up[1] * r[2][kS] + A.e_up[2] * r[3][kS];
+            rvS[1] = A.e_up[0] * r1[1][kS] + A.e_up[1] * r1[2][kS] + A.e_up[2] * r1[3][kS];
+            rvS[2] = A.e_up[0] * r2[1][kS] + A.e_up[1] * r2[2][kS] + A.e_up[2] * r2[3][kS];
+            rvR[0] = A.e_up[0] * r[1][kR] + A.e_up[1] * r[2][kR] + A.e_up[2] * r[3][kR];
+            rvR[1] = A.e_up[0] * r1[1][kR] + A.e_up[1] * r1[2][kR] + A.e_up[2] * r1[3][kR];
+            rvR[2] = A.e_up[0] * r2[1][kR] + A.e_up[1] * r2[2][kR] + A.e_up[2] * r2[3][kR];
+          }
+          const real c[3] = {real(AB::c1), real(AB::c2), real(AB::c3)};
+          const real C[3][3] = {{real(4703.0 / 5040.0), real(-457.0 / 840.0), real(52.0 / 315.0)},
+                                {real(-457.0 / 840.0), real(103.0 / 315.0), real(-251.0 / 2520.0)},
+                                {real(52.0 / 315.0), real(-251.0 / 2520.0), real(17.0 / 560.0)}};
+          // classical image
+          real incP, incQ;
+          {
+            real t2 = 0, t3 = 0;
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+              t2 += c[s] * (xS * rR[s] + rS[s] * xR);
+#pragma unroll
+              for (int u = 0; u < 3; ++u) t3 += C[s][u] * rS[s] * rR[u];
+            }
+            incP = h * (xS * xR + h * (t2 + h * t3));
+          }
+          // characteristic image: q^-_S = p - Z e.v, q^+_R = p + Z e.v
+          {
+            real qS = xS - Z * vS, qR = xR + Z * vR;
+            real sS3[3], sR3[3];
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+              sS3[s] = rS[s] - Z * rvS[s];
+              sR3[s] = rR[s] + Z * rvR[s];
+            }
+            real t2 = 0, t3 = 0;
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+              t2 += c[s] * (qS * sR3[s] + sS3[s] * qR);
+#pragma unroll
+              for (int u = 0; u < 3; ++u) t3 += C[s][u] * sS3[s] * sR3[u];
+            }
+            incQ = h * (qS * qR + h * (t2 + h * t3));
+          }
+          const int64_t io = (blk * Np + n) * 32 + lane0 + eidx[kS];
+          A.image_p[io] -= double(incP);
+          A.image_q[io] -= double(incQ);
+        }
+      }
+      real rr[4][4];
+#pragma unroll
+      for (int fld = 0; fld < 4; ++fld)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          real q0 = sQ[(fld * Np + n) * CS + c0 + k];
+          real upd = real(AB::a1) * r[fld][k] + real(AB::a2) * r1[fld][k] + real(AB::a3) * r2[fld][k];
+          qn[fld][k] = q0 + h * upd;
+          real hb = real(AB::b1) * r[fld][k] + real(AB::b2) * r1[fld][k] + real(AB::b3) * r2[fld][k];
+          sH[(fld * Np + n) * CS + c0 + k] = q0 + h * hb;
+          rr[fld][k] = r[fld][k];
+        }
+#pragma unroll
+      for (int fld = 0; fld < 4; ++fld) {
+        const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + col_off;
+        gstore_cols<real, W>(qb, off, qn[fld], ok);
+        gstore_cols<real, W>(rnew, off, rr[fld], ok);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) sQ[(fld * Np + n) * CS + c0 + k] = qn[fld][k];
+      }
+    }
+  }
+  if (A.mode & kModeRhsOnly) return;
+  __syncthreads();
+
+  // ---------------------------------------------------------------- phase 5: traces
+  {
+    const int hw = tid >> 4, j = tid & 15;
+    const int ws = A.trace_write[lev], hs = A.trace_half[lev];
+    for (int item = hw; item < 32 * 4; item += NT / 16) {
+      int c = item >> 2, f = item & 3;
+      int e = c / W, w = c % W;
+      int meta = sMeta[e];
+      if (!(meta & kMetaValid)) continue;
+      const real* G = sG + e * NG;
+      int64_t s = slot0 + e;
+      real* tw = A.wave[w].trace + (int64_t(ws) * A.n_slots + s) * (8 * NFPP) + f * 2 * NFPP;
+      real* th = A.wave[w].trace + (int64_t(hs) * A.n_slots + s) * (8 * NFPP) + f * 2 * NFPP;
+      for (int jj = j; jj < Nfp; jj += 16) {
+        int n = sFm[f * 32 + jj];
+        real p = sQ[(0 * Np + n) * CS + c];
+        real vn = G[18 + 3 * f] * sQ[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sQ[(2 * Np + n) * CS + c] +
+                  G[20 + 3 * f] * sQ[(3 * Np + n) * CS + c];
+        tw[jj] = p;
+        tw[NFPP + jj] = vn;
+        if (meta & kMetaHalf) {
+          real ph = sH[(0 * Np + n) * CS + c];
+          real vh = G[18 + 3 * f] * sH[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sH[(2 * Np + n) * CS + c] +
+                    G[20 + 3 * f] * sH[(3 * Np + n) * CS + c];
+          th[jj] = ph;
+          th[NFPP + jj] = vh;
+        }
+      }
+    }
+  }
+}
+
+// shared-memory bytes of dg_step_kernel<N, real, W>
+template <int N, typename real, int W>
+constexpr size_t step_smem_bytes() {
+  using O = Order<N>;
+  constexpr int CS = ColStride<real>::value;
+  constexpr int UX = (3 * O::Np * CS > 8 * O::Nfp * 33) ? 3 * O::Np * CS : 8 * O::Nfp * 33;
+  constexpr int EPB = 32 / W;
+  size_t reals = size_t(4 * O::Np * CS) + 2 * size_t(4 * O::Nfp * CS) + UX + EPB * 48;
+  size_t ints = 4 * EPB + 4 * EPB + EPB + EPB + 128 + 192;
+  return reals * sizeof(real) + ints * sizeof(int);
+}
+
+}  // namespace ridg

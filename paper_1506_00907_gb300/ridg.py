@@ -1,0 +1,258 @@
+"""ctypes binding of the C ABI in ``include/ridg.h`` (argument marshalling only).
+
+Every computation runs in ``libridg.so``: the mesh setup on the host, everything in the time loop
+in CUDA kernels.  Host arrays are numpy float64/int64 arrays; device buffers may be given as
+torch CUDA tensors (their ``data_ptr()`` is passed through).  There is no fallback: if the
+library is missing or was built for another machine, importing this module raises.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libridg.so")
+
+RIDG_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "OOM", -4: "CUDA", -5: "UNSTABLE", -6: "TIMEOUT", -7: "NOT_FOUND"}
+BC_AUTO, BC_FREE, BC_TRANSPARENT, BC_RIGID = 0, 1, 2, 3
+F32, F64 = 0, 1
+
+EXPORTED = [
+    "ridg_last_error", "ridg_version", "ridg_mesh_create", "ridg_mesh_destroy", "ridg_mesh_counts",
+    "ridg_reference_operators", "ridg_solver_create", "ridg_solver_destroy", "ridg_solver_info",
+    "ridg_solver_levels", "ridg_solver_nodes", "ridg_set_state", "ridg_set_history", "ridg_eval_rhs", "ridg_step",
+    "ridg_get_state", "ridg_energy", "ridg_trace_len", "ridg_rtm_shot", "ridg_rtm_shot_device",
+    "ridg_last_shot_stats", "ridg_set_profiling",
+]
+
+
+class RidgError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"ridg error {code} ({ERRORS.get(code, '?')}): {msg}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("dtype", C.c_int32), ("cfl", C.c_double), ("n_levels_max", C.c_int32), ("reserved", C.c_int32 * 5)]
+
+
+class Info(C.Structure):
+    _fields_ = [("N", C.c_int32), ("Np", C.c_int32), ("Nfp", C.c_int32), ("n_levels", C.c_int32), ("K", C.c_int64),
+                ("dt_local", C.c_double), ("dt_global", C.c_double), ("level_count", C.c_int64 * 8),
+                ("n_boundary_faces", C.c_int64), ("device_bytes", C.c_int64), ("n_half_step", C.c_int64)]
+
+
+class Source(C.Structure):
+    _fields_ = [("xyz", C.c_double * 3), ("f0", C.c_double), ("t_peak", C.c_double), ("amplitude", C.c_double)]
+
+
+class ShotStats(C.Structure):
+    _fields_ = [("dof_updates_forward", C.c_int64), ("dof_updates_backward", C.c_int64),
+                ("fused_launches", C.c_int64), ("kernel_launches", C.c_int64), ("n_global", C.c_int64),
+                ("boundary_trace_bytes", C.c_int64), ("prof_forward_ms", C.c_double),
+                ("prof_backward_ms", C.c_double), ("prof_forward_launches", C.c_int64),
+                ("prof_backward_launches", C.c_int64)]
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_1506_00907_gb300.build.build()")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "ridg_last_error": (C.c_char_p, []),
+        "ridg_version": (C.c_char_p, []),
+        "ridg_mesh_create": (C.c_int, [P, C.c_int64, P, C.c_int64, P, C.c_int8, C.POINTER(P)]),
+        "ridg_mesh_destroy": (None, [P]),
+        "ridg_mesh_counts": (C.c_int, [P, P, P]),
+        "ridg_reference_operators": (C.c_int, [C.c_int, P, P, P, P, P]),
+        "ridg_solver_create": (C.c_int, [P, C.c_int, P, P, P, C.c_size_t, C.POINTER(P)]),
+        "ridg_solver_destroy": (None, [P]),
+        "ridg_solver_info": (C.c_int, [P, P]),
+        "ridg_solver_levels": (C.c_int, [P, P]),
+        "ridg_solver_nodes": (C.c_int, [P, P]),
+        "ridg_set_state": (C.c_int, [P, P]),
+        "ridg_set_history": (C.c_int, [P, P, P]),
+        "ridg_eval_rhs": (C.c_int, [P, P, P]),
+        "ridg_step": (C.c_int, [P, C.c_int64]),
+        "ridg_get_state": (C.c_int, [P, P]),
+        "ridg_energy": (C.c_int, [P, P]),
+        "ridg_trace_len": (C.c_int64, [P, C.c_double]),
+        "ridg_rtm_shot": (C.c_int, [P, P, P, C.c_int64, C.c_double, C.c_double, P, P, P, P, P]),
+        "ridg_rtm_shot_device": (C.c_int, [P, P, P, C.c_int64, C.c_double, C.c_double, P, P, P, P, P]),
+        "ridg_last_shot_stats": (C.c_int, [P, P]),
+        "ridg_set_profiling": (C.c_int, [P, C.c_int32]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(code):
+    if code != RIDG_OK:
+        raise RidgError(code, lib().ridg_last_error().decode())
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _f64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != tuple(shape):
+        a = a.reshape(shape)
+    return a
+
+
+def reference_operators(N: int):
+    Np = (N + 1) * (N + 2) * (N + 3) // 6
+    Nfp = (N + 1) * (N + 2) // 2
+    rst = np.zeros((Np, 3))
+    D = np.zeros((3, Np, Np))
+    M = np.zeros((Np, Np))
+    LIFT = np.zeros((Np, 4 * Nfp))
+    fm = np.zeros((4, Nfp), dtype=np.int32)
+    _check(lib().ridg_reference_operators(N, _ptr(rst), _ptr(D), _ptr(M), _ptr(LIFT), _ptr(fm)))
+    return dict(rst=rst, D=D, M=M, LIFT=LIFT, fmask=fm)
+
+
+class Mesh:
+    def __init__(self, xyz, tets, face_bc=None, default_bc=BC_TRANSPARENT):
+        self.xyz = _f64(xyz)
+        self.tets = np.ascontiguousarray(tets, dtype=np.int64)
+        fb = None if face_bc is None else np.ascontiguousarray(face_bc, dtype=np.int8)
+        h = C.c_void_p()
+        _check(lib().ridg_mesh_create(_ptr(self.xyz), self.xyz.shape[0], _ptr(self.tets), self.tets.shape[0],
+                                      _ptr(fb), int(default_bc), C.byref(h)))
+        self._h = h
+        self.K = self.tets.shape[0]
+
+    def counts(self):
+        nb, ni = C.c_int64(), C.c_int64()
+        _check(lib().ridg_mesh_counts(self._h, C.byref(nb), C.byref(ni)))
+        return nb.value, ni.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ridg_mesh_destroy(self._h)
+            self._h = None
+
+
+class Solver:
+    def __init__(self, mesh: Mesh, N: int, c, rho, dtype="f32", cfl=0.15, n_levels_max=3, stream=0):
+        self.mesh = mesh
+        c = _f64(c)
+        rho = _f64(rho)
+        opt = Options(F64 if dtype == "f64" else F32, float(cfl), int(n_levels_max))
+        h = C.c_void_p()
+        _check(lib().ridg_solver_create(mesh._h, int(N), _ptr(c), _ptr(rho), C.byref(opt), int(stream), C.byref(h)))
+        self._h = h
+        self.info = self.get_info()
+        self.N, self.Np, self.K = self.info.N, self.info.Np, self.info.K
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ridg_solver_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def get_info(self) -> Info:
+        inf = Info()
+        _check(lib().ridg_solver_info(self._h, C.byref(inf)))
+        return inf
+
+    def levels(self):
+        out = np.zeros(self.K, dtype=np.int32)
+        _check(lib().ridg_solver_levels(self._h, _ptr(out)))
+        return out
+
+    def nodes(self):
+        out = np.zeros((self.K, self.Np, 3))
+        _check(lib().ridg_solver_nodes(self._h, _ptr(out)))
+        return out
+
+    def set_state(self, q):
+        q = _f64(q, (self.K, 4, self.Np))
+        _check(lib().ridg_set_state(self._h, _ptr(q)))
+
+    def set_history(self, r1=None, r2=None):
+        a = None if r1 is None else _f64(r1, (self.K, 4, self.Np))
+        b = None if r2 is None else _f64(r2, (self.K, 4, self.Np))
+        _check(lib().ridg_set_history(self._h, _ptr(a), _ptr(b)))
+
+    def eval_rhs(self, q):
+        q = _f64(q, (self.K, 4, self.Np))
+        out = np.zeros_like(q)
+        _check(lib().ridg_eval_rhs(self._h, _ptr(q), _ptr(out)))
+        return out
+
+    def step(self, n_global=1):
+        _check(lib().ridg_step(self._h, int(n_global)))
+
+    def get_state(self):
+        out = np.zeros((self.K, 4, self.Np))
+        _check(lib().ridg_get_state(self._h, _ptr(out)))
+        return out
+
+    def energy(self):
+        e = C.c_double()
+        _check(lib().ridg_energy(self._h, C.byref(e)))
+        return e.value
+
+    def trace_len(self, t_final):
+        return int(lib().ridg_trace_len(self._h, float(t_final)))
+
+    def rtm_shot(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0, observed=None,
+                 e_up=(0.0, 0.0, -1.0), want_images=True):
+        """Host-buffer shot: returns (traces [nrec, n_t], image_p [K, Np], image_q [K, Np])."""
+        src = Source((C.c_double * 3)(*source_xyz), f0, t_peak, amplitude)
+        rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
+        n_t = self.trace_len(t_final)
+        traces = np.zeros((rec.shape[0], n_t))
+        ip = np.zeros((self.K, self.Np)) if want_images else None
+        iq = np.zeros((self.K, self.Np)) if want_images else None
+        obs = None if observed is None else _f64(observed, (rec.shape[0], n_t))
+        eu = _f64(e_up)
+        _check(lib().ridg_rtm_shot(self._h, C.byref(src), _ptr(rec), rec.shape[0], float(t_final),
+                                   float(t_image_start), _ptr(obs), _ptr(traces), _ptr(ip), _ptr(iq), _ptr(eu)))
+        return traces, ip, iq
+
+    def rtm_shot_device(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0,
+                        observed=None, traces=None, image_p=None, image_q=None, e_up=(0.0, 0.0, -1.0)):
+        """Device-buffer shot (torch CUDA float64 tensors or None); returns after enqueueing."""
+        src = Source((C.c_double * 3)(*source_xyz), f0, t_peak, amplitude)
+        rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
+        eu = _f64(e_up)
+        _check(lib().ridg_rtm_shot_device(self._h, C.byref(src), _ptr(rec), rec.shape[0], float(t_final),
+                                          float(t_image_start), _ptr(observed), _ptr(traces), _ptr(image_p),
+                                          _ptr(image_q), _ptr(eu)))
+
+    def set_profiling(self, every: int):
+        _check(lib().ridg_set_profiling(self._h, int(every)))
+
+    def shot_stats(self) -> ShotStats:
+        st = ShotStats()
+        _check(lib().ridg_last_shot_stats(self._h, C.byref(st)))
+        return st
