@@ -1,22 +1,38 @@
 // Explicit instantiation of the kernels of one order (RIDG_ORDER), included by kernels_n<N>.cu.
 #include "aux_kernels.cuh"
 #include "dispatch.hpp"
+#include "step_kernel_tc.cuh"
+
+#include <type_traits>
 
 namespace ridg {
 
 template <int N, typename real, int W>
 static cudaError_t launch_step_w(const StepArgs<real>& a, cudaStream_t st) {
-  constexpr size_t smem = step_smem_bytes<N, real, W>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         int(smem));
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   int64_t blocks = (a.slot_hi - a.slot_lo) / (32 / W);
   if (blocks <= 0) return cudaSuccess;
-  dg_step_kernel<N, real, W><<<dim3(unsigned(blocks)), Order<N>::NT, smem, st>>>(a);
+  if constexpr (std::is_same<real, float>::value) {
+    // FP32: element products on tensor cores (TF32 three-term split)
+    constexpr size_t smem = SmemTc<N, W>::bytes;
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(dg_step_kernel_tc<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(smem));
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    dg_step_kernel_tc<N, W><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a);
+  } else {
+    constexpr size_t smem = step_smem_bytes<N, real, W>();
+    static bool configured = false;
+    if (!configured) {
+      cudaError_t e = cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           int(smem));
+      if (e != cudaSuccess) return e;
+      configured = true;
+    }
+    dg_step_kernel<N, real, W><<<dim3(unsigned(blocks)), Order<N>::NT, smem, st>>>(a);
+  }
   return cudaGetLastError();
 }
 

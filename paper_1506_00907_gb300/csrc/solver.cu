@@ -14,6 +14,7 @@
 #include "../../include/ridg.h"
 #include "dispatch.hpp"
 #include "setup.hpp"
+#include "step_kernel_tc.cuh"
 
 namespace ridg {
 
@@ -277,7 +278,8 @@ class Engine final : public ridg_solver {
   // ------------------------------------------------------------------ one shot
   void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i, const double* obs_dev,
             double* traces_dev, double* imgp_dev, double* imgq_dev, const double* e_up) override {
-    if (!(t_final > 0.0) || !(t_i >= 0.0) || t_i > t_final) throw Error{RIDG_E_INVALID_ARG, "bad time span"};
+    if (!(t_final > 0.0) || !(t_i >= 0.0) || t_i > t_final + lv_.dt_local * double(NL_))
+      throw Error{RIDG_E_INVALID_ARG, "bad time span"};
     if (nrec < 0 || (nrec > 0 && !rec)) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
     std::memset(&stats_, 0, sizeof(stats_));
     prof_used_ = 0;
@@ -491,7 +493,10 @@ class Engine final : public ridg_solver {
     RIDG_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     size_t need = dispatch_order(N_, [&](auto NC) {
       constexpr int NN = decltype(NC)::value;
-      return std::max(step_smem_bytes<NN, real, 1>(), step_smem_bytes<NN, real, 2>());
+      if constexpr (std::is_same<real, float>::value)
+        return std::max(SmemTc<NN, 1>::bytes, SmemTc<NN, 2>::bytes);
+      else
+        return std::max(step_smem_bytes<NN, real, 1>(), step_smem_bytes<NN, real, 2>());
     });
     if (need > size_t(optin))
       throw Error{RIDG_E_INVALID_ARG, "order " + std::to_string(N_) + " in this precision needs " +
@@ -578,6 +583,7 @@ class Engine final : public ridg_solver {
       for (int n = 0; n < Np_; ++n) Lt[fm * NPa_ + n] = real(ref_.LIFT(n, fm));
     upload(Dt_d_, Dt, st_);
     upload(Lt_d_, Lt, st_);
+    if (std::is_same<real, float>::value) upload(afrag_d_, operator_fragments(), st_);
     std::vector<int> fm(128, 0), pm(192, 0);
     for (int f = 0; f < 4; ++f)
       for (int j = 0; j < Nfp_; ++j) fm[f * 32 + j] = ref_.fmask[f][j];
@@ -589,6 +595,53 @@ class Engine final : public ridg_solver {
     upload(slot_of_d_, ord_.slot_of, st_);
     level_count_.assign(L_, 0);
     for (int64_t k = 0; k < mesh_.K; ++k) level_count_[lv_.level[k] - 1]++;
+  }
+
+  // TF32 rounding (round to nearest, ties away from zero) of an FP32 value
+  static uint32_t tf32_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u;
+    u += 0x1000u;
+    return u & 0xffffe000u;
+  }
+  // Operator fragments of mma.m16n8k8 (A: 16 x 8 row major; lane (g, t) holds rows g, g+8 and
+  // columns t, t+4) for D_r, D_s, D_t and the four LIFT blocks, tiles of 16 nodes x 8 nodes,
+  // each value split into TF32 hi and lo (hi + lo = the FP64 operator to ~2^-22).
+  std::vector<uint32_t> operator_fragments() const {
+    const int MT = (Np_ + 15) / 16, KSD = (Np_ + 7) / 8, KSF = (Nfp_ + 7) / 8;
+    std::vector<uint32_t> out(size_t(3 * MT * KSD + 4 * MT * KSF) * 256, 0u);
+    auto put = [&](size_t tile, int lane, int q, double v) {
+      float hf = float(v);
+      uint32_t hi = tf32_bits(hf);
+      float hiv;
+      std::memcpy(&hiv, &hi, 4);
+      uint32_t lo = tf32_bits(float(v - double(hiv)));
+      out[tile * 256 + lane * 8 + q] = hi;
+      out[tile * 256 + lane * 8 + 4 + q] = lo;
+    };
+    for (int lane = 0; lane < 32; ++lane) {
+      const int g = lane >> 2, t = lane & 3;
+      const int rr[4] = {g, g + 8, g, g + 8}, cc[4] = {t, t, t + 4, t + 4};
+      for (int jd = 0; jd < 3; ++jd)
+        for (int mt = 0; mt < MT; ++mt)
+          for (int kb = 0; kb < KSD; ++kb)
+            for (int q = 0; q < 4; ++q) {
+              int r = mt * 16 + rr[q], c = kb * 8 + cc[q];
+              double v = (r < Np_ && c < Np_) ? ref_.D[jd](r, c) : 0.0;
+              put(size_t((jd * MT + mt) * KSD + kb), lane, q, v);
+            }
+      const size_t baseL = size_t(3 * MT * KSD);
+      for (int f = 0; f < 4; ++f)
+        for (int mt = 0; mt < MT; ++mt)
+          for (int kb = 0; kb < KSF; ++kb)
+            for (int q = 0; q < 4; ++q) {
+              int r = mt * 16 + rr[q], c = kb * 8 + cc[q];
+              double v = (r < Np_ && c < Nfp_) ? ref_.LIFT(r, f * Nfp_ + c) : 0.0;
+              put(baseL + size_t((f * MT + mt) * KSF + kb), lane, q, v);
+            }
+    }
+    return out;
   }
 
   void alloc_wave(Wave<real>& w) {
@@ -649,6 +702,7 @@ class Engine final : public ridg_solver {
     a.Lt = dptr<const real>(Lt_d_);
     a.fmask = dptr<const int>(fmask_d_);
     a.perm = dptr<const int>(perm_d_);
+    a.afrag = dptr<const uint32_t>(afrag_d_);
     a.e_up[2] = real(-1);
     return a;
   }
@@ -785,6 +839,7 @@ class Engine final : public ridg_solver {
   std::vector<int> bface_host_;
   std::vector<int64_t> level_count_;
   DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
+  DBuf afrag_d_;
   DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_;
   Wave<real> w_[2];
   int64_t tau_ = 0, dof_ = 0;

@@ -105,6 +105,7 @@ struct StepArgs {
   const int* fmask;      // [4][32]
   const int* perm;       // [6][32]
   real* rhs_out;         // kModeRhsOnly: q-sized
+  const uint32_t* afrag; // tensor-core variant: operator fragments (TF32 hi/lo), see step_kernel_tc.cuh
 };
 
 template <int N>
@@ -208,42 +209,126 @@ __device__ __forceinline__ void gstore_cols(real* const base[2], int64_t off, co
   }
 }
 
+// ---------------------------------------------------------------- asynchronous copies
+__device__ __forceinline__ void cp_async_bytes16(void* smem, const void* gmem) {
+  unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(gmem), "n"(B));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+template <typename real>
+__device__ __forceinline__ void st4(real* p, const real v[4]) {
+  if constexpr (sizeof(real) == 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+    *reinterpret_cast<double2*>(p + 2) = make_double2(v[2], v[3]);
+  }
+}
+
+// Shared-memory plan of dg_step_kernel<N, real, W> (offsets in reals).
+template <int N, typename real, int W>
+struct Smem {
+  using O = Order<N>;
+  static constexpr int Np = O::Np, Nfp = O::Nfp;
+  static constexpr int CS = ColStride<real>::value;  // padded column rows (face-node gathers)
+  static constexpr int RS = 32;                      // ring rows: read by their owner thread only
+  static constexpr int XS = 33;                      // exterior-trace staging rows
+  static constexpr int NG = 49;                      // per-element coefficients (odd: conflict-free)
+  static constexpr int EPB = 32 / W;
+  static constexpr int Q = 4 * Np * CS;
+  static constexpr int R = 4 * Np * RS;
+  static constexpr int ST = 4 * Nfp * CS;
+  static constexpr int UX = (3 * Np * CS > 8 * Nfp * XS) ? 3 * Np * CS : 8 * Nfp * XS;
+  static constexpr int G = EPB * NG;
+  static constexpr int INTS = 4 * EPB + 4 * EPB + EPB + EPB + 128 + 192;
+  static constexpr size_t bytes_with(bool ring) {
+    return (size_t(Q) + (ring ? 2 * size_t(R) : 0) + 2 * size_t(ST) + UX + G) * sizeof(real) + INTS * sizeof(int);
+  }
+  // the history is staged in shared memory when it leaves room for at least one block
+  static constexpr bool ring_in_smem = bytes_with(true) <= 200 * 1024;
+  static constexpr size_t bytes = bytes_with(ring_in_smem);
+  static_assert(4 * Np * CS <= 2 * ST + UX, "half-step staging must fit in the penalty/U region");
+};
+
 template <int N, typename real, int W>
 __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<real> A) {
   using O = Order<N>;
+  using SM = Smem<N, real, W>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NPa = O::NPa, NT = O::NT, NFPP = O::NFPP;
-  constexpr int CS = ColStride<real>::value;  // column-row stride in shared memory
-  constexpr int EPB = 32 / W;                 // elements per CTA
-  constexpr int XS = 33;                      // stride of the exterior-trace staging rows
-  constexpr int NG = 48;                      // per-element coefficient block
+  constexpr int CS = SM::CS, RS = SM::RS, XS = SM::XS, NG = SM::NG, EPB = SM::EPB;
+  constexpr bool RING = SM::ring_in_smem;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  real* sQ = reinterpret_cast<real*>(smem_raw);          // [4][Np][CS]
-  real* sS = sQ + 4 * Np * CS;                           // [4*Nfp][CS] velocity penalty scalars
-  real* sT = sS + 4 * Nfp * CS;                          // [4*Nfp][CS] pressure penalties
-  constexpr int UX = (3 * Np * CS > 8 * Nfp * XS) ? 3 * Np * CS : 8 * Nfp * XS;
-  real* sU = sT + 4 * Nfp * CS;                          // [3][Np][CS]   (aliases sX)
-  real* sX = sU;                                         // [4][Nfp][2][XS] exterior traces
-  real* sG = sU + UX;                                    // [EPB][NG] per-element coefficients
-  int* sI = reinterpret_cast<int*>(sG + EPB * NG);       // per-element ints
-  int* sNbr = sI;                                        // [EPB][4]
-  int* sInfo = sNbr + 4 * EPB;                           // [EPB][4]
-  int* sBf = sInfo + 4 * EPB;                            // [EPB]
-  int* sMeta = sBf + EPB;                                // [EPB]
-  int* sFm = sMeta + EPB;                                // [4][32]
-  int* sPerm = sFm + 128;                                // [6][32]
-  real* sH = sS;  // half-step fields [4][Np][CS] reuse sS/sT/sU after the products
+  real* sQ = reinterpret_cast<real*>(smem_raw);  // [4][Np][CS]  q at t_start, then q at t_new
+  real* sR1 = sQ + SM::Q;                         // [4][Np][RS]  history r^{m-1}   (if RING)
+  real* sR2 = sR1 + (RING ? SM::R : 0);           // [4][Np][RS]  history r^{m-2}   (if RING)
+  real* sS = sR2 + (RING ? SM::R : 0);            // [4*Nfp][CS]  velocity penalty scalars
+  real* sT = sS + SM::ST;                         // [4*Nfp][CS]  pressure penalties
+  real* sU = sT + SM::ST;                         // [3][Np][CS]  U_j (aliases sX)
+  real* sX = sU;                                  // [4*Nfp][2][XS] exterior traces
+  real* sG = sU + SM::UX;                         // [EPB][NG]
+  int* sI = reinterpret_cast<int*>(sG + SM::G);
+  int* sNbr = sI;                // [EPB][4]
+  int* sInfo = sNbr + 4 * EPB;   // [EPB][4]
+  int* sBf = sInfo + 4 * EPB;    // [EPB]
+  int* sMeta = sBf + EPB;        // [EPB]
+  int* sFm = sMeta + EPB;        // [4][32]
+  int* sPerm = sFm + 128;        // [6][32]
+  real* sH = sS;                 // [4][Np][CS] half-step fields, after the products
 
   const int tid = threadIdx.x;
   const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * EPB;
   if (slot0 >= A.slot_hi) return;
-  const int64_t blk = slot0 >> 5;        // 32-slot block of the q layout
-  const int lane0 = int(slot0 & 31);     // first element's lane in that block (0 or 16)
-  // level of this CTA (all its slots share one level)
+  const int64_t blk = slot0 >> 5;     // 32-slot block of the field layout
+  const int lane0 = int(slot0 & 31);  // first element's lane in that block (0 or 16)
   int lev = 0;
   for (int l = 0; l < A.n_levels; ++l)
     if (slot0 >= A.level_begin[l]) lev = l;
   const real h = A.h[lev];
+  const bool rhs_only = (A.mode & kModeRhsOnly) != 0;
+  const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
+  const int rn = A.ring_new[lev], r1i = A.ring_old1[lev], r2i = A.ring_old2[lev];
+
+  // ---------------------------------------------------------------- phase 1: async field loads
+  // q at t_start and (unless only the right-hand side is wanted) the two older right-hand sides
+  {
+    const int64_t fbase = (blk * 4) * Np * 32;
+    if constexpr (W == 1) {
+      constexpr int CH = 16 / sizeof(real);  // reals per 16-byte chunk
+      constexpr int NCH = 32 / CH;           // chunks per row
+      const real* src0 = A.wave[0].q + fbase;
+      const real* src1 = A.wave[0].ring + r1i * qsize + fbase;
+      const real* src2 = A.wave[0].ring + r2i * qsize + fbase;
+      const int narr = (RING && !rhs_only) ? 3 : 1;
+      for (int i = tid; i < narr * 4 * Np * NCH; i += NT) {
+        int arr = i / (4 * Np * NCH);
+        int rem = i - arr * 4 * Np * NCH;
+        int row = rem / NCH, ch = rem - row * NCH;
+        real* dst = arr == 0 ? sQ + row * CS : (arr == 1 ? sR1 : sR2) + row * RS;
+        const real* src = arr == 0 ? src0 : (arr == 1 ? src1 : src2);
+        cp_async_bytes16(dst + ch * CH, src + row * 32 + ch * CH);
+      }
+    } else {
+      const int narr = (RING && !rhs_only) ? 3 : 1;
+      for (int i = tid; i < narr * 4 * Np * 32; i += NT) {
+        int arr = i / (4 * Np * 32);
+        int rem = i - arr * 4 * Np * 32;
+        int row = rem >> 5, c = rem & 31;
+        int e = c >> 1, w = c & 1;
+        const real* base = arr == 0 ? A.wave[w].q : A.wave[w].ring + (arr == 1 ? r1i : r2i) * qsize;
+        real* dst = arr == 0 ? sQ + row * CS + c : (arr == 1 ? sR1 : sR2) + row * RS + c;
+        cp_async_small<sizeof(real)>(dst, base + fbase + row * 32 + lane0 + e);
+      }
+    }
+    cp_async_commit();
+  }
 
   // ---------------------------------------------------------------- phase 0: tables
   for (int i = tid; i < 128; i += NT) sFm[i] = A.fmask[i];
@@ -280,67 +365,77 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
       G[30 + 4 * f + 3] = -real(0.5) * fs * irho * tauv;
     }
     G[46] = m[2];  // rho c
-    G[47] = 0;
-  }
-  // ---------------------------------------------------------------- phase 1: fields -> smem
-  for (int i = tid; i < 4 * Np * 32; i += NT) {
-    int c = i & 31, row = i >> 5;  // row = field*Np + node
-    int e = c / W, w = c % W;
-    int64_t off = ((blk * 4) * Np + row) * 32 + lane0 + e;
-    sQ[row * CS + c] = A.wave[w].q[off];
   }
   __syncthreads();
 
   // ---------------------------------------------------------------- phase 2a: exterior traces
   // half-warp per (column, face), lanes over face nodes: coalesced reads of the neighbour's face
-  // block, permuted by the face correspondence
+  // block, permuted by the face correspondence; four items' loads are issued before any store.
+  // Boundary faces of the backward source run read the recorded forward traces instead.
   {
+    constexpr int NH = NT / 16;
     const int hw = tid >> 4, j = tid & 15;
-    for (int item = hw; item < 32 * 4; item += NT / 16) {
-      int c = item >> 2, f = item & 3;
-      int e = c / W, w = c % W;
-      if (!(sMeta[e] & kMetaValid)) continue;
-      int info = sInfo[e * 4 + f];
-      int bc = finfo_bc(uint8_t(info));
-      for (int jj = j; jj < Nfp; jj += 16) {
-        real xp = 0, xv = 0;
-        bool have = false;
+    for (int base = hw; base < 32 * 4; base += 4 * NH) {
+      real xp[4][2], xv[4][2];
+      bool have[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        have[u] = false;
+        int item = base + u * NH;
+        if (item >= 128) continue;
+        int c = item >> 2, f = item & 3;
+        int e = c / W, w = c % W;
+        if (!(sMeta[e] & kMetaValid)) continue;
+        int info = sInfo[e * 4 + f];
+        int bc = finfo_bc(uint8_t(info));
         if (bc == 0) {
           int64_t s2 = sNbr[e * 4 + f];
           int f2 = finfo_face(uint8_t(info));
-          int j2 = sPerm[finfo_perm(uint8_t(info)) * 32 + jj];
           const real* tb = A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + s2) * (8 * NFPP) + f2 * 2 * NFPP;
-          xp = tb[j2];
-          xv = -tb[NFPP + j2];  // neighbour's n.v with our normal
-          have = true;
-        } else {
-          // own traces of the boundary face at t_start
-          int n = sFm[f * 32 + jj];
-          const real* G = sG + e * NG;
-          real p = sQ[(0 * Np + n) * CS + c];
-          real vn = G[18 + 3 * f] * sQ[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sQ[(2 * Np + n) * CS + c] +
-                    G[20 + 3 * f] * sQ[(3 * Np + n) * CS + c];
+          const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            int jj = j + 16 * t;
+            if (jj < Nfp) {
+              int j2 = pm[jj];
+              xp[u][t] = tb[j2];
+              xv[u][t] = -tb[NFPP + j2];  // neighbour's n.v taken with our normal
+            }
+          }
+          have[u] = true;
+        } else if (w == 0 && (A.mode & kModeReplay)) {
+          // backward source run: the recorded forward traces are the exterior state
           int b = sBf[e];
           for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
-          if ((A.mode & kModeRecord) && w == 0) {
-            real* rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
-            rec[jj] = p;
-            rec[NFPP + jj] = vn;
+          const real* rec = A.arena_read + (A.arena_offset + b) * (2 * NFPP);
+#pragma unroll
+          for (int t = 0; t < 2; ++t) {
+            int jj = j + 16 * t;
+            if (jj < Nfp) {
+              xp[u][t] = rec[jj];
+              xv[u][t] = rec[NFPP + jj];
+            }
           }
-          if ((A.mode & kModeReplay) && w == 0) {
-            const real* rec = A.arena_read + (A.arena_offset + b) * (2 * NFPP);
-            xp = rec[jj];
-            xv = rec[NFPP + jj];
-            have = true;
-          }
+          have[u] = true;
         }
-        if (have) {
-          sX[((f * Nfp + jj) * 2 + 0) * XS + c] = xp;
-          sX[((f * Nfp + jj) * 2 + 1) * XS + c] = xv;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (!have[u]) continue;
+        int item = base + u * NH;
+        int c = item >> 2, f = item & 3;
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          int jj = j + 16 * t;
+          if (jj < Nfp) {
+            sX[((f * Nfp + jj) * 2 + 0) * XS + c] = xp[u][t];
+            sX[((f * Nfp + jj) * 2 + 1) * XS + c] = xv[u][t];
+          }
         }
       }
     }
   }
+  cp_async_wait_all();
   __syncthreads();
 
   // ---------------------------------------------------------------- phase 2b: penalties
@@ -355,6 +450,15 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
               G[20 + 3 * f] * sQ[(3 * Np + n) * CS + c];
     int info = sInfo[e * 4 + f];
     int bc = finfo_bc(uint8_t(info));
+    const bool valid = (sMeta[e] & kMetaValid) != 0;
+    if (bc != 0 && valid && w == 0 && (A.mode & kModeRecord)) {
+      // forward run: record the traces of this boundary face at t_start
+      int b = sBf[e];
+      for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
+      real* rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
+      rec[jj] = p;
+      rec[NFPP + jj] = vn;
+    }
     real jp, jv;
     bool replay = (A.mode & kModeReplay) && w == 0 && bc != 0;
     if (bc == 0 || replay) {
@@ -373,7 +477,7 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
     const real* pc = G + 30 + 4 * f;
     real t = pc[0] * jv + pc[1] * jp;
     real sv = pc[2] * jp + pc[3] * jv;
-    if (!(sMeta[e] & kMetaValid)) {
+    if (!valid) {
       t = 0;
       sv = 0;
     }
@@ -382,7 +486,7 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
   }
   __syncthreads();
 
-  // ---------------------------------------------------------------- phase 2c: U_j = G_p * v
+  // ---------------------------------------------------------------- phase 2c: U_j = G_p v
   for (int i = tid; i < Np * 32; i += NT) {
     int c = i & 31, m = i >> 5;
     int e = c / W;
@@ -393,8 +497,8 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
   __syncthreads();
 
   // ---------------------------------------------------------------- phase 3: element products
-  const int np = tid >> 3;      // node pair
-  const int cq = tid & 7;       // column quad
+  const int np = tid >> 3;  // node pair
+  const int cq = tid & 7;   // column quad
   const bool gemm = np < O::NPP;
   const int c0 = cq * 4;
   real rp[2][4], dp[3][2][4], ls[4][2][4];
@@ -454,8 +558,6 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
 
   // ---------------------------------------------------------------- phase 4: update
   if (gemm) {
-    const int rn = A.ring_new[lev], r1i = A.ring_old1[lev], r2i = A.ring_old2[lev];
-    const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
     real* qb[2] = {A.wave[0].q, W == 2 ? A.wave[1].q : nullptr};
     real* rnew[2] = {A.wave[0].ring + rn * qsize, W == 2 ? A.wave[1].ring + rn * qsize : nullptr};
     real* rold1[2] = {A.wave[0].ring + r1i * qsize, W == 2 ? A.wave[1].ring + r1i * qsize : nullptr};
@@ -463,10 +565,12 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
     real* rout[2] = {A.rhs_out, nullptr};
     bool ok[4];
     int eidx[4];
+    const real* Gk[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       eidx[k] = (c0 + k) / W;
       ok[k] = (sMeta[eidx[k]] & kMetaValid) != 0;
+      Gk[k] = sG + eidx[k] * NG;
     }
     const int64_t col_off = (W == 1) ? (lane0 + c0) : (lane0 + c0 / 2);
 #pragma unroll
@@ -476,7 +580,7 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
       real r[4][4];  // [field][column]
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const real* G = sG + eidx[k] * NG;
+        const real* G = Gk[k];
         r[0][k] = rp[i][k];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -509,7 +613,7 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
           r[0][k] += amp * wa.inj_w[int64_t(q) * Np + n];
         }
       }
-      if (A.mode & kModeRhsOnly) {
+      if (rhs_only) {
 #pragma unroll
         for (int fld = 0; fld < 4; ++fld) {
           const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + col_off;
@@ -517,12 +621,18 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
         }
         continue;
       }
-      real qn[4][4], r1[4][4], r2[4][4];
+      real q0[4][4], r1[4][4], r2[4][4];
 #pragma unroll
       for (int fld = 0; fld < 4; ++fld) {
-        const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + col_off;
-        gload_cols<real, W>(rold1, off, r1[fld]);
-        gload_cols<real, W>(rold2, off, r2[fld]);
+        ld4<real>(sQ + (fld * Np + n) * CS + c0, q0[fld]);
+        if constexpr (RING) {
+          ld4<real>(sR1 + (fld * Np + n) * RS + c0, r1[fld]);
+          ld4<real>(sR2 + (fld * Np + n) * RS + c0, r2[fld]);
+        } else {
+          const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + col_off;
+          gload_cols<real, W>(rold1, off, r1[fld]);
+          gload_cols<real, W>(rold2, off, r2[fld]);
+        }
       }
       // images from the fields and histories at t_start, before the update
       if ((A.mode & kModeImage) && W == 2) {
@@ -530,29 +640,23 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
         for (int pr = 0; pr < 2; ++pr) {
           const int kS = 2 * pr, kR = 2 * pr + 1;
           if (!ok[kS]) continue;
-          const real* G = sG + eidx[kS] * NG;
-          const real Z = G[46];
-          real xS = sQ[(0 * Np + n) * CS + c0 + kS], xR = sQ[(0 * Np + n) * CS + c0 + kR];
-          real vS = A.e_up[0] * sQ[(1 * Np + n) * CS + c0 + kS] + A.e_up[1] * sQ[(2 * Np + n) * CS + c0 + kS] +
-                    A.e_up[2] * sQ[(3 * Np + n) * CS + c0 + kS];
-          real vR = A.e_up[0] * sQ[(1 * Np + n) * CS + c0 + kR] + A.e_up[1] * sQ[(2 * Np + n) * CS + c0 + kR] +
-                    A.e_up[2] * sQ[(3 * Np + n) * CS + c0 + kR];
+          const real Z = Gk[kS][46];
+          const real* eu = A.e_up;
+          real xS = q0[0][kS], xR = q0[0][kR];
+          real vS = eu[0] * q0[1][kS] + eu[1] * q0[2][kS] + eu[2] * q0[3][kS];
+          real vR = eu[0] * q0[1][kR] + eu[1] * q0[2][kR] + eu[2] * q0[3][kR];
           real rS[3] = {r[0][kS], r1[0][kS], r2[0][kS]};
           real rR[3] = {r[0][kR], r1[0][kR], r2[0][kR]};
-          real rvS[3], rvR[3];
-          {
-            rvS[0] = A.e_up[0] * r[1][kS] + A.e_up[1] * r[2][kS] + A.e_up[2] * r[3][kS];
-            rvS[1] = A.e_up[0] * r1[1][kS] + A.e_up[1] * r1[2][kS] + A.e_up[2] * r1[3][kS];
-            rvS[2] = A.e_up[0] * r2[1][kS] + A.e_up[1] * r2[2][kS] + A.e_up[2] * r2[3][kS];
-            rvR[0] = A.e_up[0] * r[1][kR] + A.e_up[1] * r[2][kR] + A.e_up[2] * r[3][kR];
-            rvR[1] = A.e_up[0] * r1[1][kR] + A.e_up[1] * r1[2][kR] + A.e_up[2] * r1[3][kR];
-            rvR[2] = A.e_up[0] * r2[1][kR] + A.e_up[1] * r2[2][kR] + A.e_up[2] * r2[3][kR];
-          }
+          real rvS[3] = {eu[0] * r[1][kS] + eu[1] * r[2][kS] + eu[2] * r[3][kS],
+                         eu[0] * r1[1][kS] + eu[1] * r1[2][kS] + eu[2] * r1[3][kS],
+                         eu[0] * r2[1][kS] + eu[1] * r2[2][kS] + eu[2] * r2[3][kS]};
+          real rvR[3] = {eu[0] * r[1][kR] + eu[1] * r[2][kR] + eu[2] * r[3][kR],
+                         eu[0] * r1[1][kR] + eu[1] * r1[2][kR] + eu[2] * r1[3][kR],
+                         eu[0] * r2[1][kR] + eu[1] * r2[2][kR] + eu[2] * r2[3][kR]};
           const real c[3] = {real(AB::c1), real(AB::c2), real(AB::c3)};
           const real C[3][3] = {{real(4703.0 / 5040.0), real(-457.0 / 840.0), real(52.0 / 315.0)},
                                 {real(-457.0 / 840.0), real(103.0 / 315.0), real(-251.0 / 2520.0)},
                                 {real(52.0 / 315.0), real(-251.0 / 2520.0), real(17.0 / 560.0)}};
-          // classical image
           real incP, incQ;
           {
             real t2 = 0, t3 = 0;
@@ -564,8 +668,8 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
             }
             incP = h * (xS * xR + h * (t2 + h * t3));
           }
-          // characteristic image: q^-_S = p - Z e.v, q^+_R = p + Z e.v
           {
+            // characteristic image: q^-_S = p - Z e.v, q^+_R = p + Z e.v
             real qS = xS - Z * vS, qR = xR + Z * vR;
             real sS3[3], sR3[3];
 #pragma unroll
@@ -587,29 +691,25 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
           A.image_q[io] -= double(incQ);
         }
       }
-      real rr[4][4];
-#pragma unroll
-      for (int fld = 0; fld < 4; ++fld)
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          real q0 = sQ[(fld * Np + n) * CS + c0 + k];
-          real upd = real(AB::a1) * r[fld][k] + real(AB::a2) * r1[fld][k] + real(AB::a3) * r2[fld][k];
-          qn[fld][k] = q0 + h * upd;
-          real hb = real(AB::b1) * r[fld][k] + real(AB::b2) * r1[fld][k] + real(AB::b3) * r2[fld][k];
-          sH[(fld * Np + n) * CS + c0 + k] = q0 + h * hb;
-          rr[fld][k] = r[fld][k];
-        }
 #pragma unroll
       for (int fld = 0; fld < 4; ++fld) {
-        const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + col_off;
-        gstore_cols<real, W>(qb, off, qn[fld], ok);
-        gstore_cols<real, W>(rnew, off, rr[fld], ok);
+        real qn[4], qh[4];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) sQ[(fld * Np + n) * CS + c0 + k] = qn[fld][k];
+        for (int k = 0; k < 4; ++k) {
+          real upd = real(AB::a1) * r[fld][k] + real(AB::a2) * r1[fld][k] + real(AB::a3) * r2[fld][k];
+          qn[k] = q0[fld][k] + h * upd;
+          real hb = real(AB::b1) * r[fld][k] + real(AB::b2) * r1[fld][k] + real(AB::b3) * r2[fld][k];
+          qh[k] = q0[fld][k] + h * hb;
+        }
+        const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + col_off;
+        gstore_cols<real, W>(qb, off, qn, ok);
+        gstore_cols<real, W>(rnew, off, r[fld], ok);
+        st4<real>(sQ + (fld * Np + n) * CS + c0, qn);
+        st4<real>(sH + (fld * Np + n) * CS + c0, qh);
       }
     }
   }
-  if (A.mode & kModeRhsOnly) return;
+  if (rhs_only) return;
   __syncthreads();
 
   // ---------------------------------------------------------------- phase 5: traces
@@ -647,13 +747,7 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
 // shared-memory bytes of dg_step_kernel<N, real, W>
 template <int N, typename real, int W>
 constexpr size_t step_smem_bytes() {
-  using O = Order<N>;
-  constexpr int CS = ColStride<real>::value;
-  constexpr int UX = (3 * O::Np * CS > 8 * O::Nfp * 33) ? 3 * O::Np * CS : 8 * O::Nfp * 33;
-  constexpr int EPB = 32 / W;
-  size_t reals = size_t(4 * O::Np * CS) + 2 * size_t(4 * O::Nfp * CS) + UX + EPB * 48;
-  size_t ints = 4 * EPB + 4 * EPB + EPB + EPB + 128 + 192;
-  return reals * sizeof(real) + ints * sizeof(int);
+  return Smem<N, real, W>::bytes;
 }
 
 }  // namespace ridg

@@ -140,8 +140,9 @@ def test_rtm_edge_cases():
     # no receivers: the receiver wavefield stays zero, so do the images
     tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, np.zeros((0, 3)), w.t_final)
     assert tr.shape[0] == 0 and np.all(ip == 0) and np.all(iq == 0)
-    # empty image window
-    tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, t_image_start=w.t_final)
+    # empty image window: t_i is rounded down to a global step, so start it at the last one
+    t_last = (s.trace_len(w.t_final) - 1) * s.info.dt_global
+    tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, t_image_start=t_last)
     assert np.all(ip == 0) and np.abs(tr).max() > 0
     with pytest.raises(ridg.RidgError) as e:
         s.rtm_shot((1e6, 0, 0), w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
