@@ -253,12 +253,13 @@ def run_ridg(args):
     img_p = torch.zeros((w.K, info.Np), dtype=torch.float64, device=dev)
     img_q = torch.zeros_like(img_p)
 
+    from paper_1506_00907_gb300.shots import reduce_images
+
     def shot(obs):
         s.rtm_shot_device(src_x, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start, observed=obs,
                           traces=traces, image_p=img_p, image_q=img_q)
         if dist is not None:
-            dist.all_reduce(img_p)
-            dist.all_reduce(img_q)
+            reduce_images([img_p, img_q])
 
     # warm-up: the first shot models the data that later shots migrate
     s.set_profiling(16)
@@ -359,6 +360,23 @@ def run_ridg(args):
     return 0
 
 
+def profile_shot(t_final):
+    """One short shot of the bench workload (same mesh, order, precision and launch configuration),
+    for ncu captures: the first fused launch covers every element forward, the first backward
+    launch every element with two wavefields."""
+    from paper_1506_00907_gb300 import ridg
+
+    w = _workload()
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max)
+    tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, t_final)
+    st = s.shot_stats()
+    print(json.dumps({"n_global": st.n_global, "fused_launches": st.fused_launches,
+                      "first_backward_fused_launch": st.fused_launches - st.n_global * (2 ** (s.info.n_levels - 1)),
+                      "kernel_launches": st.kernel_launches, "finite": bool(np.isfinite(ip).all())}))
+    return 0
+
+
 def _kernel_hash():
     import hashlib
 
@@ -375,7 +393,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ridg", choices=["ridg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-shot", type=float, default=0.0,
+                    help="run one shot of the bench workload with this record length (s) and exit (profiling case)")
     args = ap.parse_args()
+    if args.profile_shot > 0:
+        from paper_1506_00907_gb300.build import build
+
+        build()
+        return profile_shot(args.profile_shot)
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

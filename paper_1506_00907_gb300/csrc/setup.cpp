@@ -12,7 +12,7 @@
 #include <cmath>
 #include <numeric>
 
-#include "../../include/ridg.h"
+#include "ridg.h"
 
 namespace ridg {
 

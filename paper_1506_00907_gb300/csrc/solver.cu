@@ -11,7 +11,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "../../include/ridg.h"
+#include "ridg.h"
 #include "dispatch.hpp"
 #include "setup.hpp"
 #include "step_kernel_tc.cuh"

@@ -16,7 +16,6 @@
 #include "step_kernel.cuh"
 
 namespace ridg {
-
 template <int N>
 struct TcOrder {
   using O = Order<N>;
@@ -39,11 +38,18 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
 }
 
 __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], const uint32_t b[2]) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
       "{%0,%1,%2,%3};\n"
       : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// TF32 split by truncation: hi keeps the top 10 mantissa bits of x, lo = x - hi is exact in FP32
+// and is itself truncated to TF32 (the discarded part is below 2^-21 |x|).
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = __float_as_uint(x) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
 }
 
 // acc += A * B with A = (a_hi, a_lo), B = (b_hi, b_lo): small terms first
@@ -61,10 +67,8 @@ __device__ __forceinline__ void load_b(const float* X, int row0, int kvalid_rel,
                                        uint32_t bl[2]) {
   float x0 = (t < kvalid_rel) ? X[(row0 + t) * CS + col] : 0.f;
   float x1 = (t + 4 < kvalid_rel) ? X[(row0 + t + 4) * CS + col] : 0.f;
-  bh[0] = to_tf32(x0);
-  bh[1] = to_tf32(x1);
-  bl[0] = to_tf32(x0 - __uint_as_float(bh[0]));
-  bl[1] = to_tf32(x1 - __uint_as_float(bh[1]));
+  split_tf32(x0, bh[0], bl[0]);
+  split_tf32(x1, bh[1], bl[1]);
 }
 
 __device__ __forceinline__ void load_a(const uint32_t* frag, int lane, uint32_t ah[4], uint32_t al[4]) {
@@ -85,29 +89,29 @@ struct SmemTc {
   using O = Order<N>;
   static constexpr int Np = O::Np, Nfp = O::Nfp;
   static constexpr int CS = 36;  // column rows (16-byte aligned, few conflicts in fragment loads)
-  static constexpr int XS = 33;
   static constexpr int NG = 49;
   static constexpr int EPB = 32 / W;
   static constexpr int Q = 4 * Np * CS;
   static constexpr int ST = 4 * Nfp * CS;
-  static constexpr int UX = (3 * Np * CS > 8 * Nfp * XS) ? 3 * Np * CS : 8 * Nfp * XS;
+  static constexpr int UX = (3 * Np * CS > EPB * (2 * kGeo + kMat)) ? 3 * Np * CS : EPB * (2 * kGeo + kMat);
   static constexpr int G = EPB * NG;
-  static constexpr int INTS = 4 * EPB + 4 * EPB + EPB + EPB + 128 + 192;
+  static constexpr int INTS = 4 * EPB + 4 * EPB + EPB + EPB + 128 + 192 + 4 * EPB;
   static constexpr size_t bytes_with(bool ring) {
     return (size_t(Q) * (ring ? 3 : 1) + 2 * size_t(ST) + UX + G) * sizeof(float) + INTS * sizeof(int);
   }
   static constexpr bool ring_in_smem = bytes_with(true) <= 200 * 1024;
   static constexpr size_t bytes = bytes_with(ring_in_smem);
   static_assert(4 * Np * CS <= 2 * ST + UX, "half-step staging must fit in the penalty/U region");
+  static_assert(EPB * (2 * kGeo + kMat) <= UX, "raw geometry staging must fit in the U region");
 };
 
 template <int N, int W>
-__global__ void __launch_bounds__(TcOrder<N>::NT) dg_step_kernel_tc(const StepArgs<float> A) {
+__global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const StepArgs<float> A) {
   using O = Order<N>;
   using T = TcOrder<N>;
   using SM = SmemTc<N, W>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NT = T::NT, NFPP = O::NFPP;
-  constexpr int CS = SM::CS, XS = SM::XS, NG = SM::NG, EPB = SM::EPB;
+  constexpr int CS = SM::CS, NG = SM::NG, EPB = SM::EPB;
   constexpr bool RING = SM::ring_in_smem;
   constexpr int MT = T::MT, KSD = T::KSD, KSF = T::KSF;
 
@@ -117,8 +121,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT) dg_step_kernel_tc(const StepAr
   float* sR2 = sR1 + (RING ? SM::Q : 0);           // [4][Np][CS] (if RING)
   float* sS = sR2 + (RING ? SM::Q : 0);            // [4*Nfp][CS]
   float* sT = sS + SM::ST;                         // [4*Nfp][CS]
-  float* sU = sT + SM::ST;                         // [3][Np][CS] (aliases sX)
-  float* sX = sU;                                  // [4*Nfp][2][XS]
+  float* sU = sT + SM::ST;                         // [3][Np][CS]
   float* sG = sU + SM::UX;                         // [EPB][NG]
   int* sI = reinterpret_cast<int*>(sG + SM::G);
   int* sNbr = sI;
@@ -127,6 +130,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT) dg_step_kernel_tc(const StepAr
   int* sMeta = sBf + EPB;
   int* sFm = sMeta + EPB;
   int* sPerm = sFm + 128;
+  int2* sInj = reinterpret_cast<int2*>(sPerm + 192);  // [2][EPB] injection ranges per wavefield
   float* sH = sS;  // [4][Np][CS] half-step fields, after the products
 
   const int tid = threadIdx.x;
@@ -142,27 +146,29 @@ __global__ void __launch_bounds__(TcOrder<N>::NT) dg_step_kernel_tc(const StepAr
   const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
   const int rn = A.ring_new[lev], r1i = A.ring_old1[lev], r2i = A.ring_old2[lev];
 
+
   // column c -> (element, wavefield)
   auto col_e = [](int c) { return W == 1 ? c : (c & 15); };
   auto col_w = [](int c) { return W == 1 ? 0 : (c >> 4); };
 
   // ---------------------------------------------------------------- phase 1: async field loads
+  // q at t_start (group 0) and the two older right-hand sides (group 1), 16-byte copies
   {
     const int64_t fbase = (blk * 4) * Np * 32 + lane0;
-    constexpr int CPR = EPB / 4;             // 16-byte chunks per row and wavefield
-    constexpr int PER = 4 * Np * W * CPR;    // chunks per array
+    constexpr int CPR = EPB / 4;          // 16-byte chunks per row and wavefield
+    constexpr int PER = 4 * Np * 8;       // chunks per array (8 per 32-column row)
     const int narr = (RING && !rhs_only) ? 3 : 1;
-    for (int i = tid; i < narr * PER; i += NT) {
-      int arr = i / PER;
-      int rem = i - arr * PER;
-      int row = rem / (W * CPR);
-      int r2 = rem - row * (W * CPR);
-      int w = r2 / CPR, ch = r2 - w * CPR;
-      const float* base = arr == 0 ? A.wave[w].q : A.wave[w].ring + (arr == 1 ? r1i : r2i) * qsize;
-      float* dst = (arr == 0 ? sQ : (arr == 1 ? sR1 : sR2)) + row * CS + w * 16 + ch * 4;
-      cp_async_bytes16(dst, base + fbase + row * 32 + ch * 4);
+    for (int arr = 0; arr < narr; ++arr) {
+      const int ring = arr == 1 ? r1i : r2i;
+      float* dbase = arr == 0 ? sQ : (arr == 1 ? sR1 : sR2);
+      for (int i = tid; i < PER; i += NT) {
+        const int row = i >> 3, sub = i & 7;  // sub = w * CPR + ch
+        const int w = sub / CPR, ch = sub - w * CPR;
+        const float* base = arr == 0 ? A.wave[w].q : A.wave[w].ring + ring * qsize;
+        cp_async_bytes16(dbase + row * CS + sub * 4, base + fbase + row * 32 + ch * 4);
+      }
+      cp_async_commit();
     }
-    cp_async_commit();
   }
 
   // ---------------------------------------------------------------- phase 0: tables
@@ -174,146 +180,159 @@ __global__ void __launch_bounds__(TcOrder<N>::NT) dg_step_kernel_tc(const StepAr
     sNbr[i] = A.nbr[s * 4 + f];
     sInfo[i] = A.finfo[s * 4 + f];
   }
+  for (int i = tid; i < 2 * EPB; i += NT) {
+    const int w = i / EPB, e = i - w * EPB;
+    sInj[i] = (w < W && A.wave[w].amp_mode != 0) ? A.wave[w].inj_range[slot0 + e] : make_int2(0, 0);
+  }
+  // raw per-element geometry (FP64) and material, loaded cooperatively into the sU region
+  double* sGeoRaw = reinterpret_cast<double*>(sU);  // [EPB][kGeo]
+  float* sMatRaw = reinterpret_cast<float*>(sGeoRaw + EPB * kGeo);  // [EPB][kMat]
+  for (int i = tid; i < EPB * kGeo; i += NT) sGeoRaw[i] = A.geo[slot0 * kGeo + i];
+  for (int i = tid; i < EPB * kMat; i += NT) sMatRaw[i] = A.mat[slot0 * kMat + i];
   for (int e = tid; e < EPB; e += NT) {
-    int64_t s = slot0 + e;
-    sBf[e] = A.bface[s];
-    sMeta[e] = A.meta[s];
-    const double* g = A.geo + s * kGeo;
-    const float* m = A.mat + s * kMat;
+    sBf[e] = A.bface[slot0 + e];
+    sMeta[e] = A.meta[slot0 + e];
+  }
+  __syncthreads();
+  for (int i = tid; i < EPB * 48; i += NT) {
+    const int e = i / 48, k = i - e * 48;
+    const double* g = sGeoRaw + e * kGeo;
+    const float* m = sMatRaw + e * kMat;
     float* G = sG + e * NG;
-    float rc2 = m[0], irho = m[1];
-    for (int ij = 0; ij < 9; ++ij) {
-      float rxij = float(g[ij]);
-      G[ij] = -rc2 * rxij;
-      G[9 + ij] = -irho * rxij;
-    }
-    for (int k = 0; k < 12; ++k) G[18 + k] = float(g[9 + k]);
-    for (int f = 0; f < 4; ++f) {
-      float fs = float(g[21 + f]);
-      float taup = A.tau_sign * m[3 + f], tauv = A.tau_sign * m[7 + f];
-      G[30 + 4 * f + 0] = -0.5f * fs * rc2;
-      G[30 + 4 * f + 1] = 0.5f * fs * rc2 * taup;
-      G[30 + 4 * f + 2] = 0.5f * fs * irho;
-      G[30 + 4 * f + 3] = -0.5f * fs * irho * tauv;
-    }
-    G[46] = m[2];
-  }
-  __syncthreads();
-
-  // ---------------------------------------------------------------- phase 2a: exterior traces
-  {
-    constexpr int NH = NT / 16;
-    const int hw = tid >> 4, j = tid & 15;
-    for (int base = hw; base < 32 * 4; base += 4 * NH) {
-      float xp[4][2], xv[4][2];
-      bool have[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        have[u] = false;
-        int item = base + u * NH;
-        if (item >= 128) continue;
-        int c = item >> 2, f = item & 3;
-        int e = col_e(c), w = col_w(c);
-        if (!(sMeta[e] & kMetaValid)) continue;
-        int info = sInfo[e * 4 + f];
-        int bc = finfo_bc(uint8_t(info));
-        if (bc == 0) {
-          int64_t s2 = sNbr[e * 4 + f];
-          int f2 = finfo_face(uint8_t(info));
-          const float* tb = A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + s2) * (8 * NFPP) + f2 * 2 * NFPP;
-          const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
-#pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            int jj = j + 16 * t;
-            if (jj < Nfp) {
-              int j2 = pm[jj];
-              xp[u][t] = tb[j2];
-              xv[u][t] = -tb[NFPP + j2];
-            }
-          }
-          have[u] = true;
-        } else if (w == 0 && (A.mode & kModeReplay)) {
-          int b = sBf[e];
-          for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
-          const float* rec = A.arena_read + (A.arena_offset + b) * (2 * NFPP);
-#pragma unroll
-          for (int t = 0; t < 2; ++t) {
-            int jj = j + 16 * t;
-            if (jj < Nfp) {
-              xp[u][t] = rec[jj];
-              xv[u][t] = rec[NFPP + jj];
-            }
-          }
-          have[u] = true;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (!have[u]) continue;
-        int item = base + u * NH;
-        int c = item >> 2, f = item & 3;
-#pragma unroll
-        for (int t = 0; t < 2; ++t) {
-          int jj = j + 16 * t;
-          if (jj < Nfp) {
-            sX[((f * Nfp + jj) * 2 + 0) * XS + c] = xp[u][t];
-            sX[((f * Nfp + jj) * 2 + 1) * XS + c] = xv[u][t];
-          }
-        }
-      }
-    }
-  }
-  cp_async_wait_all();
-  __syncthreads();
-
-  // ---------------------------------------------------------------- phase 2b: penalties
-  for (int i = tid; i < 4 * Nfp * 32; i += NT) {
-    int c = i & 31, fj = i >> 5;
-    int f = fj / Nfp, jj = fj - f * Nfp;
-    int e = col_e(c), w = col_w(c);
-    const float* G = sG + e * NG;
-    int n = sFm[f * 32 + jj];
-    float p = sQ[(0 * Np + n) * CS + c];
-    float vn = G[18 + 3 * f] * sQ[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sQ[(2 * Np + n) * CS + c] +
-               G[20 + 3 * f] * sQ[(3 * Np + n) * CS + c];
-    int info = sInfo[e * 4 + f];
-    int bc = finfo_bc(uint8_t(info));
-    const bool valid = (sMeta[e] & kMetaValid) != 0;
-    if (bc != 0 && valid && w == 0 && (A.mode & kModeRecord)) {
-      int b = sBf[e];
-      for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
-      float* rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
-      rec[jj] = p;
-      rec[NFPP + jj] = vn;
-    }
-    float jp, jv;
-    bool replay = (A.mode & kModeReplay) && w == 0 && bc != 0;
-    if (bc == 0 || replay) {
-      jp = sX[((f * Nfp + jj) * 2 + 0) * XS + c] - p;
-      jv = sX[((f * Nfp + jj) * 2 + 1) * XS + c] - vn;
-    } else if (bc == 1) {
-      jp = -2.f * p;
-      jv = 0.f;
-    } else if (bc == 2) {
-      jp = -p;
-      jv = -vn;
+    const float rc2 = m[0], irho = m[1];
+    float v;
+    if (k < 9) {
+      v = -rc2 * float(g[k]);  // -rho c^2 rx_ij (volume p equation)
+    } else if (k < 18) {
+      v = -irho * float(g[k - 9]);  // -rx_ij / rho (volume v equation)
+    } else if (k < 30) {
+      v = float(g[9 + (k - 18)]);  // outward normals
+    } else if (k < 46) {
+      // penalty coefficients per face: t = A_f [nv] + B_f [p], s = C_f [p] + D_f [nv]
+      const int f = (k - 30) >> 2, r = (k - 30) & 3;
+      const float fs = float(g[21 + f]);
+      const float taup = A.tau_sign * m[3 + f], tauv = A.tau_sign * m[7 + f];
+      v = r == 0 ? -0.5f * fs * rc2 : (r == 1 ? 0.5f * fs * rc2 * taup : (r == 2 ? 0.5f * fs * irho : -0.5f * fs * irho * tauv));
     } else {
-      jp = 0.f;
-      jv = -2.f * vn;
+      v = k == 46 ? m[2] : 0.f;  // rho c
     }
-    const float* pc = G + 30 + 4 * f;
-    float t = pc[0] * jv + pc[1] * jp;
-    float sv = pc[2] * jp + pc[3] * jv;
-    if (!valid) {
-      t = 0.f;
-      sv = 0.f;
-    }
-    sT[fj * CS + c] = t;
-    sS[fj * CS + c] = sv;
+    G[k] = v;
+  }
+  // fields at t_start have landed (the history may still be in flight)
+  if (RING && !rhs_only) {
+    asm volatile("cp.async.wait_group 2;\n" ::: "memory");
+  } else {
+    cp_async_wait_all();
   }
   __syncthreads();
 
-  // ---------------------------------------------------------------- phase 2c: U_j = G_p v
+  // ---------------------------------------------------------------- phase 2: face penalties
+  // half-warp per (column, face), lanes over face nodes.  Interior faces read the neighbour's
+  // traces at t_start (a coalesced face block, permuted by the face correspondence); boundary
+  // faces use the ghost state of their condition, or, in the backward source run, the recorded
+  // forward traces; forward runs record the traces of boundary faces.  Loads of four items are
+  // issued before their use.
+  {
+    constexpr int NH = NT / 16;               // half-warps
+    constexpr int NU = (128 + NH - 1) / NH;   // items per half-warp
+    constexpr int NJ = (Nfp + 15) / 16;       // face nodes per lane
+    const int hw = tid >> 4, j = tid & 15;
+    float xp[NU][NJ], xv[NU][NJ];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+      const int item = hw + u * NH;
+      if (item >= 128) continue;
+      const int c = item >> 2, f = item & 3;
+      const int e = col_e(c), w = col_w(c);
+      const int info = sInfo[e * 4 + f];
+      const int bc = finfo_bc(uint8_t(info));
+      if (!(sMeta[e] & kMetaValid)) continue;
+      if (bc == 0) {
+        const int64_t s2 = sNbr[e * 4 + f];
+        const float* tb =
+            A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + s2) * (8 * NFPP) + finfo_face(uint8_t(info)) * 2 * NFPP;
+        const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
+#pragma unroll
+        for (int t = 0; t < NJ; ++t) {
+          const int jj = j + 16 * t;
+          if (jj < Nfp) {
+            const int j2 = pm[jj];
+            xp[u][t] = tb[j2];
+            xv[u][t] = -tb[NFPP + j2];
+          }
+        }
+      } else if (w == 0 && (A.mode & kModeReplay)) {
+        int b = sBf[e];
+        for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
+        const float* rec = A.arena_read + (A.arena_offset + b) * (2 * NFPP);
+#pragma unroll
+        for (int t = 0; t < NJ; ++t) {
+          const int jj = j + 16 * t;
+          if (jj < Nfp) {
+            xp[u][t] = rec[jj];
+            xv[u][t] = rec[NFPP + jj];
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+      const int item = hw + u * NH;
+      if (item >= 128) continue;
+      const int c = item >> 2, f = item & 3;
+      const int e = col_e(c), w = col_w(c);
+      const bool valid = (sMeta[e] & kMetaValid) != 0;
+      const int bc = finfo_bc(uint8_t(sInfo[e * 4 + f]));
+      const float* G = sG + e * NG;
+      const float n0 = G[18 + 3 * f], n1 = G[19 + 3 * f], n2 = G[20 + 3 * f];
+      const float* pc = G + 30 + 4 * f;
+      float* rec = nullptr;
+      if (bc != 0 && valid && w == 0 && (A.mode & kModeRecord)) {
+        int b = sBf[e];
+        for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
+        rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
+      }
+      const bool ext = bc == 0 || (w == 0 && (A.mode & kModeReplay));
+#pragma unroll
+      for (int t = 0; t < NJ; ++t) {
+        const int jj = j + 16 * t;
+        if (jj >= Nfp) continue;
+        const int n = sFm[f * 32 + jj];
+        const float p = sQ[(0 * Np + n) * CS + c];
+        const float vn = n0 * sQ[(1 * Np + n) * CS + c] + n1 * sQ[(2 * Np + n) * CS + c] + n2 * sQ[(3 * Np + n) * CS + c];
+        if (rec) {
+          rec[jj] = p;
+          rec[NFPP + jj] = vn;
+        }
+        float jp, jv;
+        if (ext) {
+          jp = xp[u][t] - p;
+          jv = xv[u][t] - vn;
+        } else if (bc == 1) {  // free surface: p+ = -p-, n.v+ = n.v-
+          jp = -2.f * p;
+          jv = 0.f;
+        } else if (bc == 2) {  // transparent: p+ = 0, v+ = 0
+          jp = -p;
+          jv = -vn;
+        } else {  // rigid: p+ = p-, n.v+ = -n.v-
+          jp = 0.f;
+          jv = -2.f * vn;
+        }
+        float tt = pc[0] * jv + pc[1] * jp;
+        float sv = pc[2] * jp + pc[3] * jv;
+        if (!valid) {
+          tt = 0.f;
+          sv = 0.f;
+        }
+        const int fj = f * Nfp + jj;
+        sT[fj * CS + c] = tt;
+        sS[fj * CS + c] = sv;
+      }
+    }
+  }
+  __syncthreads();
+
+// ---------------------------------------------------------------- phase 2c: U_j = G_p v
   for (int i = tid; i < Np * 32; i += NT) {
     int c = i & 31, m = i >> 5;
     const float* G = sG + col_e(c) * NG;
@@ -323,7 +342,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT) dg_step_kernel_tc(const StepAr
   }
   __syncthreads();
 
-  // ---------------------------------------------------------------- phase 3: tensor-core products
+// ---------------------------------------------------------------- phase 3: tensor-core products
   const int lane = tid & 31, wid = tid >> 5;
   const int mt = wid >> 1, pair = wid & 1;
   const int g = lane >> 2, t4 = lane & 3;
@@ -345,212 +364,225 @@ __global__ void __launch_bounds__(TcOrder<N>::NT) dg_step_kernel_tc(const StepAr
 #pragma unroll
     for (int jd = 0; jd < 3; ++jd) {
       const float* Ub = sU + jd * Np * CS;
-#pragma unroll
+      const uint32_t* fr = fragD + (jd * MT + mt) * KSD * 256;
+      uint32_t ah[4], al[4];
+      load_a(fr, lane, ah, al);
+#pragma unroll 1
       for (int kb = 0; kb < KSD; ++kb) {
-        uint32_t ah[4], al[4];
-        load_a(fragD + ((jd * MT + mt) * KSD + kb) * 256, lane, ah, al);
+        uint32_t nh[4], nl[4];
+        if (kb + 1 < KSD) load_a(fr + (kb + 1) * 256, lane, nh, nl);
         const int kv = Np - kb * 8;
+        uint32_t ph[2][2], pl[2][2], uh[2][2], ul[2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          uint32_t bh[2], bl[2];
-          load_b<CS>(sQ, kb * 8, kv, t4, colb[b], bh, bl);
-          mma3(dp[jd][b], ah, al, bh, bl);
-          load_b<CS>(Ub, kb * 8, kv, t4, colb[b], bh, bl);
-          mma3(rp[b], ah, al, bh, bl);
+          load_b<CS>(sQ, kb * 8, kv, t4, colb[b], ph[b], pl[b]);
+          load_b<CS>(Ub, kb * 8, kv, t4, colb[b], uh[b], ul[b]);
+        }
+        // the three split terms of four independent accumulators, interleaved
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          mma_tf32(dp[jd][b], al, ph[b]);
+          mma_tf32(rp[b], al, uh[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          mma_tf32(dp[jd][b], ah, pl[b]);
+          mma_tf32(rp[b], ah, ul[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          mma_tf32(dp[jd][b], ah, ph[b]);
+          mma_tf32(rp[b], ah, uh[b]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ah[q] = nh[q];
+          al[q] = nl[q];
         }
       }
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-#pragma unroll
+      const uint32_t* fr = fragL + (f * MT + mt) * KSF * 256;
+      uint32_t ah[4], al[4];
+      load_a(fr, lane, ah, al);
+#pragma unroll 1
       for (int kb = 0; kb < KSF; ++kb) {
-        uint32_t ah[4], al[4];
-        load_a(fragL + ((f * MT + mt) * KSF + kb) * 256, lane, ah, al);
+        uint32_t nh[4], nl[4];
+        if (kb + 1 < KSF) load_a(fr + (kb + 1) * 256, lane, nh, nl);
         const int kv = Nfp - kb * 8;
+        uint32_t th[2][2], tl[2][2], sh[2][2], sl[2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          uint32_t bh[2], bl[2];
-          load_b<CS>(sT, f * Nfp + kb * 8, kv, t4, colb[b], bh, bl);
-          mma3(rp[b], ah, al, bh, bl);
-          load_b<CS>(sS, f * Nfp + kb * 8, kv, t4, colb[b], bh, bl);
-          mma3(ls[f][b], ah, al, bh, bl);
+          load_b<CS>(sT, f * Nfp + kb * 8, kv, t4, colb[b], th[b], tl[b]);
+          load_b<CS>(sS, f * Nfp + kb * 8, kv, t4, colb[b], sh[b], sl[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          mma_tf32(rp[b], al, th[b]);
+          mma_tf32(ls[f][b], al, sh[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          mma_tf32(rp[b], ah, tl[b]);
+          mma_tf32(ls[f][b], ah, sl[b]);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          mma_tf32(rp[b], ah, th[b]);
+          mma_tf32(ls[f][b], ah, sh[b]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          ah[q] = nh[q];
+          al[q] = nl[q];
         }
       }
     }
   }
-  __syncthreads();  // every warp is done reading sQ/sS/sT/sU
+  cp_async_wait_all();  // the history slots
+  __syncthreads();
 
   // ---------------------------------------------------------------- phase 4: update
-  {
-    // accumulator entry q of block b: node mt*16 + g + 8*(q>>1), column (pair + 2b)*8 + 2 t4 + (q&1)
-    float* rout = A.rhs_out;
+  // accumulator entry q = 2 hn + k of block b: node mt*16 + g + 8 hn, column (pair + 2b)*8 + 2 t4 + k.
+  // One column pair (k) at a time: with two wavefields its two columns are the source and receiver
+  // values of the same element, which the image needs together.
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    int cb[2], eb[2], wb[2];
+    bool okb[2];
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      cb[b] = (pair + 2 * b) * 8 + 2 * t4 + k;
+      eb[b] = col_e(cb[b]);
+      wb[b] = col_w(cb[b]);
+      okb[b] = (sMeta[eb[b]] & kMetaValid) != 0;
+    }
 #pragma unroll
     for (int hn = 0; hn < 2; ++hn) {
       const int n = mt * 16 + g + 8 * hn;
       if (n >= Np) continue;
-      // r[b][k][fld] for the two columns k of block b
-      float r[2][2][4];
-      int cols[2][2], es[2][2];
-      bool ok[2][2];
+      const int q = 2 * hn + k;
+      float r[2][4];
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < 2; ++b) {
+        const float* G = sG + eb[b] * NG;
+        r[b][0] = rp[b][q];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int q = 2 * hn + k;
-          const int c = (pair + 2 * b) * 8 + 2 * t4 + k;
-          cols[b][k] = c;
-          const int e = col_e(c);
-          es[b][k] = e;
-          ok[b][k] = (sMeta[e] & kMetaValid) != 0;
-          const float* G = sG + e * NG;
-          r[b][k][0] = rp[b][q];
+        for (int d = 0; d < 3; ++d) {
+          float v = G[9 + 3 * d + 0] * dp[0][b][q] + G[9 + 3 * d + 1] * dp[1][b][q] + G[9 + 3 * d + 2] * dp[2][b][q];
 #pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            float v = G[9 + 3 * d + 0] * dp[0][b][q] + G[9 + 3 * d + 1] * dp[1][b][q] + G[9 + 3 * d + 2] * dp[2][b][q];
-#pragma unroll
-            for (int f = 0; f < 4; ++f) v -= G[18 + 3 * f + d] * ls[f][b][q];
-            r[b][k][1 + d] = v;
-          }
-          // point injections
-          const int w = col_w(c);
-          const WaveArgs<float>& wa = A.wave[w];
-          if (wa.amp_mode != 0 && ok[b][k]) {
-            int2 ir = wa.inj_range[slot0 + e];
-            for (int qq = ir.x; qq < ir.x + ir.y; ++qq) {
-              float amp;
-              if (wa.amp_mode == 1) {
-                amp = wa.amp;
-              } else {
-                double acc = 0.0;
-                int row = wa.inj_row[qq];
-                for (int tt = 0; tt < 4; ++tt) {
-                  int nt = A.interp_n0 + tt;
-                  if (nt >= 0 && nt < wa.n_time) acc += A.interp_w[tt] * wa.data[int64_t(row) * wa.n_time + nt];
-                }
-                amp = float(acc);
+          for (int f = 0; f < 4; ++f) v -= G[18 + 3 * f + d] * ls[f][b][q];
+          r[b][1 + d] = v;
+        }
+        // point injections (source wavelet or receiver traces)
+        const WaveArgs<float>& wa = A.wave[wb[b]];
+        const int2 ir = sInj[wb[b] * EPB + eb[b]];
+        if (ir.y > 0 && okb[b]) {
+          for (int qq = ir.x; qq < ir.x + ir.y; ++qq) {
+            float amp;
+            if (wa.amp_mode == 1) {
+              amp = wa.amp;
+            } else {
+              double acc = 0.0;
+              const int row = wa.inj_row[qq];
+              for (int tt = 0; tt < 4; ++tt) {
+                const int nt = A.interp_n0 + tt;
+                if (nt >= 0 && nt < wa.n_time) acc += A.interp_w[tt] * wa.data[int64_t(row) * wa.n_time + nt];
               }
-              r[b][k][0] += amp * wa.inj_w[int64_t(qq) * Np + n];
+              amp = float(acc);
             }
+            r[b][0] += amp * wa.inj_w[int64_t(qq) * Np + n];
           }
         }
+      }
       if (rhs_only) {
 #pragma unroll
         for (int b = 0; b < 2; ++b)
+          if (okb[b])
 #pragma unroll
-          for (int k = 0; k < 2; ++k)
-            if (ok[b][k])
-#pragma unroll
-              for (int fld = 0; fld < 4; ++fld)
-                rout[((blk * 4 + fld) * Np + n) * 32 + lane0 + es[b][k]] = r[b][k][fld];
+            for (int fld = 0; fld < 4; ++fld) A.rhs_out[((blk * 4 + fld) * Np + n) * 32 + lane0 + eb[b]] = r[b][fld];
         continue;
       }
-      float q0[2][2][4], r1[2][2][4], r2[2][2][4];
+      float q0[2][4], r1[2][4], r2[2][4];
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int c = cols[b][k];
-#pragma unroll
-          for (int fld = 0; fld < 4; ++fld) {
-            q0[b][k][fld] = sQ[(fld * Np + n) * CS + c];
-            if constexpr (RING) {
-              r1[b][k][fld] = sR1[(fld * Np + n) * CS + c];
-              r2[b][k][fld] = sR2[(fld * Np + n) * CS + c];
-            } else {
-              const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + lane0 + es[b][k];
-              const int w = col_w(c);
-              r1[b][k][fld] = A.wave[w].ring[r1i * qsize + off];
-              r2[b][k][fld] = A.wave[w].ring[r2i * qsize + off];
-            }
+        for (int fld = 0; fld < 4; ++fld) {
+          const int sidx = (fld * Np + n) * CS + cb[b];
+          q0[b][fld] = sQ[sidx];
+          if constexpr (RING) {
+            r1[b][fld] = sR1[sidx];
+            r2[b][fld] = sR2[sidx];
+          } else {
+            const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + lane0 + eb[b];
+            r1[b][fld] = A.wave[wb[b]].ring[r1i * qsize + off];
+            r2[b][fld] = A.wave[wb[b]].ring[r2i * qsize + off];
           }
         }
-      // images (two wavefields): block 0 holds the source wavefield, block 1 the receivers'
-      if (W == 2 && (A.mode & kModeImage)) {
+      // images from the fields and histories at t_start, before the update
+      if (W == 2 && (A.mode & kModeImage) && okb[0]) {
+        const float Z = sG[eb[0] * NG + 46];
+        const float* eu = A.e_up;
+        const float xS = q0[0][0], xR = q0[1][0];
+        const float vS = eu[0] * q0[0][1] + eu[1] * q0[0][2] + eu[2] * q0[0][3];
+        const float vR = eu[0] * q0[1][1] + eu[1] * q0[1][2] + eu[2] * q0[1][3];
+        const float rS[3] = {r[0][0], r1[0][0], r2[0][0]};
+        const float rR[3] = {r[1][0], r1[1][0], r2[1][0]};
+        const float sS3[3] = {rS[0] - Z * (eu[0] * r[0][1] + eu[1] * r[0][2] + eu[2] * r[0][3]),
+                              rS[1] - Z * (eu[0] * r1[0][1] + eu[1] * r1[0][2] + eu[2] * r1[0][3]),
+                              rS[2] - Z * (eu[0] * r2[0][1] + eu[1] * r2[0][2] + eu[2] * r2[0][3])};
+        const float sR3[3] = {rR[0] + Z * (eu[0] * r[1][1] + eu[1] * r[1][2] + eu[2] * r[1][3]),
+                              rR[1] + Z * (eu[0] * r1[1][1] + eu[1] * r1[1][2] + eu[2] * r1[1][3]),
+                              rR[2] + Z * (eu[0] * r2[1][1] + eu[1] * r2[1][2] + eu[2] * r2[1][3])};
+        const float cc[3] = {float(AB::c1), float(AB::c2), float(AB::c3)};
+        const float C[3][3] = {{float(4703.0 / 5040.0), float(-457.0 / 840.0), float(52.0 / 315.0)},
+                               {float(-457.0 / 840.0), float(103.0 / 315.0), float(-251.0 / 2520.0)},
+                               {float(52.0 / 315.0), float(-251.0 / 2520.0), float(17.0 / 560.0)}};
+        const float qS = xS - Z * vS, qR = xR + Z * vR;
+        float t2p = 0.f, t3p = 0.f, t2q = 0.f, t3q = 0.f;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          if (!ok[0][k]) continue;
-          const float* G = sG + es[0][k] * NG;
-          const float Z = G[46];
-          const float* eu = A.e_up;
-          const float* qS_ = q0[0][k];
-          const float* qR_ = q0[1][k];
-          float xS = qS_[0], xR = qR_[0];
-          float vS = eu[0] * qS_[1] + eu[1] * qS_[2] + eu[2] * qS_[3];
-          float vR = eu[0] * qR_[1] + eu[1] * qR_[2] + eu[2] * qR_[3];
-          const float* hS[3] = {r[0][k], r1[0][k], r2[0][k]};
-          const float* hR[3] = {r[1][k], r1[1][k], r2[1][k]};
-          float rS[3], rR[3], rvS[3], rvR[3];
+        for (int s3 = 0; s3 < 3; ++s3) {
+          t2p += cc[s3] * (xS * rR[s3] + rS[s3] * xR);
+          t2q += cc[s3] * (qS * sR3[s3] + sS3[s3] * qR);
 #pragma unroll
-          for (int s = 0; s < 3; ++s) {
-            rS[s] = hS[s][0];
-            rR[s] = hR[s][0];
-            rvS[s] = eu[0] * hS[s][1] + eu[1] * hS[s][2] + eu[2] * hS[s][3];
-            rvR[s] = eu[0] * hR[s][1] + eu[1] * hR[s][2] + eu[2] * hR[s][3];
+          for (int u = 0; u < 3; ++u) {
+            t3p += C[s3][u] * rS[s3] * rR[u];
+            t3q += C[s3][u] * sS3[s3] * sR3[u];
           }
-          const float cc[3] = {float(AB::c1), float(AB::c2), float(AB::c3)};
-          const float C[3][3] = {{float(4703.0 / 5040.0), float(-457.0 / 840.0), float(52.0 / 315.0)},
-                                 {float(-457.0 / 840.0), float(103.0 / 315.0), float(-251.0 / 2520.0)},
-                                 {float(52.0 / 315.0), float(-251.0 / 2520.0), float(17.0 / 560.0)}};
-          float incP, incQ;
-          {
-            float t2 = 0.f, t3 = 0.f;
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-              t2 += cc[s] * (xS * rR[s] + rS[s] * xR);
-#pragma unroll
-              for (int u = 0; u < 3; ++u) t3 += C[s][u] * rS[s] * rR[u];
-            }
-            incP = h * (xS * xR + h * (t2 + h * t3));
-          }
-          {
-            float qS = xS - Z * vS, qR = xR + Z * vR;
-            float sS3[3], sR3[3];
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-              sS3[s] = rS[s] - Z * rvS[s];
-              sR3[s] = rR[s] + Z * rvR[s];
-            }
-            float t2 = 0.f, t3 = 0.f;
-#pragma unroll
-            for (int s = 0; s < 3; ++s) {
-              t2 += cc[s] * (qS * sR3[s] + sS3[s] * qR);
-#pragma unroll
-              for (int u = 0; u < 3; ++u) t3 += C[s][u] * sS3[s] * sR3[u];
-            }
-            incQ = h * (qS * qR + h * (t2 + h * t3));
-          }
-          const int64_t io = (blk * Np + n) * 32 + lane0 + es[0][k];
-          A.image_p[io] -= double(incP);
-          A.image_q[io] -= double(incQ);
         }
+        const float incP = h * (xS * xR + h * (t2p + h * t3p));
+        const float incQ = h * (qS * qR + h * (t2q + h * t3q));
+        const int64_t io = (blk * Np + n) * 32 + lane0 + eb[0];
+        A.image_p[io] -= double(incP);
+        A.image_q[io] -= double(incQ);
       }
 #pragma unroll
-      for (int b = 0; b < 2; ++b)
+      for (int b = 0; b < 2; ++b) {
+        const int64_t gofs = ((blk * 4) * Np + n) * 32 + lane0 + eb[b];
+        float* qg = A.wave[wb[b]].q + gofs;
+        float* rg = A.wave[wb[b]].ring + rn * qsize + gofs;
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-          const int c = cols[b][k];
-          const int w = col_w(c);
-#pragma unroll
-          for (int fld = 0; fld < 4; ++fld) {
-            const float rr = r[b][k][fld];
-            const float upd = float(AB::a1) * rr + float(AB::a2) * r1[b][k][fld] + float(AB::a3) * r2[b][k][fld];
-            const float hb = float(AB::b1) * rr + float(AB::b2) * r1[b][k][fld] + float(AB::b3) * r2[b][k][fld];
-            const float qn = q0[b][k][fld] + h * upd;
-            sQ[(fld * Np + n) * CS + c] = qn;
-            sH[(fld * Np + n) * CS + c] = q0[b][k][fld] + h * hb;
-            if (ok[b][k]) {
-              const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + lane0 + es[b][k];
-              A.wave[w].q[off] = qn;
-              A.wave[w].ring[rn * qsize + off] = rr;
-            }
+        for (int fld = 0; fld < 4; ++fld) {
+          const float rr = r[b][fld];
+          const float upd = float(AB::a1) * rr + float(AB::a2) * r1[b][fld] + float(AB::a3) * r2[b][fld];
+          const float hb = float(AB::b1) * rr + float(AB::b2) * r1[b][fld] + float(AB::b3) * r2[b][fld];
+          const float qn = q0[b][fld] + h * upd;
+          const int sidx = (fld * Np + n) * CS + cb[b];
+          sQ[sidx] = qn;
+          sH[sidx] = q0[b][fld] + h * hb;
+          if (okb[b]) {
+            qg[fld * Np * 32] = qn;
+            rg[fld * Np * 32] = rr;
           }
         }
+      }
     }
   }
   if (rhs_only) return;
   __syncthreads();
 
-  // ---------------------------------------------------------------- phase 5: traces
+// ---------------------------------------------------------------- phase 5: traces
   {
     const int hw = tid >> 4, j = tid & 15;
     const int ws = A.trace_write[lev], hs = A.trace_half[lev];
