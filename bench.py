@@ -389,7 +389,7 @@ def _kernel_hash():
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ridg", choices=["ridg", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
