@@ -314,10 +314,10 @@ def run_ridg(args):
     ach_fw = bytes_fw / (fw_ms * 1e-3) / 1e9
     tr = _traffic()
     traffic = None
-    if tr and tr.get("kernel") == "dg_step_kernel<4,float,2>" and tr.get("source_hash") == _kernel_hash():
+    if tr and tr.get("kernel") == "dg_step_kernel_tc<4,2>" and tr.get("source_hash") == _kernel_hash():
         traffic = tr.get("bytes_per_launch_full_mesh")
     roofline = {"bound": "hbm", "achieved": ach_bw, "peak": peak, "unit": "GB/s", "frac": ach_bw / peak,
-                "traffic": traffic, "kernel": "dg_step_kernel<4,float,2> (backward S+R+images, all levels)",
+                "traffic": traffic, "kernel": "dg_step_kernel_tc<4,2> (backward S+R+images, all levels)",
                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": bytes_bw, "avg_launch_ms": bw_ms,
                 "forward_kernel": {"achieved": ach_fw, "frac": ach_fw / peak, "avg_launch_ms": fw_ms,
                                    "algorithmic_bytes_per_launch": bytes_fw}}
@@ -381,7 +381,7 @@ def _kernel_hash():
     import hashlib
 
     h = hashlib.sha1()
-    for f in ("step_kernel.cuh",):
+    for f in ("step_kernel.cuh", "step_kernel_tc.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1506_00907_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:12]
 
