@@ -141,6 +141,20 @@ int ridg_get_state(ridg_solver* s, double* q_out);
 /* Discrete energy sum_k J_k/2 (p^T M p/(rho c^2) + rho v^T M v), accumulated in FP64 on the device. */
 int ridg_energy(ridg_solver* s, double* energy);
 
+/* The same energy of the solver's current fields, for callers that cannot allocate device memory
+ * when they need it (for instance while a stream is being captured into a CUDA graph, or inside a
+ * loop that must not touch the allocator).  The paper has no counterpart: this is an interface
+ * variant of ridg_energy.
+ *   energy_dev  device double[1] owned by the caller; written asynchronously on the solver's stream.
+ * Allocates no device memory: its scratch (per-block partial sums) is a fixed 32 KiB device array
+ * that every GPU loading the library keeps until exit.  Solvers with more than 1,048,576 element
+ * slots (elements padded to multiples of 32 per level) are rejected with RIDG_E_INVALID_ARG.  The
+ * first call on a device looks up the scratch array's device address with that device current;
+ * make that first call before any stream capture.  Calls share the scratch array: calls that overlap
+ * on the GPU (other streams or unordered solvers on the same device) race.
+ * Errors: RIDG_E_INVALID_ARG, RIDG_E_CUDA. */
+int ridg_energy_noalloc(ridg_solver* s, double* energy_dev);
+
 /* ------------------------------------------------------------------ one RTM shot (Sec. 2, Sec. 4.3)
  * Source: Ricker pulse f(t) = amplitude (1 - 2 pi^2 f0^2 tau^2) exp(-pi^2 f0^2 tau^2), tau = t - t_peak,
  * at source_xyz (Eq. waveSyst1, L2-projected Dirac of Eq. sourceTerm).

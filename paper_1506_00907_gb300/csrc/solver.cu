@@ -13,6 +13,7 @@
 
 #include "ridg.h"
 #include "dispatch.hpp"
+#include "energy_noalloc.hpp"
 #include "setup.hpp"
 #include "step_kernel_tc.cuh"
 
@@ -103,6 +104,7 @@ struct ridg_solver {
   virtual void step(int64_t n) = 0;
   virtual void get_state(double* q) = 0;
   virtual double energy() = 0;
+  virtual void energy_noalloc(double* out_dev) = 0;
   virtual int64_t trace_len(double t_final) const = 0;
   virtual void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i,
                     const double* obs_dev, double* traces_dev, double* imgp_dev, double* imgq_dev,
@@ -270,6 +272,16 @@ class Engine final : public ridg_solver {
     from_slots(h, q);
   }
   double energy() override { return energy_of(dptr<real>(w_[0].q)); }
+  void energy_noalloc(double* out_dev) override {
+    if (n_slots_ > ridg::energy_noalloc_max_slots())
+      throw Error{RIDG_E_INVALID_ARG, "ridg_energy_noalloc: " + std::to_string(n_slots_) +
+                                          " element slots exceed the fixed scratch limit of " +
+                                          std::to_string(ridg::energy_noalloc_max_slots())};
+    cudaError_t e = ridg::energy_noalloc(N_, std::is_same<real, double>::value, w_[0].q.p, n_slots_,
+                                         dptr<const double>(J_d_), mat_d_.p, dptr<const int>(meta_d_),
+                                         dptr<const double>(M_d_), out_dev, st_);
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("ridg_energy_noalloc: ") + cudaGetErrorString(e)};
+  }
   int64_t trace_len(double t_final) const override {
     double dtg = lv_.dt_local * double(NL_);
     return int64_t(std::ceil(t_final / dtg - 1e-9)) + 1;
@@ -1017,6 +1029,14 @@ int ridg_energy(ridg_solver* s, double* e) {
     *e = s->energy();
   });
 }
+int ridg_energy_noalloc(ridg_solver* s, double* energy_dev) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!energy_dev) throw Error{RIDG_E_INVALID_ARG, "energy_dev is null"};
+    s->energy_noalloc(energy_dev);
+  });
+}
+
 int64_t ridg_trace_len(const ridg_solver* s, double t_final) {
   if (!s || !(t_final > 0.0)) return 0;
   return s->trace_len(t_final);

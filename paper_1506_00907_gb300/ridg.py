@@ -26,7 +26,7 @@ EXPORTED = [
     "ridg_reference_operators", "ridg_solver_create", "ridg_solver_destroy", "ridg_solver_info",
     "ridg_solver_levels", "ridg_solver_nodes", "ridg_set_state", "ridg_set_history", "ridg_eval_rhs", "ridg_step",
     "ridg_get_state", "ridg_energy", "ridg_trace_len", "ridg_rtm_shot", "ridg_rtm_shot_device",
-    "ridg_last_shot_stats", "ridg_set_profiling",
+    "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc",
 ]
 
 
@@ -86,6 +86,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_rtm_shot_device": (C.c_int, [P, P, P, C.c_int64, C.c_double, C.c_double, P, P, P, P, P]),
         "ridg_last_shot_stats": (C.c_int, [P, P]),
         "ridg_set_profiling": (C.c_int, [P, C.c_int32]),
+        "ridg_energy_noalloc": (C.c_int, [P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,6 +221,11 @@ class Solver:
         e = C.c_double()
         _check(lib().ridg_energy(self._h, C.byref(e)))
         return e.value
+
+    def energy_noalloc(self, out):
+        """Energy into a caller-owned device buffer (torch CUDA float64 tensor with >= 1 element),
+        without any device allocation; asynchronous on the solver's stream."""
+        _check(lib().ridg_energy_noalloc(self._h, _ptr(out)))
 
     def trace_len(self, t_final):
         return int(lib().ridg_trace_len(self._h, float(t_final)))
