@@ -93,16 +93,19 @@ struct SmemTc {
   static constexpr int EPB = 32 / W;
   static constexpr int Q = 4 * Np * CS;
   static constexpr int ST = 4 * Nfp * CS;
-  static constexpr int UX = (3 * Np * CS > EPB * (2 * kGeo + kMat)) ? 3 * Np * CS : EPB * (2 * kGeo + kMat);
+  static constexpr int NFPP = O::NFPP;
+  static constexpr int XR = 128 * 2 * NFPP;  // neighbour face blocks of the 128 (column, face) items
+  static constexpr int UX = (3 * Np * CS > XR) ? 3 * Np * CS : XR;
   static constexpr int G = EPB * NG;
-  static constexpr int INTS = 4 * EPB + 4 * EPB + EPB + EPB + 128 + 192 + 4 * EPB;
+  static constexpr int IMG = (W == 2) ? 2 * 2 * Np * EPB : 0;  // two FP64 image tiles, in floats
+  static constexpr int INTS = 4 * EPB + EPB + EPB + EPB + 128 + 192 + 4 * EPB;  // nbr, finfo bytes, bface, meta, ...
   static constexpr size_t bytes_with(bool ring) {
-    return (size_t(Q) * (ring ? 3 : 1) + 2 * size_t(ST) + UX + G) * sizeof(float) + INTS * sizeof(int);
+    return (size_t(Q) * (ring ? 3 : 1) + 2 * size_t(ST) + UX + G + IMG) * sizeof(float) + INTS * sizeof(int);
   }
   static constexpr bool ring_in_smem = bytes_with(true) <= 200 * 1024;
   static constexpr size_t bytes = bytes_with(ring_in_smem);
   static_assert(4 * Np * CS <= 2 * ST + UX, "half-step staging must fit in the penalty/U region");
-  static_assert(EPB * (2 * kGeo + kMat) <= UX, "raw geometry staging must fit in the U region");
+  static_assert(EPB * (2 * kGeo + kMat) <= 2 * ST + UX, "raw geometry staging must fit in the penalty/U region");
 };
 
 template <int N, int W>
@@ -122,15 +125,19 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   float* sS = sR2 + (RING ? SM::Q : 0);            // [4*Nfp][CS]
   float* sT = sS + SM::ST;                         // [4*Nfp][CS]
   float* sU = sT + SM::ST;                         // [3][Np][CS]
+  float* sX = sU;                                  // [128][2*NFPP] neighbour face blocks (before U)
   float* sG = sU + SM::UX;                         // [EPB][NG]
-  int* sI = reinterpret_cast<int*>(sG + SM::G);
-  int* sNbr = sI;
-  int* sInfo = sNbr + 4 * EPB;
-  int* sBf = sInfo + 4 * EPB;
-  int* sMeta = sBf + EPB;
-  int* sFm = sMeta + EPB;
-  int* sPerm = sFm + 128;
-  int2* sInj = reinterpret_cast<int2*>(sPerm + 192);  // [2][EPB] injection ranges per wavefield
+  double* sImg = reinterpret_cast<double*>(sG + SM::G);  // W == 2: [2][Np][EPB] image tiles
+  int* sI = reinterpret_cast<int*>(sG + SM::G + SM::IMG);
+  int* sNbr = sI;                                           // [EPB][4]
+  uint8_t* sInfo = reinterpret_cast<uint8_t*>(sNbr + 4 * EPB);  // [EPB][4] face info bytes
+  int* sBf = sNbr + 4 * EPB + EPB;                          // [EPB]
+  int* sMeta = sBf + EPB;                                   // [EPB]
+  int* sFm = sMeta + EPB;                                   // [4][32]
+  int* sPerm = sFm + 128;                                   // [6][32]
+  int2* sInj = reinterpret_cast<int2*>(sPerm + 192);        // [2][EPB] injection ranges per wavefield
+  double* sGeoRaw = reinterpret_cast<double*>(sS);          // [EPB][kGeo] (before the penalties)
+  float* sMatRaw = reinterpret_cast<float*>(sGeoRaw + EPB * kGeo);  // [EPB][kMat]
   float* sH = sS;  // [4][Np][CS] half-step fields, after the products
 
   const int tid = threadIdx.x;
@@ -151,48 +158,43 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   auto col_e = [](int c) { return W == 1 ? c : (c & 15); };
   auto col_w = [](int c) { return W == 1 ? 0 : (c >> 4); };
 
-  // ---------------------------------------------------------------- phase 1: async field loads
-  // q at t_start (group 0) and the two older right-hand sides (group 1), 16-byte copies
+  // ---------------------------------------------------------------- phase 0/1: asynchronous loads
+  // group 0: per-element tables; group 1: fields at t_start; group 2 (once the tables are in): the
+  // neighbours' face blocks; group 3: the two older right-hand sides (and, with two wavefields, the
+  // image tiles), which only the epilogue needs.  All copies are 16 bytes.
+  const int64_t fbase = (blk * 4) * Np * 32 + lane0;
+  constexpr int CPR = EPB / 4;  // 16-byte chunks per row and wavefield
   {
-    const int64_t fbase = (blk * 4) * Np * 32 + lane0;
-    constexpr int CPR = EPB / 4;          // 16-byte chunks per row and wavefield
-    constexpr int PER = 4 * Np * 8;       // chunks per array (8 per 32-column row)
-    const int narr = (RING && !rhs_only) ? 3 : 1;
-    for (int arr = 0; arr < narr; ++arr) {
-      const int ring = arr == 1 ? r1i : r2i;
-      float* dbase = arr == 0 ? sQ : (arr == 1 ? sR1 : sR2);
-      for (int i = tid; i < PER; i += NT) {
-        const int row = i >> 3, sub = i & 7;  // sub = w * CPR + ch
-        const int w = sub / CPR, ch = sub - w * CPR;
-        const float* base = arr == 0 ? A.wave[w].q : A.wave[w].ring + ring * qsize;
-        cp_async_bytes16(dbase + row * CS + sub * 4, base + fbase + row * 32 + ch * 4);
+    auto copy_bytes = [&](void* dst, const void* src, int bytes) {
+      for (int i = tid; i < bytes / 16; i += NT)
+        cp_async_bytes16(static_cast<char*>(dst) + 16 * i, static_cast<const char*>(src) + 16 * i);
+    };
+    copy_bytes(sNbr, A.nbr + slot0 * 4, EPB * 4 * 4);
+    copy_bytes(sInfo, A.finfo + slot0 * 4, EPB * 4);
+    copy_bytes(sBf, A.bface + slot0, EPB * 4);
+    copy_bytes(sMeta, A.meta + slot0, EPB * 4);
+    copy_bytes(sFm, A.fmask, 128 * 4);
+    copy_bytes(sPerm, A.perm, 192 * 4);
+    copy_bytes(sGeoRaw, A.geo + slot0 * kGeo, EPB * kGeo * 8);
+    copy_bytes(sMatRaw, A.mat + slot0 * kMat, EPB * kMat * 4);
+#pragma unroll
+    for (int w = 0; w < 2; ++w) {
+      if (w < W && A.wave[w].amp_mode != 0) {
+        copy_bytes(sInj + w * EPB, A.wave[w].inj_range + slot0, EPB * 8);
+      } else {
+        for (int i = tid; i < EPB; i += NT) sInj[w * EPB + i] = make_int2(0, 0);
       }
-      cp_async_commit();
     }
+    cp_async_commit();
+    constexpr int PER = 4 * Np * 8;  // 16-byte chunks of one field array (8 per 32-column row)
+    for (int i = tid; i < PER; i += NT) {
+      const int row = i >> 3, sub = i & 7;  // sub = w * CPR + ch
+      const int w = sub / CPR, ch = sub - w * CPR;
+      cp_async_bytes16(sQ + row * CS + sub * 4, A.wave[w].q + fbase + row * 32 + ch * 4);
+    }
+    cp_async_commit();
   }
-
-  // ---------------------------------------------------------------- phase 0: tables
-  for (int i = tid; i < 128; i += NT) sFm[i] = A.fmask[i];
-  for (int i = tid; i < 192; i += NT) sPerm[i] = A.perm[i];
-  for (int i = tid; i < EPB * 4; i += NT) {
-    int e = i >> 2, f = i & 3;
-    int64_t s = slot0 + e;
-    sNbr[i] = A.nbr[s * 4 + f];
-    sInfo[i] = A.finfo[s * 4 + f];
-  }
-  for (int i = tid; i < 2 * EPB; i += NT) {
-    const int w = i / EPB, e = i - w * EPB;
-    sInj[i] = (w < W && A.wave[w].amp_mode != 0) ? A.wave[w].inj_range[slot0 + e] : make_int2(0, 0);
-  }
-  // raw per-element geometry (FP64) and material, loaded cooperatively into the sU region
-  double* sGeoRaw = reinterpret_cast<double*>(sU);  // [EPB][kGeo]
-  float* sMatRaw = reinterpret_cast<float*>(sGeoRaw + EPB * kGeo);  // [EPB][kMat]
-  for (int i = tid; i < EPB * kGeo; i += NT) sGeoRaw[i] = A.geo[slot0 * kGeo + i];
-  for (int i = tid; i < EPB * kMat; i += NT) sMatRaw[i] = A.mat[slot0 * kMat + i];
-  for (int e = tid; e < EPB; e += NT) {
-    sBf[e] = A.bface[slot0 + e];
-    sMeta[e] = A.meta[slot0 + e];
-  }
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // the tables
   __syncthreads();
   for (int i = tid; i < EPB * 48; i += NT) {
     const int e = i / 48, k = i - e * 48;
@@ -218,63 +220,66 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
     }
     G[k] = v;
   }
-  // fields at t_start have landed (the history may still be in flight)
-  if (RING && !rhs_only) {
-    asm volatile("cp.async.wait_group 2;\n" ::: "memory");
-  } else {
-    cp_async_wait_all();
+  // neighbours' face blocks (interior faces) or recorded forward traces (boundary faces of the
+  // backward source run), one (column, face) item of 2*NFPP values each
+  {
+    constexpr int CHI = 2 * NFPP / 4;  // 16-byte chunks per item
+    for (int i = tid; i < 128 * CHI; i += NT) {
+      const int item = i / CHI, ch = i - item * CHI;
+      const int c = item >> 2, f = item & 3;
+      const int e = col_e(c), w = col_w(c);
+      if (!(sMeta[e] & kMetaValid)) continue;
+      const int info = sInfo[e * 4 + f];
+      const int bc = finfo_bc(uint8_t(info));
+      const float* src = nullptr;
+      if (bc == 0) {
+        src = A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + sNbr[e * 4 + f]) * (8 * NFPP) +
+              finfo_face(uint8_t(info)) * 2 * NFPP;
+      } else if (w == 0 && (A.mode & kModeReplay)) {
+        int b = sBf[e];
+        for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
+        src = A.arena_read + (A.arena_offset + b) * (2 * NFPP);
+      }
+      if (src) cp_async_bytes16(sX + item * 2 * NFPP + ch * 4, src + ch * 4);
+    }
+    cp_async_commit();
   }
+  // the history (and the image tiles), needed only by the epilogue
+  if (RING && !rhs_only) {
+    constexpr int PER = 4 * Np * 8;
+    for (int arr = 1; arr < 3; ++arr) {
+      const int ring = arr == 1 ? r1i : r2i;
+      float* dbase = arr == 1 ? sR1 : sR2;
+      for (int i = tid; i < PER; i += NT) {
+        const int row = i >> 3, sub = i & 7;
+        const int w = sub / CPR, ch = sub - w * CPR;
+        cp_async_bytes16(dbase + row * CS + sub * 4, A.wave[w].ring + ring * qsize + fbase + row * 32 + ch * 4);
+      }
+    }
+  }
+  if (W == 2 && (A.mode & kModeImage)) {
+    constexpr int CPN = EPB * 8 / 16;  // 16-byte chunks per node row of one image
+    for (int i = tid; i < 2 * Np * CPN; i += NT) {
+      const int im = i / (Np * CPN), rem = i - im * Np * CPN;
+      const int n = rem / CPN, ch = rem - n * CPN;
+      const double* src = (im == 0 ? A.image_p : A.image_q) + (blk * Np + n) * 32 + lane0 + ch * 2;
+      cp_async_bytes16(sImg + (im * Np + n) * EPB + ch * 2, src);
+    }
+  }
+  cp_async_commit();
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // fields and face blocks
   __syncthreads();
 
   // ---------------------------------------------------------------- phase 2: face penalties
-  // half-warp per (column, face), lanes over face nodes.  Interior faces read the neighbour's
-  // traces at t_start (a coalesced face block, permuted by the face correspondence); boundary
-  // faces use the ghost state of their condition, or, in the backward source run, the recorded
-  // forward traces; forward runs record the traces of boundary faces.  Loads of four items are
-  // issued before their use.
+  // half-warp per (column, face), lanes over face nodes.  Interior faces take the neighbour's
+  // traces at t_start (its face block, staged in shared memory, permuted by the face
+  // correspondence); boundary faces use the ghost state of their condition, or, in the backward
+  // source run, the recorded forward traces; forward runs record the traces of boundary faces.
   {
     constexpr int NH = NT / 16;               // half-warps
     constexpr int NU = (128 + NH - 1) / NH;   // items per half-warp
     constexpr int NJ = (Nfp + 15) / 16;       // face nodes per lane
     const int hw = tid >> 4, j = tid & 15;
-    float xp[NU][NJ], xv[NU][NJ];
-#pragma unroll
-    for (int u = 0; u < NU; ++u) {
-      const int item = hw + u * NH;
-      if (item >= 128) continue;
-      const int c = item >> 2, f = item & 3;
-      const int e = col_e(c), w = col_w(c);
-      const int info = sInfo[e * 4 + f];
-      const int bc = finfo_bc(uint8_t(info));
-      if (!(sMeta[e] & kMetaValid)) continue;
-      if (bc == 0) {
-        const int64_t s2 = sNbr[e * 4 + f];
-        const float* tb =
-            A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + s2) * (8 * NFPP) + finfo_face(uint8_t(info)) * 2 * NFPP;
-        const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
-#pragma unroll
-        for (int t = 0; t < NJ; ++t) {
-          const int jj = j + 16 * t;
-          if (jj < Nfp) {
-            const int j2 = pm[jj];
-            xp[u][t] = tb[j2];
-            xv[u][t] = -tb[NFPP + j2];
-          }
-        }
-      } else if (w == 0 && (A.mode & kModeReplay)) {
-        int b = sBf[e];
-        for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
-        const float* rec = A.arena_read + (A.arena_offset + b) * (2 * NFPP);
-#pragma unroll
-        for (int t = 0; t < NJ; ++t) {
-          const int jj = j + 16 * t;
-          if (jj < Nfp) {
-            xp[u][t] = rec[jj];
-            xv[u][t] = rec[NFPP + jj];
-          }
-        }
-      }
-    }
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
       const int item = hw + u * NH;
@@ -282,17 +287,19 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
       const int c = item >> 2, f = item & 3;
       const int e = col_e(c), w = col_w(c);
       const bool valid = (sMeta[e] & kMetaValid) != 0;
-      const int bc = finfo_bc(uint8_t(sInfo[e * 4 + f]));
+      const int bc = finfo_bc(sInfo[e * 4 + f]);
       const float* G = sG + e * NG;
       const float n0 = G[18 + 3 * f], n1 = G[19 + 3 * f], n2 = G[20 + 3 * f];
       const float* pc = G + 30 + 4 * f;
       float* rec = nullptr;
       if (bc != 0 && valid && w == 0 && (A.mode & kModeRecord)) {
         int b = sBf[e];
-        for (int ff = 0; ff < f; ++ff) b += (finfo_bc(uint8_t(sInfo[e * 4 + ff])) != 0);
+        for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
         rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
       }
       const bool ext = bc == 0 || (w == 0 && (A.mode & kModeReplay));
+      const int* pm = sPerm + finfo_perm(sInfo[e * 4 + f]) * 32;
+      const float* xb = sX + item * 2 * NFPP;
 #pragma unroll
       for (int t = 0; t < NJ; ++t) {
         const int jj = j + 16 * t;
@@ -306,8 +313,11 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
         }
         float jp, jv;
         if (ext) {
-          jp = xp[u][t] - p;
-          jv = xv[u][t] - vn;
+          // interior: the neighbour's node matching ours, its n.v taken with our normal;
+          // replayed boundary: the recorded trace of this very face (no permutation, same normal)
+          const int j2 = bc == 0 ? pm[jj] : jj;
+          jp = xb[j2] - p;
+          jv = (bc == 0 ? -xb[NFPP + j2] : xb[NFPP + j2]) - vn;
         } else if (bc == 1) {  // free surface: p+ = -p-, n.v+ = n.v-
           jp = -2.f * p;
           jv = 0.f;
@@ -554,8 +564,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
         const float incP = h * (xS * xR + h * (t2p + h * t3p));
         const float incQ = h * (qS * qR + h * (t2q + h * t3q));
         const int64_t io = (blk * Np + n) * 32 + lane0 + eb[0];
-        A.image_p[io] -= double(incP);
-        A.image_q[io] -= double(incQ);
+        A.image_p[io] = sImg[(0 * Np + n) * EPB + eb[0]] - double(incP);
+        A.image_q[io] = sImg[(1 * Np + n) * EPB + eb[0]] - double(incQ);
       }
 #pragma unroll
       for (int b = 0; b < 2; ++b) {
