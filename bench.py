@@ -116,12 +116,12 @@ def step_bytes_per_element(Np, Nfp, W, real_bytes=4):
     """Algorithmic bytes one element moves in one fused step with W wavefields.
 
     Per wavefield: q read + write (8 Np), two older right-hand sides read and the new one written
-    (12 Np), neighbour traces read and own traces written (2 x 8 Nfp), injection range (8 B).
-    Per element: FP64 geometry (25 doubles), material and penalties (11 words), connectivity and
-    flags (4 neighbour slots + 4 face bytes + boundary index + flags = 28 B); with W = 2 the two
-    FP64 images are read and written (32 Np B)."""
+    (12 Np), the face inbox read and the traces pushed to the neighbours (2 x 8 Nfp), injection
+    range (8 B).  Per element: the FP32 coefficient table (48 floats: geometric factors, normals,
+    penalty coefficients, impedance), connectivity and flags (4 neighbour slots + 4 face bytes +
+    boundary index + flags = 28 B); with W = 2 the two FP64 images are read and written (32 Np B)."""
     per_wave = (20 * Np + 16 * Nfp) * real_bytes + 8
-    per_elem = 25 * 8 + 11 * real_bytes + 28
+    per_elem = 48 * 4 + 28
     img = 32 * Np if W == 2 else 0
     return W * per_wave + per_elem + img
 

@@ -5,11 +5,14 @@
 
 namespace ridg {
 
-// Traces (p, n.v) of the fields q into trace slot `slot` for every valid slot.
+// Traces (p, n.v) of the fields q pushed into the neighbours' face inboxes of trace slot `slot`
+// (see WaveArgs::trace): node j of face f of slot s lands at index perm[j] of face f2 of the
+// neighbour s2, with n.v taken with the neighbour's normal.
 template <int N, typename real>
 __global__ void init_traces_kernel(const real* __restrict__ q, real* __restrict__ trace, int slot, int64_t n_slots,
                                    const double* __restrict__ geo, const int* __restrict__ meta,
-                                   const int* __restrict__ fmask) {
+                                   const int* __restrict__ fmask, const int* __restrict__ nbr,
+                                   const uint8_t* __restrict__ finfo, const int* __restrict__ perm) {
   using O = Order<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -18,6 +21,8 @@ __global__ void init_traces_kernel(const real* __restrict__ q, real* __restrict_
   int r = int(i - s * 4 * Nfp);
   int f = r / Nfp, j = r - f * Nfp;
   if (!(meta[s] & kMetaValid)) return;
+  const uint8_t info = finfo[s * 4 + f];
+  if (finfo_bc(info) != 0) return;
   int n = fmask[f * 32 + j];
   int64_t blk = s >> 5;
   int lane = int(s & 31);
@@ -25,9 +30,11 @@ __global__ void init_traces_kernel(const real* __restrict__ q, real* __restrict_
   const double* g = geo + s * kGeo;
   real p = at(0);
   real vn = real(g[9 + 3 * f]) * at(1) + real(g[10 + 3 * f]) * at(2) + real(g[11 + 3 * f]) * at(3);
-  real* t = trace + (int64_t(slot) * n_slots + s) * (8 * NFPP) + f * 2 * NFPP;
-  t[j] = p;
-  t[NFPP + j] = vn;
+  const int64_t s2 = nbr[s * 4 + f];
+  const int j2 = perm[finfo_perm(info) * 32 + j];
+  real* t = trace + (int64_t(slot) * n_slots + s2) * (8 * NFPP) + finfo_face(info) * 2 * NFPP;
+  t[j2] = p;
+  t[NFPP + j2] = -vn;
 }
 
 // Receiver pressures: out[r * n_time + col] = sum_m row_r[m] p(slot_r, m).

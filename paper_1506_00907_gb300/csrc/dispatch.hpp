@@ -10,7 +10,8 @@ template <int N, typename real>
 struct Launch {
   static cudaError_t step(const StepArgs<real>& a, int W, cudaStream_t st);
   static cudaError_t init_traces(const real* q, real* trace, int slot, int64_t n_slots, const double* geo,
-                                 const int* meta, const int* fmask, cudaStream_t st);
+                                 const int* meta, const int* fmask, const int* nbr, const uint8_t* finfo,
+                                 const int* perm, cudaStream_t st);
   static cudaError_t sample(const real* q, const int64_t* rec_slot, const real* rec_row, int nrec, double* out,
                             int64_t n_time, int64_t col, cudaStream_t st);
   static cudaError_t energy(const real* q, int64_t n_slots, const double* J, const real* mat, const int* meta,

@@ -43,9 +43,11 @@ cudaError_t Launch<N, real>::step(const StepArgs<real>& a, int W, cudaStream_t s
 
 template <int N, typename real>
 cudaError_t Launch<N, real>::init_traces(const real* q, real* trace, int slot, int64_t n_slots, const double* geo,
-                                         const int* meta, const int* fmask, cudaStream_t st) {
+                                         const int* meta, const int* fmask, const int* nbr, const uint8_t* finfo,
+                                         const int* perm, cudaStream_t st) {
   int64_t n = n_slots * 4 * Order<N>::Nfp;
-  init_traces_kernel<N, real><<<unsigned((n + 255) / 256), 256, 0, st>>>(q, trace, slot, n_slots, geo, meta, fmask);
+  init_traces_kernel<N, real><<<unsigned((n + 255) / 256), 256, 0, st>>>(q, trace, slot, n_slots, geo, meta, fmask,
+                                                                           nbr, finfo, perm);
   return cudaGetLastError();
 }
 

@@ -462,7 +462,8 @@ class Engine final : public ridg_solver {
   size_t device_bytes() const {
     size_t b = 0;
     const DBuf* all[] = {&geo_d_, &J_d_, &mat_d_, &nbr_d_, &finfo_d_, &bface_d_, &meta_d_, &Dt_d_, &Lt_d_,
-                         &fmask_d_, &perm_d_, &M_d_, &slot_of_d_, &q_snap_, &ring_snap_, &img_p_, &img_q_, &arena_};
+                         &fmask_d_, &perm_d_, &M_d_, &slot_of_d_, &q_snap_, &ring_snap_, &img_p_, &img_q_, &arena_,
+                         &afrag_d_, &gtab_d_[0], &gtab_d_[1]};
     for (auto* x : all) b += x->bytes;
     for (auto& w : w_) b += w.q.bytes + w.ring.bytes + w.trace.bytes;
     return b;
@@ -540,6 +541,12 @@ class Engine final : public ridg_solver {
           double d = std::fabs(xa[0] - xb[0]) + std::fabs(xa[1] - xb[1]) + std::fabs(xa[2] - xb[2]);
           if (d > tol) throw Error{RIDG_E_BAD_MESH, "face nodes of neighbouring elements do not coincide"};
         }
+        // traces are pushed with the writer's correspondence and read without one: the two sides'
+        // correspondences must be mutually inverse
+        int code2 = mesh_.perm_code[4 * k2 + f2];
+        for (int j = 0; j < Nfp_; ++j)
+          if (ref_.perm[code2][ref_.perm[code][j]] != j)
+            throw Error{RIDG_E_BAD_MESH, "face-node correspondences of a shared face are not mutually inverse"};
       }
   }
 
@@ -595,7 +602,11 @@ class Engine final : public ridg_solver {
       for (int n = 0; n < Np_; ++n) Lt[fm * NPa_ + n] = real(ref_.LIFT(n, fm));
     upload(Dt_d_, Dt, st_);
     upload(Lt_d_, Lt, st_);
-    if (std::is_same<real, float>::value) upload(afrag_d_, operator_fragments(), st_);
+    if (std::is_same<real, float>::value) {
+      upload(afrag_d_, operator_fragments(), st_);
+      upload(gtab_d_[0], coefficient_table(+1), st_);
+      upload(gtab_d_[1], coefficient_table(-1), st_);
+    }
     std::vector<int> fm(128, 0), pm(192, 0);
     for (int f = 0; f < 4; ++f)
       for (int j = 0; j < Nfp_; ++j) fm[f * 32 + j] = ref_.fmask[f][j];
@@ -607,6 +618,38 @@ class Engine final : public ridg_solver {
     upload(slot_of_d_, ord_.slot_of, st_);
     level_count_.assign(L_, 0);
     for (int64_t k = 0; k < mesh_.K; ++k) level_count_[lv_.level[k] - 1]++;
+  }
+
+  // Per-element coefficients of the FP32 tensor-core kernel for penalty sign `sigma` (Eq. penaltyFlux
+  // with tau negated in backward runs), [n_slots/32][kGtab][32]: -rho c^2 rx_ij (volume p equation,
+  // Eq. dgLocalSchemeP), -rx_ij / rho (volume v equation, Eq. dgLocalSchemeU), the outward normals, per
+  // face the coefficients of t = A [n.v] + B [p] and s = C [p] + D [n.v] with the surface Jacobian and the
+  // 1/2 of the weak form folded in, and rho c.
+  std::vector<float> coefficient_table(int sigma) const {
+    const int64_t S = n_slots_;
+    std::vector<float> g(size_t(S) * kGtab, 0.f);
+    for (int64_t s = 0; s < S; ++s) {
+      int64_t k = ord_.elem_of[s];
+      if (k < 0) continue;
+      auto at = [&](int i) -> float& { return g[size_t(((s >> 5) * kGtab + i) * 32 + (s & 31))]; };
+      const double rho = rho_[k], c = c_[k], rc2 = rho * c * c, irho = 1.0 / rho, Zk = rho * c;
+      for (int i = 0; i < 9; ++i) {
+        at(i) = float(-rc2 * geo_.rx[9 * k + i]);
+        at(9 + i) = float(-irho * geo_.rx[9 * k + i]);
+      }
+      for (int i = 0; i < 12; ++i) at(18 + i) = float(geo_.normal[12 * k + i]);
+      for (int f = 0; f < 4; ++f) {
+        int64_t k2 = mesh_.nbr[4 * k + f];
+        double Zb = k2 >= 0 ? 0.5 * (Zk + rho_[k2] * c_[k2]) : Zk;
+        double fs = geo_.fscale[4 * k + f], taup = sigma / Zb, tauv = sigma * Zb;
+        at(30 + 4 * f + 0) = float(-0.5 * fs * rc2);
+        at(30 + 4 * f + 1) = float(0.5 * fs * rc2 * taup);
+        at(30 + 4 * f + 2) = float(0.5 * fs * irho);
+        at(30 + 4 * f + 3) = float(-0.5 * fs * irho * tauv);
+      }
+      at(46) = float(Zk);
+    }
+    return g;
   }
 
   // TF32 rounding (round to nearest, ties away from zero) of an FP32 value
@@ -742,7 +785,9 @@ class Engine final : public ridg_solver {
     return a;
   }
 
-  void launch(const StepArgs<real>& a, int W) {
+  void launch(const StepArgs<real>& a0, int W) {
+    StepArgs<real> a = a0;
+    a.gtab = dptr<const float>(gtab_d_[a.tau_sign > real(0) ? 0 : 1]);
     cudaError_t e = dispatch_order(N_, [&](auto NC) { return Launch<decltype(NC)::value, real>::step(a, W, st_); });
     if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("step kernel launch: ") + cudaGetErrorString(e)};
     ++stats_.kernel_launches;
@@ -778,8 +823,9 @@ class Engine final : public ridg_solver {
 
   void init_traces_into(const real* q, real* trace, int slot) {
     cudaError_t e = dispatch_order(N_, [&](auto NC) {
-      return Launch<decltype(NC)::value, real>::init_traces(q, trace, slot, n_slots_, dptr<const double>(geo_d_),
-                                                             dptr<const int>(meta_d_), dptr<const int>(fmask_d_), st_);
+      return Launch<decltype(NC)::value, real>::init_traces(
+          q, trace, slot, n_slots_, dptr<const double>(geo_d_), dptr<const int>(meta_d_), dptr<const int>(fmask_d_),
+          dptr<const int>(nbr_d_), dptr<const uint8_t>(finfo_d_), dptr<const int>(perm_d_), st_);
     });
     if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
     ++stats_.kernel_launches;
@@ -851,7 +897,7 @@ class Engine final : public ridg_solver {
   std::vector<int> bface_host_;
   std::vector<int64_t> level_count_;
   DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
-  DBuf afrag_d_;
+  DBuf afrag_d_, gtab_d_[2];
   DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_;
   Wave<real> w_[2];
   int64_t tau_ = 0, dof_ = 0;

@@ -53,12 +53,16 @@ constexpr int kModeRhsOnly = 8;  // only write the right-hand side to rhs_out
 constexpr int kGeo = 25;
 // per-element material (working precision): rho c^2, 1/rho, rho c, tau_p[4], tau_v[4]
 constexpr int kMat = 11;
+// per-element coefficients of the FP32 tensor-core kernel: -rho c^2 rx[9], -rx/rho[9], normal[12],
+// penalty coefficients [4 faces][4], rho c, one spare
+constexpr int kGtab = 48;
 
 template <typename real>
 struct WaveArgs {
   real* q;           // [n_slots/32][4][Np][32]
   real* ring;        // 3 x q-sized
-  real* trace;       // 3 slots x [n_slots][4][2][NFPP]
+  real* trace;       // face inboxes, 3 time slots x [n_slots][4][2][NFPP]: (p, n.v) of the neighbour
+                     // across face f of slot s, in s's face-node order and with s's outward normal
   const int2* inj_range;  // [n_slots] (first, count) or null
   const real* inj_w;      // [n_inj][Np]
   const int* inj_row;     // [n_inj] data row
@@ -106,6 +110,7 @@ struct StepArgs {
   const int* perm;       // [6][32]
   real* rhs_out;         // kModeRhsOnly: q-sized
   const uint32_t* afrag; // tensor-core variant: operator fragments (TF32 hi/lo), see step_kernel_tc.cuh
+  const float* gtab;     // tensor-core variant: per-element coefficients [n_slots/32][kGtab][32] (this tau sign)
 };
 
 template <int N>
@@ -369,9 +374,10 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
   __syncthreads();
 
   // ---------------------------------------------------------------- phase 2a: exterior traces
-  // half-warp per (column, face), lanes over face nodes: coalesced reads of the neighbour's face
-  // block, permuted by the face correspondence; four items' loads are issued before any store.
-  // Boundary faces of the backward source run read the recorded forward traces instead.
+  // half-warp per (column, face), lanes over face nodes: coalesced reads of this element's own
+  // face inbox, which the neighbour filled in our face-node order and with our normal; four items'
+  // loads are issued before any store.  Boundary faces of the backward source run read the
+  // recorded forward traces instead.
   {
     constexpr int NH = NT / 16;
     const int hw = tid >> 4, j = tid & 15;
@@ -389,17 +395,14 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
         int info = sInfo[e * 4 + f];
         int bc = finfo_bc(uint8_t(info));
         if (bc == 0) {
-          int64_t s2 = sNbr[e * 4 + f];
-          int f2 = finfo_face(uint8_t(info));
-          const real* tb = A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + s2) * (8 * NFPP) + f2 * 2 * NFPP;
-          const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
+          const real* tb =
+              A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + slot0 + e) * (8 * NFPP) + f * 2 * NFPP;
 #pragma unroll
           for (int t = 0; t < 2; ++t) {
             int jj = j + 16 * t;
             if (jj < Nfp) {
-              int j2 = pm[jj];
-              xp[u][t] = tb[j2];
-              xv[u][t] = -tb[NFPP + j2];  // neighbour's n.v taken with our normal
+              xp[u][t] = tb[jj];
+              xv[u][t] = tb[NFPP + jj];
             }
           }
           have[u] = true;
@@ -713,6 +716,9 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
   __syncthreads();
 
   // ---------------------------------------------------------------- phase 5: traces
+  // pushed into the neighbour's inbox: face f2 of slot s2, at the neighbour's face-node index
+  // perm[j] of our node j (the correspondences of the two sides are mutually inverse), with n.v
+  // taken with the neighbour's normal.  Boundary faces have no reader.
   {
     const int hw = tid >> 4, j = tid & 15;
     const int ws = A.trace_write[lev], hs = A.trace_half[lev];
@@ -721,23 +727,28 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
       int e = c / W, w = c % W;
       int meta = sMeta[e];
       if (!(meta & kMetaValid)) continue;
+      const int info = sInfo[e * 4 + f];
+      if (finfo_bc(uint8_t(info)) != 0) continue;
       const real* G = sG + e * NG;
-      int64_t s = slot0 + e;
-      real* tw = A.wave[w].trace + (int64_t(ws) * A.n_slots + s) * (8 * NFPP) + f * 2 * NFPP;
-      real* th = A.wave[w].trace + (int64_t(hs) * A.n_slots + s) * (8 * NFPP) + f * 2 * NFPP;
+      const int64_t s2 = sNbr[e * 4 + f];
+      const int f2 = finfo_face(uint8_t(info));
+      const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
+      real* tw = A.wave[w].trace + (int64_t(ws) * A.n_slots + s2) * (8 * NFPP) + f2 * 2 * NFPP;
+      real* th = A.wave[w].trace + (int64_t(hs) * A.n_slots + s2) * (8 * NFPP) + f2 * 2 * NFPP;
       for (int jj = j; jj < Nfp; jj += 16) {
         int n = sFm[f * 32 + jj];
+        int j2 = pm[jj];
         real p = sQ[(0 * Np + n) * CS + c];
         real vn = G[18 + 3 * f] * sQ[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sQ[(2 * Np + n) * CS + c] +
                   G[20 + 3 * f] * sQ[(3 * Np + n) * CS + c];
-        tw[jj] = p;
-        tw[NFPP + jj] = vn;
+        tw[j2] = p;
+        tw[NFPP + j2] = -vn;
         if (meta & kMetaHalf) {
           real ph = sH[(0 * Np + n) * CS + c];
           real vh = G[18 + 3 * f] * sH[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sH[(2 * Np + n) * CS + c] +
                     G[20 + 3 * f] * sH[(3 * Np + n) * CS + c];
-          th[jj] = ph;
-          th[NFPP + jj] = vh;
+          th[j2] = ph;
+          th[NFPP + j2] = -vh;
         }
       }
     }

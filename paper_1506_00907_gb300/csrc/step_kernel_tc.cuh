@@ -8,10 +8,14 @@
 // The operator fragments (hi and lo) are prepared on the host in fragment order.
 //
 // Work split: a CTA owns 32 columns (32 elements, or 16 elements x 2 wavefields with the source
-// wavefield in columns 0-15 and the receiver wavefield in 16-31).  Warp (mt, pair) computes, for
-// the 16 nodes of node tile mt and the two 8-column blocks pair and pair+2, the pressure
-// right-hand side, the three reference derivatives of p and the four per-face velocity lifts,
-// and then runs the update/image epilogue for its nodes and columns straight from registers.
+// wavefield in columns 0-15 and the receiver wavefield in 16-31).  Everything it reads is issued
+// at once as asynchronous copies: the fields, the per-element coefficients (precomputed, with the
+// penalty sign of the run) and the face inboxes, into which each neighbour pushed its traces in
+// this element's face-node order.  Warp (mt, pair) computes, for the 16 nodes of node tile mt and
+// the two 8-column blocks pair and pair+2, the pressure right-hand side, the three reference
+// derivatives of p and the four per-face velocity lifts, and leaves the right-hand sides in shared
+// memory; the update then runs with a thread per (node, element), so that every global store is
+// 32 (or 2 x 16) consecutive columns.
 #pragma once
 #include "step_kernel.cuh"
 
@@ -89,14 +93,13 @@ struct SmemTc {
   using O = Order<N>;
   static constexpr int Np = O::Np, Nfp = O::Nfp;
   static constexpr int CS = 36;  // column rows (16-byte aligned, few conflicts in fragment loads)
-  static constexpr int NG = 49;
   static constexpr int EPB = 32 / W;
   static constexpr int Q = 4 * Np * CS;
   static constexpr int ST = 4 * Nfp * CS;
   static constexpr int NFPP = O::NFPP;
-  static constexpr int XR = 128 * 2 * NFPP;  // neighbour face blocks of the 128 (column, face) items
+  static constexpr int XR = 32 * 8 * NFPP;  // face inboxes of the 32 columns
   static constexpr int UX = (3 * Np * CS > XR) ? 3 * Np * CS : XR;
-  static constexpr int G = EPB * NG;
+  static constexpr int G = kGtab * EPB;                        // coefficients [kGtab][EPB]
   static constexpr int IMG = (W == 2) ? 2 * 2 * Np * EPB : 0;  // two FP64 image tiles, in floats
   static constexpr int INTS = 4 * EPB + EPB + EPB + EPB + 128 + 192 + 4 * EPB;  // nbr, finfo bytes, bface, meta, ...
   static constexpr size_t bytes_with(bool ring) {
@@ -104,8 +107,7 @@ struct SmemTc {
   }
   static constexpr bool ring_in_smem = bytes_with(true) <= 200 * 1024;
   static constexpr size_t bytes = bytes_with(ring_in_smem);
-  static_assert(4 * Np * CS <= 2 * ST + UX, "half-step staging must fit in the penalty/U region");
-  static_assert(EPB * (2 * kGeo + kMat) <= 2 * ST + UX, "raw geometry staging must fit in the penalty/U region");
+  static_assert(4 * Np * CS <= 2 * ST + UX, "right-hand-side staging must fit in the penalty/U region");
 };
 
 template <int N, int W>
@@ -114,7 +116,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   using T = TcOrder<N>;
   using SM = SmemTc<N, W>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NT = T::NT, NFPP = O::NFPP;
-  constexpr int CS = SM::CS, NG = SM::NG, EPB = SM::EPB;
+  constexpr int CS = SM::CS, EPB = SM::EPB;
   constexpr bool RING = SM::ring_in_smem;
   constexpr int MT = T::MT, KSD = T::KSD, KSF = T::KSF;
 
@@ -125,8 +127,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   float* sS = sR2 + (RING ? SM::Q : 0);            // [4*Nfp][CS]
   float* sT = sS + SM::ST;                         // [4*Nfp][CS]
   float* sU = sT + SM::ST;                         // [3][Np][CS]
-  float* sX = sU;                                  // [128][2*NFPP] neighbour face blocks (before U)
-  float* sG = sU + SM::UX;                         // [EPB][NG]
+  float* sX = sU;                                  // [32 columns][4][2][NFPP] face inboxes (before U)
+  float* sG = sU + SM::UX;                         // [kGtab][EPB]
   double* sImg = reinterpret_cast<double*>(sG + SM::G);  // W == 2: [2][Np][EPB] image tiles
   int* sI = reinterpret_cast<int*>(sG + SM::G + SM::IMG);
   int* sNbr = sI;                                           // [EPB][4]
@@ -136,9 +138,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   int* sFm = sMeta + EPB;                                   // [4][32]
   int* sPerm = sFm + 128;                                   // [6][32]
   int2* sInj = reinterpret_cast<int2*>(sPerm + 192);        // [2][EPB] injection ranges per wavefield
-  double* sGeoRaw = reinterpret_cast<double*>(sS);          // [EPB][kGeo] (before the penalties)
-  float* sMatRaw = reinterpret_cast<float*>(sGeoRaw + EPB * kGeo);  // [EPB][kMat]
-  float* sH = sS;  // [4][Np][CS] half-step fields, after the products
+  float* sRhs = sS;  // [4][Np][CS] right-hand sides after the products, then the half-step fields
 
   const int tid = threadIdx.x;
   const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * EPB;
@@ -153,15 +153,17 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
   const int rn = A.ring_new[lev], r1i = A.ring_old1[lev], r2i = A.ring_old2[lev];
 
-
   // column c -> (element, wavefield)
   auto col_e = [](int c) { return W == 1 ? c : (c & 15); };
   auto col_w = [](int c) { return W == 1 ? 0 : (c >> 4); };
+  auto gcoef = [&](int k, int e) { return sG[k * EPB + e]; };
 
-  // ---------------------------------------------------------------- phase 0/1: asynchronous loads
-  // group 0: per-element tables; group 1: fields at t_start; group 2 (once the tables are in): the
-  // neighbours' face blocks; group 3: the two older right-hand sides (and, with two wavefields, the
-  // image tiles), which only the epilogue needs.  All copies are 16 bytes.
+  // ---------------------------------------------------------------- phase 1: asynchronous loads
+  // group 0, nothing depends on anything: the tables, the coefficients, the fields at t_start and
+  // the face inboxes (the neighbours' traces at t_start, already in this element's face-node order).
+  // Then, once the tables are in: group 1, the recorded traces of boundary faces (backward source
+  // run only), and group 2, the two older right-hand sides and the image tiles, which only the
+  // update needs.  All copies are 16 bytes.
   const int64_t fbase = (blk * 4) * Np * 32 + lane0;
   constexpr int CPR = EPB / 4;  // 16-byte chunks per row and wavefield
   {
@@ -175,8 +177,6 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
     copy_bytes(sMeta, A.meta + slot0, EPB * 4);
     copy_bytes(sFm, A.fmask, 128 * 4);
     copy_bytes(sPerm, A.perm, 192 * 4);
-    copy_bytes(sGeoRaw, A.geo + slot0 * kGeo, EPB * kGeo * 8);
-    copy_bytes(sMatRaw, A.mat + slot0 * kMat, EPB * kMat * 4);
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
       if (w < W && A.wave[w].amp_mode != 0) {
@@ -185,66 +185,49 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
         for (int i = tid; i < EPB; i += NT) sInj[w * EPB + i] = make_int2(0, 0);
       }
     }
-    cp_async_commit();
+    for (int i = tid; i < kGtab * CPR; i += NT) {
+      const int row = i / CPR, ch = i - row * CPR;
+      cp_async_bytes16(sG + row * EPB + ch * 4, A.gtab + (blk * kGtab + row) * 32 + lane0 + ch * 4);
+    }
     constexpr int PER = 4 * Np * 8;  // 16-byte chunks of one field array (8 per 32-column row)
     for (int i = tid; i < PER; i += NT) {
       const int row = i >> 3, sub = i & 7;  // sub = w * CPR + ch
       const int w = sub / CPR, ch = sub - w * CPR;
       cp_async_bytes16(sQ + row * CS + sub * 4, A.wave[w].q + fbase + row * 32 + ch * 4);
     }
+    constexpr int CHW = EPB * 8 * NFPP / 4;  // 16-byte chunks of one wavefield's inboxes
+    for (int i = tid; i < W * CHW; i += NT) {
+      const int w = i / CHW, ch = i - w * CHW;
+      cp_async_bytes16(sX + w * (EPB * 8 * NFPP) + ch * 4,
+                       A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + slot0) * (8 * NFPP) + ch * 4);
+    }
     cp_async_commit();
   }
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // the tables
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
-  for (int i = tid; i < EPB * 48; i += NT) {
-    const int e = i / 48, k = i - e * 48;
-    const double* g = sGeoRaw + e * kGeo;
-    const float* m = sMatRaw + e * kMat;
-    float* G = sG + e * NG;
-    const float rc2 = m[0], irho = m[1];
-    float v;
-    if (k < 9) {
-      v = -rc2 * float(g[k]);  // -rho c^2 rx_ij (volume p equation)
-    } else if (k < 18) {
-      v = -irho * float(g[k - 9]);  // -rx_ij / rho (volume v equation)
-    } else if (k < 30) {
-      v = float(g[9 + (k - 18)]);  // outward normals
-    } else if (k < 46) {
-      // penalty coefficients per face: t = A_f [nv] + B_f [p], s = C_f [p] + D_f [nv]
-      const int f = (k - 30) >> 2, r = (k - 30) & 3;
-      const float fs = float(g[21 + f]);
-      const float taup = A.tau_sign * m[3 + f], tauv = A.tau_sign * m[7 + f];
-      v = r == 0 ? -0.5f * fs * rc2 : (r == 1 ? 0.5f * fs * rc2 * taup : (r == 2 ? 0.5f * fs * irho : -0.5f * fs * irho * tauv));
-    } else {
-      v = k == 46 ? m[2] : 0.f;  // rho c
-    }
-    G[k] = v;
-  }
-  // neighbours' face blocks (interior faces) or recorded forward traces (boundary faces of the
-  // backward source run), one (column, face) item of 2*NFPP values each
-  {
-    constexpr int CHI = 2 * NFPP / 4;  // 16-byte chunks per item
-    for (int i = tid; i < 128 * CHI; i += NT) {
-      const int item = i / CHI, ch = i - item * CHI;
-      const int c = item >> 2, f = item & 3;
-      const int e = col_e(c), w = col_w(c);
-      if (!(sMeta[e] & kMetaValid)) continue;
-      const int info = sInfo[e * 4 + f];
-      const int bc = finfo_bc(uint8_t(info));
-      const float* src = nullptr;
-      if (bc == 0) {
-        src = A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + sNbr[e * 4 + f]) * (8 * NFPP) +
-              finfo_face(uint8_t(info)) * 2 * NFPP;
-      } else if (w == 0 && (A.mode & kModeReplay)) {
+  // recorded forward traces as the exterior state of boundary faces (backward source run), into the
+  // inbox places of those faces; only blocks that have boundary faces take part
+  bool replay_block = false;
+  if (A.mode & kModeReplay) {
+    int nlast = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) nlast += finfo_bc(sInfo[(EPB - 1) * 4 + f]) != 0;
+    replay_block = sBf[EPB - 1] + nlast > sBf[0];
+    if (replay_block) {
+      constexpr int CHI = 2 * NFPP / 4;  // 16-byte chunks per face record
+      for (int i = tid; i < EPB * 4 * CHI; i += NT) {
+        const int item = i / CHI, ch = i - item * CHI;
+        const int e = item >> 2, f = item & 3;
+        if (!(sMeta[e] & kMetaValid) || finfo_bc(sInfo[e * 4 + f]) == 0) continue;
         int b = sBf[e];
         for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
-        src = A.arena_read + (A.arena_offset + b) * (2 * NFPP);
+        cp_async_bytes16(sX + e * (8 * NFPP) + f * 2 * NFPP + ch * 4,
+                         A.arena_read + (A.arena_offset + b) * (2 * NFPP) + ch * 4);
       }
-      if (src) cp_async_bytes16(sX + item * 2 * NFPP + ch * 4, src + ch * 4);
     }
-    cp_async_commit();
   }
-  // the history (and the image tiles), needed only by the epilogue
+  cp_async_commit();
+  // the history (and the image tiles), needed only by the update
   if (RING && !rhs_only) {
     constexpr int PER = 4 * Np * 8;
     for (int arr = 1; arr < 3; ++arr) {
@@ -267,39 +250,38 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
     }
   }
   cp_async_commit();
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");  // fields and face blocks
-  __syncthreads();
+  if (replay_block) {
+    asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+    __syncthreads();
+  }
 
   // ---------------------------------------------------------------- phase 2: face penalties
   // half-warp per (column, face), lanes over face nodes.  Interior faces take the neighbour's
-  // traces at t_start (its face block, staged in shared memory, permuted by the face
-  // correspondence); boundary faces use the ghost state of their condition, or, in the backward
-  // source run, the recorded forward traces; forward runs record the traces of boundary faces.
+  // traces at t_start from the inbox; boundary faces use the ghost state of their condition, or, in
+  // the backward source run, the recorded forward traces; forward runs record the traces of
+  // boundary faces.  All items are evaluated before any is stored.
   {
     constexpr int NH = NT / 16;               // half-warps
     constexpr int NU = (128 + NH - 1) / NH;   // items per half-warp
     constexpr int NJ = (Nfp + 15) / 16;       // face nodes per lane
     const int hw = tid >> 4, j = tid & 15;
+    float tv[NU][NJ], sv[NU][NJ], pv[NU][NJ], vv[NU][NJ];
+    bool recu[NU];
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
       const int item = hw + u * NH;
+      recu[u] = false;
       if (item >= 128) continue;
       const int c = item >> 2, f = item & 3;
       const int e = col_e(c), w = col_w(c);
       const bool valid = (sMeta[e] & kMetaValid) != 0;
       const int bc = finfo_bc(sInfo[e * 4 + f]);
-      const float* G = sG + e * NG;
-      const float n0 = G[18 + 3 * f], n1 = G[19 + 3 * f], n2 = G[20 + 3 * f];
-      const float* pc = G + 30 + 4 * f;
-      float* rec = nullptr;
-      if (bc != 0 && valid && w == 0 && (A.mode & kModeRecord)) {
-        int b = sBf[e];
-        for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
-        rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
-      }
+      const float n0 = gcoef(18 + 3 * f, e), n1 = gcoef(19 + 3 * f, e), n2 = gcoef(20 + 3 * f, e);
+      const float pa = gcoef(30 + 4 * f, e), pb = gcoef(31 + 4 * f, e), pcc = gcoef(32 + 4 * f, e),
+                  pd = gcoef(33 + 4 * f, e);
+      recu[u] = bc != 0 && valid && w == 0 && (A.mode & kModeRecord);
       const bool ext = bc == 0 || (w == 0 && (A.mode & kModeReplay));
-      const int* pm = sPerm + finfo_perm(sInfo[e * 4 + f]) * 32;
-      const float* xb = sX + item * 2 * NFPP;
+      const float* xb = sX + c * (8 * NFPP) + f * 2 * NFPP;
 #pragma unroll
       for (int t = 0; t < NJ; ++t) {
         const int jj = j + 16 * t;
@@ -307,17 +289,14 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
         const int n = sFm[f * 32 + jj];
         const float p = sQ[(0 * Np + n) * CS + c];
         const float vn = n0 * sQ[(1 * Np + n) * CS + c] + n1 * sQ[(2 * Np + n) * CS + c] + n2 * sQ[(3 * Np + n) * CS + c];
-        if (rec) {
-          rec[jj] = p;
-          rec[NFPP + jj] = vn;
-        }
+        pv[u][t] = p;
+        vv[u][t] = vn;
         float jp, jv;
         if (ext) {
-          // interior: the neighbour's node matching ours, its n.v taken with our normal;
-          // replayed boundary: the recorded trace of this very face (no permutation, same normal)
-          const int j2 = bc == 0 ? pm[jj] : jj;
-          jp = xb[j2] - p;
-          jv = (bc == 0 ? -xb[NFPP + j2] : xb[NFPP + j2]) - vn;
+          // exterior state in our node order and with our normal: the neighbour's traces, or the
+          // recorded traces of this very face
+          jp = xb[jj] - p;
+          jv = xb[NFPP + jj] - vn;
         } else if (bc == 1) {  // free surface: p+ = -p-, n.v+ = n.v-
           jp = -2.f * p;
           jv = 0.f;
@@ -328,15 +307,33 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
           jp = 0.f;
           jv = -2.f * vn;
         }
-        float tt = pc[0] * jv + pc[1] * jp;
-        float sv = pc[2] * jp + pc[3] * jv;
-        if (!valid) {
-          tt = 0.f;
-          sv = 0.f;
-        }
+        tv[u][t] = valid ? pa * jv + pb * jp : 0.f;
+        sv[u][t] = valid ? pcc * jp + pd * jv : 0.f;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+      const int item = hw + u * NH;
+      if (item >= 128) continue;
+      const int c = item >> 2, f = item & 3;
+      float* rec = nullptr;
+      if (recu[u]) {
+        const int e = col_e(c);
+        int b = sBf[e];
+        for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
+        rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
+      }
+#pragma unroll
+      for (int t = 0; t < NJ; ++t) {
+        const int jj = j + 16 * t;
+        if (jj >= Nfp) continue;
         const int fj = f * Nfp + jj;
-        sT[fj * CS + c] = tt;
-        sS[fj * CS + c] = sv;
+        sT[fj * CS + c] = tv[u][t];
+        sS[fj * CS + c] = sv[u][t];
+        if (rec) {
+          rec[jj] = pv[u][t];
+          rec[NFPP + jj] = vv[u][t];
+        }
       }
     }
   }
@@ -345,10 +342,11 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
 // ---------------------------------------------------------------- phase 2c: U_j = G_p v
   for (int i = tid; i < Np * 32; i += NT) {
     int c = i & 31, m = i >> 5;
-    const float* G = sG + col_e(c) * NG;
+    const int e = col_e(c);
     float vx = sQ[(1 * Np + m) * CS + c], vy = sQ[(2 * Np + m) * CS + c], vz = sQ[(3 * Np + m) * CS + c];
 #pragma unroll
-    for (int jd = 0; jd < 3; ++jd) sU[(jd * Np + m) * CS + c] = G[0 + jd] * vx + G[3 + jd] * vy + G[6 + jd] * vz;
+    for (int jd = 0; jd < 3; ++jd)
+      sU[(jd * Np + m) * CS + c] = gcoef(0 + jd, e) * vx + gcoef(3 + jd, e) * vy + gcoef(6 + jd, e) * vz;
   }
   __syncthreads();
 
@@ -450,141 +448,153 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
       }
     }
   }
-  cp_async_wait_all();  // the history slots
-  __syncthreads();
+  __syncthreads();  // the products have read sS, sT and sU: they now hold the right-hand sides
 
-  // ---------------------------------------------------------------- phase 4: update
+  // ---------------------------------------------------------------- phase 4a: right-hand sides
   // accumulator entry q = 2 hn + k of block b: node mt*16 + g + 8 hn, column (pair + 2b)*8 + 2 t4 + k.
-  // One column pair (k) at a time: with two wavefields its two columns are the source and receiver
-  // values of the same element, which the image needs together.
+  // r_p = rp (Eq. dgLocalSchemeP); r_v = -(1/rho) grad p - sum_f n_f (L_f s_f) (Eq. dgLocalSchemeU).
 #pragma unroll
-  for (int k = 0; k < 2; ++k) {
-    int cb[2], eb[2], wb[2];
-    bool okb[2];
+  for (int k = 0; k < 2; ++k)
 #pragma unroll
     for (int b = 0; b < 2; ++b) {
-      cb[b] = (pair + 2 * b) * 8 + 2 * t4 + k;
-      eb[b] = col_e(cb[b]);
-      wb[b] = col_w(cb[b]);
-      okb[b] = (sMeta[eb[b]] & kMetaValid) != 0;
-    }
+      const int cb = (pair + 2 * b) * 8 + 2 * t4 + k;
+      const int e = col_e(cb);
+      float gv[9], gn[12];
 #pragma unroll
-    for (int hn = 0; hn < 2; ++hn) {
-      const int n = mt * 16 + g + 8 * hn;
-      if (n >= Np) continue;
-      const int q = 2 * hn + k;
-      float r[2][4];
+      for (int i = 0; i < 9; ++i) gv[i] = gcoef(9 + i, e);
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const float* G = sG + eb[b] * NG;
-        r[b][0] = rp[b][q];
+      for (int i = 0; i < 12; ++i) gn[i] = gcoef(18 + i, e);
+#pragma unroll
+      for (int hn = 0; hn < 2; ++hn) {
+        const int n = mt * 16 + g + 8 * hn;
+        if (n >= Np) continue;
+        const int q = 2 * hn + k;
+        sRhs[(0 * Np + n) * CS + cb] = rp[b][q];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          float v = G[9 + 3 * d + 0] * dp[0][b][q] + G[9 + 3 * d + 1] * dp[1][b][q] + G[9 + 3 * d + 2] * dp[2][b][q];
+          float v = gv[3 * d + 0] * dp[0][b][q] + gv[3 * d + 1] * dp[1][b][q] + gv[3 * d + 2] * dp[2][b][q];
 #pragma unroll
-          for (int f = 0; f < 4; ++f) v -= G[18 + 3 * f + d] * ls[f][b][q];
-          r[b][1 + d] = v;
-        }
-        // point injections (source wavelet or receiver traces)
-        const WaveArgs<float>& wa = A.wave[wb[b]];
-        const int2 ir = sInj[wb[b] * EPB + eb[b]];
-        if (ir.y > 0 && okb[b]) {
-          for (int qq = ir.x; qq < ir.x + ir.y; ++qq) {
-            float amp;
-            if (wa.amp_mode == 1) {
-              amp = wa.amp;
-            } else {
-              double acc = 0.0;
-              const int row = wa.inj_row[qq];
-              for (int tt = 0; tt < 4; ++tt) {
-                const int nt = A.interp_n0 + tt;
-                if (nt >= 0 && nt < wa.n_time) acc += A.interp_w[tt] * wa.data[int64_t(row) * wa.n_time + nt];
-              }
-              amp = float(acc);
-            }
-            r[b][0] += amp * wa.inj_w[int64_t(qq) * Np + n];
-          }
+          for (int f = 0; f < 4; ++f) v -= gn[3 * f + d] * ls[f][b][q];
+          sRhs[((1 + d) * Np + n) * CS + cb] = v;
         }
       }
-      if (rhs_only) {
+    }
+  cp_async_wait_all();  // the history slots and image tiles
+  __syncthreads();
+
+  // ---------------------------------------------------------------- phase 4b: update
+  // thread per (node, element), all wavefields: point injections, the images from the fields and
+  // histories at t_start (Eq. updateABcorr), the new fields (Eq. updateAB) and the half-step fields
+  // (Eq. updateABcoarse); global stores are 32 consecutive columns per warp.
+  for (int i = tid; i < Np * EPB; i += NT) {
+    const int n = i / EPB, e = i - n * EPB;
+    const bool ok = (sMeta[e] & kMetaValid) != 0;
+    float r[W][4], q0[W][4], r1[W][4], r2[W][4];
 #pragma unroll
-        for (int b = 0; b < 2; ++b)
-          if (okb[b])
+    for (int w = 0; w < W; ++w) {
+      const int c = w * 16 + e;
 #pragma unroll
-            for (int fld = 0; fld < 4; ++fld) A.rhs_out[((blk * 4 + fld) * Np + n) * 32 + lane0 + eb[b]] = r[b][fld];
-        continue;
+      for (int fld = 0; fld < 4; ++fld) {
+        const int sidx = (fld * Np + n) * CS + c;
+        r[w][fld] = sRhs[sidx];
+        q0[w][fld] = sQ[sidx];
       }
-      float q0[2][4], r1[2][4], r2[2][4];
-#pragma unroll
-      for (int b = 0; b < 2; ++b)
-#pragma unroll
-        for (int fld = 0; fld < 4; ++fld) {
-          const int sidx = (fld * Np + n) * CS + cb[b];
-          q0[b][fld] = sQ[sidx];
-          if constexpr (RING) {
-            r1[b][fld] = sR1[sidx];
-            r2[b][fld] = sR2[sidx];
+      // point injections (source wavelet or receiver traces)
+      const WaveArgs<float>& wa = A.wave[w];
+      const int2 ir = sInj[w * EPB + e];
+      if (ir.y > 0 && ok) {
+        for (int qq = ir.x; qq < ir.x + ir.y; ++qq) {
+          float amp;
+          if (wa.amp_mode == 1) {
+            amp = wa.amp;
           } else {
-            const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + lane0 + eb[b];
-            r1[b][fld] = A.wave[wb[b]].ring[r1i * qsize + off];
-            r2[b][fld] = A.wave[wb[b]].ring[r2i * qsize + off];
+            double acc = 0.0;
+            const int row = wa.inj_row[qq];
+            for (int tt = 0; tt < 4; ++tt) {
+              const int nt = A.interp_n0 + tt;
+              if (nt >= 0 && nt < wa.n_time) acc += A.interp_w[tt] * wa.data[int64_t(row) * wa.n_time + nt];
+            }
+            amp = float(acc);
           }
+          r[w][0] += amp * wa.inj_w[int64_t(qq) * Np + n];
         }
-      // images from the fields and histories at t_start, before the update
-      if (W == 2 && (A.mode & kModeImage) && okb[0]) {
-        const float Z = sG[eb[0] * NG + 46];
-        const float* eu = A.e_up;
-        const float xS = q0[0][0], xR = q0[1][0];
-        const float vS = eu[0] * q0[0][1] + eu[1] * q0[0][2] + eu[2] * q0[0][3];
-        const float vR = eu[0] * q0[1][1] + eu[1] * q0[1][2] + eu[2] * q0[1][3];
-        const float rS[3] = {r[0][0], r1[0][0], r2[0][0]};
-        const float rR[3] = {r[1][0], r1[1][0], r2[1][0]};
-        const float sS3[3] = {rS[0] - Z * (eu[0] * r[0][1] + eu[1] * r[0][2] + eu[2] * r[0][3]),
-                              rS[1] - Z * (eu[0] * r1[0][1] + eu[1] * r1[0][2] + eu[2] * r1[0][3]),
-                              rS[2] - Z * (eu[0] * r2[0][1] + eu[1] * r2[0][2] + eu[2] * r2[0][3])};
-        const float sR3[3] = {rR[0] + Z * (eu[0] * r[1][1] + eu[1] * r[1][2] + eu[2] * r[1][3]),
-                              rR[1] + Z * (eu[0] * r1[1][1] + eu[1] * r1[1][2] + eu[2] * r1[1][3]),
-                              rR[2] + Z * (eu[0] * r2[1][1] + eu[1] * r2[1][2] + eu[2] * r2[1][3])};
-        const float cc[3] = {float(AB::c1), float(AB::c2), float(AB::c3)};
-        const float C[3][3] = {{float(4703.0 / 5040.0), float(-457.0 / 840.0), float(52.0 / 315.0)},
-                               {float(-457.0 / 840.0), float(103.0 / 315.0), float(-251.0 / 2520.0)},
-                               {float(52.0 / 315.0), float(-251.0 / 2520.0), float(17.0 / 560.0)}};
-        const float qS = xS - Z * vS, qR = xR + Z * vR;
-        float t2p = 0.f, t3p = 0.f, t2q = 0.f, t3q = 0.f;
-#pragma unroll
-        for (int s3 = 0; s3 < 3; ++s3) {
-          t2p += cc[s3] * (xS * rR[s3] + rS[s3] * xR);
-          t2q += cc[s3] * (qS * sR3[s3] + sS3[s3] * qR);
-#pragma unroll
-          for (int u = 0; u < 3; ++u) {
-            t3p += C[s3][u] * rS[s3] * rR[u];
-            t3q += C[s3][u] * sS3[s3] * sR3[u];
-          }
-        }
-        const float incP = h * (xS * xR + h * (t2p + h * t3p));
-        const float incQ = h * (qS * qR + h * (t2q + h * t3q));
-        const int64_t io = (blk * Np + n) * 32 + lane0 + eb[0];
-        A.image_p[io] = sImg[(0 * Np + n) * EPB + eb[0]] - double(incP);
-        A.image_q[io] = sImg[(1 * Np + n) * EPB + eb[0]] - double(incQ);
       }
+    }
+    if (rhs_only) {
+      if (ok)
 #pragma unroll
-      for (int b = 0; b < 2; ++b) {
-        const int64_t gofs = ((blk * 4) * Np + n) * 32 + lane0 + eb[b];
-        float* qg = A.wave[wb[b]].q + gofs;
-        float* rg = A.wave[wb[b]].ring + rn * qsize + gofs;
+        for (int fld = 0; fld < 4; ++fld) A.rhs_out[((blk * 4 + fld) * Np + n) * 32 + lane0 + e] = r[0][fld];
+      continue;
+    }
 #pragma unroll
-        for (int fld = 0; fld < 4; ++fld) {
-          const float rr = r[b][fld];
-          const float upd = float(AB::a1) * rr + float(AB::a2) * r1[b][fld] + float(AB::a3) * r2[b][fld];
-          const float hb = float(AB::b1) * rr + float(AB::b2) * r1[b][fld] + float(AB::b3) * r2[b][fld];
-          const float qn = q0[b][fld] + h * upd;
-          const int sidx = (fld * Np + n) * CS + cb[b];
-          sQ[sidx] = qn;
-          sH[sidx] = q0[b][fld] + h * hb;
-          if (okb[b]) {
-            qg[fld * Np * 32] = qn;
-            rg[fld * Np * 32] = rr;
-          }
+    for (int w = 0; w < W; ++w)
+#pragma unroll
+      for (int fld = 0; fld < 4; ++fld) {
+        if constexpr (RING) {
+          const int sidx = (fld * Np + n) * CS + w * 16 + e;
+          r1[w][fld] = sR1[sidx];
+          r2[w][fld] = sR2[sidx];
+        } else {
+          const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + lane0 + e;
+          r1[w][fld] = A.wave[w].ring[r1i * qsize + off];
+          r2[w][fld] = A.wave[w].ring[r2i * qsize + off];
+        }
+      }
+    // images from the fields and histories at t_start, before the update
+    if (W == 2 && (A.mode & kModeImage) && ok) {
+      const int wR = W - 1;  // receiver wavefield (1 when W == 2)
+      const float Z = gcoef(46, e);
+      const float* eu = A.e_up;
+      const float xS = q0[0][0], xR = q0[wR][0];
+      const float vS = eu[0] * q0[0][1] + eu[1] * q0[0][2] + eu[2] * q0[0][3];
+      const float vR = eu[0] * q0[wR][1] + eu[1] * q0[wR][2] + eu[2] * q0[wR][3];
+      const float rS[3] = {r[0][0], r1[0][0], r2[0][0]};
+      const float rR[3] = {r[wR][0], r1[wR][0], r2[wR][0]};
+      const float sS3[3] = {rS[0] - Z * (eu[0] * r[0][1] + eu[1] * r[0][2] + eu[2] * r[0][3]),
+                            rS[1] - Z * (eu[0] * r1[0][1] + eu[1] * r1[0][2] + eu[2] * r1[0][3]),
+                            rS[2] - Z * (eu[0] * r2[0][1] + eu[1] * r2[0][2] + eu[2] * r2[0][3])};
+      const float sR3[3] = {rR[0] + Z * (eu[0] * r[wR][1] + eu[1] * r[wR][2] + eu[2] * r[wR][3]),
+                            rR[1] + Z * (eu[0] * r1[wR][1] + eu[1] * r1[wR][2] + eu[2] * r1[wR][3]),
+                            rR[2] + Z * (eu[0] * r2[wR][1] + eu[1] * r2[wR][2] + eu[2] * r2[wR][3])};
+      const float cc[3] = {float(AB::c1), float(AB::c2), float(AB::c3)};
+      const float C[3][3] = {{float(4703.0 / 5040.0), float(-457.0 / 840.0), float(52.0 / 315.0)},
+                             {float(-457.0 / 840.0), float(103.0 / 315.0), float(-251.0 / 2520.0)},
+                             {float(52.0 / 315.0), float(-251.0 / 2520.0), float(17.0 / 560.0)}};
+      const float qS = xS - Z * vS, qR = xR + Z * vR;
+      float t2p = 0.f, t3p = 0.f, t2q = 0.f, t3q = 0.f;
+#pragma unroll
+      for (int s3 = 0; s3 < 3; ++s3) {
+        t2p += cc[s3] * (xS * rR[s3] + rS[s3] * xR);
+        t2q += cc[s3] * (qS * sR3[s3] + sS3[s3] * qR);
+#pragma unroll
+        for (int u = 0; u < 3; ++u) {
+          t3p += C[s3][u] * rS[s3] * rR[u];
+          t3q += C[s3][u] * sS3[s3] * sR3[u];
+        }
+      }
+      const float incP = h * (xS * xR + h * (t2p + h * t3p));
+      const float incQ = h * (qS * qR + h * (t2q + h * t3q));
+      const int64_t io = (blk * Np + n) * 32 + lane0 + e;
+      A.image_p[io] = sImg[(0 * Np + n) * EPB + e] - double(incP);
+      A.image_q[io] = sImg[(1 * Np + n) * EPB + e] - double(incQ);
+    }
+#pragma unroll
+    for (int w = 0; w < W; ++w) {
+      const int64_t gofs = ((blk * 4) * Np + n) * 32 + lane0 + e;
+      float* qg = A.wave[w].q + gofs;
+      float* rg = A.wave[w].ring + rn * qsize + gofs;
+#pragma unroll
+      for (int fld = 0; fld < 4; ++fld) {
+        const float rr = r[w][fld];
+        const float upd = float(AB::a1) * rr + float(AB::a2) * r1[w][fld] + float(AB::a3) * r2[w][fld];
+        const float hb = float(AB::b1) * rr + float(AB::b2) * r1[w][fld] + float(AB::b3) * r2[w][fld];
+        const float qn = q0[w][fld] + h * upd;
+        const int sidx = (fld * Np + n) * CS + w * 16 + e;
+        sQ[sidx] = qn;
+        sRhs[sidx] = q0[w][fld] + h * hb;  // half-step fields, in place
+        if (ok) {
+          qg[fld * Np * 32] = qn;
+          rg[fld * Np * 32] = rr;
         }
       }
     }
@@ -593,31 +603,40 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   __syncthreads();
 
 // ---------------------------------------------------------------- phase 5: traces
+  // pushed into the neighbour's inbox: face f2 of slot s2, at the neighbour's face-node index
+  // perm[j] of our node j (the correspondences of the two sides are mutually inverse), with n.v
+  // taken with the neighbour's normal; half-step traces too where a finer neighbour needs them.
+  // Boundary faces have no reader.
   {
+    const float* sH = sRhs;
     const int hw = tid >> 4, j = tid & 15;
     const int ws = A.trace_write[lev], hs = A.trace_half[lev];
+#pragma unroll 4
     for (int item = hw; item < 32 * 4; item += NT / 16) {
-      int c = item >> 2, f = item & 3;
-      int e = col_e(c), w = col_w(c);
-      int meta = sMeta[e];
-      if (!(meta & kMetaValid)) continue;
-      const float* G = sG + e * NG;
-      int64_t s = slot0 + e;
-      float* tw = A.wave[w].trace + (int64_t(ws) * A.n_slots + s) * (8 * NFPP) + f * 2 * NFPP;
-      float* th = A.wave[w].trace + (int64_t(hs) * A.n_slots + s) * (8 * NFPP) + f * 2 * NFPP;
+      const int c = item >> 2, f = item & 3;
+      const int e = col_e(c), w = col_w(c);
+      const int meta = sMeta[e];
+      const int info = sInfo[e * 4 + f];
+      if (!(meta & kMetaValid) || finfo_bc(uint8_t(info)) != 0) continue;
+      const float n0 = gcoef(18 + 3 * f, e), n1 = gcoef(19 + 3 * f, e), n2 = gcoef(20 + 3 * f, e);
+      const int64_t s2 = sNbr[e * 4 + f];
+      const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
+      const int64_t fo = s2 * (8 * NFPP) + finfo_face(uint8_t(info)) * 2 * NFPP;
+      float* tw = A.wave[w].trace + int64_t(ws) * A.n_slots * (8 * NFPP) + fo;
+      float* th = A.wave[w].trace + int64_t(hs) * A.n_slots * (8 * NFPP) + fo;
       for (int jj = j; jj < Nfp; jj += 16) {
-        int n = sFm[f * 32 + jj];
-        float p = sQ[(0 * Np + n) * CS + c];
-        float vn = G[18 + 3 * f] * sQ[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sQ[(2 * Np + n) * CS + c] +
-                   G[20 + 3 * f] * sQ[(3 * Np + n) * CS + c];
-        tw[jj] = p;
-        tw[NFPP + jj] = vn;
+        const int n = sFm[f * 32 + jj];
+        const int j2 = pm[jj];
+        const float p = sQ[(0 * Np + n) * CS + c];
+        const float vn = n0 * sQ[(1 * Np + n) * CS + c] + n1 * sQ[(2 * Np + n) * CS + c] + n2 * sQ[(3 * Np + n) * CS + c];
+        tw[j2] = p;
+        tw[NFPP + j2] = -vn;
         if (meta & kMetaHalf) {
-          float ph = sH[(0 * Np + n) * CS + c];
-          float vh = G[18 + 3 * f] * sH[(1 * Np + n) * CS + c] + G[19 + 3 * f] * sH[(2 * Np + n) * CS + c] +
-                     G[20 + 3 * f] * sH[(3 * Np + n) * CS + c];
-          th[jj] = ph;
-          th[NFPP + jj] = vh;
+          const float ph = sH[(0 * Np + n) * CS + c];
+          const float vh =
+              n0 * sH[(1 * Np + n) * CS + c] + n1 * sH[(2 * Np + n) * CS + c] + n2 * sH[(3 * Np + n) * CS + c];
+          th[j2] = ph;
+          th[NFPP + j2] = -vh;
         }
       }
     }
