@@ -662,10 +662,12 @@ class Engine final : public ridg_solver {
   }
   // Operator fragments of mma.m16n8k8 (A: 16 x 8 row major; lane (g, t) holds rows g, g+8 and
   // columns t, t+4) for D_r, D_s, D_t and the four LIFT blocks, tiles of 16 nodes x 8 nodes,
-  // each value split into TF32 hi and lo (hi + lo = the FP64 operator to ~2^-22).
+  // each value split into TF32 hi and lo (hi + lo = the FP64 operator to ~2^-22).  One stream
+  // per node tile mt, in the order the kernel consumes them: D_jd k-steps, then LIFT blocks.
   std::vector<uint32_t> operator_fragments() const {
     const int MT = (Np_ + 15) / 16, KSD = (Np_ + 7) / 8, KSF = (Nfp_ + 7) / 8;
-    std::vector<uint32_t> out(size_t(3 * MT * KSD + 4 * MT * KSF) * 256, 0u);
+    const int NSTEP = 3 * KSD + 4 * KSF;
+    std::vector<uint32_t> out(size_t(MT * NSTEP) * 256, 0u);
     auto put = [&](size_t tile, int lane, int q, double v) {
       float hf = float(v);
       uint32_t hi = tf32_bits(hf);
@@ -684,16 +686,15 @@ class Engine final : public ridg_solver {
             for (int q = 0; q < 4; ++q) {
               int r = mt * 16 + rr[q], c = kb * 8 + cc[q];
               double v = (r < Np_ && c < Np_) ? ref_.D[jd](r, c) : 0.0;
-              put(size_t((jd * MT + mt) * KSD + kb), lane, q, v);
+              put(size_t(mt * NSTEP + jd * KSD + kb), lane, q, v);
             }
-      const size_t baseL = size_t(3 * MT * KSD);
       for (int f = 0; f < 4; ++f)
         for (int mt = 0; mt < MT; ++mt)
           for (int kb = 0; kb < KSF; ++kb)
             for (int q = 0; q < 4; ++q) {
               int r = mt * 16 + rr[q], c = kb * 8 + cc[q];
               double v = (r < Np_ && c < Nfp_) ? ref_.LIFT(r, f * Nfp_ + c) : 0.0;
-              put(baseL + size_t((f * MT + mt) * KSF + kb), lane, q, v);
+              put(size_t(mt * NSTEP + 3 * KSD + f * KSF + kb), lane, q, v);
             }
     }
     return out;

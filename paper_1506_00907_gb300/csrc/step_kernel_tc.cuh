@@ -29,10 +29,14 @@ struct TcOrder {
   static constexpr int KSF = (Nfp + 7) / 8;  // k-steps over the nodes of one face
   static constexpr int NWARP = 2 * MT;
   static constexpr int NT = 32 * NWARP;
-  // operator fragments: [3][MT][KSD][32 lanes][8] then [4][MT][KSF][32][8]; 8 = 4 hi + 4 lo
-  static constexpr int FRAG_D = 3 * MT * KSD * 32 * 8;
-  static constexpr int FRAG_L = 4 * MT * KSF * 32 * 8;
-  static constexpr int FRAG = FRAG_D + FRAG_L;
+  // operator fragments, one contiguous stream per node tile: [MT][NSTEP][32 lanes][8], 8 = 4 hi +
+  // 4 lo; steps jd * KSD + kb (D_jd, k-step kb) then 3 KSD + f * KSF + kb (LIFT block f)
+  static constexpr int NSTEP = 3 * KSD + 4 * KSF;
+  static constexpr int FRAG = MT * NSTEP * 32 * 8;
+};
+
+struct FragA {
+  uint32_t h[4], l[4];
 };
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
@@ -75,6 +79,19 @@ __device__ __forceinline__ void load_b(const float* X, int row0, int kvalid_rel,
   split_tf32(x1, bh[1], bl[1]);
 }
 
+__device__ __forceinline__ void load_a(const uint32_t* frag, int lane, FragA& a) {
+  const uint4* p = reinterpret_cast<const uint4*>(frag + lane * 8);
+  uint4 h = __ldg(p), l = __ldg(p + 1);
+  a.h[0] = h.x;
+  a.h[1] = h.y;
+  a.h[2] = h.z;
+  a.h[3] = h.w;
+  a.l[0] = l.x;
+  a.l[1] = l.y;
+  a.l[2] = l.z;
+  a.l[3] = l.w;
+}
+
 __device__ __forceinline__ void load_a(const uint32_t* frag, int lane, uint32_t ah[4], uint32_t al[4]) {
   const uint4* p = reinterpret_cast<const uint4*>(frag + lane * 8);
   uint4 h = __ldg(p), l = __ldg(p + 1);
@@ -99,7 +116,8 @@ struct SmemTc {
   static constexpr int NFPP = O::NFPP;
   static constexpr int XR = 32 * 8 * NFPP;  // face inboxes of the 32 columns
   static constexpr int UX = (3 * Np * CS > XR) ? 3 * Np * CS : XR;
-  static constexpr int G = kGtab * EPB;                        // coefficients [kGtab][EPB]
+  static constexpr int GS = EPB + 4;                           // coefficient rows (16-byte aligned, skewed banks)
+  static constexpr int G = kGtab * GS;                         // coefficients [kGtab][GS]
   static constexpr int IMG = (W == 2) ? 2 * 2 * Np * EPB : 0;  // two FP64 image tiles, in floats
   static constexpr int INTS = 4 * EPB + EPB + EPB + EPB + 128 + 192 + 4 * EPB;  // nbr, finfo bytes, bface, meta, ...
   static constexpr size_t bytes_with(bool ring) {
@@ -116,9 +134,9 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   using T = TcOrder<N>;
   using SM = SmemTc<N, W>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NT = T::NT, NFPP = O::NFPP;
-  constexpr int CS = SM::CS, EPB = SM::EPB;
+  constexpr int CS = SM::CS, EPB = SM::EPB, GS = SM::GS;
   constexpr bool RING = SM::ring_in_smem;
-  constexpr int MT = T::MT, KSD = T::KSD, KSF = T::KSF;
+  constexpr int KSD = T::KSD, KSF = T::KSF, NSTEP = T::NSTEP;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sQ = reinterpret_cast<float*>(smem_raw);  // [4][Np][CS]
@@ -128,7 +146,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   float* sT = sS + SM::ST;                         // [4*Nfp][CS]
   float* sU = sT + SM::ST;                         // [3][Np][CS]
   float* sX = sU;                                  // [32 columns][4][2][NFPP] face inboxes (before U)
-  float* sG = sU + SM::UX;                         // [kGtab][EPB]
+  float* sG = sU + SM::UX;                         // [kGtab][GS]
   double* sImg = reinterpret_cast<double*>(sG + SM::G);  // W == 2: [2][Np][EPB] image tiles
   int* sI = reinterpret_cast<int*>(sG + SM::G + SM::IMG);
   int* sNbr = sI;                                           // [EPB][4]
@@ -156,7 +174,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   // column c -> (element, wavefield)
   auto col_e = [](int c) { return W == 1 ? c : (c & 15); };
   auto col_w = [](int c) { return W == 1 ? 0 : (c >> 4); };
-  auto gcoef = [&](int k, int e) { return sG[k * EPB + e]; };
+  auto gcoef = [&](int k, int e) { return sG[k * GS + e]; };
 
   // ---------------------------------------------------------------- phase 1: asynchronous loads
   // group 0, nothing depends on anything: the tables, the coefficients, the fields at t_start and
@@ -187,7 +205,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
     }
     for (int i = tid; i < kGtab * CPR; i += NT) {
       const int row = i / CPR, ch = i - row * CPR;
-      cp_async_bytes16(sG + row * EPB + ch * 4, A.gtab + (blk * kGtab + row) * 32 + lane0 + ch * 4);
+      cp_async_bytes16(sG + row * GS + ch * 4, A.gtab + (blk * kGtab + row) * 32 + lane0 + ch * 4);
     }
     constexpr int PER = 4 * Np * 8;  // 16-byte chunks of one field array (8 per 32-column row)
     for (int i = tid; i < PER; i += NT) {
@@ -256,15 +274,18 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   }
 
   // ---------------------------------------------------------------- phase 2: face penalties
-  // half-warp per (column, face), lanes over face nodes.  Interior faces take the neighbour's
-  // traces at t_start from the inbox; boundary faces use the ghost state of their condition, or, in
-  // the backward source run, the recorded forward traces; forward runs record the traces of
-  // boundary faces.  All items are evaluated before any is stored.
+  // half-warp per (face, column) item, lanes over face nodes; the two half-warps of a warp take
+  // neighbouring columns of the same face.  Interior faces take the neighbour's traces at t_start
+  // from the inbox; boundary faces use the ghost state of their condition, or, in the backward
+  // source run, the recorded forward traces; forward runs record the traces of boundary faces.
+  // All items are evaluated before any is stored.
   {
     constexpr int NH = NT / 16;               // half-warps
     constexpr int NU = (128 + NH - 1) / NH;   // items per half-warp
     constexpr int NJ = (Nfp + 15) / 16;       // face nodes per lane
+    static_assert(NH % 2 == 0, "half-warp pairs must share a face");
     const int hw = tid >> 4, j = tid & 15;
+    const int par = hw & 1;  // the odd half-warp reads n.v before p: no bank conflicts between the halves
     float tv[NU][NJ], sv[NU][NJ], pv[NU][NJ], vv[NU][NJ];
     bool recu[NU];
 #pragma unroll
@@ -272,7 +293,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
       const int item = hw + u * NH;
       recu[u] = false;
       if (item >= 128) continue;
-      const int c = item >> 2, f = item & 3;
+      const int c = item & 31, f = item >> 5;
       const int e = col_e(c), w = col_w(c);
       const bool valid = (sMeta[e] & kMetaValid) != 0;
       const int bc = finfo_bc(sInfo[e * 4 + f]);
@@ -295,8 +316,9 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
         if (ext) {
           // exterior state in our node order and with our normal: the neighbour's traces, or the
           // recorded traces of this very face
-          jp = xb[jj] - p;
-          jv = xb[NFPP + jj] - vn;
+          const float x1 = xb[par * NFPP + jj], x2 = xb[(1 - par) * NFPP + jj];
+          jp = (par ? x2 : x1) - p;
+          jv = (par ? x1 : x2) - vn;
         } else if (bc == 1) {  // free surface: p+ = -p-, n.v+ = n.v-
           jp = -2.f * p;
           jv = 0.f;
@@ -315,7 +337,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
     for (int u = 0; u < NU; ++u) {
       const int item = hw + u * NH;
       if (item >= 128) continue;
-      const int c = item >> 2, f = item & 3;
+      const int c = item & 31, f = item >> 5;
       float* rec = nullptr;
       if (recu[u]) {
         const int e = col_e(c);
@@ -367,18 +389,23 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
       for (int f = 0; f < 4; ++f) ls[f][b][q] = 0.f;
     }
   {
-    const uint32_t* fragD = A.afrag;
-    const uint32_t* fragL = A.afrag + T::FRAG_D;
+    // operator fragments stream from L2 three steps ahead of their use
+    const uint32_t* fr = A.afrag + mt * (NSTEP * 256);
+    FragA F0, F1, F2;
+    load_a(fr, lane, F0);
+    load_a(fr + (NSTEP > 1 ? 256 : 0), lane, F1);
+    load_a(fr + (NSTEP > 2 ? 512 : 0), lane, F2);
+    auto next = [&](int s) {
+      FragA F3 = F2;
+      if (s + 3 < NSTEP) load_a(fr + (s + 3) * 256, lane, F3);
+      return F3;
+    };
 #pragma unroll
     for (int jd = 0; jd < 3; ++jd) {
       const float* Ub = sU + jd * Np * CS;
-      const uint32_t* fr = fragD + (jd * MT + mt) * KSD * 256;
-      uint32_t ah[4], al[4];
-      load_a(fr, lane, ah, al);
 #pragma unroll 1
       for (int kb = 0; kb < KSD; ++kb) {
-        uint32_t nh[4], nl[4];
-        if (kb + 1 < KSD) load_a(fr + (kb + 1) * 256, lane, nh, nl);
+        const FragA F3 = next(jd * KSD + kb);
         const int kv = Np - kb * 8;
         uint32_t ph[2][2], pl[2][2], uh[2][2], ul[2][2];
 #pragma unroll
@@ -389,35 +416,29 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
         // the three split terms of four independent accumulators, interleaved
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(dp[jd][b], al, ph[b]);
-          mma_tf32(rp[b], al, uh[b]);
+          mma_tf32(dp[jd][b], F0.l, ph[b]);
+          mma_tf32(rp[b], F0.l, uh[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(dp[jd][b], ah, pl[b]);
-          mma_tf32(rp[b], ah, ul[b]);
+          mma_tf32(dp[jd][b], F0.h, pl[b]);
+          mma_tf32(rp[b], F0.h, ul[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(dp[jd][b], ah, ph[b]);
-          mma_tf32(rp[b], ah, uh[b]);
+          mma_tf32(dp[jd][b], F0.h, ph[b]);
+          mma_tf32(rp[b], F0.h, uh[b]);
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          ah[q] = nh[q];
-          al[q] = nl[q];
-        }
+        F0 = F1;
+        F1 = F2;
+        F2 = F3;
       }
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-      const uint32_t* fr = fragL + (f * MT + mt) * KSF * 256;
-      uint32_t ah[4], al[4];
-      load_a(fr, lane, ah, al);
 #pragma unroll 1
       for (int kb = 0; kb < KSF; ++kb) {
-        uint32_t nh[4], nl[4];
-        if (kb + 1 < KSF) load_a(fr + (kb + 1) * 256, lane, nh, nl);
+        const FragA F3 = next(3 * KSD + f * KSF + kb);
         const int kv = Nfp - kb * 8;
         uint32_t th[2][2], tl[2][2], sh[2][2], sl[2][2];
 #pragma unroll
@@ -427,24 +448,22 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(rp[b], al, th[b]);
-          mma_tf32(ls[f][b], al, sh[b]);
+          mma_tf32(rp[b], F0.l, th[b]);
+          mma_tf32(ls[f][b], F0.l, sh[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(rp[b], ah, tl[b]);
-          mma_tf32(ls[f][b], ah, sl[b]);
+          mma_tf32(rp[b], F0.h, tl[b]);
+          mma_tf32(ls[f][b], F0.h, sl[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(rp[b], ah, th[b]);
-          mma_tf32(ls[f][b], ah, sh[b]);
+          mma_tf32(rp[b], F0.h, th[b]);
+          mma_tf32(ls[f][b], F0.h, sh[b]);
         }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          ah[q] = nh[q];
-          al[q] = nl[q];
-        }
+        F0 = F1;
+        F1 = F2;
+        F2 = F3;
       }
     }
   }
@@ -613,7 +632,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
     const int ws = A.trace_write[lev], hs = A.trace_half[lev];
 #pragma unroll 4
     for (int item = hw; item < 32 * 4; item += NT / 16) {
-      const int c = item >> 2, f = item & 3;
+      const int c = item & 31, f = item >> 5;
       const int e = col_e(c), w = col_w(c);
       const int meta = sMeta[e];
       const int info = sInfo[e * 4 + f];
