@@ -137,6 +137,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   constexpr int CS = SM::CS, EPB = SM::EPB, GS = SM::GS;
   constexpr bool RING = SM::ring_in_smem;
   constexpr int KSD = T::KSD, KSF = T::KSF, NSTEP = T::NSTEP;
+  // the k-steps are unrolled where the registers allow it (the two highest orders keep them rolled)
+  constexpr int KUNROLL = N <= 4 ? 16 : 1;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sQ = reinterpret_cast<float*>(smem_raw);  // [4][Np][CS]
@@ -389,7 +391,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
       for (int f = 0; f < 4; ++f) ls[f][b][q] = 0.f;
     }
   {
-    // operator fragments stream from L2 three steps ahead of their use
+    // operator fragments stream from L2 three steps ahead of their use; unrolled steps rotate the
+    // fragment registers by renaming (a register copy would wait for the load to land)
     const uint32_t* fr = A.afrag + mt * (NSTEP * 256);
     FragA F0, F1, F2;
     load_a(fr, lane, F0);
@@ -403,7 +406,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
 #pragma unroll
     for (int jd = 0; jd < 3; ++jd) {
       const float* Ub = sU + jd * Np * CS;
-#pragma unroll 1
+#pragma unroll(KUNROLL)
       for (int kb = 0; kb < KSD; ++kb) {
         const FragA F3 = next(jd * KSD + kb);
         const int kv = Np - kb * 8;
@@ -436,7 +439,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-#pragma unroll 1
+#pragma unroll(KUNROLL)
       for (int kb = 0; kb < KSF; ++kb) {
         const FragA F3 = next(3 * KSD + f * KSF + kb);
         const int kv = Nfp - kb * 8;
