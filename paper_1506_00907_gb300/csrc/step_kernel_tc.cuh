@@ -33,6 +33,8 @@ struct TcOrder {
   // 4 lo; steps jd * KSD + kb (D_jd, k-step kb) then 3 KSD + f * KSF + kb (LIFT block f)
   static constexpr int NSTEP = 3 * KSD + 4 * KSF;
   static constexpr int FRAG = MT * NSTEP * 32 * 8;
+  // resident blocks per SM the kernel is built for (registers and shared memory are sized to it)
+  static constexpr int MINB = N <= 4 ? 3 : 2;
 };
 
 struct FragA {
@@ -123,13 +125,14 @@ struct SmemTc {
   static constexpr size_t bytes_with(bool ring) {
     return (size_t(Q) * (ring ? 3 : 1) + 2 * size_t(ST) + UX + G + IMG) * sizeof(float) + INTS * sizeof(int);
   }
-  static constexpr bool ring_in_smem = bytes_with(true) <= 200 * 1024;
+  // the history is staged in shared memory only where that still leaves room for MINB blocks
+  static constexpr bool ring_in_smem = TcOrder<N>::MINB * (bytes_with(true) + 1024) <= 228 * 1024;
   static constexpr size_t bytes = bytes_with(ring_in_smem);
   static_assert(4 * Np * CS <= 2 * ST + UX, "right-hand-side staging must fit in the penalty/U region");
 };
 
 template <int N, int W>
-__global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const StepArgs<float> A) {
+__global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kernel_tc(const StepArgs<float> A) {
   using O = Order<N>;
   using T = TcOrder<N>;
   using SM = SmemTc<N, W>;
@@ -222,6 +225,12 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
                        A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + slot0) * (8 * NFPP) + ch * 4);
     }
     cp_async_commit();
+    // the history slices this block reads from global memory in the update: into L2 now
+    if (!RING && !rhs_only && tid < 2 * W) {
+      const int w = tid >> 1, ring = (tid & 1) ? r2i : r1i;
+      const float* src = A.wave[w].ring + ring * qsize + blk * 4 * Np * 32;
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(4 * Np * 32 * 4) : "memory");
+    }
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
@@ -379,17 +388,23 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   const int mt = wid >> 1, pair = wid & 1;
   const int g = lane >> 2, t4 = lane & 3;
   const int colb[2] = {pair * 8 + g, (pair + 2) * 8 + g};  // B-fragment columns of the two blocks
-  float rp[2][4], dp[3][2][4], ls[4][2][4];
+  // accumulator entry q = 2 hn + k of block b: node mt*16 + g + 8 hn, column (pair + 2b)*8 + 2 t4 + k.
+  // r_p = sum_j D_j U_j + sum_f L_f t_f (Eq. dgLocalSchemeP) accumulates in rp; each D_j p and each
+  // L_f s_f is folded into r_v = -(1/rho) grad p - sum_f n_f (L_f s_f) (Eq. dgLocalSchemeU) as soon
+  // as it is complete.
+  float rp[2][4], rv[3][2][4];
+  int ecol[2][2];
 #pragma unroll
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < 2; ++b) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) ecol[b][k] = col_e((pair + 2 * b) * 8 + 2 * t4 + k);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       rp[b][q] = 0.f;
 #pragma unroll
-      for (int jd = 0; jd < 3; ++jd) dp[jd][b][q] = 0.f;
-#pragma unroll
-      for (int f = 0; f < 4; ++f) ls[f][b][q] = 0.f;
+      for (int d = 0; d < 3; ++d) rv[d][b][q] = 0.f;
     }
+  }
   {
     // operator fragments stream from L2 three steps ahead of their use; unrolled steps rotate the
     // fragment registers by renaming (a register copy would wait for the load to land)
@@ -406,6 +421,11 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
 #pragma unroll
     for (int jd = 0; jd < 3; ++jd) {
       const float* Ub = sU + jd * Np * CS;
+      float acc[2][4];
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[b][q] = 0.f;
 #pragma unroll(KUNROLL)
       for (int kb = 0; kb < KSD; ++kb) {
         const FragA F3 = next(jd * KSD + kb);
@@ -419,26 +439,42 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
         // the three split terms of four independent accumulators, interleaved
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(dp[jd][b], F0.l, ph[b]);
+          mma_tf32(acc[b], F0.l, ph[b]);
           mma_tf32(rp[b], F0.l, uh[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(dp[jd][b], F0.h, pl[b]);
+          mma_tf32(acc[b], F0.h, pl[b]);
           mma_tf32(rp[b], F0.h, ul[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(dp[jd][b], F0.h, ph[b]);
+          mma_tf32(acc[b], F0.h, ph[b]);
           mma_tf32(rp[b], F0.h, uh[b]);
         }
         F0 = F1;
         F1 = F2;
         F2 = F3;
       }
+      // r_v += (-rx_{d,jd} / rho) D_jd p
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float gvk = gcoef(9 + 3 * d + jd, ecol[b][k]);
+            rv[d][b][k] += gvk * acc[b][k];
+            rv[d][b][2 + k] += gvk * acc[b][2 + k];
+          }
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
+      float acc[2][4];
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[b][q] = 0.f;
 #pragma unroll(KUNROLL)
       for (int kb = 0; kb < KSF; ++kb) {
         const FragA F3 = next(3 * KSD + f * KSF + kb);
@@ -452,54 +488,48 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           mma_tf32(rp[b], F0.l, th[b]);
-          mma_tf32(ls[f][b], F0.l, sh[b]);
+          mma_tf32(acc[b], F0.l, sh[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           mma_tf32(rp[b], F0.h, tl[b]);
-          mma_tf32(ls[f][b], F0.h, sl[b]);
+          mma_tf32(acc[b], F0.h, sl[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           mma_tf32(rp[b], F0.h, th[b]);
-          mma_tf32(ls[f][b], F0.h, sh[b]);
+          mma_tf32(acc[b], F0.h, sh[b]);
         }
         F0 = F1;
         F1 = F2;
         F2 = F3;
       }
+      // r_v -= n_f (L_f s_f)
+#pragma unroll
+      for (int b = 0; b < 2; ++b)
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const float nfd = gcoef(18 + 3 * f + d, ecol[b][k]);
+            rv[d][b][k] -= nfd * acc[b][k];
+            rv[d][b][2 + k] -= nfd * acc[b][2 + k];
+          }
     }
   }
   __syncthreads();  // the products have read sS, sT and sU: they now hold the right-hand sides
 
   // ---------------------------------------------------------------- phase 4a: right-hand sides
-  // accumulator entry q = 2 hn + k of block b: node mt*16 + g + 8 hn, column (pair + 2b)*8 + 2 t4 + k.
-  // r_p = rp (Eq. dgLocalSchemeP); r_v = -(1/rho) grad p - sum_f n_f (L_f s_f) (Eq. dgLocalSchemeU).
 #pragma unroll
-  for (int k = 0; k < 2; ++k)
+  for (int b = 0; b < 2; ++b)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      const int cb = (pair + 2 * b) * 8 + 2 * t4 + k;
-      const int e = col_e(cb);
-      float gv[9], gn[12];
+    for (int q = 0; q < 4; ++q) {
+      const int n = mt * 16 + g + 8 * (q >> 1);
+      if (n >= Np) continue;
+      const int cb = (pair + 2 * b) * 8 + 2 * t4 + (q & 1);
+      sRhs[(0 * Np + n) * CS + cb] = rp[b][q];
 #pragma unroll
-      for (int i = 0; i < 9; ++i) gv[i] = gcoef(9 + i, e);
-#pragma unroll
-      for (int i = 0; i < 12; ++i) gn[i] = gcoef(18 + i, e);
-#pragma unroll
-      for (int hn = 0; hn < 2; ++hn) {
-        const int n = mt * 16 + g + 8 * hn;
-        if (n >= Np) continue;
-        const int q = 2 * hn + k;
-        sRhs[(0 * Np + n) * CS + cb] = rp[b][q];
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          float v = gv[3 * d + 0] * dp[0][b][q] + gv[3 * d + 1] * dp[1][b][q] + gv[3 * d + 2] * dp[2][b][q];
-#pragma unroll
-          for (int f = 0; f < 4; ++f) v -= gn[3 * f + d] * ls[f][b][q];
-          sRhs[((1 + d) * Np + n) * CS + cb] = v;
-        }
-      }
+      for (int d = 0; d < 3; ++d) sRhs[((1 + d) * Np + n) * CS + cb] = rv[d][b][q];
     }
   cp_async_wait_all();  // the history slots and image tiles
   __syncthreads();
@@ -508,6 +538,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, 2) dg_step_kernel_tc(const Ste
   // thread per (node, element), all wavefields: point injections, the images from the fields and
   // histories at t_start (Eq. updateABcorr), the new fields (Eq. updateAB) and the half-step fields
   // (Eq. updateABcoarse); global stores are 32 consecutive columns per warp.
+#pragma unroll 2
   for (int i = tid; i < Np * EPB; i += NT) {
     const int n = i / EPB, e = i - n * EPB;
     const bool ok = (sMeta[e] & kMetaValid) != 0;
