@@ -387,8 +387,13 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   const int lane = tid & 31, wid = tid >> 5;
   const int mt = wid >> 1, pair = wid & 1;
   const int g = lane >> 2, t4 = lane & 3;
-  const int colb[2] = {pair * 8 + g, (pair + 2) * 8 + g};  // B-fragment columns of the two blocks
-  // accumulator entry q = 2 hn + k of block b: node mt*16 + g + 8 hn, column (pair + 2b)*8 + 2 t4 + k.
+  // Column block beta (0..3) holds the data columns 4 beta + {0..3} and 16 + 4 beta + {0..3}; fragment
+  // column n of block beta is data column bcol(beta, n).  With rows of 36 floats this makes every
+  // B-fragment load (lanes: row t4 or t4 + 4, column bcol(g)) hit 32 distinct banks.  Warp pair
+  // takes blocks pair and pair + 2.
+  auto bcol = [](int beta, int n) { return 4 * beta + (n & 3) + 16 * (n >> 2); };
+  const int colb[2] = {bcol(pair, g), bcol(pair + 2, g)};  // B-fragment columns of the two blocks
+  // accumulator entry q = 2 hn + k of block b: node mt*16 + g + 8 hn, column bcol(pair + 2b, 2 t4 + k).
   // r_p = sum_j D_j U_j + sum_f L_f t_f (Eq. dgLocalSchemeP) accumulates in rp; each D_j p and each
   // L_f s_f is folded into r_v = -(1/rho) grad p - sum_f n_f (L_f s_f) (Eq. dgLocalSchemeU) as soon
   // as it is complete.
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
 #pragma unroll
   for (int b = 0; b < 2; ++b) {
 #pragma unroll
-    for (int k = 0; k < 2; ++k) ecol[b][k] = col_e((pair + 2 * b) * 8 + 2 * t4 + k);
+    for (int k = 0; k < 2; ++k) ecol[b][k] = col_e(bcol(pair + 2 * b, 2 * t4 + k));
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       rp[b][q] = 0.f;
@@ -526,7 +531,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     for (int q = 0; q < 4; ++q) {
       const int n = mt * 16 + g + 8 * (q >> 1);
       if (n >= Np) continue;
-      const int cb = (pair + 2 * b) * 8 + 2 * t4 + (q & 1);
+      const int cb = bcol(pair + 2 * b, 2 * t4 + (q & 1));
       sRhs[(0 * Np + n) * CS + cb] = rp[b][q];
 #pragma unroll
       for (int d = 0; d < 3; ++d) sRhs[((1 + d) * Np + n) * CS + cb] = rv[d][b][q];
@@ -535,13 +540,26 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   __syncthreads();
 
   // ---------------------------------------------------------------- phase 4b: update
-  // thread per (node, element), all wavefields: point injections, the images from the fields and
-  // histories at t_start (Eq. updateABcorr), the new fields (Eq. updateAB) and the half-step fields
-  // (Eq. updateABcoarse); global stores are 32 consecutive columns per warp.
+  // thread per (node, element), all its wavefields: point injections, the images from the fields
+  // and histories at t_start (Eq. updateABcorr), the new fields (Eq. updateAB) and the half-step
+  // fields (Eq. updateABcoarse).  One wavefield: a warp per node row.  Two: the half-warps take
+  // rows n and n + 4 (36-float rows: disjoint banks).  Shared-memory accesses are conflict-free and
+  // global stores are 32 (or 2 x 16) consecutive columns.
+  constexpr int NE = W == 1 ? Np * 32 : 4 * ((Np + 7) / 8) * 32;  // entry slots
 #pragma unroll 2
-  for (int i = tid; i < Np * EPB; i += NT) {
-    const int n = i / EPB, e = i - n * EPB;
+  for (int i = tid; i < NE; i += NT) {
+    int n, e;
+    if (W == 1) {
+      n = i >> 5;
+      e = i & 31;
+    } else {
+      const int j = i >> 5;
+      n = 8 * (j >> 2) + (j & 3) + 4 * ((i >> 4) & 1);
+      e = i & 15;
+      if (n >= Np) continue;
+    }
     const bool ok = (sMeta[e] & kMetaValid) != 0;
+    const int64_t gofs = ((blk * 4) * Np + n) * 32 + lane0 + e;
     float r[W][4], q0[W][4], r1[W][4], r2[W][4];
 #pragma unroll
     for (int w = 0; w < W; ++w) {
@@ -576,7 +594,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     if (rhs_only) {
       if (ok)
 #pragma unroll
-        for (int fld = 0; fld < 4; ++fld) A.rhs_out[((blk * 4 + fld) * Np + n) * 32 + lane0 + e] = r[0][fld];
+        for (int fld = 0; fld < 4; ++fld) A.rhs_out[gofs + fld * Np * 32] = r[0][fld];
       continue;
     }
 #pragma unroll
@@ -588,9 +606,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
           r1[w][fld] = sR1[sidx];
           r2[w][fld] = sR2[sidx];
         } else {
-          const int64_t off = ((blk * 4 + fld) * Np + n) * 32 + lane0 + e;
-          r1[w][fld] = A.wave[w].ring[r1i * qsize + off];
-          r2[w][fld] = A.wave[w].ring[r2i * qsize + off];
+          r1[w][fld] = A.wave[w].ring[r1i * qsize + gofs + fld * Np * 32];
+          r2[w][fld] = A.wave[w].ring[r2i * qsize + gofs + fld * Np * 32];
         }
       }
     // images from the fields and histories at t_start, before the update
@@ -598,17 +615,13 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       const int wR = W - 1;  // receiver wavefield (1 when W == 2)
       const float Z = gcoef(46, e);
       const float* eu = A.e_up;
+      auto up = [&](const float* x) { return eu[0] * x[1] + eu[1] * x[2] + eu[2] * x[3]; };
       const float xS = q0[0][0], xR = q0[wR][0];
-      const float vS = eu[0] * q0[0][1] + eu[1] * q0[0][2] + eu[2] * q0[0][3];
-      const float vR = eu[0] * q0[wR][1] + eu[1] * q0[wR][2] + eu[2] * q0[wR][3];
+      const float vS = up(q0[0]), vR = up(q0[wR]);
       const float rS[3] = {r[0][0], r1[0][0], r2[0][0]};
       const float rR[3] = {r[wR][0], r1[wR][0], r2[wR][0]};
-      const float sS3[3] = {rS[0] - Z * (eu[0] * r[0][1] + eu[1] * r[0][2] + eu[2] * r[0][3]),
-                            rS[1] - Z * (eu[0] * r1[0][1] + eu[1] * r1[0][2] + eu[2] * r1[0][3]),
-                            rS[2] - Z * (eu[0] * r2[0][1] + eu[1] * r2[0][2] + eu[2] * r2[0][3])};
-      const float sR3[3] = {rR[0] + Z * (eu[0] * r[wR][1] + eu[1] * r[wR][2] + eu[2] * r[wR][3]),
-                            rR[1] + Z * (eu[0] * r1[wR][1] + eu[1] * r1[wR][2] + eu[2] * r1[wR][3]),
-                            rR[2] + Z * (eu[0] * r2[wR][1] + eu[1] * r2[wR][2] + eu[2] * r2[wR][3])};
+      const float sS3[3] = {rS[0] - Z * up(r[0]), rS[1] - Z * up(r1[0]), rS[2] - Z * up(r2[0])};
+      const float sR3[3] = {rR[0] + Z * up(r[wR]), rR[1] + Z * up(r1[wR]), rR[2] + Z * up(r2[wR])};
       const float cc[3] = {float(AB::c1), float(AB::c2), float(AB::c3)};
       const float C[3][3] = {{float(4703.0 / 5040.0), float(-457.0 / 840.0), float(52.0 / 315.0)},
                              {float(-457.0 / 840.0), float(103.0 / 315.0), float(-251.0 / 2520.0)},
@@ -633,7 +646,6 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      const int64_t gofs = ((blk * 4) * Np + n) * 32 + lane0 + e;
       float* qg = A.wave[w].q + gofs;
       float* rg = A.wave[w].ring + rn * qsize + gofs;
 #pragma unroll
