@@ -117,11 +117,12 @@ def step_bytes_per_element(Np, Nfp, W, real_bytes=4):
 
     Per wavefield: q read + write (8 Np), two older right-hand sides read and the new one written
     (12 Np), the face inbox read and the traces pushed to the neighbours (2 x 8 Nfp), injection
-    range (8 B).  Per element: the FP32 coefficient table (48 floats: geometric factors, normals,
-    penalty coefficients, impedance), connectivity and flags (4 neighbour slots + 4 face bytes +
-    boundary index + flags = 28 B); with W = 2 the two FP64 images are read and written (32 Np B)."""
+    range (8 B).  Per element: the FP32 coefficient table (56 floats: geometric factors, impedance,
+    normals and penalty coefficients in 16-byte groups), connectivity and flags (4 neighbour slots +
+    4 face bytes + boundary index + flags = 28 B); with W = 2 the two FP64 images are read and
+    written (32 Np B)."""
     per_wave = (20 * Np + 16 * Nfp) * real_bytes + 8
-    per_elem = 48 * 4 + 28
+    per_elem = 56 * 4 + 28
     img = 32 * Np if W == 2 else 0
     return W * per_wave + per_elem + img
 

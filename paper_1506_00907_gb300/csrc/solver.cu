@@ -621,33 +621,33 @@ class Engine final : public ridg_solver {
   }
 
   // Per-element coefficients of the FP32 tensor-core kernel for penalty sign `sigma` (Eq. penaltyFlux
-  // with tau negated in backward runs), [n_slots/32][kGtab][32]: -rho c^2 rx_ij (volume p equation,
-  // Eq. dgLocalSchemeP), -rx_ij / rho (volume v equation, Eq. dgLocalSchemeU), the outward normals, per
-  // face the coefficients of t = A [n.v] + B [p] and s = C [p] + D [n.v] with the surface Jacobian and the
-  // 1/2 of the weak form folded in, and rho c.
+  // with tau negated in backward runs), [n_slots][kGtab]: -rho c^2 rx_ij (volume p equation,
+  // Eq. dgLocalSchemeP), rho c, -rx_ij / rho (volume v equation, Eq. dgLocalSchemeU), the outward
+  // normals, and per face the coefficients of t = A [n.v] + B [p] and s = C [p] + D [n.v] with the
+  // surface Jacobian and the 1/2 of the weak form folded in.
   std::vector<float> coefficient_table(int sigma) const {
     const int64_t S = n_slots_;
     std::vector<float> g(size_t(S) * kGtab, 0.f);
     for (int64_t s = 0; s < S; ++s) {
       int64_t k = ord_.elem_of[s];
       if (k < 0) continue;
-      auto at = [&](int i) -> float& { return g[size_t(((s >> 5) * kGtab + i) * 32 + (s & 31))]; };
+      float* at = &g[size_t(s) * kGtab];
       const double rho = rho_[k], c = c_[k], rc2 = rho * c * c, irho = 1.0 / rho, Zk = rho * c;
       for (int i = 0; i < 9; ++i) {
-        at(i) = float(-rc2 * geo_.rx[9 * k + i]);
-        at(9 + i) = float(-irho * geo_.rx[9 * k + i]);
+        at[kGtU + i] = float(-rc2 * geo_.rx[9 * k + i]);
+        at[kGtV + i] = float(-irho * geo_.rx[9 * k + i]);
       }
-      for (int i = 0; i < 12; ++i) at(18 + i) = float(geo_.normal[12 * k + i]);
+      at[kGtZ] = float(Zk);
       for (int f = 0; f < 4; ++f) {
+        for (int d = 0; d < 3; ++d) at[kGtN + 4 * f + d] = float(geo_.normal[12 * k + 3 * f + d]);
         int64_t k2 = mesh_.nbr[4 * k + f];
         double Zb = k2 >= 0 ? 0.5 * (Zk + rho_[k2] * c_[k2]) : Zk;
         double fs = geo_.fscale[4 * k + f], taup = sigma / Zb, tauv = sigma * Zb;
-        at(30 + 4 * f + 0) = float(-0.5 * fs * rc2);
-        at(30 + 4 * f + 1) = float(0.5 * fs * rc2 * taup);
-        at(30 + 4 * f + 2) = float(0.5 * fs * irho);
-        at(30 + 4 * f + 3) = float(-0.5 * fs * irho * tauv);
+        at[kGtP + 4 * f + 0] = float(-0.5 * fs * rc2);
+        at[kGtP + 4 * f + 1] = float(0.5 * fs * rc2 * taup);
+        at[kGtP + 4 * f + 2] = float(0.5 * fs * irho);
+        at[kGtP + 4 * f + 3] = float(-0.5 * fs * irho * tauv);
       }
-      at(46) = float(Zk);
     }
     return g;
   }

@@ -53,9 +53,11 @@ constexpr int kModeRhsOnly = 8;  // only write the right-hand side to rhs_out
 constexpr int kGeo = 25;
 // per-element material (working precision): rho c^2, 1/rho, rho c, tau_p[4], tau_v[4]
 constexpr int kMat = 11;
-// per-element coefficients of the FP32 tensor-core kernel: -rho c^2 rx[9], -rx/rho[9], normal[12],
-// penalty coefficients [4 faces][4], rho c, one spare
-constexpr int kGtab = 48;
+// per-element coefficients of the FP32 tensor-core kernel, in 16-byte groups: -rho c^2 rx[9] and
+// rho c at kGtU; -rx/rho[9] at kGtV; per face (normal, 0) at kGtN + 4 f and the penalty
+// coefficients (A, B, C, D) at kGtP + 4 f
+constexpr int kGtU = 0, kGtZ = 9, kGtV = 12, kGtN = 24, kGtP = 40;
+constexpr int kGtab = 56;
 
 template <typename real>
 struct WaveArgs {
@@ -110,7 +112,7 @@ struct StepArgs {
   const int* perm;       // [6][32]
   real* rhs_out;         // kModeRhsOnly: q-sized
   const uint32_t* afrag; // tensor-core variant: operator fragments (TF32 hi/lo), see step_kernel_tc.cuh
-  const float* gtab;     // tensor-core variant: per-element coefficients [n_slots/32][kGtab][32] (this tau sign)
+  const float* gtab;     // tensor-core variant: per-element coefficients [n_slots][kGtab] (this tau sign)
 };
 
 template <int N>

@@ -118,8 +118,8 @@ struct SmemTc {
   static constexpr int NFPP = O::NFPP;
   static constexpr int XR = 32 * 8 * NFPP;  // face inboxes of the 32 columns
   static constexpr int UX = (3 * Np * CS > XR) ? 3 * Np * CS : XR;
-  static constexpr int GS = EPB + 4;                           // coefficient rows (16-byte aligned, skewed banks)
-  static constexpr int G = kGtab * GS;                         // coefficients [kGtab][GS]
+  static constexpr int GS = kGtab + 4;  // coefficient rows: 16-byte aligned, 16-byte loads over lanes conflict-free
+  static constexpr int G = EPB * GS;     // coefficients [EPB][GS]
   static constexpr int IMG = (W == 2) ? 2 * 2 * Np * EPB : 0;  // two FP64 image tiles, in floats
   static constexpr int INTS = 4 * EPB + EPB + EPB + EPB + 128 + 192 + 4 * EPB;  // nbr, finfo bytes, bface, meta, ...
   static constexpr size_t bytes_with(bool ring) {
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   float* sT = sS + SM::ST;                         // [4*Nfp][CS]
   float* sU = sT + SM::ST;                         // [3][Np][CS]
   float* sX = sU;                                  // [32 columns][4][2][NFPP] face inboxes (before U)
-  float* sG = sU + SM::UX;                         // [kGtab][GS]
+  float* sG = sU + SM::UX;                         // [EPB][GS]
   double* sImg = reinterpret_cast<double*>(sG + SM::G);  // W == 2: [2][Np][EPB] image tiles
   int* sI = reinterpret_cast<int*>(sG + SM::G + SM::IMG);
   int* sNbr = sI;                                           // [EPB][4]
@@ -179,7 +179,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   // column c -> (element, wavefield)
   auto col_e = [](int c) { return W == 1 ? c : (c & 15); };
   auto col_w = [](int c) { return W == 1 ? 0 : (c >> 4); };
-  auto gcoef = [&](int k, int e) { return sG[k * GS + e]; };
+  auto gcoef = [&](int k, int e) { return sG[e * GS + k]; };
+  auto gcoef4 = [&](int k, int e) { return *reinterpret_cast<const float4*>(sG + e * GS + k); };
 
   // ---------------------------------------------------------------- phase 1: asynchronous loads
   // group 0, nothing depends on anything: the tables, the coefficients, the fields at t_start and
@@ -208,9 +209,10 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
         for (int i = tid; i < EPB; i += NT) sInj[w * EPB + i] = make_int2(0, 0);
       }
     }
-    for (int i = tid; i < kGtab * CPR; i += NT) {
-      const int row = i / CPR, ch = i - row * CPR;
-      cp_async_bytes16(sG + row * GS + ch * 4, A.gtab + (blk * kGtab + row) * 32 + lane0 + ch * 4);
+    constexpr int CPE = kGtab / 4;  // 16-byte chunks per element
+    for (int i = tid; i < EPB * CPE; i += NT) {
+      const int e = i / CPE, ch = i - e * CPE;
+      cp_async_bytes16(sG + e * GS + ch * 4, A.gtab + (slot0 + e) * kGtab + ch * 4);
     }
     constexpr int PER = 4 * Np * 8;  // 16-byte chunks of one field array (8 per 32-column row)
     for (int i = tid; i < PER; i += NT) {
@@ -308,9 +310,9 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       const int e = col_e(c), w = col_w(c);
       const bool valid = (sMeta[e] & kMetaValid) != 0;
       const int bc = finfo_bc(sInfo[e * 4 + f]);
-      const float n0 = gcoef(18 + 3 * f, e), n1 = gcoef(19 + 3 * f, e), n2 = gcoef(20 + 3 * f, e);
-      const float pa = gcoef(30 + 4 * f, e), pb = gcoef(31 + 4 * f, e), pcc = gcoef(32 + 4 * f, e),
-                  pd = gcoef(33 + 4 * f, e);
+      const float4 nf = gcoef4(kGtN + 4 * f, e), pf = gcoef4(kGtP + 4 * f, e);
+      const float n0 = nf.x, n1 = nf.y, n2 = nf.z;
+      const float pa = pf.x, pb = pf.y, pcc = pf.z, pd = pf.w;
       recu[u] = bc != 0 && valid && w == 0 && (A.mode & kModeRecord);
       const bool ext = bc == 0 || (w == 0 && (A.mode & kModeReplay));
       const float* xb = sX + c * (8 * NFPP) + f * 2 * NFPP;
@@ -377,9 +379,12 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     int c = i & 31, m = i >> 5;
     const int e = col_e(c);
     float vx = sQ[(1 * Np + m) * CS + c], vy = sQ[(2 * Np + m) * CS + c], vz = sQ[(3 * Np + m) * CS + c];
-#pragma unroll
-    for (int jd = 0; jd < 3; ++jd)
-      sU[(jd * Np + m) * CS + c] = gcoef(0 + jd, e) * vx + gcoef(3 + jd, e) * vy + gcoef(6 + jd, e) * vz;
+    const float4 g0 = gcoef4(kGtU, e), g1 = gcoef4(kGtU + 4, e);
+    const float g8 = gcoef(kGtU + 8, e);
+    // U_jd = sum_i (-rho c^2 rx_{i,jd}) v_i
+    sU[(0 * Np + m) * CS + c] = g0.x * vx + g0.w * vy + g1.z * vz;
+    sU[(1 * Np + m) * CS + c] = g0.y * vx + g1.x * vy + g1.w * vz;
+    sU[(2 * Np + m) * CS + c] = g0.z * vx + g1.y * vy + g8 * vz;
   }
   __syncthreads();
 
@@ -468,7 +473,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
         for (int k = 0; k < 2; ++k)
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const float gvk = gcoef(9 + 3 * d + jd, ecol[b][k]);
+            const float gvk = gcoef(kGtV + 3 * d + jd, ecol[b][k]);
             rv[d][b][k] += gvk * acc[b][k];
             rv[d][b][2 + k] += gvk * acc[b][2 + k];
           }
@@ -513,13 +518,15 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < 2; ++k) {
+          const float4 nf = gcoef4(kGtN + 4 * f, ecol[b][k]);
+          const float nfd[3] = {nf.x, nf.y, nf.z};
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const float nfd = gcoef(18 + 3 * f + d, ecol[b][k]);
-            rv[d][b][k] -= nfd * acc[b][k];
-            rv[d][b][2 + k] -= nfd * acc[b][2 + k];
+            rv[d][b][k] -= nfd[d] * acc[b][k];
+            rv[d][b][2 + k] -= nfd[d] * acc[b][2 + k];
           }
+        }
     }
   }
   __syncthreads();  // the products have read sS, sT and sU: they now hold the right-hand sides
@@ -613,7 +620,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     // images from the fields and histories at t_start, before the update
     if (W == 2 && (A.mode & kModeImage) && ok) {
       const int wR = W - 1;  // receiver wavefield (1 when W == 2)
-      const float Z = gcoef(46, e);
+      const float Z = gcoef(kGtZ, e);
       const float* eu = A.e_up;
       auto up = [&](const float* x) { return eu[0] * x[1] + eu[1] * x[2] + eu[2] * x[3]; };
       const float xS = q0[0][0], xR = q0[wR][0];
@@ -683,7 +690,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       const int meta = sMeta[e];
       const int info = sInfo[e * 4 + f];
       if (!(meta & kMetaValid) || finfo_bc(uint8_t(info)) != 0) continue;
-      const float n0 = gcoef(18 + 3 * f, e), n1 = gcoef(19 + 3 * f, e), n2 = gcoef(20 + 3 * f, e);
+      const float4 nf = gcoef4(kGtN + 4 * f, e);
+      const float n0 = nf.x, n1 = nf.y, n2 = nf.z;
       const int64_t s2 = sNbr[e * 4 + f];
       const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
       const int64_t fo = s2 * (8 * NFPP) + finfo_face(uint8_t(info)) * 2 * NFPP;
