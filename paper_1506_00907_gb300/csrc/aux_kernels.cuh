@@ -91,16 +91,16 @@ __global__ void energy_kernel(const real* __restrict__ q, int64_t n_slots, const
 
 // Image from the slot layout [n_slots/32][Np][32] to element order [K][Np].
 template <int N>
-__global__ void image_to_elements_kernel(const double* __restrict__ img, const int64_t* __restrict__ slot_of, int64_t K,
-                                         double* __restrict__ out) {
+__global__ void image_to_elements_kernel(const double* __restrict__ img, const int64_t* __restrict__ slot_of,
+                                         const int* __restrict__ pos_of, int64_t K, double* __restrict__ out) {
   using O = Order<N>;
   constexpr int Np = O::Np;
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= K * Np) return;
   int64_t k = i / Np;
-  int n = int(i - k * Np);
+  int n = int(i - k * Np);  // reference numbering; pos_of[n] is the node's place in the slot layout
   int64_t s = slot_of[k];
-  out[i] = img[((s >> 5) * Np + n) * 32 + (s & 31)];
+  out[i] = img[((s >> 5) * Np + pos_of[n]) * 32 + (s & 31)];
 }
 
 }  // namespace ridg

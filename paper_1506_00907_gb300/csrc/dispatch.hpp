@@ -16,7 +16,8 @@ struct Launch {
                             int64_t n_time, int64_t col, cudaStream_t st);
   static cudaError_t energy(const real* q, int64_t n_slots, const double* J, const real* mat, const int* meta,
                             const double* M, double* out, cudaStream_t st);
-  static cudaError_t image_out(const double* img, const int64_t* slot_of, int64_t K, double* out, cudaStream_t st);
+  static cudaError_t image_out(const double* img, const int64_t* slot_of, const int* pos_of, int64_t K, double* out,
+                               cudaStream_t st);
 };
 
 }  // namespace ridg

@@ -345,6 +345,90 @@ RefElem build_reference(int N) {
   return re;
 }
 
+RefElem permute_nodes(const RefElem& re, const std::vector<int>& order) {
+  const int Np = re.Np;
+  if (int(order.size()) != Np) throw Error{RIDG_E_INVALID_ARG, "node order size mismatch"};
+  std::vector<int> pos(Np, -1);
+  for (int p = 0; p < Np; ++p) {
+    if (order[p] < 0 || order[p] >= Np || pos[order[p]] >= 0) throw Error{RIDG_E_INVALID_ARG, "not a node permutation"};
+    pos[order[p]] = p;
+  }
+  RefElem out = re;
+  for (int p = 0; p < Np; ++p) {
+    out.rst[p] = re.rst[order[p]];
+    out.lattice[p] = re.lattice[order[p]];
+    for (int q = 0; q < Np; ++q) {
+      for (int d = 0; d < 3; ++d) out.D[d](p, q) = re.D[d](order[p], order[q]);
+      out.M(p, q) = re.M(order[p], order[q]);
+      out.Minv(p, q) = re.Minv(order[p], order[q]);
+      out.V(p, q) = re.V(order[p], q);     // rows: nodes, columns: basis functions
+      out.Vinv(q, p) = re.Vinv(q, order[p]);
+    }
+    for (int fm = 0; fm < 4 * re.Nfp; ++fm) out.LIFT(p, fm) = re.LIFT(order[p], fm);
+  }
+  for (int f = 0; f < 4; ++f)
+    for (int j = 0; j < re.Nfp; ++j) out.fmask[f][j] = pos[re.fmask[f][j]];
+  return out;
+}
+
+std::vector<int> bank_spread_order(const RefElem& re) {
+  const int Np = re.Np, Nfp = re.Nfp;
+  std::vector<int> order(Np);
+  for (int p = 0; p < Np; ++p) order[p] = p;
+  if (Np <= 8) return order;
+  // faces of each node
+  std::vector<std::vector<int>> faces_of(Np);
+  for (int f = 0; f < 4; ++f)
+    for (int j = 0; j < Nfp; ++j) faces_of[re.fmask[f][j]].push_back(f);
+  // cost: sum over faces and classes of (face nodes in the class)^2, minimal for an even spread
+  auto cost_of = [&](const std::vector<int>& ord) {
+    int cnt[4][8] = {};
+    for (int p = 0; p < Np; ++p)
+      for (int f : faces_of[ord[p]]) ++cnt[f][p & 7];
+    int c = 0, mx = 0;
+    for (int f = 0; f < 4; ++f)
+      for (int k = 0; k < 8; ++k) {
+        c += cnt[f][k] * cnt[f][k];
+        mx = std::max(mx, cnt[f][k]);
+      }
+    return 1000 * mx + c;
+  };
+  // deterministic restarts of a pairwise-swap descent
+  std::vector<int> best = order;
+  int best_cost = cost_of(best);
+  uint64_t rng = 0x9e3779b97f4a7c15ull;
+  for (int restart = 0; restart < 16; ++restart) {
+    std::vector<int> cur(Np);
+    for (int p = 0; p < Np; ++p) cur[p] = p;
+    if (restart > 0)
+      for (int p = Np - 1; p > 0; --p) {
+        rng = rng * 6364136223846793005ull + 1442695040888963407ull;
+        std::swap(cur[p], cur[int((rng >> 33) % uint64_t(p + 1))]);
+      }
+    int c = cost_of(cur);
+    for (bool improved = true; improved;) {
+      improved = false;
+      for (int i = 0; i < Np; ++i)
+        for (int j = i + 1; j < Np; ++j) {
+          if ((i & 7) == (j & 7)) continue;
+          std::swap(cur[i], cur[j]);
+          int c2 = cost_of(cur);
+          if (c2 < c) {
+            c = c2;
+            improved = true;
+          } else {
+            std::swap(cur[i], cur[j]);
+          }
+        }
+    }
+    if (c < best_cost) {
+      best_cost = c;
+      best = cur;
+    }
+  }
+  return best;
+}
+
 // ------------------------------------------------------------------ mesh and connectivity
 MeshData build_mesh(const double* xyz, int64_t n_vert, const int64_t* tet, int64_t K, const int8_t* face_bc,
                     int8_t default_bc) {

@@ -50,6 +50,14 @@ struct RefElem {
   std::vector<double> lagrange_at(const std::array<double, 3>& p) const;    // l(p), size Np
 };
 RefElem build_reference(int N);
+// The same reference element with its nodes renumbered: node p of the result is node order[p] of re
+// (operators, mass matrices, LIFT rows, face masks and the Lagrange basis follow).
+RefElem permute_nodes(const RefElem& re, const std::vector<int>& order);
+// A node numbering under which the Nfp nodes of every face spread as evenly as possible over the
+// eight classes p mod 8 (order[p] = node of re at position p).  In shared-memory rows of 4 (mod 32)
+// words, node rows of one class share a bank group, so a face-node gather over one column costs
+// as many bank wavefronts as the fullest class holds face nodes.
+std::vector<int> bank_spread_order(const RefElem& re);
 std::vector<double> gauss_lobatto(int N);
 
 // The six orderings of a triangle's vertices: kTriPerm[code][x] = index (in the local face's

@@ -127,7 +127,15 @@ class Engine final : public ridg_solver {
  public:
   Engine(const MeshData& mesh, int N, const double* c, const double* rho, const ridg_options& opt, cudaStream_t st)
       : mesh_(mesh), N_(N), st_(st) {
-    ref_ = build_reference(N);
+    {
+      // the device numbers the element's nodes so that face-node gathers spread over the banks;
+      // every array that crosses the C ABI stays in the reference numbering
+      RefElem r0 = build_reference(N);
+      std::vector<int> order = bank_spread_order(r0);
+      ref_ = permute_nodes(r0, order);
+      pos_of_.assign(order.size(), 0);
+      for (int p = 0; p < int(order.size()); ++p) pos_of_[order[p]] = p;
+    }
     Np_ = ref_.Np;
     Nfp_ = ref_.Nfp;
     NFPP_ = Nfp_ <= 16 ? 16 : 32;
@@ -201,7 +209,11 @@ class Engine final : public ridg_solver {
   void levels(int32_t* out) const override {
     for (int64_t k = 0; k < mesh_.K; ++k) out[k] = lv_.level[k];
   }
-  void nodes(double* out) const override { std::memcpy(out, xnodes_.data(), xnodes_.size() * sizeof(double)); }
+  void nodes(double* out) const override {
+    for (int64_t k = 0; k < mesh_.K; ++k)
+      for (int n = 0; n < Np_; ++n)
+        for (int d = 0; d < 3; ++d) out[(k * Np_ + n) * 3 + d] = xnodes_[(k * Np_ + pos_of_[n]) * 3 + d];
+  }
 
   // ------------------------------------------------------------------ state
   void set_state(const double* q) override {
@@ -488,7 +500,8 @@ class Engine final : public ridg_solver {
     for (int64_t k = 0; k < mesh_.K; ++k) {
       int64_t s = ord_.slot_of[k];
       for (int f = 0; f < 4; ++f)
-        for (int n = 0; n < Np_; ++n) h[(((s >> 5) * 4 + f) * Np_ + n) * 32 + (s & 31)] = real(q[(k * 4 + f) * Np_ + n]);
+        for (int n = 0; n < Np_; ++n)
+          h[(((s >> 5) * 4 + f) * Np_ + pos_of_[n]) * 32 + (s & 31)] = real(q[(k * 4 + f) * Np_ + n]);
     }
     return h;
   }
@@ -496,7 +509,8 @@ class Engine final : public ridg_solver {
     for (int64_t k = 0; k < mesh_.K; ++k) {
       int64_t s = ord_.slot_of[k];
       for (int f = 0; f < 4; ++f)
-        for (int n = 0; n < Np_; ++n) q[(k * 4 + f) * Np_ + n] = double(h[(((s >> 5) * 4 + f) * Np_ + n) * 32 + (s & 31)]);
+        for (int n = 0; n < Np_; ++n)
+          q[(k * 4 + f) * Np_ + n] = double(h[(((s >> 5) * 4 + f) * Np_ + pos_of_[n]) * 32 + (s & 31)]);
     }
   }
 
@@ -615,6 +629,7 @@ class Engine final : public ridg_solver {
     upload(fmask_d_, fm, st_);
     upload(perm_d_, pm, st_);
     upload(M_d_, ref_.M.a, st_);
+    upload(pos_d_, pos_of_, st_);
     upload(slot_of_d_, ord_.slot_of, st_);
     level_count_.assign(L_, 0);
     for (int64_t k = 0; k < mesh_.K; ++k) level_count_[lv_.level[k] - 1]++;
@@ -863,7 +878,8 @@ class Engine final : public ridg_solver {
 
   void image_out(const double* img, double* out) {
     cudaError_t e = dispatch_order(N_, [&](auto NC) {
-      return Launch<decltype(NC)::value, real>::image_out(img, dptr<const int64_t>(slot_of_d_), mesh_.K, out, st_);
+      return Launch<decltype(NC)::value, real>::image_out(img, dptr<const int64_t>(slot_of_d_), dptr<const int>(pos_d_),
+                                                           mesh_.K, out, st_);
     });
     if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
     ++stats_.kernel_launches;
@@ -898,7 +914,8 @@ class Engine final : public ridg_solver {
   std::vector<int> bface_host_;
   std::vector<int64_t> level_count_;
   DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
-  DBuf afrag_d_, gtab_d_[2];
+  DBuf afrag_d_, gtab_d_[2], pos_d_;
+  std::vector<int> pos_of_;  // device position of each reference node
   DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_;
   Wave<real> w_[2];
   int64_t tau_ = 0, dof_ = 0;

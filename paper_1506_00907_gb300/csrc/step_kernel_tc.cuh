@@ -119,7 +119,7 @@ struct SmemTc {
   static constexpr int XR = 32 * 8 * NFPP;  // face inboxes of the 32 columns
   static constexpr int UX = (3 * Np * CS > XR) ? 3 * Np * CS : XR;
   static constexpr int GS = kGtab + 4;  // coefficient rows: 16-byte aligned, 16-byte loads over lanes conflict-free
-  static constexpr int G = EPB * GS;     // coefficients [EPB][GS]
+  static constexpr int G = EPB * GS + 4;  // coefficients [EPB][GS], rows 16.. shifted by 4 words (see grow)
   static constexpr int IMG = (W == 2) ? 2 * 2 * Np * EPB : 0;  // two FP64 image tiles, in floats
   static constexpr int INTS = 4 * EPB + EPB + EPB + EPB + 128 + 192 + 4 * EPB;  // nbr, finfo bytes, bface, meta, ...
   static constexpr size_t bytes_with(bool ring) {
@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   float* sT = sS + SM::ST;                         // [4*Nfp][CS]
   float* sU = sT + SM::ST;                         // [3][Np][CS]
   float* sX = sU;                                  // [32 columns][4][2][NFPP] face inboxes (before U)
-  float* sG = sU + SM::UX;                         // [EPB][GS]
+  float* sG = sU + SM::UX;                         // [EPB][GS] (+4)
   double* sImg = reinterpret_cast<double*>(sG + SM::G);  // W == 2: [2][Np][EPB] image tiles
   int* sI = reinterpret_cast<int*>(sG + SM::G + SM::IMG);
   int* sNbr = sI;                                           // [EPB][4]
@@ -179,8 +179,10 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   // column c -> (element, wavefield)
   auto col_e = [](int c) { return W == 1 ? c : (c & 15); };
   auto col_w = [](int c) { return W == 1 ? 0 : (c >> 4); };
-  auto gcoef = [&](int k, int e) { return sG[e * GS + k]; };
-  auto gcoef4 = [&](int k, int e) { return *reinterpret_cast<const float4*>(sG + e * GS + k); };
+  // coefficient row of element e; elements e and e + 16 (read together by the folds) sit 4 banks apart
+  auto grow = [](int e) { return e * GS + ((e >> 4) << 2); };
+  auto gcoef = [&](int k, int e) { return sG[grow(e) + k]; };
+  auto gcoef4 = [&](int k, int e) { return *reinterpret_cast<const float4*>(sG + grow(e) + k); };
 
   // ---------------------------------------------------------------- phase 1: asynchronous loads
   // group 0, nothing depends on anything: the tables, the coefficients, the fields at t_start and
@@ -212,7 +214,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     constexpr int CPE = kGtab / 4;  // 16-byte chunks per element
     for (int i = tid; i < EPB * CPE; i += NT) {
       const int e = i / CPE, ch = i - e * CPE;
-      cp_async_bytes16(sG + e * GS + ch * 4, A.gtab + (slot0 + e) * kGtab + ch * 4);
+      cp_async_bytes16(sG + grow(e) + ch * 4, A.gtab + (slot0 + e) * kGtab + ch * 4);
     }
     constexpr int PER = 4 * Np * 8;  // 16-byte chunks of one field array (8 per 32-column row)
     for (int i = tid; i < PER; i += NT) {
