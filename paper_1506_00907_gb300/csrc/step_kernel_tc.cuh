@@ -33,6 +33,7 @@ struct TcOrder {
   // 4 lo; steps jd * KSD + kb (D_jd, k-step kb) then 3 KSD + f * KSF + kb (LIFT block f)
   static constexpr int NSTEP = 3 * KSD + 4 * KSF;
   static constexpr int FRAG = MT * NSTEP * 32 * 8;
+  static constexpr int LAST_ROWS = Np - 16 * (MT - 1);  // rows of the last node tile
   // resident blocks per SM the kernel is built for (registers and shared memory are sized to it)
   static constexpr int MINB = N <= 4 ? 3 : 2;
 };
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   constexpr int Np = O::Np, Nfp = O::Nfp, NT = T::NT, NFPP = O::NFPP;
   constexpr int CS = SM::CS, EPB = SM::EPB, GS = SM::GS;
   constexpr bool RING = SM::ring_in_smem;
-  constexpr int KSD = T::KSD, KSF = T::KSF, NSTEP = T::NSTEP;
+  constexpr int MT = T::MT, KSD = T::KSD, KSF = T::KSF, NSTEP = T::NSTEP;
   // the k-steps are unrolled where the registers allow it (the two highest orders keep them rolled)
   constexpr int KUNROLL = N <= 4 ? 16 : 1;
 
@@ -421,13 +422,24 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     // operator fragments stream from L2 three steps ahead of their use; unrolled steps rotate the
     // fragment registers by renaming (a register copy would wait for the load to land)
     const uint32_t* fr = A.afrag + mt * (NSTEP * 256);
+    // lanes whose fragment rows all lie beyond the last node (possible in the last tile) skip the
+    // load: their fragment is zero
+    const bool lane_rows = mt < MT - 1 || (lane >> 2) < T::LAST_ROWS;
+    auto fetch = [&](const uint32_t* f, FragA& a) {
+      if (lane_rows) {
+        load_a(f, lane, a);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) a.h[q] = a.l[q] = 0u;
+      }
+    };
     FragA F0, F1, F2;
-    load_a(fr, lane, F0);
-    load_a(fr + (NSTEP > 1 ? 256 : 0), lane, F1);
-    load_a(fr + (NSTEP > 2 ? 512 : 0), lane, F2);
+    fetch(fr, F0);
+    fetch(fr + (NSTEP > 1 ? 256 : 0), F1);
+    fetch(fr + (NSTEP > 2 ? 512 : 0), F2);
     auto next = [&](int s) {
       FragA F3 = F2;
-      if (s + 3 < NSTEP) load_a(fr + (s + 3) * 256, lane, F3);
+      if (s + 3 < NSTEP) fetch(fr + (s + 3) * 256, F3);
       return F3;
     };
 #pragma unroll
