@@ -332,6 +332,23 @@ def run_ridg(args):
     e2e = {"value": world * dof_shot / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": int(obs_host.nbytes),
            "d2h_bytes_per_step": int(tr_h.nbytes + ip_h.nbytes + iq_h.nbytes), "shots_per_s": world / e2e_sec}
 
+    # the stated error of the FP32 shot: the same model, source and receivers over a short record in
+    # the library's FP64 mode (itself held to the FP64 oracle at 1e-10 by the parity tests)
+    error = None
+    if rank == 0 and not args.no_error:
+        t_err = 0.01
+        s64 = ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f64", cfl=w.cfl, n_levels_max=w.n_levels_max)
+        a = s.rtm_shot(src_x, w.f0, w.t_peak, 1.0, w.receivers, t_err)
+        b = s64.rtm_shot(src_x, w.f0, w.t_peak, 1.0, w.receivers, t_err)
+        del s64
+
+        def rl2(x, y):
+            return float(np.linalg.norm(x - y) / max(np.linalg.norm(y), 1e-300))
+
+        error = {"record_s": t_err, "traces_rel_l2": rl2(a[0], b[0]), "image_p_rel_l2": rl2(a[1], b[1]),
+                 "image_q_rel_l2": rl2(a[2], b[2]),
+                 "reference": "same shot over a 0.01 s record in the library's FP64 mode"}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -346,6 +363,7 @@ def run_ridg(args):
             "wall_s": wall,
             "roofline": roofline,
             "e2e": e2e,
+            "error_vs_fp64": error,
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
@@ -393,6 +411,7 @@ def main():
     ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ridg", choices=["ridg", "reference"])
+    ap.add_argument("--no-error", action="store_true", help="skip the FP32-vs-FP64 error leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-shot", type=float, default=0.0,
                     help="run one shot of the bench workload with this record length (s) and exit (profiling case)")

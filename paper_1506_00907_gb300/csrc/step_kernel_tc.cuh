@@ -35,7 +35,7 @@ struct TcOrder {
   static constexpr int FRAG = MT * NSTEP * 32 * 8;
   static constexpr int LAST_ROWS = Np - 16 * (MT - 1);  // rows of the last node tile
   // resident blocks per SM the kernel is built for (registers and shared memory are sized to it)
-  static constexpr int MINB = N <= 4 ? 3 : 2;
+  static constexpr int MINB = N <= 4 ? 3 : (N == 5 ? 2 : 1);
 };
 
 struct FragA {
