@@ -42,12 +42,6 @@ struct FragA {
   uint32_t h[4], l[4];
 };
 
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
-  return r;
-}
-
 __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], const uint32_t b[2]) {
   asm(
       "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -61,14 +55,6 @@ __device__ __forceinline__ void mma_tf32(float c[4], const uint32_t a[4], const 
 __device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
   hi = __float_as_uint(x) & 0xffffe000u;
   lo = __float_as_uint(x - __uint_as_float(hi)) & 0xffffe000u;
-}
-
-// acc += A * B with A = (a_hi, a_lo), B = (b_hi, b_lo): small terms first
-__device__ __forceinline__ void mma3(float c[4], const uint32_t ah[4], const uint32_t al[4], const uint32_t bh[2],
-                                     const uint32_t bl[2]) {
-  mma_tf32(c, al, bh);
-  mma_tf32(c, ah, bl);
-  mma_tf32(c, ah, bh);
 }
 
 // B fragment (8 x 8, column major) of rows kb*8 + t, kb*8 + t + 4 (valid below kvalid) and column
@@ -93,19 +79,6 @@ __device__ __forceinline__ void load_a(const uint32_t* frag, int lane, FragA& a)
   a.l[1] = l.y;
   a.l[2] = l.z;
   a.l[3] = l.w;
-}
-
-__device__ __forceinline__ void load_a(const uint32_t* frag, int lane, uint32_t ah[4], uint32_t al[4]) {
-  const uint4* p = reinterpret_cast<const uint4*>(frag + lane * 8);
-  uint4 h = __ldg(p), l = __ldg(p + 1);
-  ah[0] = h.x;
-  ah[1] = h.y;
-  ah[2] = h.z;
-  ah[3] = h.w;
-  al[0] = l.x;
-  al[1] = l.y;
-  al[2] = l.z;
-  al[3] = l.w;
 }
 
 template <int N, int W>
