@@ -2,6 +2,8 @@
 inputs, element by element, at the tolerances stated in the tests (relative L2: 1e-10 in FP64
 mode, 1e-5 in FP32)."""
 
+import functools
+
 import numpy as np
 import pytest
 
@@ -93,10 +95,12 @@ def test_config1_standing_mode_fp64():
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("N", [3, 4])
+@pytest.mark.parametrize("N", [3, 4, 5, 6])
 def test_mrab_three_levels_parity(dtype, N):
     """Multi-rate stepping with half-step traces on three levels: 4 global steps from a seeded
-    state and history."""
+    state and history (orders 5 and 6 run the tensor-core kernel with rolled k-steps)."""
+    if N == 6 and dtype == "f64":
+        pytest.skip("the FP64 tile of order 6 does not fit one block's shared memory (refused, tested above)")
     w = tiny_layered_rtm(N=N)
     fb = mixed_bc(w)
     prob = _oracle_problem(w, face_bc=fb)
@@ -117,12 +121,20 @@ def test_mrab_three_levels_parity(dtype, N):
     assert rel_l2(q_gpu, st.q) < TOL[dtype]
 
 
-@pytest.mark.parametrize("dtype", ["f64", "f32"])
-def test_rtm_shot_parity(dtype):
-    """A whole shot on the tiny three-level model: receiver traces and both images."""
-    w = tiny_layered_rtm(N=3, t_final=0.006)
+@functools.lru_cache(maxsize=None)
+def _oracle_shot(N):
+    w = tiny_layered_rtm(N=N, t_final=0.006)
     prob = _oracle_problem(w)
-    ref = rtm_shot(prob, w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
+    return w, rtm_shot(prob, w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("N", [3, 4])
+def test_rtm_shot_parity(dtype, N):
+    """A whole shot on the tiny three-level model (forward with recording, overshoot, backward
+    source and receiver runs with replay and images): receiver traces and both images.  N = 4 is
+    the order of the bench."""
+    w, ref = _oracle_shot(N)
     s = _gpu(w, dtype)
     tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
     assert tr.shape == ref.traces.shape
