@@ -349,6 +349,30 @@ def run_ridg(args):
                  "image_q_rel_l2": rl2(a[2], b[2]),
                  "reference": "same shot over a 0.01 s record in the library's FP64 mode"}
 
+    # serving: short shots through the shot server with Poisson arrivals below its capacity, for the
+    # p50/p99 latency the metric quotes (a different, shorter record than the throughput shot)
+    serving = None
+    if rank == 0 and not args.no_serving:
+        n_req, t_rec = 12, 0.05
+        with ridg.Server(s, max_queued=n_req) as sv:
+            tk = sv.submit(src_x, w.f0, w.t_peak, 1.0, w.receivers, t_rec)
+            service = sv.wait(tk)[3]["run_s"]
+            rate = 0.8 / service
+            gaps = np.random.default_rng(5).exponential(1.0 / rate, n_req)
+            t0 = time.perf_counter()
+            arrive, tickets = 0.0, []
+            for i in range(n_req):
+                arrive += gaps[i]
+                time.sleep(max(0.0, arrive - (time.perf_counter() - t0)))
+                xs = (src_x[0] + 25.0 * (i % 5 - 2), src_x[1], src_x[2])
+                tickets.append(sv.submit(xs, w.f0, w.t_peak, 1.0, w.receivers, t_rec))
+            lat = [sv.wait(t)[3]["total_s"] for t in tickets]
+            span = time.perf_counter() - t0
+        serving = {"requests": n_req, "record_s": t_rec, "service_s": service,
+                   "arrivals": "Poisson at 0.8x the measured service rate (seed 5), sources along a line",
+                   "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                   "shots_per_s": n_req / span}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -364,6 +388,7 @@ def run_ridg(args):
             "roofline": roofline,
             "e2e": e2e,
             "error_vs_fp64": error,
+            "serving": serving,
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
@@ -412,6 +437,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ridg", choices=["ridg", "reference"])
     ap.add_argument("--no-error", action="store_true", help="skip the FP32-vs-FP64 error leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the shot-server latency leg")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-shot", type=float, default=0.0,
                     help="run one shot of the bench workload with this record length (s) and exit (profiling case)")

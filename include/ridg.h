@@ -42,6 +42,7 @@ extern "C" {
 #define RIDG_E_UNSTABLE -5    /* a non-finite value or energy growth was detected */
 #define RIDG_E_TIMEOUT -6     /* a bounded device-side wait gave up */
 #define RIDG_E_NOT_FOUND -7   /* a source or receiver lies outside the mesh */
+#define RIDG_E_BUSY -8        /* a shot server's queue is full */
 
 /* boundary-condition codes per local face (Sec. 2): 0 = automatic (interior where a neighbour
  * exists, else the default code), 1 = free surface p = 0, 2 = transparent p - rho c n.v = 0
@@ -210,6 +211,50 @@ int ridg_last_shot_stats(const ridg_solver* s, ridg_shot_stats* stats);
 /* Profiling: when every > 0, every every-th global step the fused launch that covers all elements
  * is bracketed by CUDA events on the solver's stream; 0 turns it off (default). */
 int ridg_set_profiling(ridg_solver* s, int32_t every);
+
+/* ------------------------------------------------------------------ shot server
+ * The paper's unit of work is the RTM shot (Sec. 2; a survey migrates many shots into one image).
+ * A server runs shot requests one after another on one solver, keeping its device buffers
+ * (fields, histories, traces, the boundary-trace arena of Sec. 4.3) resident between shots.  It
+ * has no counterpart in the paper.  A request is admitted when its turn comes if the device memory
+ * it still needs is free (the arena grows with the record length); otherwise it completes with
+ * RIDG_E_OOM.  While a server exists, its solver must not be used by any other call.  One thread
+ * should submit and wait per server (the calls are thread-safe, but the last error message is per
+ * thread). */
+typedef struct ridg_server ridg_server;
+
+typedef struct ridg_shot_request {
+  ridg_source source;
+  const double* rec_xyz; /* [nrec][3] host; copied at submission */
+  int64_t nrec;
+  double t_final, t_image_start;
+  const double* observed; /* [nrec][n_t] host or NULL (the modelled traces); copied at submission */
+  double* traces_out;     /* [nrec][n_t] host or NULL; owned by the caller, written before completion */
+  double* image_p;        /* [K][Np] host or NULL; as traces_out */
+  double* image_q;        /* [K][Np] host or NULL; as traces_out */
+  const double* e_up;     /* [3] or NULL for (0, 0, -1); copied at submission */
+} ridg_shot_request;
+
+typedef struct ridg_request_timing {
+  double queued_s; /* submission to start */
+  double run_s;    /* start to completion (the shot and the copies into the host buffers) */
+  double total_s;  /* submission to completion */
+} ridg_request_timing;
+
+/* Creates a server (and its worker thread) on solver s; at most max_queued requests may wait
+ * behind the running one (>= 1). */
+int ridg_server_create(ridg_solver* s, int64_t max_queued, ridg_server** out);
+/* Queues a request and returns its ticket.  RIDG_E_BUSY when max_queued requests are waiting;
+ * RIDG_E_INVALID_ARG for a malformed request (checked again, with the solver, when it runs). */
+int ridg_server_submit(ridg_server* sv, const ridg_shot_request* req, int64_t* ticket);
+/* Waits at most timeout_s seconds (< 0: without limit) for a request.  When it has completed,
+ * releases the ticket, fills timing (may be NULL) and returns the request's own status (0, or the
+ * error it ran into, with its message in ridg_last_error); RIDG_E_TIMEOUT if it has not completed
+ * in time (the ticket stays valid); RIDG_E_INVALID_ARG for an unknown ticket. */
+int ridg_server_wait(ridg_server* sv, int64_t ticket, double timeout_s, ridg_request_timing* timing);
+/* Finishes the running request, drops the queued ones (their buffers are not written) and frees
+ * the server; the solver can be used again afterwards. */
+int ridg_server_destroy(ridg_server* sv);
 
 #ifdef __cplusplus
 }

@@ -3,9 +3,15 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstring>
+#include <deque>
+#include <map>
 #include <memory>
+#include <mutex>
+#include <thread>
 #include <stdexcept>
 #include <string>
 #include <type_traits>
@@ -53,6 +59,11 @@ struct DBuf {
     if (p) cudaFree(p);
     p = nullptr;
     bytes = 0;
+  }
+  // at least n bytes, keeping a larger allocation (resident buffers reused across shots)
+  void reserve(size_t n) {
+    if (p && bytes >= n) return;
+    alloc(n);
   }
   void alloc(size_t n) {
     if (n == bytes && p) return;
@@ -112,6 +123,8 @@ struct ridg_solver {
   virtual cudaStream_t stream() const = 0;
   virtual const ridg_shot_stats& stats() = 0;
   virtual void set_profiling(int every) = 0;
+  // device bytes a shot of this record length would still allocate (arena growth, first-shot buffers)
+  virtual size_t shot_extra_device_bytes(double t_final) const = 0;
 };
 
 namespace ridg {
@@ -294,6 +307,18 @@ class Engine final : public ridg_solver {
                                          dptr<const double>(M_d_), out_dev, st_);
     if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("ridg_energy_noalloc: ") + cudaGetErrorString(e)};
   }
+  size_t shot_extra_device_bytes(double t_final) const override {
+    if (!(t_final > 0.0)) return 0;
+    const double dtg = lv_.dt_local * double(NL_);
+    const int64_t tau_f = int64_t(std::ceil(t_final / dtg - 1e-9)) * NL_;
+    int64_t recs = 0;
+    for (int64_t t = 0; t <= tau_f; ++t) recs += n_bfaces_ - bface_first(slot_lo(t));
+    const size_t arena = std::max<size_t>(size_t(recs) * 2 * NFPP_ * sizeof(real), 16);
+    size_t extra = arena > arena_.bytes ? arena - arena_.bytes : 0;
+    if (!q_snap_.p) extra += 4 * qsize() * sizeof(real) + 2 * size_t(n_slots_) * Np_ * sizeof(double);
+    if (!w_[1].q.p) extra += 4 * qsize() * sizeof(real) + 3 * trace_slot_elems() * sizeof(real);
+    return extra;
+  }
   int64_t trace_len(double t_final) const override {
     double dtg = lv_.dt_local * double(NL_);
     return int64_t(std::ceil(t_final / dtg - 1e-9)) + 1;
@@ -383,7 +408,7 @@ class Engine final : public ridg_solver {
     std::vector<int64_t> arena_base(tau_f + 2, 0);
     for (int64_t t = 0; t <= tau_f; ++t) arena_base[t + 1] = arena_base[t] + (n_bfaces_ - bface_first(slot_lo(t)));
     size_t arena_bytes = size_t(arena_base[tau_f + 1]) * 2 * NFPP_ * sizeof(real);
-    arena_.alloc(std::max<size_t>(arena_bytes, 16));
+    arena_.reserve(std::max<size_t>(arena_bytes, 16));
     stats_.boundary_trace_bytes = int64_t(arena_bytes);
     q_snap_.alloc(qsize() * sizeof(real));
     ring_snap_.alloc(3 * qsize() * sizeof(real));
@@ -954,6 +979,115 @@ static int guarded(F&& f) {
   }
 }
 
+namespace ridg {
+
+// Device buffers of a shot with host inputs and outputs (kept by a server between shots).
+struct HostShotBuffers {
+  DBuf obs, tr, ip, iq;
+};
+
+// One shot with host buffers: copies the observed traces in, runs the shot on the solver's stream,
+// copies traces and images out and waits for them.
+static void run_host_shot(ridg_solver* s, const ridg_source& src, const double* rec_xyz, int64_t nrec, double t_final,
+                          double t_image_start, const double* observed, double* traces_out, double* image_p,
+                          double* image_q, const double* e_up, HostShotBuffers& b) {
+  ridg_info inf;
+  s->info(&inf);
+  int64_t n_t = s->trace_len(t_final);
+  size_t tb = size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double);
+  size_t ib = size_t(inf.K) * inf.Np * sizeof(double);
+  cudaStream_t st = s->stream();
+  if (observed) {
+    b.obs.reserve(tb);
+    RIDG_CUDA(cudaMemcpyAsync(b.obs.p, observed, size_t(nrec) * n_t * sizeof(double), cudaMemcpyHostToDevice, st));
+  }
+  b.tr.reserve(tb);
+  if (image_p) b.ip.reserve(ib);
+  if (image_q) b.iq.reserve(ib);
+  s->shot(src, rec_xyz, nrec, t_final, t_image_start, observed ? dptr<double>(b.obs) : nullptr, dptr<double>(b.tr),
+          image_p ? dptr<double>(b.ip) : nullptr, image_q ? dptr<double>(b.iq) : nullptr, e_up);
+  if (traces_out && nrec > 0)
+    RIDG_CUDA(cudaMemcpyAsync(traces_out, b.tr.p, size_t(nrec) * n_t * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (image_p) RIDG_CUDA(cudaMemcpyAsync(image_p, b.ip.p, ib, cudaMemcpyDeviceToHost, st));
+  if (image_q) RIDG_CUDA(cudaMemcpyAsync(image_q, b.iq.p, ib, cudaMemcpyDeviceToHost, st));
+  RIDG_CUDA(cudaStreamSynchronize(st));
+  if (image_p)
+    for (size_t i = 0; i < ib / sizeof(double); ++i)
+      if (!std::isfinite(image_p[i])) throw Error{RIDG_E_UNSTABLE, "non-finite image value"};
+}
+
+}  // namespace ridg
+
+// Shot server: a FIFO of requests served by one worker thread on the solver's stream.
+struct ridg_server {
+  using clock = std::chrono::steady_clock;
+  struct Request {
+    ridg_shot_request r{};
+    std::vector<double> rec, obs, eup;
+    clock::time_point submitted, started, finished;
+    bool done = false;
+    int status = RIDG_OK;
+    std::string error;
+  };
+  ridg_solver* solver = nullptr;
+  int device = 0;
+  int64_t max_queued = 1;
+  std::mutex mu;
+  std::condition_variable work_cv, done_cv;
+  std::deque<int64_t> queue;
+  std::map<int64_t, std::unique_ptr<Request>> requests;
+  int64_t next_ticket = 1;
+  bool stop = false;
+  std::thread worker;
+  ridg::HostShotBuffers buffers;
+
+  void run() {
+    cudaSetDevice(device);
+    for (;;) {
+      Request* q = nullptr;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        work_cv.wait(lk, [&] { return stop || !queue.empty(); });
+        if (stop) return;
+        q = requests[queue.front()].get();
+        queue.pop_front();
+        q->started = clock::now();
+      }
+      int status = RIDG_OK;
+      std::string error;
+      try {
+        // admission: the device memory this shot would still allocate must be free
+        size_t need = solver->shot_extra_device_bytes(q->r.t_final), free_b = 0, total_b = 0;
+        RIDG_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        const size_t margin = size_t(256) << 20;
+        if (need + margin > free_b)
+          throw Error{RIDG_E_OOM, "shot needs " + std::to_string(need) + " more device bytes, " +
+                                      std::to_string(free_b) + " free"};
+        ridg::run_host_shot(solver, q->r.source, q->rec.empty() ? nullptr : q->rec.data(), q->r.nrec, q->r.t_final,
+                            q->r.t_image_start, q->obs.empty() ? nullptr : q->obs.data(), q->r.traces_out,
+                            q->r.image_p, q->r.image_q, q->eup.empty() ? nullptr : q->eup.data(), buffers);
+      } catch (const Error& e) {
+        status = e.code;
+        error = e.msg;
+      } catch (const std::bad_alloc&) {
+        status = RIDG_E_OOM;
+        error = "host allocation failed";
+      } catch (const std::exception& e) {
+        status = RIDG_E_INVALID_ARG;
+        error = e.what();
+      }
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        q->status = status;
+        q->error = error;
+        q->finished = clock::now();
+        q->done = true;
+      }
+      done_cv.notify_all();
+    }
+  }
+};
+
 extern "C" {
 
 const char* ridg_last_error(void) { return ridg::g_last_error.c_str(); }
@@ -1122,30 +1256,9 @@ int ridg_rtm_shot(ridg_solver* s, const ridg_source* src, const double* rec_xyz,
   return guarded([&] {
     RIDG_NEED(s);
     if (!src) throw Error{RIDG_E_INVALID_ARG, "source is null"};
-    ridg_info inf;
-    s->info(&inf);
-    int64_t n_t = s->trace_len(t_final);
-    size_t tb = size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double);
-    size_t ib = size_t(inf.K) * inf.Np * sizeof(double);
-    cudaStream_t st = s->stream();
-    ridg::DBuf obs, tr, ip, iq;
-    if (observed) {
-      obs.alloc(tb);
-      RIDG_CUDA(cudaMemcpyAsync(obs.p, observed, size_t(nrec) * n_t * sizeof(double), cudaMemcpyHostToDevice, st));
-    }
-    tr.alloc(tb);
-    if (image_p) ip.alloc(ib);
-    if (image_q) iq.alloc(ib);
-    s->shot(*src, rec_xyz, nrec, t_final, t_image_start, observed ? ridg::dptr<double>(obs) : nullptr, ridg::dptr<double>(tr),
-            ridg::dptr<double>(ip), ridg::dptr<double>(iq), e_up);
-    if (traces_out && nrec > 0)
-      RIDG_CUDA(cudaMemcpyAsync(traces_out, tr.p, size_t(nrec) * n_t * sizeof(double), cudaMemcpyDeviceToHost, st));
-    if (image_p) RIDG_CUDA(cudaMemcpyAsync(image_p, ip.p, ib, cudaMemcpyDeviceToHost, st));
-    if (image_q) RIDG_CUDA(cudaMemcpyAsync(image_q, iq.p, ib, cudaMemcpyDeviceToHost, st));
-    RIDG_CUDA(cudaStreamSynchronize(st));
-    if (image_p)
-      for (size_t i = 0; i < ib / sizeof(double); ++i)
-        if (!std::isfinite(image_p[i])) throw Error{RIDG_E_UNSTABLE, "non-finite image value"};
+    ridg::HostShotBuffers b;
+    ridg::run_host_shot(s, *src, rec_xyz, nrec, t_final, t_image_start, observed, traces_out, image_p, image_q, e_up,
+                        b);
   });
 }
 
@@ -1161,6 +1274,92 @@ int ridg_set_profiling(ridg_solver* s, int32_t every) {
   return guarded([&] {
     RIDG_NEED(s);
     s->set_profiling(every);
+  });
+}
+
+int ridg_server_create(ridg_solver* s, int64_t max_queued, ridg_server** out) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!out) throw Error{RIDG_E_INVALID_ARG, "out is null"};
+    if (max_queued < 1) throw Error{RIDG_E_INVALID_ARG, "max_queued must be >= 1"};
+    auto sv = std::make_unique<ridg_server>();
+    sv->solver = s;
+    sv->max_queued = max_queued;
+    RIDG_CUDA(cudaGetDevice(&sv->device));
+    ridg_server* raw = sv.get();
+    sv->worker = std::thread([raw] { raw->run(); });
+    *out = sv.release();
+  });
+}
+
+int ridg_server_submit(ridg_server* sv, const ridg_shot_request* req, int64_t* ticket) {
+  return guarded([&] {
+    if (!sv || !req || !ticket) throw Error{RIDG_E_INVALID_ARG, "null argument"};
+    if (!(req->t_final > 0.0) || !(req->t_image_start >= 0.0)) throw Error{RIDG_E_INVALID_ARG, "bad time span"};
+    if (req->nrec < 0 || (req->nrec > 0 && !req->rec_xyz)) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
+    auto q = std::make_unique<ridg_server::Request>();
+    q->r = *req;
+    q->rec.assign(req->rec_xyz, req->rec_xyz + 3 * req->nrec);
+    if (req->observed) {
+      const int64_t n_t = sv->solver->trace_len(req->t_final);
+      q->obs.assign(req->observed, req->observed + req->nrec * n_t);
+    }
+    if (req->e_up) q->eup.assign(req->e_up, req->e_up + 3);
+    q->submitted = ridg_server::clock::now();
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      if (int64_t(sv->queue.size()) >= sv->max_queued)
+        throw Error{RIDG_E_BUSY, "server queue full (" + std::to_string(sv->max_queued) + " waiting)"};
+      const int64_t t = sv->next_ticket++;
+      sv->requests[t] = std::move(q);
+      sv->queue.push_back(t);
+      *ticket = t;
+    }
+    sv->work_cv.notify_one();
+  });
+}
+
+int ridg_server_wait(ridg_server* sv, int64_t ticket, double timeout_s, ridg_request_timing* timing) {
+  int status = RIDG_OK;
+  std::string error;
+  int rc = guarded([&] {
+    if (!sv) throw Error{RIDG_E_INVALID_ARG, "server handle is null"};
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->requests.find(ticket);
+    if (it == sv->requests.end()) throw Error{RIDG_E_INVALID_ARG, "unknown ticket " + std::to_string(ticket)};
+    ridg_server::Request* q = it->second.get();
+    auto ready = [&] { return q->done; };
+    if (timeout_s < 0) {
+      sv->done_cv.wait(lk, ready);
+    } else if (!sv->done_cv.wait_for(lk, std::chrono::duration<double>(timeout_s), ready)) {
+      throw Error{RIDG_E_TIMEOUT, "request " + std::to_string(ticket) + " has not completed"};
+    }
+    if (timing) {
+      using sec = std::chrono::duration<double>;
+      timing->queued_s = sec(q->started - q->submitted).count();
+      timing->run_s = sec(q->finished - q->started).count();
+      timing->total_s = sec(q->finished - q->submitted).count();
+    }
+    status = q->status;
+    error = q->error;
+    sv->requests.erase(it);
+  });
+  if (rc != RIDG_OK) return rc;
+  if (status != RIDG_OK) ridg::set_error(error);
+  return status;
+}
+
+int ridg_server_destroy(ridg_server* sv) {
+  return guarded([&] {
+    if (!sv) throw Error{RIDG_E_INVALID_ARG, "server handle is null"};
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->stop = true;
+      sv->queue.clear();
+    }
+    sv->work_cv.notify_all();
+    if (sv->worker.joinable()) sv->worker.join();
+    delete sv;
   });
 }
 

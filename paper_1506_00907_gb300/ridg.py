@@ -17,7 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libridg.so")
 
 RIDG_OK = 0
-ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "OOM", -4: "CUDA", -5: "UNSTABLE", -6: "TIMEOUT", -7: "NOT_FOUND"}
+ERRORS = {-1: "INVALID_ARG", -2: "BAD_MESH", -3: "OOM", -4: "CUDA", -5: "UNSTABLE", -6: "TIMEOUT", -7: "NOT_FOUND",
+          -8: "BUSY"}
 BC_AUTO, BC_FREE, BC_TRANSPARENT, BC_RIGID = 0, 1, 2, 3
 F32, F64 = 0, 1
 
@@ -26,7 +27,8 @@ EXPORTED = [
     "ridg_reference_operators", "ridg_solver_create", "ridg_solver_destroy", "ridg_solver_info",
     "ridg_solver_levels", "ridg_solver_nodes", "ridg_set_state", "ridg_set_history", "ridg_eval_rhs", "ridg_step",
     "ridg_get_state", "ridg_energy", "ridg_trace_len", "ridg_rtm_shot", "ridg_rtm_shot_device",
-    "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc",
+    "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc", "ridg_server_create", "ridg_server_submit",
+    "ridg_server_wait", "ridg_server_destroy",
 ]
 
 
@@ -58,6 +60,16 @@ class ShotStats(C.Structure):
                 ("prof_backward_launches", C.c_int64)]
 
 
+class ShotRequest(C.Structure):
+    _fields_ = [("source", Source), ("rec_xyz", C.c_void_p), ("nrec", C.c_int64), ("t_final", C.c_double),
+                ("t_image_start", C.c_double), ("observed", C.c_void_p), ("traces_out", C.c_void_p),
+                ("image_p", C.c_void_p), ("image_q", C.c_void_p), ("e_up", C.c_void_p)]
+
+
+class RequestTiming(C.Structure):
+    _fields_ = [("queued_s", C.c_double), ("run_s", C.c_double), ("total_s", C.c_double)]
+
+
 def load_library(path: str = LIB_PATH) -> C.CDLL:
     if not os.path.exists(path):
         raise ImportError(f"{path} is missing: build it with paper_1506_00907_gb300.build.build()")
@@ -87,6 +99,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_last_shot_stats": (C.c_int, [P, P]),
         "ridg_set_profiling": (C.c_int, [P, C.c_int32]),
         "ridg_energy_noalloc": (C.c_int, [P, P]),
+        "ridg_server_create": (C.c_int, [P, C.c_int64, C.POINTER(P)]),
+        "ridg_server_submit": (C.c_int, [P, P, C.POINTER(C.c_int64)]),
+        "ridg_server_wait": (C.c_int, [P, C.c_int64, C.c_double, P]),
+        "ridg_server_destroy": (C.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -262,3 +278,55 @@ class Solver:
         st = ShotStats()
         _check(lib().ridg_last_shot_stats(self._h, C.byref(st)))
         return st
+
+
+class Server:
+    """Shot server on a solver (``ridg_server_*``): requests run one after another on the solver's
+    resident buffers.  The solver must not be used directly while the server exists."""
+
+    def __init__(self, solver: Solver, max_queued: int = 8):
+        self.solver = solver
+        h = C.c_void_p()
+        _check(lib().ridg_server_create(solver._h, int(max_queued), C.byref(h)))
+        self._h = h
+        self._pending = {}
+
+    def submit(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0, observed=None,
+               e_up=(0.0, 0.0, -1.0), want_images=True) -> int:
+        """Queues a shot; its host output buffers are kept here until ``wait`` returns them."""
+        rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
+        n_t = self.solver.trace_len(t_final)
+        traces = np.zeros((rec.shape[0], n_t))
+        ip = np.zeros((self.solver.K, self.solver.Np)) if want_images else None
+        iq = np.zeros((self.solver.K, self.solver.Np)) if want_images else None
+        obs = None if observed is None else _f64(observed, (rec.shape[0], n_t))
+        eu = _f64(e_up)
+        req = ShotRequest(Source((C.c_double * 3)(*source_xyz), f0, t_peak, amplitude), _ptr(rec), rec.shape[0],
+                          float(t_final), float(t_image_start), _ptr(obs), _ptr(traces), _ptr(ip), _ptr(iq), _ptr(eu))
+        t = C.c_int64()
+        _check(lib().ridg_server_submit(self._h, C.byref(req), C.byref(t)))
+        self._pending[t.value] = (traces, ip, iq)
+        return t.value
+
+    def wait(self, ticket: int, timeout=None):
+        """(traces, image_p, image_q, timing) of a completed request; RidgError (TIMEOUT) if it has not
+        completed within ``timeout`` seconds (None: no limit), or the request's own error."""
+        tm = RequestTiming()
+        code = lib().ridg_server_wait(self._h, int(ticket), -1.0 if timeout is None else float(timeout), C.byref(tm))
+        if code == -6:
+            _check(code)
+        out = self._pending.pop(ticket, None)
+        _check(code)
+        traces, ip, iq = out
+        return traces, ip, iq, {"queued_s": tm.queued_s, "run_s": tm.run_s, "total_s": tm.total_s}
+
+    def close(self):
+        if self._h:
+            _check(lib().ridg_server_destroy(self._h))
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
