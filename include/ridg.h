@@ -40,7 +40,7 @@ extern "C" {
 #define RIDG_E_OOM -3         /* device or host memory could not be allocated */
 #define RIDG_E_CUDA -4        /* a CUDA call failed (message holds cudaGetErrorString) */
 #define RIDG_E_UNSTABLE -5    /* a non-finite value or energy growth was detected */
-#define RIDG_E_TIMEOUT -6     /* a bounded device-side wait gave up */
+#define RIDG_E_TIMEOUT -6     /* a bounded wait gave up (ridg_server_wait's timeout) */
 #define RIDG_E_NOT_FOUND -7   /* a source or receiver lies outside the mesh */
 #define RIDG_E_BUSY -8        /* a shot server's queue is full */
 
