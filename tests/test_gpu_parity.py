@@ -129,7 +129,7 @@ def _oracle_shot(N):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
-@pytest.mark.parametrize("N", [3, 4])
+@pytest.mark.parametrize("N", [3, 4, 5])
 def test_rtm_shot_parity(dtype, N):
     """A whole shot on the tiny three-level model (forward with recording, overshoot, backward
     source and receiver runs with replay and images): receiver traces and both images.  N = 4 is
@@ -144,6 +144,43 @@ def test_rtm_shot_parity(dtype, N):
     st = s.shot_stats()
     assert st.n_global == ref.n_global
     assert st.dof_updates_forward + st.dof_updates_backward > 0
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_shot_variant(variant):
+    """Tiny N = 3 shot variants: an image window that starts half-way, observed data that are not
+    the modelled traces, a free-surface top and rigid bottom (boundary records of every kind),
+    receivers on element vertices and faces (point-location ties)."""
+    w = tiny_layered_rtm(N=3, t_final=0.004)
+    fb, rec, obs, t_i = None, w.receivers, None, 0.0
+    if variant == "window":
+        t_i = 0.5 * w.t_final
+    elif variant == "observed":
+        n_t = int(np.ceil(w.t_final / _oracle_problem(w).dt_global - 1e-9)) + 1
+        obs = np.random.default_rng(17).standard_normal((len(rec), n_t))
+    elif variant == "free_top":
+        fb = mixed_bc(w)
+    elif variant == "ties":
+        # interior mesh vertices, midpoints of the edges between them, and the centroid of a face
+        # shared by two elements: points on the closure of several elements
+        v = np.array([[100.0, 100.0, 25.0], [100.0, 125.0, 25.0], [100.0, 150.0, 25.0], [75.0, 100.0, 50.0]])
+        k = int(np.argmin(np.linalg.norm(w.xyz[w.tets].mean(axis=1) - [101.0, 101.0, 26.0], axis=1)))
+        face = w.xyz[w.tets[k, :3]].mean(axis=0)
+        rec = np.concatenate([v, 0.5 * (v[:2] + v[1:3]), face[None, :]])
+    prob = _oracle_problem(w, face_bc=fb)
+    ref = rtm_shot(prob, w.source_xyz, w.f0, w.t_peak, 1.0, rec, w.t_final, t_i, observed=obs)
+    return w, fb, rec, obs, t_i, ref
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("variant", ["window", "observed", "free_top", "ties"])
+def test_rtm_shot_variants_parity(dtype, variant):
+    w, fb, rec, obs, t_i, ref = _oracle_shot_variant(variant)
+    s = _gpu(w, dtype, face_bc=fb)
+    tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, rec, w.t_final, t_i, observed=obs)
+    assert rel_l2(tr, ref.traces) < TOL[dtype]
+    assert rel_l2(ip, ref.image_p) < (10 * TOL[dtype] if dtype == "f32" else TOL[dtype])
+    assert rel_l2(iq, ref.image_q) < (10 * TOL[dtype] if dtype == "f32" else TOL[dtype])
 
 
 def test_rtm_edge_cases():
