@@ -25,6 +25,11 @@ Galerkin simulations for reverse-time migration on GPU clusters"):
 
 Every function is FP64 and follows the paper's steps in the paper's order; matrix
 products from numpy serve as single steps.  Readings of places where the paper is
-silent or garbled are listed in the repository's design notes and restated in the
-docstrings where they apply.
+silent or garbled are stated in the docstrings where they apply.
+
+Every function is pinned by CPU tests against closed forms, invariants, printed
+coefficients or brute force.  Parity unpinned: the absolute images of a whole shot on
+a large model (the paper publishes no image values); they are held only by this
+oracle's agreement with the CUDA path on the shots it can run and by the invariants
+of the image increments.
 """
