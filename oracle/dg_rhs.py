@@ -15,7 +15,9 @@ element.  Readings (where the paper is silent or differs from itself):
   the central parts of the interface terms cancel in the energy balance.
 * tau_p = 1/Zbar, tau_v = Zbar with Zbar = (rho^- c^- + rho^+ c^+)/2 on interior faces
   (the upwind values of Sec. 3.1 when the medium is homogeneous), Zbar = rho c on
-  boundary faces; tau is multiplied by -1 in backward-in-time runs (Sec. 3.2).
+  boundary faces; tau is multiplied by -1 in backward-in-time runs (Sec. 3.2).  A
+  penalty scale s (``geo.tau_scale``, 1 by default) multiplies both: s = 1 is the upwind
+  flux of Sec. 3.1, s = 0 the central flux, and every face's energy loss is linear in s.
 * Boundary conditions through an exterior ("ghost") state: free surface p^+ = -p^-,
   n.v^+ = n.v^-; transparent (Eq. ABC) p^+ = 0, v^+ = 0; rigid wall p^+ = p^-,
   n.v^+ = -n.v^-.  Only p and n.v enter the fluxes, so traces (p, n.v) suffice, as in
@@ -62,6 +64,7 @@ def face_jumps(elems, qf, geo: MeshGeometry, sign=1.0, replay=None):
     pm = qf[elems, 0]  # [E, 4, Nfp]
     vm = qf[elems, 1]
     Z = geo.Z
+    sign = sign * geo.tau_scale
     jp = np.zeros((E, 4, Nfp))
     jv = np.zeros((E, 4, Nfp))
     taup = np.zeros((E, 4))
@@ -148,8 +151,9 @@ def energy(q, geo: MeshGeometry) -> float:
     return float(np.sum(0.5 * geo.J * (ep + ev)))
 
 
-def attach_media(geo: MeshGeometry, c, rho):
+def attach_media(geo: MeshGeometry, c, rho, tau_scale=1.0):
     geo.c = np.asarray(c, dtype=np.float64)
     geo.rho = np.asarray(rho, dtype=np.float64)
     geo.Z = geo.rho * geo.c
+    geo.tau_scale = float(tau_scale)
     return geo

@@ -28,7 +28,7 @@ from .imaging import characteristic, step_increment
 from .mesh_geometry import MeshGeometry
 from .mrab import MRAB, assign_levels
 from .reference_element import reference_element
-from .wavelet import interpolate_trace, ricker
+from .wavelet import interpolate_trace, ricker, sampled
 
 
 @dataclass
@@ -48,9 +48,10 @@ class Problem:
         return self.dt_local * self.n_local
 
 
-def make_problem(xyz, tets, c, rho, N, face_bc=None, default_bc=2, cfl=0.15, n_levels_max=3) -> Problem:
+def make_problem(xyz, tets, c, rho, N, face_bc=None, default_bc=2, cfl=0.15, n_levels_max=3,
+                 tau_scale=1.0) -> Problem:
     ref = reference_element(N)
-    geo = attach_media(MeshGeometry(xyz, tets, ref, face_bc=face_bc, default_bc=default_bc), c, rho)
+    geo = attach_media(MeshGeometry(xyz, tets, ref, face_bc=face_bc, default_bc=default_bc), c, rho, tau_scale)
     lev, nl, dtl = assign_levels(geo, N, c, cfl, n_levels_max)
     return Problem(geo, N, lev, nl, dtl)
 
@@ -72,8 +73,49 @@ class ShotResult:
     n_global: int
 
 
+def _source_signal(f0, t_peak, amplitude, dtl, wavelet=None, wavelet_dt=None):
+    """Source amplitude at integer fine time tau: the Ricker pulse, or the sampled signal."""
+    if wavelet is None:
+        return lambda tau: float(ricker(tau * dtl, f0, t_peak, amplitude))
+    samples = np.asarray(wavelet, dtype=np.float64).reshape(-1)
+    return lambda tau: sampled(tau * dtl, samples, wavelet_dt, amplitude)
+
+
+def _receivers(geo, rec_xyz):
+    rec = []
+    for x in np.atleast_2d(rec_xyz):
+        if x.size == 0:
+            continue
+        kr, rr = geo.locate(x)
+        if kr < 0:
+            raise ValueError("receiver outside the mesh")
+        rec.append((kr, geo.interpolation_row(rr), geo.source_weights(kr, rr)))
+    return rec
+
+
+def forward(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, wavelet=None,
+            wavelet_dt=None) -> np.ndarray:
+    """Forward modelling alone (Eq. waveSyst1 from a medium at rest): the receiver traces
+    [nrec, n_global + 1] sampled at every global step t_n = n Delta t_global."""
+    geo = prob.geo
+    n_global = int(np.ceil(t_final / prob.dt_global - 1e-9))
+    ks, rs = geo.locate(source_xyz)
+    if ks < 0:
+        raise ValueError("source outside the mesh")
+    rec = _receivers(geo, rec_xyz)
+    S = MRAB(geo, prob.levels, prob.n_levels, prob.dt_local, direction=+1, tau0=0)
+    S.injections = [(ks, geo.source_weights(ks, rs),
+                     _source_signal(f0, t_peak, amplitude, prob.dt_local, wavelet, wavelet_dt))]
+    tr = np.zeros((len(rec), n_global + 1))
+    for n in range(n_global + 1):
+        if n > 0:
+            S.global_step()
+        tr[:, n] = [row @ S.q[k, 0] for k, row, _ in rec]
+    return tr
+
+
 def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0,
-             observed=None, e_up=(0.0, 0.0, -1.0)) -> ShotResult:
+             observed=None, e_up=(0.0, 0.0, -1.0), wavelet=None, wavelet_dt=None) -> ShotResult:
     geo = prob.geo
     K, Np = geo.K, geo.ref.Np
     nl = prob.n_local
@@ -85,13 +127,8 @@ def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final,
     if ks < 0:
         raise ValueError("source outside the mesh")
     w_src = geo.source_weights(ks, rs)
-    rec = []
-    for x in np.atleast_2d(rec_xyz):
-        kr, rr = geo.locate(x)
-        if kr < 0:
-            raise ValueError("receiver outside the mesh")
-        rec.append((kr, geo.interpolation_row(rr), geo.source_weights(kr, rr)))
-    src_amp = lambda tau: float(ricker(tau * dtl, f0, t_peak, amplitude))  # noqa: E731
+    rec = _receivers(geo, rec_xyz)
+    src_amp = _source_signal(f0, t_peak, amplitude, dtl, wavelet, wavelet_dt)
 
     def sample(q):
         return np.array([row @ q[k, 0] for k, row, _ in rec])

@@ -188,3 +188,17 @@ def test_locate_ties_take_lowest_index():
     owners = [e for e in range(g.K) if np.any(np.all(np.isclose(g.P[e], [0.5, 0.5, 0.5]), axis=1))]
     assert k == min(owners)
     assert g.locate([2.0, 0.0, 0.0])[0] == -1
+
+
+@pytest.mark.parametrize("bc", [1, 2, 3])
+def test_energy_rate_is_linear_in_the_penalty_scale(bc):
+    """Scaling tau_p and tau_v by s scales every face's energy loss by s: the central flux
+    (s = 0) conserves the discrete energy exactly, s = 2.5 loses 2.5 times the upwind loss."""
+    xyz, tets = unit_cube_mesh(2)
+    g = _geo(xyz, tets, N=3, bc=bc)
+    q = np.random.default_rng(5).standard_normal((g.K, 4, g.ref.Np))
+    upwind = _face_dissipation(g, q)
+    for s in (0.0, 2.5):
+        g.tau_scale = s
+        r = rhs(np.arange(g.K), q, traces(q, g), g)
+        assert abs(_dEdt(g, q, r) - s * upwind) < 1e-10 * abs(upwind)
