@@ -26,4 +26,6 @@ from .workloads import (  # noqa: F401
     small_layered_rtm,
     tiny_layered_rtm,
     adjoint_box,
+    adjoint_box_small,
+    adjoint_observed_velocity,
 )

@@ -131,6 +131,31 @@ def adjoint_box(seed=0) -> Workload:
                     f0=10.0, t_peak=0.13524, receivers=rec, t_final=0.5)
 
 
+def adjoint_observed_velocity(w: Workload, amplitude=0.05, sigma=100.0) -> np.ndarray:
+    """Velocity of the observed data: c (1 + amplitude g), g a Gaussian bump of width sigma at the
+    centre of the box."""
+    cen = w.xyz[w.tets].mean(axis=1)
+    mid = 0.5 * (w.xyz.min(axis=0) + w.xyz.max(axis=0))
+    g = np.exp(-((cen - mid) ** 2).sum(axis=1) / (2 * sigma ** 2))
+    return w.c * (1.0 + amplitude * g)
+
+
+def adjoint_box_small() -> Workload:
+    """2 x 2 x 1 hexahedra x 6 = 24 tetrahedra on 200 x 200 x 100 m, N = 2, a velocity that
+    varies per element, one level; for checks the oracle's gradient can run on the CPU."""
+    ax = np.linspace(0.0, 200.0, 3)
+    g = HexGrid(ax, ax.copy(), np.linspace(0.0, 100.0, 2))
+    xyz, tets = g.mesh()
+    K = tets.shape[0]
+    c = 1500.0 + 1000.0 * np.random.default_rng(1).uniform(size=K)
+    rec = np.array([[50.0, 50.0, 10.0], [150.0, 60.0, 10.0], [100.0, 150.0, 20.0]])
+    w = Workload("box24_N2_adjoint", xyz, tets, c, np.full(K, 1000.0), N=2, default_bc=BC_TRANSPARENT, cfl=0.15,
+                 n_levels_max=1, dtype="f64", source_xyz=(100.0, 100.0, 8.0), f0=40.0,
+                 t_peak=0.1127 * 12.0 / 40.0, receivers=rec, t_final=0.08)
+    w.c_observed = adjoint_observed_velocity(w, sigma=60.0)
+    return w
+
+
 def tiny_layered_rtm(N=3, t_final=0.03) -> Workload:
     """200 x 200 x 100 m, two layers (interface at 50 m), refined bands around the source:
     three rate levels on 1440 tetrahedra.  Small enough for the oracle to run a whole shot."""
