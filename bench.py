@@ -214,29 +214,56 @@ def run_reference(args):
     return 0
 
 
-def _serving(ridg, s, w, src_x):
-    """p50/p99 latency of short shots through the shot server: Poisson arrivals at 0.8x the
-    measured service rate (seed 5), sources along a line."""
-    n_req, t_rec = 12, 0.05
-    with ridg.Server(s, max_queued=n_req) as sv:
-        tk = sv.submit(src_x, w.f0, w.t_peak, 1.0, w.receivers, t_rec)
-        service = sv.wait(tk)[3]["run_s"]
-        rate = 0.8 / service
-        gaps = np.random.default_rng(5).exponential(1.0 / rate, n_req)
+def _poisson_stream(ridg, sv, w, src_x, rate, n_req, t_rec, seed=5):
+    """Submits n_req short shots at Poisson arrival times of the given rate (sources along a line);
+    returns (latencies, span from the first arrival to the last completion)."""
+    gaps = np.random.default_rng(seed).exponential(1.0 / rate, n_req)
+    t0 = time.perf_counter()
+    arrive, tickets = 0.0, []
+    for i in range(n_req):
+        arrive += gaps[i]
+        time.sleep(max(0.0, arrive - (time.perf_counter() - t0)))
+        xs = (src_x[0] + 25.0 * (i % 5 - 2), src_x[1], src_x[2])
+        tickets.append(sv.submit(xs, w.f0, w.t_peak, 1.0, w.receivers, t_rec))
+    lat = [sv.wait(t)[3]["total_s"] for t in tickets]
+    return lat, time.perf_counter() - t0 - gaps[0]
+
+
+def _serving(ridg, torch, mesh, w, src_x):
+    """Shot serving on the bench model: short shots through the shot server with one slot and with
+    two slots (two solvers of the model on their own streams, whose shots overlap on the device),
+    Poisson arrivals (seed 5) at 0.8x and 1.5x the measured sequential single-shot rate; p50/p99
+    latency (submission to completion, host copies included) and shots/s."""
+    n_req, t_rec = 16, 0.05
+    streams = [torch.cuda.Stream() for _ in range(2)]
+    slots = [ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max,
+                         stream=st.cuda_stream) for st in streams]
+    out = {"requests": n_req, "record_s": t_rec,
+           "arrivals": "Poisson (seed 5) at 0.8x and 1.5x the sequential single-shot rate, sources along a line"}
+    with ridg.Server(slots[:1], max_queued=n_req) as sv:
+        sv.wait(sv.submit(src_x, w.f0, w.t_peak, 1.0, w.receivers, t_rec))  # buffers and arena in place
         t0 = time.perf_counter()
-        arrive, tickets = 0.0, []
-        for i in range(n_req):
-            arrive += gaps[i]
-            time.sleep(max(0.0, arrive - (time.perf_counter() - t0)))
-            xs = (src_x[0] + 25.0 * (i % 5 - 2), src_x[1], src_x[2])
-            tickets.append(sv.submit(xs, w.f0, w.t_peak, 1.0, w.receivers, t_rec))
-        lat = [sv.wait(t)[3]["total_s"] for t in tickets]
-        span = time.perf_counter() - t0
-    serving = {"requests": n_req, "record_s": t_rec, "service_s": service,
-               "arrivals": "Poisson at 0.8x the measured service rate (seed 5), sources along a line",
-               "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-               "shots_per_s": n_req / span}
-    return serving
+        for t in [sv.submit(src_x, w.f0, w.t_peak, 1.0, w.receivers, t_rec) for _ in range(3)]:
+            sv.wait(t)
+        service = (time.perf_counter() - t0) / 3
+    out["sequential_service_s"] = service
+    out["sequential_shots_per_s"] = 1.0 / service
+    with ridg.Server(slots, max_queued=n_req) as sv:
+        for t in [sv.submit(src_x, w.f0, w.t_peak, 1.0, w.receivers, t_rec) for _ in range(2)]:
+            sv.wait(t)  # both slots' buffers in place
+    for factor in (0.8, 1.5):
+        for n_slots in (1, 2):
+            with ridg.Server(slots[:n_slots], max_queued=n_req) as sv:
+                lat, span = _poisson_stream(ridg, sv, w, src_x, factor / service, n_req, t_rec)
+            out[f"rate{factor}x_slots{n_slots}"] = {
+                "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                "shots_per_s": n_req / span}
+    base = out["rate0.8x_slots1"]
+    out.update({"p50_s": base["p50_s"], "p99_s": base["p99_s"], "shots_per_s": base["shots_per_s"],
+                "overload_two_slots_vs_sequential": out["rate1.5x_slots2"]["shots_per_s"] * service})
+    for sl in slots:
+        sl.close()
+    return out
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -382,7 +409,7 @@ def run_ridg(args):
     serving = None
     if rank == 0 and not args.no_serving:
         try:
-            serving = _serving(ridg, s, w, src_x)
+            serving = _serving(ridg, torch, mesh, w, src_x)
         except ridg.RidgError as exc:  # reported in the line; the throughput stands on its own
             serving = {"failed": str(exc)}
 

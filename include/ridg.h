@@ -93,8 +93,14 @@ typedef struct ridg_options {
   int32_t dtype;        /* RIDG_F32 (default) or RIDG_F64 */
   double cfl;           /* C in Delta t_k = C l_k / ((N+1)^2 c_k) (Sec. 5.1); <= 0 selects 0.15 */
   int32_t n_levels_max; /* maximum number of multi-rate levels (Sec. 3.2); <= 0 selects 3 */
-  int32_t reserved[5];
+  int32_t image_mask;   /* images a shot accumulates: RIDG_IMAGE_P | RIDG_IMAGE_Q; 0 selects both */
+  double tau_scale;     /* multiplies the penalty parameters tau_p = 1/Zbar, tau_v = Zbar of the
+                           upwind fluxes (Sec. 3.1, Eqs. weakFormP/V); <= 0 selects 1 (upwind) */
+  int32_t reserved[4];
 } ridg_options;
+
+#define RIDG_IMAGE_P 1 /* classical image, Eq. imageP */
+#define RIDG_IMAGE_Q 2 /* characteristic image, Eq. imageQ */
 
 typedef struct ridg_info {
   int32_t N, Np, Nfp, n_levels;
@@ -133,8 +139,13 @@ int ridg_solver_nodes(const ridg_solver* s, double* xyz);
  *   Does not change the solver's state.
  * ridg_step: advances n_global global steps (Algorithm 1; one fused kernel launch per step of the
  *   finest level), asynchronously on the solver's stream.
- * ridg_get_state: copies the fields to host double [K][4][Np] (synchronises the stream). */
+ * ridg_get_state: copies the fields to host double [K][4][Np] (synchronises the stream).
+ * ridg_set_state_device / ridg_get_state_device: the same with a device double [K][4][Np] buffer
+ *   owned by the caller (for instance a torch tensor's data_ptr()); asynchronous on the solver's
+ *   stream (ridg_set_state_device keeps no reference to q_dev once the stream has passed it). */
 int ridg_set_state(ridg_solver* s, const double* q);
+int ridg_set_state_device(ridg_solver* s, const double* q_dev);
+int ridg_get_state_device(ridg_solver* s, double* q_dev);
 int ridg_set_history(ridg_solver* s, const double* rhs_prev1, const double* rhs_prev2);
 int ridg_eval_rhs(ridg_solver* s, const double* q, double* rhs_out);
 int ridg_step(ridg_solver* s, int64_t n_global);
@@ -157,8 +168,12 @@ int ridg_energy(ridg_solver* s, double* energy);
 int ridg_energy_noalloc(ridg_solver* s, double* energy_dev);
 
 /* ------------------------------------------------------------------ one RTM shot (Sec. 2, Sec. 4.3)
- * Source: Ricker pulse f(t) = amplitude (1 - 2 pi^2 f0^2 tau^2) exp(-pi^2 f0^2 tau^2), tau = t - t_peak,
- * at source_xyz (Eq. waveSyst1, L2-projected Dirac of Eq. sourceTerm).
+ * Source at xyz (Eq. waveSyst1, L2-projected Dirac of Eq. sourceTerm) with wavelet f(t):
+ *   kind RIDG_SRC_RICKER (0): f(t) = amplitude (1 - 2 pi^2 f0^2 tau^2) exp(-pi^2 f0^2 tau^2),
+ *     tau = t - t_peak;
+ *   kind RIDG_SRC_SAMPLED (1): f(t) = amplitude * interpolant of samples[n] at t = n sample_dt
+ *     (n = 0 .. n_samples-1; 4-point Lagrange interpolation in time, zero outside the samples);
+ *     samples is a host array, copied by the call.
  * Receivers: rec_xyz host double [nrec][3]; traces are sampled at t_n = n Delta t_global for
  * n = 0 .. n_t-1 with n_t = ridg_trace_len(s, t_final) = ceil(t_final / Delta t_global) + 1.
  *
@@ -173,14 +188,29 @@ int ridg_energy_noalloc(ridg_solver* s, double* energy_dev);
  *   image_p    host double [K][Np] or NULL: classical image int p_S p_R dt (Eq. imageP)
  *   image_q    host double [K][Np] or NULL: characteristic image int q^-_S q^+_R dt (Eq. imageQ),
  *              q^{+/-} = p +/- c rho (e_up . v)
+ *              (an image left out of the solver's image_mask is not accumulated and reads zero)
  *   e_up       host double [3] or NULL (= (0,0,-1): z is depth)
  * The images are accumulated in FP64.  The call synchronises the stream before returning.
  * Errors: RIDG_E_INVALID_ARG, RIDG_E_NOT_FOUND, RIDG_E_OOM (boundary-trace arena), RIDG_E_CUDA,
  * RIDG_E_UNSTABLE. */
+#define RIDG_SRC_RICKER 0
+#define RIDG_SRC_SAMPLED 1
 typedef struct ridg_source {
   double xyz[3];
-  double f0, t_peak, amplitude;
+  double f0, t_peak, amplitude; /* f0, t_peak: RIDG_SRC_RICKER only */
+  int32_t kind;                 /* RIDG_SRC_RICKER (0) or RIDG_SRC_SAMPLED */
+  int32_t reserved;
+  double sample_dt;             /* RIDG_SRC_SAMPLED: sample spacing (> 0) */
+  int64_t n_samples;            /* RIDG_SRC_SAMPLED: number of samples (>= 1) */
+  const double* samples;        /* RIDG_SRC_SAMPLED: host double [n_samples] */
 } ridg_source;
+
+/* Forward modelling: the forward source run of ridg_rtm_shot alone (no boundary records, no
+ * backward runs), from rest at t = 0 to t_final, with the receiver pressures sampled at
+ * t_n = n Delta t_global.  traces_out: host double [nrec][n_t], n_t = ridg_trace_len(s, t_final).
+ * Leaves the solver's fields at t_final.  Errors: RIDG_E_INVALID_ARG, RIDG_E_NOT_FOUND, RIDG_E_CUDA. */
+int ridg_forward(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                 double* traces_out);
 
 int64_t ridg_trace_len(const ridg_solver* s, double t_final);
 int ridg_rtm_shot(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
@@ -212,15 +242,52 @@ int ridg_last_shot_stats(const ridg_solver* s, ridg_shot_stats* stats);
  * is bracketed by CUDA events on the solver's stream; 0 turns it off (default). */
 int ridg_set_profiling(ridg_solver* s, int32_t every);
 
+/* ------------------------------------------------------------------ velocity gradient
+ * The paper migrates with the imaging condition; these calls give the gradient of a least-squares
+ * trace misfit with respect to the per-element velocity, as the exact discrete adjoint of the
+ * single-rate scheme (Sec. 3.1 right-hand side, Sec. 3.2 AB3 on one rate level: create the solver
+ * with n_levels_max = 1).  The velocity enters through rho c^2 in the pressure equation; the time
+ * step, the level and the penalty parameters tau_p, tau_v (and the impedance of I_Q) keep the
+ * values of the model the solver was created with. */
+
+/* Velocity per element (host double [K], > 0) in rho c^2; see above for what stays frozen.
+ * Invalidates the last misfit forward run. */
+int ridg_set_velocity(ridg_solver* s, const double* c);
+/* out = A^T lam, the transposed right-hand-side operator (no source), host double [K][4][Np] each
+ * in the reference node numbering.  The parity check of the adjoint kernels. */
+int ridg_eval_adjoint_rhs(ridg_solver* s, const double* lam, double* out);
+/* Forward run from rest with the source, receiver traces y_r^n at every step t_n = n Dt
+ * (n = 0 .. n_t-1, n_t from ridg_trace_len) and the misfit
+ *   J = 1/2 Dt sum_n sum_r (y_r^n - observed_r^n)^2      (observed: host double [nrec][n_t], nrec >= 1).
+ * Keeps n_checkpoints (<= 0 selects 16) snapshots of the state for ridg_misfit_backward.
+ * traces_out (host double [nrec][n_t]) may be NULL.  Errors: RIDG_E_INVALID_ARG (more than one rate
+ * level, missing receivers or data), RIDG_E_NOT_FOUND, RIDG_E_UNSTABLE. */
+int ridg_misfit_forward(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                        const double* observed, int32_t n_checkpoints, double* misfit, double* traces_out);
+/* grad (host double [K]) = dJ/dc of the last ridg_misfit_forward: the adjoint recursion
+ *   lambda^m = lambda^{m+1} + Dt A^T sum_s a_s lambda^{m+1+s} - Dt sum_r (y_r^m - d_r^m) l(x_r),
+ * run backward from m = n_t-1, recomputing the forward states segment by segment from the
+ * checkpoints, with dJ/dc_k = -(2/c_k) sum_n lambda^{n+1}_p,k . (A (q^{n+1} - q^n source-free))_p,k.
+ * RIDG_E_INVALID_ARG without a valid forward run (none yet, or the velocity changed since). */
+int ridg_misfit_backward(ridg_solver* s, double* grad);
+
 /* ------------------------------------------------------------------ shot server
  * The paper's unit of work is the RTM shot (Sec. 2; a survey migrates many shots into one image).
- * A server runs shot requests one after another on one solver, keeping its device buffers
- * (fields, histories, traces, the boundary-trace arena of Sec. 4.3) resident between shots.  It
- * has no counterpart in the paper.  A request is admitted when its turn comes if the device memory
- * it still needs is free (the arena grows with the record length); otherwise it completes with
- * RIDG_E_OOM.  While a server exists, its solver must not be used by any other call.  One thread
- * should submit and wait per server (the calls are thread-safe, but the last error message is per
- * thread). */
+ * A server serves shot requests on a set of slots.  A slot is a solver: one model (mesh, c, rho,
+ * order, precision) with its own CUDA stream and device buffers (fields, histories, traces, the
+ * boundary-trace arena of Sec. 4.3), kept resident between shots.  Slots are numbered by model:
+ * several solvers built from the same inputs serve one model concurrently.  Each slot has a worker
+ * thread; an idle slot takes the oldest waiting request of its model, so requests that arrive
+ * while others run start as soon as a slot of their model is free, and the shots of different
+ * slots overlap on the device (their solvers must use different non-default streams for that).
+ * Admission by device memory: before a shot starts, the memory it still needs (the arena grows
+ * with the record length) must be free; if it is not, the buffers of idle slots are released and,
+ * while other slots run, the request waits for them to finish; if the memory cannot be found it
+ * completes with RIDG_E_OOM.  While a request waits for memory, idle slots start no new requests.
+ * A shot's results do not depend on the slot or on the other shots.  The server has no
+ * counterpart in the paper.  While a server exists, its solvers must not be used by any other
+ * call.  One thread should submit and wait per server (the calls are thread-safe, but the last
+ * error message is per thread). */
 typedef struct ridg_server ridg_server;
 
 typedef struct ridg_shot_request {
@@ -230,30 +297,42 @@ typedef struct ridg_shot_request {
   double t_final, t_image_start;
   const double* observed; /* [nrec][n_t] host or NULL (the modelled traces); copied at submission */
   double* traces_out;     /* [nrec][n_t] host or NULL; owned by the caller, written before completion */
-  double* image_p;        /* [K][Np] host or NULL; as traces_out */
+  double* image_p;        /* [K][Np] host or NULL (K, Np of the request's model); as traces_out */
   double* image_q;        /* [K][Np] host or NULL; as traces_out */
   const double* e_up;     /* [3] or NULL for (0, 0, -1); copied at submission */
+  int32_t model;          /* model number of the slots that may serve the request (0 for one model) */
+  int32_t reserved;
 } ridg_shot_request;
 
 typedef struct ridg_request_timing {
   double queued_s; /* submission to start */
-  double run_s;    /* start to completion (the shot and the copies into the host buffers) */
+  double run_s;    /* start to completion (admission, the shot and the copies into the host buffers) */
   double total_s;  /* submission to completion */
+  double start_s;  /* start, in seconds since the server was created */
+  double end_s;    /* completion, in seconds since the server was created */
+  int64_t slot;    /* the slot that served the request */
 } ridg_request_timing;
 
-/* Creates a server (and its worker thread) on solver s; at most max_queued requests may wait
- * behind the running one (>= 1). */
+/* Creates a server with one slot (solver s, model 0) and its worker thread; at most max_queued
+ * requests may wait (>= 1). */
 int ridg_server_create(ridg_solver* s, int64_t max_queued, ridg_server** out);
+/* Creates a server over n_slots solvers; models[i] (>= 0) is the model number of solvers[i]
+ * (NULL: all model 0).  Solvers of one model must have the same element count, order, levels and
+ * time step (checked) and should be built from the same mesh, media and options.  Each solver
+ * appears once. */
+int ridg_server_create_slots(ridg_solver* const* solvers, const int32_t* models, int64_t n_slots, int64_t max_queued,
+                             ridg_server** out);
 /* Queues a request and returns its ticket.  RIDG_E_BUSY when max_queued requests are waiting;
- * RIDG_E_INVALID_ARG for a malformed request (checked again, with the solver, when it runs). */
+ * RIDG_E_INVALID_ARG for a malformed request or a model no slot serves (checked again, with the
+ * solver, when it runs). */
 int ridg_server_submit(ridg_server* sv, const ridg_shot_request* req, int64_t* ticket);
 /* Waits at most timeout_s seconds (< 0: without limit) for a request.  When it has completed,
  * releases the ticket, fills timing (may be NULL) and returns the request's own status (0, or the
  * error it ran into, with its message in ridg_last_error); RIDG_E_TIMEOUT if it has not completed
  * in time (the ticket stays valid); RIDG_E_INVALID_ARG for an unknown ticket. */
 int ridg_server_wait(ridg_server* sv, int64_t ticket, double timeout_s, ridg_request_timing* timing);
-/* Finishes the running request, drops the queued ones (their buffers are not written) and frees
- * the server; the solver can be used again afterwards. */
+/* Finishes the running requests, drops the queued ones (their buffers are not written) and frees
+ * the server; the solvers can be used again afterwards. */
 int ridg_server_destroy(ridg_server* sv);
 
 #ifdef __cplusplus

@@ -103,4 +103,29 @@ __global__ void image_to_elements_kernel(const double* __restrict__ img, const i
   out[i] = img[((s >> 5) * Np + pos_of[n]) * 32 + (s & 31)];
 }
 
+// Fields between the C-ABI layout [K][4][Np] (double, reference node numbering) and the slot
+// layout [n_slots/32][4][Np][32] (working precision, device node numbering pos_of).
+template <int N, typename real>
+__global__ void state_from_abi_kernel(const double* __restrict__ q_abi, const int64_t* __restrict__ slot_of,
+                                      const int* __restrict__ pos_of, int64_t K, real* __restrict__ q) {
+  constexpr int Np = Order<N>::Np;
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= K * 4 * Np) return;
+  int64_t k = i / (4 * Np);
+  int r = int(i - k * 4 * Np), fld = r / Np, n = r - fld * Np;
+  int64_t s = slot_of[k];
+  q[(((s >> 5) * 4 + fld) * Np + pos_of[n]) * 32 + (s & 31)] = real(q_abi[i]);
+}
+template <int N, typename real>
+__global__ void state_to_abi_kernel(const real* __restrict__ q, const int64_t* __restrict__ slot_of,
+                                    const int* __restrict__ pos_of, int64_t K, double* __restrict__ q_abi) {
+  constexpr int Np = Order<N>::Np;
+  int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= K * 4 * Np) return;
+  int64_t k = i / (4 * Np);
+  int r = int(i - k * 4 * Np), fld = r / Np, n = r - fld * Np;
+  int64_t s = slot_of[k];
+  q_abi[i] = double(q[(((s >> 5) * 4 + fld) * Np + pos_of[n]) * 32 + (s & 31)]);
+}
+
 }  // namespace ridg

@@ -1,4 +1,5 @@
 // Explicit instantiation of the kernels of one order (RIDG_ORDER), included by kernels_n<N>.cu.
+#include "adjoint_kernels.cuh"
 #include "aux_kernels.cuh"
 #include "dispatch.hpp"
 #include "step_kernel_tc.cuh"
@@ -14,23 +15,16 @@ static cudaError_t launch_step_w(const StepArgs<real>& a, cudaStream_t st) {
   if constexpr (std::is_same<real, float>::value) {
     // FP32: element products on tensor cores (TF32 three-term split)
     constexpr size_t smem = SmemTc<N, W>::bytes;
-    static bool configured = false;
-    if (!configured) {
-      cudaError_t e = cudaFuncSetAttribute(dg_step_kernel_tc<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(smem));
-      if (e != cudaSuccess) return e;
-      configured = true;
-    }
+    // set once per process (thread-safe initialisation: shot servers launch from several threads)
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(dg_step_kernel_tc<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (configured != cudaSuccess) return configured;
     dg_step_kernel_tc<N, W><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a);
   } else {
     constexpr size_t smem = step_smem_bytes<N, real, W>();
-    static bool configured = false;
-    if (!configured) {
-      cudaError_t e = cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           int(smem));
-      if (e != cudaSuccess) return e;
-      configured = true;
-    }
+    static const cudaError_t configured =
+        cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    if (configured != cudaSuccess) return configured;
     dg_step_kernel<N, real, W><<<dim3(unsigned(blocks)), Order<N>::NT, smem, st>>>(a);
   }
   return cudaGetLastError();
@@ -72,6 +66,57 @@ cudaError_t Launch<N, real>::image_out(const double* img, const int64_t* slot_of
                                        double* out, cudaStream_t st) {
   int64_t n = K * Order<N>::Np;
   image_to_elements_kernel<N><<<unsigned((n + 255) / 256), 256, 0, st>>>(img, slot_of, pos_of, K, out);
+  return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t Launch<N, real>::state_io(bool to_slots, const double* q_abi_in, double* q_abi_out, real* q,
+                                      const int64_t* slot_of, const int* pos_of, int64_t K, cudaStream_t st) {
+  int64_t n = K * 4 * Order<N>::Np;
+  if (n <= 0) return cudaSuccess;
+  if (to_slots)
+    state_from_abi_kernel<N, real><<<unsigned((n + 255) / 256), 256, 0, st>>>(q_abi_in, slot_of, pos_of, K, q);
+  else
+    state_to_abi_kernel<N, real><<<unsigned((n + 255) / 256), 256, 0, st>>>(q, slot_of, pos_of, K, q_abi_out);
+  return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t Launch<N, real>::adj_rhs(const real* lam, real* adjt, real* out, int64_t n_slots, const double* geo,
+                                     const real* mat, const int* meta, const real* Dt, const real* Lt, int NPa,
+                                     const int* fmask, const int* nbr, const uint8_t* finfo, const int* perm,
+                                     cudaStream_t st) {
+  const int64_t nt = n_slots * 4 * Order<N>::Nfp, nn = n_slots * Order<N>::Np;
+  if (nn <= 0) return cudaSuccess;
+  adj_traces_kernel<N, real><<<unsigned((nt + 127) / 128), 128, 0, st>>>(lam, adjt, n_slots, geo, mat, meta, Lt, NPa);
+  adj_rhs_kernel<N, real><<<unsigned((nn + 127) / 128), 128, 0, st>>>(lam, adjt, out, n_slots, geo, mat, meta, Dt, NPa,
+                                                                       fmask, nbr, finfo, perm);
+  return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t Launch<N, real>::adj_update(real* lam, const real* s0, const real* s1, const real* s2, double h, int64_t n,
+                                        cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  adj_update_kernel<real><<<unsigned((n + 255) / 256), 256, 0, st>>>(lam, s0, s1, s2, h, n);
+  return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t Launch<N, real>::adj_inject(real* lam, const int64_t* rec_slot, const real* rec_row, int nrec,
+                                        const double* res, int64_t n_time, int64_t col, double coef, cudaStream_t st) {
+  if (nrec <= 0) return cudaSuccess;
+  adj_inject_kernel<N, real><<<1, 128, 0, st>>>(lam, rec_slot, rec_row, nrec, res, n_time, col, coef);
+  return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t Launch<N, real>::adj_grad(const real* lam, const real* q1, const real* q0, int64_t n_slots,
+                                      const int* meta, int64_t src_slot, const real* w_src, double F, double* acc,
+                                      cudaStream_t st) {
+  if (n_slots <= 0) return cudaSuccess;
+  adj_grad_kernel<N, real><<<unsigned((n_slots + 127) / 128), 128, 0, st>>>(lam, q1, q0, n_slots, meta, src_slot,
+                                                                           w_src, F, acc);
   return cudaGetLastError();
 }
 

@@ -98,6 +98,46 @@ static double ricker(double t, double f0, double tp, double amp) {
   return amp * (1.0 - 2.0 * a) * std::exp(-a);
 }
 
+// Source wavelet of a ridg_source (a copy: sampled wavelets keep their own samples).
+struct Wavelet {
+  int kind = RIDG_SRC_RICKER;
+  double f0 = 0.0, tp = 0.0, amp = 1.0, dt = 0.0;
+  std::vector<double> samples;
+  static Wavelet of(const ridg_source& s) {
+    Wavelet w;
+    w.kind = s.kind;
+    w.f0 = s.f0;
+    w.tp = s.t_peak;
+    w.amp = s.amplitude;
+    if (s.kind == RIDG_SRC_SAMPLED) {
+      if (!(s.sample_dt > 0.0) || s.n_samples < 1 || !s.samples)
+        throw Error{RIDG_E_INVALID_ARG, "sampled source needs sample_dt > 0, n_samples >= 1 and samples"};
+      w.dt = s.sample_dt;
+      w.samples.assign(s.samples, s.samples + s.n_samples);
+    } else if (s.kind != RIDG_SRC_RICKER) {
+      throw Error{RIDG_E_INVALID_ARG, "unknown source kind"};
+    }
+    return w;
+  }
+  // f(t): the Ricker pulse, or the 4-point Lagrange interpolant of the samples on the nodes
+  // n_lo - 1 .. n_lo + 2 around t / dt (zero outside the samples)
+  double operator()(double t) const {
+    if (kind == RIDG_SRC_RICKER) return ricker(t, f0, tp, amp);
+    const double u = t / dt, n_lo = std::floor(u), x = u - n_lo;
+    const double xs[4] = {-1.0, 0.0, 1.0, 2.0};
+    double acc = 0.0;
+    for (int i = 0; i < 4; ++i) {
+      const double n = n_lo - 1.0 + i;
+      if (n < 0.0 || n >= double(samples.size())) continue;
+      double li = 1.0;
+      for (int j = 0; j < 4; ++j)
+        if (j != i) li *= (x - xs[j]) / (xs[i] - xs[j]);
+      acc += li * samples[size_t(n)];
+    }
+    return amp * acc;
+  }
+};
+
 }  // namespace ridg
 
 struct ridg_mesh {
@@ -125,6 +165,18 @@ struct ridg_solver {
   virtual void set_profiling(int every) = 0;
   // device bytes a shot of this record length would still allocate (arena growth, first-shot buffers)
   virtual size_t shot_extra_device_bytes(double t_final) const = 0;
+  // frees the device buffers only a shot uses (the next shot allocates them again); returns their bytes
+  virtual size_t release_shot_buffers() = 0;
+  virtual void forward(const ridg_source& src, const double* rec, int64_t nrec, double t_final,
+                       double* traces_dev) = 0;
+  virtual void set_state_device(const double* q_dev) = 0;
+  virtual void get_state_device(double* q_dev) = 0;
+  // velocity gradient (single rate level): see ridg_set_velocity / ridg_misfit_forward / _backward
+  virtual void set_velocity(const double* c) = 0;
+  virtual void eval_adjoint_rhs(const double* lam, double* out) = 0;
+  virtual double misfit_forward(const ridg_source& src, const double* rec, int64_t nrec, double t_final,
+                                const double* observed, int n_ckpt, double* traces_host) = 0;
+  virtual void misfit_backward(double* grad) = 0;
 };
 
 namespace ridg {
@@ -155,12 +207,16 @@ class Engine final : public ridg_solver {
     NPa_ = 2 * ((Np_ + 1) / 2);
     geo_ = build_geometry(mesh_);
     c_.assign(c, c + mesh_.K);
+    c_ref_ = c_;
     rho_.assign(rho, rho + mesh_.K);
     for (int64_t k = 0; k < mesh_.K; ++k)
       if (!(rho_[k] > 0.0) || !(c_[k] > 0.0) || !std::isfinite(rho_[k]) || !std::isfinite(c_[k]))
         throw Error{RIDG_E_INVALID_ARG, "c and rho must be positive and finite"};
     double cfl = opt.cfl > 0 ? opt.cfl : 0.15;
     int nlm = opt.n_levels_max > 0 ? opt.n_levels_max : 3;
+    tau_scale_ = opt.tau_scale > 0 ? opt.tau_scale : 1.0;
+    image_mode_ = ((opt.image_mask & RIDG_IMAGE_P) || !(opt.image_mask & 3) ? kModeImageP : 0) |
+                  ((opt.image_mask & RIDG_IMAGE_Q) || !(opt.image_mask & 3) ? kModeImageQ : 0);
     if (nlm > kMaxLevels) throw Error{RIDG_E_INVALID_ARG, "n_levels_max too large"};
     lv_ = assign_levels(mesh_, geo_, N, c_.data(), cfl, nlm);
     ord_ = build_ordering(lv_, mesh_.K);
@@ -307,6 +363,277 @@ class Engine final : public ridg_solver {
                                          dptr<const double>(M_d_), out_dev, st_);
     if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("ridg_energy_noalloc: ") + cudaGetErrorString(e)};
   }
+  void set_state_device(const double* q_dev) override {
+    if (!q_dev) throw Error{RIDG_E_INVALID_ARG, "q_dev is null"};
+    state_io(true, q_dev, nullptr);
+    RIDG_CUDA(cudaMemsetAsync(w_[0].ring.p, 0, w_[0].ring.bytes, st_));
+    reset_time();
+    init_traces(w_[0], mod3(tau_));
+  }
+  void get_state_device(double* q_dev) override {
+    if (!q_dev) throw Error{RIDG_E_INVALID_ARG, "q_dev is null"};
+    state_io(false, nullptr, q_dev);
+  }
+  void state_io(bool to_slots, const double* in, double* out) {
+    cudaError_t e = dispatch_order(N_, [&](auto NC) {
+      return Launch<decltype(NC)::value, real>::state_io(to_slots, in, out, dptr<real>(w_[0].q),
+                                                          dptr<const int64_t>(slot_of_d_), dptr<const int>(pos_d_),
+                                                          mesh_.K, st_);
+    });
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
+    ++stats_.kernel_launches;
+  }
+
+  // Forward modelling: the forward source run of a shot alone (Sec. 2), receiver pressures
+  // sampled at every global step into traces_dev [nrec][n_t].
+  void forward(const ridg_source& src, const double* rec, int64_t nrec, double t_final,
+               double* traces_dev) override {
+    if (!(t_final > 0.0)) throw Error{RIDG_E_INVALID_ARG, "t_final must be > 0"};
+    if (nrec < 0 || (nrec > 0 && (!rec || !traces_dev))) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
+    const Wavelet wav = Wavelet::of(src);
+    std::memset(&stats_, 0, sizeof(stats_));
+    prof_used_ = 0;
+    const double dtl = lv_.dt_local, dtg = dtl * double(NL_);
+    const int64_t n_global = int64_t(std::ceil(t_final / dtg - 1e-9));
+    const int64_t n_t = n_global + 1;
+    stats_.n_global = n_global;
+    double rst[3];
+    const int64_t ks = locate_point(mesh_, geo_, src.xyz, rst);
+    if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
+    {
+      std::vector<int2> range(n_slots_, make_int2(0, 0));
+      range[ord_.slot_of[ks]] = make_int2(0, 1);
+      upload(w_[0].inj_range, range, st_);
+      upload(w_[0].inj_w, projected_dirac(ks, rst), st_);
+      upload(w_[0].inj_row, std::vector<int>{0}, st_);
+    }
+    std::vector<int64_t> rslot(std::max<int64_t>(nrec, 1), 0);
+    std::vector<real> rrow(std::max<int64_t>(nrec, 1) * Np_, real(0));
+    for (int64_t r = 0; r < nrec; ++r) {
+      const int64_t kr = locate_point(mesh_, geo_, rec + 3 * r, rst);
+      if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
+      rslot[r] = ord_.slot_of[kr];
+      std::vector<double> l = ref_.lagrange_at({rst[0], rst[1], rst[2]});
+      for (int m = 0; m < Np_; ++m) rrow[r * Np_ + m] = real(l[m]);
+    }
+    upload(rec_slot_, rslot, st_);
+    upload(rec_row_, rrow, st_);
+    zero_wave(w_[0]);
+    reset_time();
+    if (nrec > 0) RIDG_CUDA(cudaMemsetAsync(traces_dev, 0, size_t(nrec) * n_t * sizeof(double), st_));
+    sample(traces_dev, n_t, 0, nrec);
+    for (int64_t g = 0; g < n_global; ++g) {
+      for (int64_t sub = 0; sub < NL_; ++sub) {
+        StepArgs<real> a = fine_args(+1, 1, 0);
+        a.wave[0] = wave_args(w_[0]);
+        a.wave[0].amp_mode = 1;
+        a.wave[0].amp = real(wav(double(tau_) * dtl));
+        launch_fine(a, +1, 1);
+      }
+      sample(traces_dev, n_t, g + 1, nrec);
+    }
+    stats_.dof_updates_forward = dof_;
+    RIDG_CUDA(cudaGetLastError());
+  }
+
+  // ------------------------------------------------------------------ velocity gradient
+  void set_velocity(const double* c) override {
+    if (!c) throw Error{RIDG_E_INVALID_ARG, "c is null"};
+    for (int64_t k = 0; k < mesh_.K; ++k)
+      if (!(c[k] > 0.0) || !std::isfinite(c[k])) throw Error{RIDG_E_INVALID_ARG, "c must be positive and finite"};
+    c_.assign(c, c + mesh_.K);
+    upload_material();
+    adj_.ready = false;
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+  }
+
+  void adjoint_rhs_into(const real* lam, real* out, real* adjt) {
+    cudaError_t e = dispatch_order(N_, [&](auto NC) {
+      return Launch<decltype(NC)::value, real>::adj_rhs(
+          lam, adjt, out, n_slots_, dptr<const double>(geo_d_), dptr<const real>(mat_d_), dptr<const int>(meta_d_),
+          dptr<const real>(Dt_d_), dptr<const real>(Lt_d_), NPa_, dptr<const int>(fmask_d_), dptr<const int>(nbr_d_),
+          dptr<const uint8_t>(finfo_d_), dptr<const int>(perm_d_), st_);
+    });
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
+  }
+
+  void eval_adjoint_rhs(const double* lam, double* out) override {
+    if (!lam || !out) throw Error{RIDG_E_INVALID_ARG, "null lam or out"};
+    DBuf l, o, t;
+    l.alloc(qsize() * sizeof(real));
+    o.alloc(qsize() * sizeof(real));
+    t.alloc(trace_slot_elems() * sizeof(real));
+    std::vector<real> h = to_slots(lam);
+    RIDG_CUDA(cudaMemcpyAsync(l.p, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice, st_));
+    adjoint_rhs_into(dptr<real>(l), dptr<real>(o), dptr<real>(t));
+    std::vector<real> r(qsize());
+    RIDG_CUDA(cudaMemcpyAsync(r.data(), o.p, o.bytes, cudaMemcpyDeviceToHost, st_));
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    from_slots(r, out);
+  }
+
+  void misfit_step(const Wavelet& wav) {
+    StepArgs<real> a = fine_args(+1, 1, 0);
+    a.wave[0] = wave_args(w_[0]);
+    a.wave[0].amp_mode = 1;
+    a.wave[0].amp = real(wav(double(tau_) * lv_.dt_local));
+    launch_fine(a, +1, 1);
+  }
+
+  double misfit_forward(const ridg_source& src, const double* rec, int64_t nrec, double t_final,
+                        const double* observed, int n_ckpt, double* traces_host) override {
+    if (L_ != 1)
+      throw Error{RIDG_E_INVALID_ARG, "the misfit gradient needs one rate level (create the solver with n_levels_max = 1)"};
+    if (!(t_final > 0.0)) throw Error{RIDG_E_INVALID_ARG, "t_final must be > 0"};
+    if (nrec < 1 || !rec || !observed) throw Error{RIDG_E_INVALID_ARG, "receivers and observed traces are required"};
+    adj_.ready = false;
+    adj_.wav = Wavelet::of(src);
+    const double dt = lv_.dt_local;
+    const int64_t n_global = int64_t(std::ceil(t_final / dt - 1e-9)), n_t = n_global + 1;
+    const int64_t n_ck_max = n_ckpt > 0 ? n_ckpt : 16;
+    adj_.n_global = n_global;
+    adj_.seg = std::max<int64_t>(1, (n_global + n_ck_max - 1) / n_ck_max);
+    adj_.n_ck = (n_global + adj_.seg - 1) / adj_.seg;
+    adj_.nrec = nrec;
+    double rst[3];
+    const int64_t ks = locate_point(mesh_, geo_, src.xyz, rst);
+    if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
+    adj_.src_slot = ord_.slot_of[ks];
+    const std::vector<real> w_src = projected_dirac(ks, rst);
+    {
+      std::vector<int2> range(n_slots_, make_int2(0, 0));
+      range[adj_.src_slot] = make_int2(0, 1);
+      upload(w_[0].inj_range, range, st_);
+      upload(w_[0].inj_w, w_src, st_);
+      upload(w_[0].inj_row, std::vector<int>{0}, st_);
+      upload(adj_w_, w_src, st_);
+    }
+    std::vector<int64_t> rslot(nrec, 0);
+    std::vector<real> rrow(nrec * Np_, real(0));
+    for (int64_t r = 0; r < nrec; ++r) {
+      const int64_t kr = locate_point(mesh_, geo_, rec + 3 * r, rst);
+      if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
+      rslot[r] = ord_.slot_of[kr];
+      std::vector<double> l = ref_.lagrange_at({rst[0], rst[1], rst[2]});
+      for (int m = 0; m < Np_; ++m) rrow[r * Np_ + m] = real(l[m]);
+    }
+    upload(rec_slot_, rslot, st_);
+    upload(rec_row_, rrow, st_);
+    upload(adj_rec_slot_, rslot, st_);
+    upload(adj_rec_row_, rrow, st_);
+    adj_.amp.assign(n_global + 1, 0.0);
+    for (int64_t n = 0; n <= n_global; ++n) adj_.amp[n] = double(real(adj_.wav(double(n) * dt)));
+    const size_t qb = qsize() * sizeof(real), tb = 3 * trace_slot_elems() * sizeof(real);
+    ck_q_.reserve(size_t(adj_.n_ck) * qb);
+    ck_ring_.reserve(size_t(adj_.n_ck) * 3 * qb);
+    ck_trace_.reserve(size_t(adj_.n_ck) * tb);
+    adj_.ck_tau.assign(adj_.n_ck, 0);
+    adj_.ck_count.assign(adj_.n_ck, 0);
+    DBuf y;
+    y.alloc(size_t(nrec) * n_t * sizeof(double));
+    zero_wave(w_[0]);
+    reset_time();
+    std::memset(&stats_, 0, sizeof(stats_));
+    stats_.n_global = n_global;
+    sample(dptr<double>(y), n_t, 0, nrec);
+    for (int64_t g = 0; g < n_global; ++g) {
+      if (g % adj_.seg == 0) {
+        const int64_t j = g / adj_.seg;
+        char* cq = static_cast<char*>(ck_q_.p) + size_t(j) * qb;
+        char* cr = static_cast<char*>(ck_ring_.p) + size_t(j) * 3 * qb;
+        char* ct = static_cast<char*>(ck_trace_.p) + size_t(j) * tb;
+        RIDG_CUDA(cudaMemcpyAsync(cq, w_[0].q.p, qb, cudaMemcpyDeviceToDevice, st_));
+        RIDG_CUDA(cudaMemcpyAsync(cr, w_[0].ring.p, 3 * qb, cudaMemcpyDeviceToDevice, st_));
+        RIDG_CUDA(cudaMemcpyAsync(ct, w_[0].trace.p, tb, cudaMemcpyDeviceToDevice, st_));
+        adj_.ck_tau[j] = tau_;
+        adj_.ck_count[j] = ring_count_[0];
+      }
+      misfit_step(adj_.wav);
+      sample(dptr<double>(y), n_t, g + 1, nrec);
+    }
+    stats_.dof_updates_forward = dof_;
+    std::vector<double> yh(size_t(nrec) * n_t);
+    RIDG_CUDA(cudaMemcpyAsync(yh.data(), y.p, yh.size() * sizeof(double), cudaMemcpyDeviceToHost, st_));
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    double J = 0.0;
+    for (size_t i = 0; i < yh.size(); ++i) {
+      const double r = yh[i] - observed[i];
+      J += r * r;
+      yh[i] = r;
+    }
+    J *= 0.5 * dt;
+    if (traces_host)
+      for (size_t i = 0; i < yh.size(); ++i) traces_host[i] = yh[i] + observed[i];
+    upload(adj_res_, yh, st_);
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    if (!std::isfinite(J)) throw Error{RIDG_E_UNSTABLE, "non-finite misfit"};
+    adj_.ready = true;
+    return J;
+  }
+
+  void misfit_backward(double* grad) override {
+    if (!adj_.ready) throw Error{RIDG_E_INVALID_ARG, "no misfit forward run to differentiate (or the velocity changed)"};
+    if (!grad) throw Error{RIDG_E_INVALID_ARG, "grad is null"};
+    const double h = lv_.dt_local;
+    const size_t qn = qsize(), qb = qn * sizeof(real), tb = 3 * trace_slot_elems() * sizeof(real);
+    const int64_t n_t = adj_.n_global + 1;
+    DBuf lam, sring, adjt, seg, acc;
+    lam.alloc(qb);
+    sring.alloc(3 * qb);
+    adjt.alloc(trace_slot_elems() * sizeof(real));
+    seg.alloc(size_t(adj_.seg + 1) * qb);
+    acc.alloc(size_t(n_slots_) * sizeof(double));
+    RIDG_CUDA(cudaMemsetAsync(lam.p, 0, lam.bytes, st_));
+    RIDG_CUDA(cudaMemsetAsync(sring.p, 0, sring.bytes, st_));
+    RIDG_CUDA(cudaMemsetAsync(acc.p, 0, acc.bytes, st_));
+    real* L = dptr<real>(lam);
+    auto sr = [&](int64_t j) { return dptr<real>(sring) + size_t(j % 3) * qn; };
+    auto sg = [&](int64_t i) { return dptr<real>(seg) + size_t(i) * qn; };
+    const double a[3] = {AB::a1, AB::a2, AB::a3};
+    for (int64_t j = adj_.n_ck - 1; j >= 0; --j) {
+      const int64_t a0 = j * adj_.seg, b0 = std::min(a0 + adj_.seg, adj_.n_global);
+      // recompute the forward states q^a0 .. q^b0 from the checkpoint
+      RIDG_CUDA(cudaMemcpyAsync(w_[0].q.p, static_cast<char*>(ck_q_.p) + size_t(j) * qb, qb, cudaMemcpyDeviceToDevice,
+                                st_));
+      RIDG_CUDA(cudaMemcpyAsync(w_[0].ring.p, static_cast<char*>(ck_ring_.p) + size_t(j) * 3 * qb, 3 * qb,
+                                cudaMemcpyDeviceToDevice, st_));
+      RIDG_CUDA(cudaMemcpyAsync(w_[0].trace.p, static_cast<char*>(ck_trace_.p) + size_t(j) * tb, tb,
+                                cudaMemcpyDeviceToDevice, st_));
+      tau_ = adj_.ck_tau[j];
+      ring_count_[0] = int(adj_.ck_count[j]);
+      RIDG_CUDA(cudaMemcpyAsync(sg(0), w_[0].q.p, qb, cudaMemcpyDeviceToDevice, st_));
+      for (int64_t n = a0; n < b0; ++n) {
+        misfit_step(adj_.wav);
+        RIDG_CUDA(cudaMemcpyAsync(sg(n + 1 - a0), w_[0].q.p, qb, cudaMemcpyDeviceToDevice, st_));
+      }
+      // adjoint steps m = b0 .. a0 + 1: lambda^m = lambda^{m+1} + h sum_s a_s A^T lambda^{m+1+s} - g^m
+      for (int64_t m = b0; m > a0; --m) {
+        adjoint_rhs_into(L, sr(m + 1), dptr<real>(adjt));
+        double F = 0.0;  // source part of q^m - q^{m-1}
+        for (int s = 0; s < 3; ++s)
+          if (m - 1 - s >= 0) F += h * a[s] * adj_.amp[m - 1 - s];
+        cudaError_t e = dispatch_order(N_, [&](auto NC) {
+          using LN = Launch<decltype(NC)::value, real>;
+          cudaError_t e2 = LN::adj_update(L, sr(m + 1), sr(m + 2), sr(m + 3), h, int64_t(qn), st_);
+          if (e2 == cudaSuccess)
+            e2 = LN::adj_inject(L, dptr<const int64_t>(adj_rec_slot_), dptr<const real>(adj_rec_row_), int(adj_.nrec),
+                                dptr<const double>(adj_res_), n_t, m, h, st_);
+          if (e2 == cudaSuccess)
+            e2 = LN::adj_grad(L, sg(m - a0), sg(m - 1 - a0), n_slots_, dptr<const int>(meta_d_), adj_.src_slot,
+                              dptr<const real>(adj_w_), F, dptr<double>(acc), st_);
+          return e2;
+        });
+        if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
+      }
+    }
+    std::vector<double> sums(n_slots_);
+    RIDG_CUDA(cudaMemcpyAsync(sums.data(), acc.p, acc.bytes, cudaMemcpyDeviceToHost, st_));
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    for (int64_t k = 0; k < mesh_.K; ++k) grad[k] = -2.0 / c_[k] * sums[ord_.slot_of[k]];
+    for (int64_t k = 0; k < mesh_.K; ++k)
+      if (!std::isfinite(grad[k])) throw Error{RIDG_E_UNSTABLE, "non-finite gradient"};
+  }
+
   size_t shot_extra_device_bytes(double t_final) const override {
     if (!(t_final > 0.0)) return 0;
     const double dtg = lv_.dt_local * double(NL_);
@@ -318,6 +645,16 @@ class Engine final : public ridg_solver {
     if (!q_snap_.p) extra += 4 * qsize() * sizeof(real) + 2 * size_t(n_slots_) * Np_ * sizeof(double);
     if (!w_[1].q.p) extra += 4 * qsize() * sizeof(real) + 3 * trace_slot_elems() * sizeof(real);
     return extra;
+  }
+  size_t release_shot_buffers() override {
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    size_t bytes = 0;
+    for (DBuf* d : {&arena_, &q_snap_, &ring_snap_, &img_p_, &img_q_, &traces_tmp_, &w_[1].q, &w_[1].ring, &w_[1].trace,
+                    &w_[1].inj_range, &w_[1].inj_w, &w_[1].inj_row}) {
+      bytes += d->bytes;
+      d->release();
+    }
+    return bytes;
   }
   int64_t trace_len(double t_final) const override {
     double dtg = lv_.dt_local * double(NL_);
@@ -344,6 +681,7 @@ class Engine final : public ridg_solver {
     int64_t ks = locate_point(mesh_, geo_, src.xyz, rst);
     if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
     std::vector<real> w_src = projected_dirac(ks, rst);
+    const Wavelet wav = Wavelet::of(src);
     struct Rec {
       int64_t slot;
       std::vector<real> row, w;
@@ -424,7 +762,7 @@ class Engine final : public ridg_solver {
       StepArgs<real> a = fine_args(+1, 1, mode);
       a.wave[0] = wave_args(w_[0]);
       a.wave[0].amp_mode = 1;
-      a.wave[0].amp = real(ricker(double(tau_) * dtl, src.f0, src.t_peak, src.amplitude));
+      a.wave[0].amp = real(wav(double(tau_) * dtl));
       a.arena_write = dptr<real>(arena_);
       a.arena_offset = arena_base[std::min<int64_t>(tau_, tau_f)] - bface_first(a.slot_lo);
       launch_fine(a, +1, 1);
@@ -459,10 +797,10 @@ class Engine final : public ridg_solver {
     const double* data = obs_dev ? obs_dev : traces;
     int64_t dof_before = dof_;
     while (tau_ > tau_i) {
-      StepArgs<real> a = fine_args(-1, 2, kModeReplay | kModeImage);
+      StepArgs<real> a = fine_args(-1, 2, kModeReplay | image_mode_);
       a.wave[0] = wave_args(w_[0]);
       a.wave[0].amp_mode = 1;
-      a.wave[0].amp = real(ricker(double(tau_) * dtl, src.f0, src.t_peak, src.amplitude));
+      a.wave[0].amp = real(wav(double(tau_) * dtl));
       a.wave[1] = wave_args(w_[1]);
       a.wave[1].amp_mode = nrec > 0 ? 2 : 0;
       a.wave[1].data = data;
@@ -592,7 +930,6 @@ class Engine final : public ridg_solver {
   void build_tables() {
     const int64_t S = n_slots_;
     std::vector<double> geo(S * kGeo, 0.0), J(S, 0.0);
-    std::vector<real> mat(S * kMat, real(0));
     std::vector<int> nbr(S * 4, -1), bface(S, 0), meta(S, 0);
     std::vector<uint8_t> finfo(S * 4, 0);
     int64_t nb = 0;
@@ -605,15 +942,8 @@ class Engine final : public ridg_solver {
       for (int i = 0; i < 12; ++i) geo[s * kGeo + 9 + i] = geo_.normal[12 * k + i];
       for (int f = 0; f < 4; ++f) geo[s * kGeo + 21 + f] = geo_.fscale[4 * k + f];
       J[s] = geo_.J[k];
-      double Zk = rho_[k] * c_[k];
-      mat[s * kMat + 0] = real(rho_[k] * c_[k] * c_[k]);
-      mat[s * kMat + 1] = real(1.0 / rho_[k]);
-      mat[s * kMat + 2] = real(Zk);
       for (int f = 0; f < 4; ++f) {
         int64_t k2 = mesh_.nbr[4 * k + f];
-        double Zb = k2 >= 0 ? 0.5 * (Zk + rho_[k2] * c_[k2]) : Zk;
-        mat[s * kMat + 3 + f] = real(1.0 / Zb);
-        mat[s * kMat + 7 + f] = real(Zb);
         int bc = k2 >= 0 ? 0 : mesh_.bc[4 * k + f];
         int nf = k2 >= 0 ? mesh_.nbr_face[4 * k + f] : 0;
         int pc = k2 >= 0 ? mesh_.perm_code[4 * k + f] : 0;
@@ -628,7 +958,7 @@ class Engine final : public ridg_solver {
     bface_host_ = bface;
     upload(geo_d_, geo, st_);
     upload(J_d_, J, st_);
-    upload(mat_d_, mat, st_);
+    upload_material();
     upload(nbr_d_, nbr, st_);
     upload(finfo_d_, finfo, st_);
     upload(bface_d_, bface, st_);
@@ -641,11 +971,7 @@ class Engine final : public ridg_solver {
       for (int n = 0; n < Np_; ++n) Lt[fm * NPa_ + n] = real(ref_.LIFT(n, fm));
     upload(Dt_d_, Dt, st_);
     upload(Lt_d_, Lt, st_);
-    if (std::is_same<real, float>::value) {
-      upload(afrag_d_, operator_fragments(), st_);
-      upload(gtab_d_[0], coefficient_table(+1), st_);
-      upload(gtab_d_[1], coefficient_table(-1), st_);
-    }
+    if (std::is_same<real, float>::value) upload(afrag_d_, operator_fragments(), st_);
     std::vector<int> fm(128, 0), pm(192, 0);
     for (int f = 0; f < 4; ++f)
       for (int j = 0; j < Nfp_; ++j) fm[f * 32 + j] = ref_.fmask[f][j];
@@ -665,6 +991,32 @@ class Engine final : public ridg_solver {
   // Eq. dgLocalSchemeP), rho c, -rx_ij / rho (volume v equation, Eq. dgLocalSchemeU), the outward
   // normals, and per face the coefficients of t = A [n.v] + B [p] and s = C [p] + D [n.v] with the
   // surface Jacobian and the 1/2 of the weak form folded in.
+  // Per-element material factors: rho c^2 with the current velocity; the impedance (penalty
+  // parameters, characteristics of I_Q) with the velocity the solver was created with.
+  void upload_material() {
+    const int64_t S = n_slots_;
+    std::vector<real> mat(S * kMat, real(0));
+    for (int64_t s = 0; s < S; ++s) {
+      int64_t k = ord_.elem_of[s];
+      if (k < 0) continue;
+      const double Zk = rho_[k] * c_ref_[k];
+      mat[s * kMat + 0] = real(rho_[k] * c_[k] * c_[k]);
+      mat[s * kMat + 1] = real(1.0 / rho_[k]);
+      mat[s * kMat + 2] = real(Zk);
+      for (int f = 0; f < 4; ++f) {
+        int64_t k2 = mesh_.nbr[4 * k + f];
+        double Zb = k2 >= 0 ? 0.5 * (Zk + rho_[k2] * c_ref_[k2]) : Zk;
+        mat[s * kMat + 3 + f] = real(tau_scale_ / Zb);
+        mat[s * kMat + 7 + f] = real(tau_scale_ * Zb);
+      }
+    }
+    upload(mat_d_, mat, st_);
+    if (std::is_same<real, float>::value) {
+      upload(gtab_d_[0], coefficient_table(+1), st_);
+      upload(gtab_d_[1], coefficient_table(-1), st_);
+    }
+  }
+
   std::vector<float> coefficient_table(int sigma) const {
     const int64_t S = n_slots_;
     std::vector<float> g(size_t(S) * kGtab, 0.f);
@@ -672,7 +1024,7 @@ class Engine final : public ridg_solver {
       int64_t k = ord_.elem_of[s];
       if (k < 0) continue;
       float* at = &g[size_t(s) * kGtab];
-      const double rho = rho_[k], c = c_[k], rc2 = rho * c * c, irho = 1.0 / rho, Zk = rho * c;
+      const double rho = rho_[k], c = c_[k], rc2 = rho * c * c, irho = 1.0 / rho, Zk = rho * c_ref_[k];
       for (int i = 0; i < 9; ++i) {
         at[kGtU + i] = float(-rc2 * geo_.rx[9 * k + i]);
         at[kGtV + i] = float(-irho * geo_.rx[9 * k + i]);
@@ -681,8 +1033,8 @@ class Engine final : public ridg_solver {
       for (int f = 0; f < 4; ++f) {
         for (int d = 0; d < 3; ++d) at[kGtN + 4 * f + d] = float(geo_.normal[12 * k + 3 * f + d]);
         int64_t k2 = mesh_.nbr[4 * k + f];
-        double Zb = k2 >= 0 ? 0.5 * (Zk + rho_[k2] * c_[k2]) : Zk;
-        double fs = geo_.fscale[4 * k + f], taup = sigma / Zb, tauv = sigma * Zb;
+        double Zb = k2 >= 0 ? 0.5 * (Zk + rho_[k2] * c_ref_[k2]) : Zk;
+        double fs = geo_.fscale[4 * k + f], taup = sigma * tau_scale_ / Zb, tauv = sigma * tau_scale_ * Zb;
         at[kGtP + 4 * f + 0] = float(-0.5 * fs * rc2);
         at[kGtP + 4 * f + 1] = float(0.5 * fs * rc2 * taup);
         at[kGtP + 4 * f + 2] = float(0.5 * fs * irho);
@@ -933,13 +1285,24 @@ class Engine final : public ridg_solver {
   Geometry geo_;
   Levels lv_;
   Ordering ord_;
-  std::vector<double> c_, rho_, xnodes_;
+  std::vector<double> c_, c_ref_, rho_, xnodes_;
+  // misfit gradient: the last misfit forward run (checkpoints of the single-level state)
+  struct AdjointRun {
+    bool ready = false;
+    Wavelet wav;
+    int64_t n_global = 0, seg = 1, n_ck = 0, nrec = 0, src_slot = 0;
+    std::vector<int64_t> ck_tau, ck_count;
+    std::vector<double> amp;
+  } adj_;
+  DBuf ck_q_, ck_ring_, ck_trace_, adj_res_, adj_w_, adj_rec_slot_, adj_rec_row_;
   int64_t n_slots_ = 0, NL_ = 1, n_bfaces_ = 0;
   int L_ = 1;
   std::vector<int> bface_host_;
   std::vector<int64_t> level_count_;
   DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
   DBuf afrag_d_, gtab_d_[2], pos_d_;
+  double tau_scale_ = 1.0;
+  int image_mode_ = kModeImage;
   std::vector<int> pos_of_;  // device position of each reference node
   DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_;
   Wave<real> w_[2];
@@ -1018,54 +1381,144 @@ static void run_host_shot(ridg_solver* s, const ridg_source& src, const double* 
 
 }  // namespace ridg
 
-// Shot server: a FIFO of requests served by one worker thread on the solver's stream.
+// Shot server: requests queued in arrival order, served by slots (one solver and one worker thread
+// each); an idle slot takes the oldest request of its model.
 struct ridg_server {
   using clock = std::chrono::steady_clock;
   struct Request {
     ridg_shot_request r{};
-    std::vector<double> rec, obs, eup;
+    std::vector<double> rec, obs, eup, samples;
     clock::time_point submitted, started, finished;
+    int64_t slot = -1;
     bool done = false;
     int status = RIDG_OK;
     std::string error;
   };
-  ridg_solver* solver = nullptr;
+  struct Slot {
+    ridg_solver* solver = nullptr;
+    int32_t model = 0;
+    bool busy = false;     // running a request, or its buffers being released
+    bool waiting = false;  // its request waits for device memory (counts as not running)
+    std::thread worker;
+    ridg::HostShotBuffers buffers;
+  };
+  std::vector<std::unique_ptr<Slot>> slots;
   int device = 0;
   int64_t max_queued = 1;
+  clock::time_point created = clock::now();
   std::mutex mu;
   std::condition_variable work_cv, done_cv;
   std::deque<int64_t> queue;
   std::map<int64_t, std::unique_ptr<Request>> requests;
   int64_t next_ticket = 1;
+  int64_t finished_shots = 0;
+  bool memory_wait = false;  // a request waits for device memory: idle slots start nothing new
   bool stop = false;
-  std::thread worker;
-  ridg::HostShotBuffers buffers;
 
-  void run() {
+  bool serves(int32_t model) const {
+    for (const auto& s : slots)
+      if (s->model == model) return true;
+    return false;
+  }
+  // oldest queued request of a model (queue.end() if none); mu held
+  std::deque<int64_t>::iterator next_of(int32_t model) {
+    for (auto it = queue.begin(); it != queue.end(); ++it)
+      if (requests[*it]->r.model == model) return it;
+    return queue.end();
+  }
+
+  // Device memory for the shot slot s is about to run: free it from idle slots, or wait for
+  // running ones, or give up with RIDG_E_OOM.
+  void admit(Slot* s, const Request* q) {
+    const size_t margin = size_t(256) << 20;
+    struct Done {
+      ridg_server* sv;
+      Slot* s;
+      ~Done() {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        s->waiting = false;
+        bool any = false;
+        for (auto& o : sv->slots) any = any || o->waiting;
+        sv->memory_wait = any;
+      }
+    } done{this, s};
+    for (;;) {
+      const size_t need = s->solver->shot_extra_device_bytes(q->r.t_final);
+      size_t free_b = 0, total_b = 0;
+      RIDG_CUDA(cudaMemGetInfo(&free_b, &total_b));
+      if (need + margin <= free_b) return;
+      std::vector<Slot*> idle;
+      bool running = false;
+      int64_t seen = 0;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        memory_wait = true;
+        s->waiting = true;
+        seen = finished_shots;
+        for (auto& o : slots) {
+          if (o.get() == s) continue;
+          if (o->busy) {
+            running = running || !o->waiting;
+          } else {
+            o->busy = true;
+            idle.push_back(o.get());
+          }
+        }
+      }
+      size_t released = 0;
+      for (Slot* o : idle) {
+        released += o->solver->release_shot_buffers();
+        for (ridg::DBuf* d : {&o->buffers.obs, &o->buffers.tr, &o->buffers.ip, &o->buffers.iq}) {
+          released += d->bytes;
+          d->release();
+        }
+      }
+      released += [&] {
+        // this slot's own host-shot buffers are re-reserved by the shot
+        size_t b = 0;
+        for (ridg::DBuf* d : {&s->buffers.obs, &s->buffers.tr, &s->buffers.ip, &s->buffers.iq}) {
+          b += d->bytes;
+          d->release();
+        }
+        return b;
+      }();
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        for (Slot* o : idle) o->busy = false;
+        if (released > 0) continue;
+        if (!running)
+          throw Error{RIDG_E_OOM, "shot needs " + std::to_string(need) + " more device bytes, " +
+                                      std::to_string(free_b) + " free"};
+        done_cv.wait(lk, [&] { return stop || finished_shots != seen; });
+        if (stop) throw Error{RIDG_E_INVALID_ARG, "server stopped while the request waited for device memory"};
+      }
+    }
+  }
+
+  void run(Slot* s, int64_t index) {
     cudaSetDevice(device);
     for (;;) {
       Request* q = nullptr;
       {
         std::unique_lock<std::mutex> lk(mu);
-        work_cv.wait(lk, [&] { return stop || !queue.empty(); });
+        work_cv.wait(lk, [&] { return stop || (!memory_wait && !s->busy && next_of(s->model) != queue.end()); });
         if (stop) return;
-        q = requests[queue.front()].get();
-        queue.pop_front();
+        auto it = next_of(s->model);
+        q = requests[*it].get();
+        queue.erase(it);
+        s->busy = true;
         q->started = clock::now();
+        q->slot = index;
       }
       int status = RIDG_OK;
       std::string error;
       try {
-        // admission: the device memory this shot would still allocate must be free
-        size_t need = solver->shot_extra_device_bytes(q->r.t_final), free_b = 0, total_b = 0;
-        RIDG_CUDA(cudaMemGetInfo(&free_b, &total_b));
-        const size_t margin = size_t(256) << 20;
-        if (need + margin > free_b)
-          throw Error{RIDG_E_OOM, "shot needs " + std::to_string(need) + " more device bytes, " +
-                                      std::to_string(free_b) + " free"};
-        ridg::run_host_shot(solver, q->r.source, q->rec.empty() ? nullptr : q->rec.data(), q->r.nrec, q->r.t_final,
-                            q->r.t_image_start, q->obs.empty() ? nullptr : q->obs.data(), q->r.traces_out,
-                            q->r.image_p, q->r.image_q, q->eup.empty() ? nullptr : q->eup.data(), buffers);
+        admit(s, q);
+        work_cv.notify_all();
+        ridg::run_host_shot(s->solver, q->r.source, q->rec.empty() ? nullptr : q->rec.data(), q->r.nrec,
+                            q->r.t_final, q->r.t_image_start, q->obs.empty() ? nullptr : q->obs.data(),
+                            q->r.traces_out, q->r.image_p, q->r.image_q, q->eup.empty() ? nullptr : q->eup.data(),
+                            s->buffers);
       } catch (const Error& e) {
         status = e.code;
         error = e.msg;
@@ -1082,8 +1535,20 @@ struct ridg_server {
         q->error = error;
         q->finished = clock::now();
         q->done = true;
+        s->busy = false;
+        ++finished_shots;
       }
       done_cv.notify_all();
+      work_cv.notify_all();
+    }
+  }
+
+  void start(int64_t max_q) {
+    max_queued = max_q;
+    RIDG_CUDA(cudaGetDevice(&device));
+    for (size_t i = 0; i < slots.size(); ++i) {
+      Slot* s = slots[i].get();
+      s->worker = std::thread([this, s, i] { run(s, int64_t(i)); });
     }
   }
 };
@@ -1277,17 +1742,101 @@ int ridg_set_profiling(ridg_solver* s, int32_t every) {
   });
 }
 
-int ridg_server_create(ridg_solver* s, int64_t max_queued, ridg_server** out) {
+int ridg_forward(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                 double* traces_out) {
   return guarded([&] {
     RIDG_NEED(s);
+    if (!src) throw Error{RIDG_E_INVALID_ARG, "source is null"};
+    const int64_t n_t = s->trace_len(t_final);
+    ridg::DBuf tr;
+    tr.alloc(size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double));
+    s->forward(*src, rec_xyz, nrec, t_final, ridg::dptr<double>(tr));
+    if (traces_out && nrec > 0)
+      RIDG_CUDA(cudaMemcpyAsync(traces_out, tr.p, size_t(nrec) * n_t * sizeof(double), cudaMemcpyDeviceToHost,
+                                s->stream()));
+    RIDG_CUDA(cudaStreamSynchronize(s->stream()));
+  });
+}
+
+int ridg_set_state_device(ridg_solver* s, const double* q_dev) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->set_state_device(q_dev);
+  });
+}
+
+int ridg_get_state_device(ridg_solver* s, double* q_dev) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->get_state_device(q_dev);
+  });
+}
+
+int ridg_set_velocity(ridg_solver* s, const double* c) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->set_velocity(c);
+  });
+}
+
+int ridg_eval_adjoint_rhs(ridg_solver* s, const double* lam, double* out) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->eval_adjoint_rhs(lam, out);
+  });
+}
+
+int ridg_misfit_forward(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                        const double* observed, int32_t n_checkpoints, double* misfit, double* traces_out) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (!src || !misfit) throw Error{RIDG_E_INVALID_ARG, "null source or misfit"};
+    *misfit = s->misfit_forward(*src, rec_xyz, nrec, t_final, observed, n_checkpoints, traces_out);
+  });
+}
+
+int ridg_misfit_backward(ridg_solver* s, double* grad) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->misfit_backward(grad);
+  });
+}
+
+int ridg_server_create(ridg_solver* s, int64_t max_queued, ridg_server** out) {
+  return ridg_server_create_slots(&s, nullptr, 1, max_queued, out);
+}
+
+int ridg_server_create_slots(ridg_solver* const* solvers, const int32_t* models, int64_t n_slots, int64_t max_queued,
+                             ridg_server** out) {
+  return guarded([&] {
     if (!out) throw Error{RIDG_E_INVALID_ARG, "out is null"};
+    *out = nullptr;
+    if (!solvers || n_slots < 1) throw Error{RIDG_E_INVALID_ARG, "a server needs at least one solver"};
     if (max_queued < 1) throw Error{RIDG_E_INVALID_ARG, "max_queued must be >= 1"};
     auto sv = std::make_unique<ridg_server>();
-    sv->solver = s;
-    sv->max_queued = max_queued;
-    RIDG_CUDA(cudaGetDevice(&sv->device));
-    ridg_server* raw = sv.get();
-    sv->worker = std::thread([raw] { raw->run(); });
+    std::map<int32_t, ridg_info> model_info;
+    for (int64_t i = 0; i < n_slots; ++i) {
+      ridg_solver* s = solvers[i];
+      RIDG_NEED(s);
+      const int32_t m = models ? models[i] : 0;
+      if (m < 0) throw Error{RIDG_E_INVALID_ARG, "model numbers must be >= 0"};
+      for (int64_t j = 0; j < i; ++j)
+        if (solvers[j] == s) throw Error{RIDG_E_INVALID_ARG, "a solver appears twice among the slots"};
+      ridg_info inf;
+      s->info(&inf);
+      auto it = model_info.find(m);
+      if (it == model_info.end()) {
+        model_info[m] = inf;
+      } else if (it->second.K != inf.K || it->second.N != inf.N || it->second.n_levels != inf.n_levels ||
+                 it->second.dt_local != inf.dt_local) {
+        throw Error{RIDG_E_INVALID_ARG, "solvers of model " + std::to_string(m) + " differ in K, N or time step"};
+      }
+      auto slot = std::make_unique<ridg_server::Slot>();
+      slot->solver = s;
+      slot->model = m;
+      sv->slots.push_back(std::move(slot));
+    }
+    sv->start(max_queued);
     *out = sv.release();
   });
 }
@@ -1297,14 +1846,22 @@ int ridg_server_submit(ridg_server* sv, const ridg_shot_request* req, int64_t* t
     if (!sv || !req || !ticket) throw Error{RIDG_E_INVALID_ARG, "null argument"};
     if (!(req->t_final > 0.0) || !(req->t_image_start >= 0.0)) throw Error{RIDG_E_INVALID_ARG, "bad time span"};
     if (req->nrec < 0 || (req->nrec > 0 && !req->rec_xyz)) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
+    if (!sv->serves(req->model)) throw Error{RIDG_E_INVALID_ARG, "no slot serves model " + std::to_string(req->model)};
+    ridg_solver* model_solver = nullptr;
+    for (const auto& sl : sv->slots)
+      if (sl->model == req->model) model_solver = sl->solver;
     auto q = std::make_unique<ridg_server::Request>();
     q->r = *req;
     q->rec.assign(req->rec_xyz, req->rec_xyz + 3 * req->nrec);
     if (req->observed) {
-      const int64_t n_t = sv->solver->trace_len(req->t_final);
+      const int64_t n_t = model_solver->trace_len(req->t_final);
       q->obs.assign(req->observed, req->observed + req->nrec * n_t);
     }
     if (req->e_up) q->eup.assign(req->e_up, req->e_up + 3);
+    if (req->source.kind == RIDG_SRC_SAMPLED && req->source.samples && req->source.n_samples > 0) {
+      q->samples.assign(req->source.samples, req->source.samples + req->source.n_samples);
+      q->r.source.samples = q->samples.data();
+    }
     q->submitted = ridg_server::clock::now();
     {
       std::lock_guard<std::mutex> lk(sv->mu);
@@ -1315,7 +1872,7 @@ int ridg_server_submit(ridg_server* sv, const ridg_shot_request* req, int64_t* t
       sv->queue.push_back(t);
       *ticket = t;
     }
-    sv->work_cv.notify_one();
+    sv->work_cv.notify_all();
   });
 }
 
@@ -1339,6 +1896,9 @@ int ridg_server_wait(ridg_server* sv, int64_t ticket, double timeout_s, ridg_req
       timing->queued_s = sec(q->started - q->submitted).count();
       timing->run_s = sec(q->finished - q->started).count();
       timing->total_s = sec(q->finished - q->submitted).count();
+      timing->start_s = sec(q->started - sv->created).count();
+      timing->end_s = sec(q->finished - sv->created).count();
+      timing->slot = q->slot;
     }
     status = q->status;
     error = q->error;
@@ -1358,7 +1918,9 @@ int ridg_server_destroy(ridg_server* sv) {
       sv->queue.clear();
     }
     sv->work_cv.notify_all();
-    if (sv->worker.joinable()) sv->worker.join();
+    sv->done_cv.notify_all();
+    for (auto& sl : sv->slots)
+      if (sl->worker.joinable()) sl->worker.join();
     delete sv;
   });
 }

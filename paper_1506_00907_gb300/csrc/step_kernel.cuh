@@ -46,7 +46,9 @@ constexpr int kMetaHalf = 2;
 // kernel modes
 constexpr int kModeRecord = 1;   // forward: record boundary-face traces
 constexpr int kModeReplay = 2;   // wavefield 0 takes recorded traces as exterior state on boundary faces
-constexpr int kModeImage = 4;    // accumulate the images (W == 2)
+constexpr int kModeImageP = 4;   // accumulate the classical image (W == 2)
+constexpr int kModeImageQ = 16;  // accumulate the characteristic image (W == 2)
+constexpr int kModeImage = kModeImageP | kModeImageQ;
 constexpr int kModeRhsOnly = 8;  // only write the right-hand side to rhs_out
 
 // per-element geometry (double): rx[9], normal[12], fscale[4]
@@ -692,8 +694,8 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
             incQ = h * (qS * qR + h * (t2 + h * t3));
           }
           const int64_t io = (blk * Np + n) * 32 + lane0 + eidx[kS];
-          A.image_p[io] -= double(incP);
-          A.image_q[io] -= double(incQ);
+          if (A.mode & kModeImageP) A.image_p[io] -= double(incP);
+          if (A.mode & kModeImageQ) A.image_q[io] -= double(incQ);
         }
       }
 #pragma unroll

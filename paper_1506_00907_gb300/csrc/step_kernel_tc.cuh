@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     constexpr int CPN = EPB * 8 / 16;  // 16-byte chunks per node row of one image
     for (int i = tid; i < 2 * Np * CPN; i += NT) {
       const int im = i / (Np * CPN), rem = i - im * Np * CPN;
+      if (!(A.mode & (im == 0 ? kModeImageP : kModeImageQ))) continue;
       const int n = rem / CPN, ch = rem - n * CPN;
       const double* src = (im == 0 ? A.image_p : A.image_q) + (blk * Np + n) * 32 + lane0 + ch * 2;
       cp_async_bytes16(sImg + (im * Np + n) * EPB + ch * 2, src);
@@ -635,8 +636,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       const float incP = h * (xS * xR + h * (t2p + h * t3p));
       const float incQ = h * (qS * qR + h * (t2q + h * t3q));
       const int64_t io = (blk * Np + n) * 32 + lane0 + e;
-      A.image_p[io] = sImg[(0 * Np + n) * EPB + e] - double(incP);
-      A.image_q[io] = sImg[(1 * Np + n) * EPB + e] - double(incQ);
+      if (A.mode & kModeImageP) A.image_p[io] = sImg[(0 * Np + n) * EPB + e] - double(incP);
+      if (A.mode & kModeImageQ) A.image_q[io] = sImg[(1 * Np + n) * EPB + e] - double(incQ);
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) {

@@ -27,8 +27,9 @@ EXPORTED = [
     "ridg_reference_operators", "ridg_solver_create", "ridg_solver_destroy", "ridg_solver_info",
     "ridg_solver_levels", "ridg_solver_nodes", "ridg_set_state", "ridg_set_history", "ridg_eval_rhs", "ridg_step",
     "ridg_get_state", "ridg_energy", "ridg_trace_len", "ridg_rtm_shot", "ridg_rtm_shot_device",
-    "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc", "ridg_server_create", "ridg_server_submit",
-    "ridg_server_wait", "ridg_server_destroy",
+    "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc", "ridg_server_create", "ridg_server_create_slots", "ridg_server_submit",
+    "ridg_server_wait", "ridg_server_destroy", "ridg_forward", "ridg_set_state_device", "ridg_get_state_device",
+    "ridg_set_velocity", "ridg_eval_adjoint_rhs", "ridg_misfit_forward", "ridg_misfit_backward",
 ]
 
 
@@ -39,7 +40,12 @@ class RidgError(RuntimeError):
 
 
 class Options(C.Structure):
-    _fields_ = [("dtype", C.c_int32), ("cfl", C.c_double), ("n_levels_max", C.c_int32), ("reserved", C.c_int32 * 5)]
+    _fields_ = [("dtype", C.c_int32), ("cfl", C.c_double), ("n_levels_max", C.c_int32), ("image_mask", C.c_int32),
+                ("tau_scale", C.c_double), ("reserved", C.c_int32 * 4)]
+
+
+IMAGE_P, IMAGE_Q = 1, 2
+SRC_RICKER, SRC_SAMPLED = 0, 1
 
 
 class Info(C.Structure):
@@ -49,7 +55,19 @@ class Info(C.Structure):
 
 
 class Source(C.Structure):
-    _fields_ = [("xyz", C.c_double * 3), ("f0", C.c_double), ("t_peak", C.c_double), ("amplitude", C.c_double)]
+    _fields_ = [("xyz", C.c_double * 3), ("f0", C.c_double), ("t_peak", C.c_double), ("amplitude", C.c_double),
+                ("kind", C.c_int32), ("reserved", C.c_int32), ("sample_dt", C.c_double), ("n_samples", C.c_int64),
+                ("samples", C.c_void_p)]
+
+
+def _source(source_xyz, f0, t_peak, amplitude, wavelet=None, wavelet_dt=None):
+    """Source struct and the array it points to (kept alive by the caller): a Ricker pulse, or with
+    ``wavelet`` (samples at t = n * wavelet_dt) a sampled wavelet scaled by ``amplitude``."""
+    if wavelet is None:
+        return Source((C.c_double * 3)(*source_xyz), f0, t_peak, amplitude, SRC_RICKER, 0, 0.0, 0, None), None
+    w = _f64(wavelet).reshape(-1)
+    return Source((C.c_double * 3)(*source_xyz), 0.0, 0.0, amplitude, SRC_SAMPLED, 0, float(wavelet_dt), w.size,
+                  _ptr(w)), w
 
 
 class ShotStats(C.Structure):
@@ -63,11 +81,13 @@ class ShotStats(C.Structure):
 class ShotRequest(C.Structure):
     _fields_ = [("source", Source), ("rec_xyz", C.c_void_p), ("nrec", C.c_int64), ("t_final", C.c_double),
                 ("t_image_start", C.c_double), ("observed", C.c_void_p), ("traces_out", C.c_void_p),
-                ("image_p", C.c_void_p), ("image_q", C.c_void_p), ("e_up", C.c_void_p)]
+                ("image_p", C.c_void_p), ("image_q", C.c_void_p), ("e_up", C.c_void_p), ("model", C.c_int32),
+                ("reserved", C.c_int32)]
 
 
 class RequestTiming(C.Structure):
-    _fields_ = [("queued_s", C.c_double), ("run_s", C.c_double), ("total_s", C.c_double)]
+    _fields_ = [("queued_s", C.c_double), ("run_s", C.c_double), ("total_s", C.c_double), ("start_s", C.c_double),
+                ("end_s", C.c_double), ("slot", C.c_int64)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:
@@ -99,7 +119,15 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_last_shot_stats": (C.c_int, [P, P]),
         "ridg_set_profiling": (C.c_int, [P, C.c_int32]),
         "ridg_energy_noalloc": (C.c_int, [P, P]),
+        "ridg_forward": (C.c_int, [P, P, P, C.c_int64, C.c_double, P]),
+        "ridg_set_state_device": (C.c_int, [P, P]),
+        "ridg_get_state_device": (C.c_int, [P, P]),
+        "ridg_set_velocity": (C.c_int, [P, P]),
+        "ridg_eval_adjoint_rhs": (C.c_int, [P, P, P]),
+        "ridg_misfit_forward": (C.c_int, [P, P, P, C.c_int64, C.c_double, P, C.c_int32, P, P]),
+        "ridg_misfit_backward": (C.c_int, [P, P]),
         "ridg_server_create": (C.c_int, [P, C.c_int64, C.POINTER(P)]),
+        "ridg_server_create_slots": (C.c_int, [P, P, C.c_int64, C.c_int64, C.POINTER(P)]),
         "ridg_server_submit": (C.c_int, [P, P, C.POINTER(C.c_int64)]),
         "ridg_server_wait": (C.c_int, [P, C.c_int64, C.c_double, P]),
         "ridg_server_destroy": (C.c_int, [P]),
@@ -176,11 +204,13 @@ class Mesh:
 
 
 class Solver:
-    def __init__(self, mesh: Mesh, N: int, c, rho, dtype="f32", cfl=0.15, n_levels_max=3, stream=0):
+    def __init__(self, mesh: Mesh, N: int, c, rho, dtype="f32", cfl=0.15, n_levels_max=3, stream=0, tau_scale=1.0,
+                 image_mask=IMAGE_P | IMAGE_Q):
         self.mesh = mesh
         c = _f64(c)
         rho = _f64(rho)
-        opt = Options(F64 if dtype == "f64" else F32, float(cfl), int(n_levels_max))
+        opt = Options(F64 if dtype == "f64" else F32, float(cfl), int(n_levels_max), int(image_mask),
+                      float(tau_scale))
         h = C.c_void_p()
         _check(lib().ridg_solver_create(mesh._h, int(N), _ptr(c), _ptr(rho), C.byref(opt), int(stream), C.byref(h)))
         self._h = h
@@ -246,10 +276,58 @@ class Solver:
     def trace_len(self, t_final):
         return int(lib().ridg_trace_len(self._h, float(t_final)))
 
+    def set_state_device(self, q):
+        """Fields from a torch CUDA float64 tensor [K, 4, Np] (asynchronous on the solver's stream)."""
+        _check(lib().ridg_set_state_device(self._h, _ptr(q)))
+
+    def get_state_device(self, q):
+        """Fields into a torch CUDA float64 tensor [K, 4, Np] (asynchronous on the solver's stream)."""
+        _check(lib().ridg_get_state_device(self._h, _ptr(q)))
+
+    def set_velocity(self, c):
+        """Velocity per element in rho c^2 (time step, level and penalty parameters stay frozen)."""
+        c = _f64(c, (self.K,))
+        _check(lib().ridg_set_velocity(self._h, _ptr(c)))
+
+    def eval_adjoint_rhs(self, lam):
+        """A^T lam for the transposed right-hand-side operator ([K, 4, Np] host arrays)."""
+        lam = _f64(lam, (self.K, 4, self.Np))
+        out = np.zeros_like(lam)
+        _check(lib().ridg_eval_adjoint_rhs(self._h, _ptr(lam), _ptr(out)))
+        return out
+
+    def misfit_forward(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, observed, n_checkpoints=16,
+                       wavelet=None, wavelet_dt=None):
+        """(J, traces) of a forward run against observed traces [nrec, n_t]; keeps checkpoints for
+        ``misfit_backward`` (one rate level only)."""
+        src, _keep = _source(source_xyz, f0, t_peak, amplitude, wavelet, wavelet_dt)
+        rec = _f64(np.atleast_2d(rec_xyz))
+        n_t = self.trace_len(t_final)
+        obs = _f64(observed, (rec.shape[0], n_t))
+        traces = np.zeros((rec.shape[0], n_t))
+        J = C.c_double()
+        _check(lib().ridg_misfit_forward(self._h, C.byref(src), _ptr(rec), rec.shape[0], float(t_final), _ptr(obs),
+                                         int(n_checkpoints), C.byref(J), _ptr(traces)))
+        return J.value, traces
+
+    def misfit_backward(self):
+        """dJ/dc [K] of the last ``misfit_forward`` (discrete adjoint, checkpointed recomputation)."""
+        g = np.zeros(self.K)
+        _check(lib().ridg_misfit_backward(self._h, _ptr(g)))
+        return g
+
+    def forward(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, wavelet=None, wavelet_dt=None):
+        """Forward modelling: receiver traces [nrec, n_t] of the forward run alone."""
+        src, _keep = _source(source_xyz, f0, t_peak, amplitude, wavelet, wavelet_dt)
+        rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
+        traces = np.zeros((rec.shape[0], self.trace_len(t_final)))
+        _check(lib().ridg_forward(self._h, C.byref(src), _ptr(rec), rec.shape[0], float(t_final), _ptr(traces)))
+        return traces
+
     def rtm_shot(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0, observed=None,
-                 e_up=(0.0, 0.0, -1.0), want_images=True):
+                 e_up=(0.0, 0.0, -1.0), want_images=True, wavelet=None, wavelet_dt=None):
         """Host-buffer shot: returns (traces [nrec, n_t], image_p [K, Np], image_q [K, Np])."""
-        src = Source((C.c_double * 3)(*source_xyz), f0, t_peak, amplitude)
+        src, _keep = _source(source_xyz, f0, t_peak, amplitude, wavelet, wavelet_dt)
         rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
         n_t = self.trace_len(t_final)
         traces = np.zeros((rec.shape[0], n_t))
@@ -264,7 +342,7 @@ class Solver:
     def rtm_shot_device(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0,
                         observed=None, traces=None, image_p=None, image_q=None, e_up=(0.0, 0.0, -1.0)):
         """Device-buffer shot (torch CUDA float64 tensors or None); returns after enqueueing."""
-        src = Source((C.c_double * 3)(*source_xyz), f0, t_peak, amplitude)
+        src, _keep = _source(source_xyz, f0, t_peak, amplitude)
         rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
         eu = _f64(e_up)
         _check(lib().ridg_rtm_shot_device(self._h, C.byref(src), _ptr(rec), rec.shape[0], float(t_final),
@@ -281,28 +359,50 @@ class Solver:
 
 
 class Server:
-    """Shot server on a solver (``ridg_server_*``): requests run one after another on the solver's
-    resident buffers.  The solver must not be used directly while the server exists."""
+    """Shot server (``ridg_server_*``) over one solver or several slots.  ``solvers`` is a Solver or a
+    list of them; ``models[i]`` is the model number of ``solvers[i]`` (default: all 0).  An idle slot
+    takes the oldest waiting request of its model, so shots on different slots run concurrently
+    (give those solvers different CUDA streams).  The solvers must not be used directly while the
+    server exists."""
 
-    def __init__(self, solver: Solver, max_queued: int = 8):
-        self.solver = solver
+    def __init__(self, solvers, max_queued: int = 8, models=None):
+        solvers = list(solvers) if isinstance(solvers, (list, tuple)) else [solvers]
+        models = [0] * len(solvers) if models is None else [int(m) for m in models]
+        if len(models) != len(solvers):
+            raise ValueError("one model number per solver")
+        self.solvers = solvers
+        self.models = models
+        hs = (C.c_void_p * len(solvers))(*[s._h.value for s in solvers])
+        ms = (C.c_int32 * len(models))(*models)
         h = C.c_void_p()
-        _check(lib().ridg_server_create(solver._h, int(max_queued), C.byref(h)))
+        _check(lib().ridg_server_create_slots(hs, ms, len(solvers), int(max_queued), C.byref(h)))
         self._h = h
         self._pending = {}
 
+    @property
+    def solver(self):
+        return self.solvers[0]
+
+    def _model_solver(self, model):
+        for s, m in zip(self.solvers, self.models):
+            if m == model:
+                return s
+        raise ValueError(f"no slot serves model {model}")
+
     def submit(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0, observed=None,
-               e_up=(0.0, 0.0, -1.0), want_images=True) -> int:
-        """Queues a shot; its host output buffers are kept here until ``wait`` returns them."""
+               e_up=(0.0, 0.0, -1.0), want_images=True, wavelet=None, wavelet_dt=None, model=0) -> int:
+        """Queues a shot for ``model``; its host output buffers are kept here until ``wait`` returns them."""
+        ms = self._model_solver(model)
         rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
-        n_t = self.solver.trace_len(t_final)
+        n_t = ms.trace_len(t_final)
         traces = np.zeros((rec.shape[0], n_t))
-        ip = np.zeros((self.solver.K, self.solver.Np)) if want_images else None
-        iq = np.zeros((self.solver.K, self.solver.Np)) if want_images else None
+        ip = np.zeros((ms.K, ms.Np)) if want_images else None
+        iq = np.zeros((ms.K, ms.Np)) if want_images else None
         obs = None if observed is None else _f64(observed, (rec.shape[0], n_t))
         eu = _f64(e_up)
-        req = ShotRequest(Source((C.c_double * 3)(*source_xyz), f0, t_peak, amplitude), _ptr(rec), rec.shape[0],
-                          float(t_final), float(t_image_start), _ptr(obs), _ptr(traces), _ptr(ip), _ptr(iq), _ptr(eu))
+        src, _keep = _source(source_xyz, f0, t_peak, amplitude, wavelet, wavelet_dt)
+        req = ShotRequest(src, _ptr(rec), rec.shape[0], float(t_final), float(t_image_start), _ptr(obs),
+                          _ptr(traces), _ptr(ip), _ptr(iq), _ptr(eu), int(model), 0)
         t = C.c_int64()
         _check(lib().ridg_server_submit(self._h, C.byref(req), C.byref(t)))
         self._pending[t.value] = (traces, ip, iq)
@@ -318,7 +418,8 @@ class Server:
         out = self._pending.pop(ticket, None)
         _check(code)
         traces, ip, iq = out
-        return traces, ip, iq, {"queued_s": tm.queued_s, "run_s": tm.run_s, "total_s": tm.total_s}
+        return traces, ip, iq, {"queued_s": tm.queued_s, "run_s": tm.run_s, "total_s": tm.total_s,
+                                "start_s": tm.start_s, "end_s": tm.end_s, "slot": tm.slot}
 
     def close(self):
         if self._h:
@@ -330,3 +431,25 @@ class Server:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def misfit(c, solver: Solver, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, observed, n_checkpoints=16):
+    """Least-squares trace misfit as a differentiable function of the per-element velocity ``c``
+    (a torch float64 tensor [K]): forward run in ``forward``, gradient by the library's adjoint
+    kernels with checkpointed recomputation in ``backward``."""
+    import torch
+
+    class _Misfit(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, cv):
+            solver.set_velocity(cv.detach().cpu().numpy())
+            J, _ = solver.misfit_forward(source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, observed, n_checkpoints)
+            ctx.device = cv.device
+            return torch.tensor(J, dtype=torch.float64, device=cv.device)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            g = torch.from_numpy(solver.misfit_backward()).to(ctx.device)
+            return gJ * g
+
+    return _Misfit.apply(c)

@@ -11,7 +11,8 @@ from oracle.dg_rhs import attach_media, rhs, traces
 from oracle.mesh_geometry import MeshGeometry
 from oracle.mrab import MRAB, assign_levels
 from oracle.reference_element import reference_element
-from oracle.rtm import make_problem, rtm_shot
+from oracle.rtm import forward, make_problem, rtm_shot
+from oracle.wavelet import ricker
 from paper_1506_00907_gb300 import ridg
 from synth import config1_cube, random_state, standing_mode, tiny_layered_rtm, unit_cube_mesh
 from tests.parity_cases import TOL, mixed_bc, rel_l2
@@ -19,15 +20,16 @@ from tests.parity_cases import TOL, mixed_bc, rel_l2
 pytestmark = pytest.mark.gpu
 
 
-def _oracle_problem(w, face_bc=None, N=None):
+def _oracle_problem(w, face_bc=None, N=None, tau_scale=1.0):
     N = w.N if N is None else N
     return make_problem(w.xyz, w.tets, w.c, w.rho, N, face_bc=face_bc, default_bc=w.default_bc, cfl=w.cfl,
-                        n_levels_max=w.n_levels_max)
+                        n_levels_max=w.n_levels_max, tau_scale=tau_scale)
 
 
-def _gpu(w, dtype, face_bc=None, N=None):
+def _gpu(w, dtype, face_bc=None, N=None, **kw):
     mesh = ridg.Mesh(w.xyz, w.tets, face_bc=face_bc, default_bc=w.default_bc)
-    return ridg.Solver(mesh, w.N if N is None else N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=w.n_levels_max)
+    return ridg.Solver(mesh, w.N if N is None else N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=w.n_levels_max,
+                       **kw)
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -209,3 +211,85 @@ def test_single_element_mesh():
     q = random_state(1, s.Np, seed=9)
     g = attach_media(MeshGeometry(xyz, tets, reference_element(3), default_bc=1), [2.0], [1.5])
     assert rel_l2(s.eval_rhs(q), rhs(np.arange(1), q, traces(q, g), g)) < TOL["f64"]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+@pytest.mark.parametrize("tau_scale", [0.5, 2.0])
+def test_rhs_parity_penalty_scale(dtype, tau_scale):
+    """The penalty scale multiplies tau_p and tau_v on interior and boundary faces alike."""
+    w = tiny_layered_rtm(N=4)
+    fb = mixed_bc(w)
+    prob = _oracle_problem(w, face_bc=fb, tau_scale=tau_scale)
+    s = _gpu(w, dtype, face_bc=fb, tau_scale=tau_scale)
+    q = random_state(w.K, s.Np, seed=12)
+    g = prob.geo
+    assert rel_l2(s.eval_rhs(q), rhs(np.arange(g.K), q, traces(q, g), g)) < TOL[dtype]
+
+
+@functools.lru_cache(maxsize=None)
+def _oracle_forward():
+    """Forward modelling on the tiny three-level model, driven by the Ricker pulse and by samples
+    of a different signal at a spacing unrelated to the time step (ragged: the last samples end
+    before the record does)."""
+    w = tiny_layered_rtm(N=3, t_final=0.004)
+    prob = _oracle_problem(w)
+    dt_s = 0.7 * prob.dt_local
+    n_s = int(0.8 * w.t_final / dt_s)
+    t = np.arange(n_s) * dt_s
+    wav = ricker(t, 1.5 * w.f0, 0.6 * w.t_peak) + 0.2 * np.sin(2 * np.pi * w.f0 * t)
+    tr = forward(prob, w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
+    tr_s = forward(prob, w.source_xyz, 0.0, 0.0, 0.5, w.receivers, w.t_final, wavelet=wav, wavelet_dt=dt_s)
+    return w, wav, dt_s, tr, tr_s
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_forward_parity(dtype):
+    w, wav, dt_s, tr_ref, tr_s_ref = _oracle_forward()
+    s = _gpu(w, dtype)
+    tr = s.forward(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
+    assert tr.shape == tr_ref.shape and rel_l2(tr, tr_ref) < TOL[dtype]
+    tr_s = s.forward(w.source_xyz, 0.0, 0.0, 0.5, w.receivers, w.t_final, wavelet=wav, wavelet_dt=dt_s)
+    assert rel_l2(tr_s, tr_s_ref) < TOL[dtype]
+    # the forward run of a shot is the same computation
+    tr_shot, _, _ = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
+    assert np.array_equal(tr_shot, tr)
+    # a sampled source in a whole shot
+    tr_shot_s, ip, _ = s.rtm_shot(w.source_xyz, 0.0, 0.0, 0.5, w.receivers, w.t_final, wavelet=wav, wavelet_dt=dt_s)
+    assert np.array_equal(tr_shot_s, tr_s) and np.abs(ip).max() > 0
+    with pytest.raises(ridg.RidgError) as e:
+        s.forward(w.source_xyz, 0.0, 0.0, 1.0, w.receivers, w.t_final, wavelet=wav, wavelet_dt=0.0)
+    assert e.value.code == -1
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_image_mask(dtype):
+    """A solver restricted to one imaging condition accumulates that image unchanged and leaves the
+    other at zero."""
+    w = tiny_layered_rtm(N=3, t_final=0.004)
+    args = (w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
+    tr, ip, iq = _gpu(w, dtype).rtm_shot(*args)
+    trp, ipp, iqp = _gpu(w, dtype, image_mask=ridg.IMAGE_P).rtm_shot(*args)
+    trq, ipq, iqq = _gpu(w, dtype, image_mask=ridg.IMAGE_Q).rtm_shot(*args)
+    assert np.array_equal(trp, tr) and np.array_equal(trq, tr)
+    assert rel_l2(ipp, ip) < 1e-12 and np.all(iqp == 0)
+    assert rel_l2(iqq, iq) < 1e-12 and np.all(ipq == 0)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_device_state_round_trip(dtype):
+    """Fields set and read through device buffers are those of the host-buffer calls."""
+    torch = pytest.importorskip("torch")
+    w = tiny_layered_rtm(N=3)
+    s = _gpu(w, dtype)
+    q = random_state(w.K, s.Np, seed=31)
+    s.set_state(q)
+    s.step(2)
+    q_host = s.get_state()
+    qd = torch.tensor(q, dtype=torch.float64, device="cuda")
+    s.set_state_device(qd)
+    s.step(2)
+    out = torch.zeros_like(qd)
+    s.get_state_device(out)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), q_host)
+    assert np.array_equal(s.get_state(), q_host)
