@@ -461,6 +461,123 @@ def profile_shot(t_final):
     return 0
 
 
+def precision_sweep(orders, t_final=0.01):
+    """Per order: the bench model's shot over a short record in FP64, in FP32 with the element
+    products on tensor cores (three-term TF32 split) and in FP32 with them on CUDA cores; throughput,
+    fused-kernel times and the relative L2 error of traces and images against the FP64 shot.  One
+    JSON line per order."""
+    from paper_1506_00907_gb300 import ridg
+
+    w = _workload()
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+
+    def rel(a, b):
+        return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+    for N in orders:
+        out = {"order": N, "elements": int(w.K), "record_s": t_final}
+        res = {}
+        for name, dtype, contraction in (("f64", "f64", ridg.CONTRACT_TENSOR),
+                                         ("f32_tensor_tf32x3", "f32", ridg.CONTRACT_TENSOR),
+                                         ("f32_cuda_cores", "f32", ridg.CONTRACT_CUDA_CORES)):
+            try:
+                s = ridg.Solver(mesh, N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=w.n_levels_max,
+                                contraction=contraction)
+            except ridg.RidgError as exc:
+                out[name] = {"unavailable": str(exc)}
+                continue
+            s.set_profiling(1)
+            s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, 0.002)  # warm-up
+            t0 = time.perf_counter()
+            tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, t_final)
+            wall = time.perf_counter() - t0
+            st = s.shot_stats()
+            res[name] = (tr, ip, iq)
+            out[name] = {"dof_updates_per_s": (st.dof_updates_forward + st.dof_updates_backward) / wall,
+                         "forward_full_launch_ms": st.prof_forward_ms / max(1, st.prof_forward_launches),
+                         "backward_full_launch_ms": st.prof_backward_ms / max(1, st.prof_backward_launches)}
+            s.close()
+        if "f64" in res:
+            for name in ("f32_tensor_tf32x3", "f32_cuda_cores"):
+                if name in res:
+                    out[name].update({k: rel(a, b) for k, a, b in zip(("traces_rel_l2", "image_p_rel_l2",
+                                                                      "image_q_rel_l2"), res[name], res["f64"])})
+        elif "f32_tensor_tf32x3" in res and "f32_cuda_cores" in res:
+            out["tensor_vs_cuda_cores"] = {k: rel(a, b) for k, a, b in zip(
+                ("traces_rel_l2", "image_p_rel_l2", "image_q_rel_l2"), res["f32_tensor_tf32x3"], res["f32_cuda_cores"])}
+        print(json.dumps(out), flush=True)
+    return 0
+
+
+def serving_stream(n_req, t_rec=0.01):
+    """Shot-serving stream over three models (about 5e4 / 2e5 / 8e5 elements at N = 3 / 4 / 5,
+    three layers, three rate levels): n_req requests (model, surface source, 101-401 receivers;
+    seed 5) with Poisson arrivals (seed 5) at 0.8x and 1.5x the measured sequential rate, served
+    with one and with two slots per model.  Prints one JSON line."""
+    import torch
+
+    from paper_1506_00907_gb300 import ridg
+    from synth import serving_model, serving_requests
+
+    sizes = ("50k", "200k", "800k")
+    models = [serving_model(sz) for sz in sizes]
+    meshes = [ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc) for w in models]
+    streams, slots = [], {}
+    for m, (w, mesh) in enumerate(zip(models, meshes)):
+        slots[m] = []
+        for _ in range(2):
+            st = torch.cuda.Stream()
+            streams.append(st)
+            slots[m].append(ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max,
+                                        stream=st.cuda_stream))
+    reqs = serving_requests(n_req)
+    out = {"requests": n_req, "record_s": t_rec,
+           "models": [{"elements": int(w.K), "order": w.N, "levels": s[0].info.n_levels} for w, s in
+                      zip(models, slots.values())],
+           "arrivals": "Poisson (seed 5) at 0.8x and 1.5x the sequential rate; model, source and receiver count "
+                       "drawn per request (seed 5)"}
+
+    def submit(sv, r):
+        m, src, rec = r
+        w = models[m]
+        return sv.submit(src, w.f0, w.t_peak, 1.0, rec, t_rec, model=m)
+
+    def server(k):
+        sl = [slots[m][i] for m in range(3) for i in range(k)]
+        return ridg.Server(sl, max_queued=n_req, models=[m for m in range(3) for _ in range(k)])
+
+    with server(2) as sv:  # buffers of every slot in place
+        for t in [submit(sv, (m, (1000.0, 1000.0, 8.0), reqs[0][2])) for m in range(3) for _ in range(2)]:
+            sv.wait(t)
+    n_seq = min(n_req, 24)
+    with server(1) as sv:
+        t0 = time.perf_counter()
+        for r in reqs[:n_seq]:
+            sv.wait(submit(sv, r))
+        seq = n_seq / (time.perf_counter() - t0)
+    out["sequential_shots_per_s"] = seq
+    for k in (1, 2):
+        for factor in (0.8, 1.5):
+            gaps = np.random.default_rng(5).exponential(1.0 / (factor * seq), n_req)
+            with server(k) as sv:
+                t0 = time.perf_counter()
+                arrive, tickets = 0.0, []
+                for i, r in enumerate(reqs):
+                    arrive += gaps[i]
+                    time.sleep(max(0.0, arrive - (time.perf_counter() - t0)))
+                    tickets.append(submit(sv, r))
+                lat = [sv.wait(t)[3]["total_s"] for t in tickets]
+                span = time.perf_counter() - t0 - gaps[0]
+            out[f"rate{factor}x_slots{k}"] = {"p50_s": float(np.percentile(lat, 50)),
+                                              "p99_s": float(np.percentile(lat, 99)), "shots_per_s": n_req / span,
+                                              "vs_sequential": n_req / span / seq}
+    for ss in slots.values():
+        for x in ss:
+            x.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 def _kernel_hash():
     import hashlib
 
@@ -481,7 +598,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--profile-shot", type=float, default=0.0,
                     help="run one shot of the bench workload with this record length (s) and exit (profiling case)")
+    ap.add_argument("--precision-sweep", default="",
+                    help="comma-separated orders: FP64 / FP32 tensor-core / FP32 CUDA-core shots of the bench model")
+    ap.add_argument("--serving-stream", type=int, default=0,
+                    help="run the three-model shot-serving stream with this many requests and exit")
     args = ap.parse_args()
+    if args.serving_stream > 0:
+        from paper_1506_00907_gb300.build import build
+
+        build()
+        return serving_stream(args.serving_stream)
+    if args.precision_sweep:
+        from paper_1506_00907_gb300.build import build
+
+        build()
+        return precision_sweep([int(x) for x in args.precision_sweep.split(",")])
     if args.profile_shot > 0:
         from paper_1506_00907_gb300.build import build
 

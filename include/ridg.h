@@ -96,8 +96,13 @@ typedef struct ridg_options {
   int32_t image_mask;   /* images a shot accumulates: RIDG_IMAGE_P | RIDG_IMAGE_Q; 0 selects both */
   double tau_scale;     /* multiplies the penalty parameters tau_p = 1/Zbar, tau_v = Zbar of the
                            upwind fluxes (Sec. 3.1, Eqs. weakFormP/V); <= 0 selects 1 (upwind) */
-  int32_t reserved[4];
+  int32_t contraction;  /* RIDG_F32 only: RIDG_CONTRACT_TENSOR (0, default) runs the D_r/D_s/D_t and
+                           LIFT products on tensor cores (three-term TF32 split, FP32 accumulation);
+                           RIDG_CONTRACT_CUDA_CORES runs them as plain FP32 FMAs */
+  int32_t reserved[3];
 } ridg_options;
+#define RIDG_CONTRACT_TENSOR 0
+#define RIDG_CONTRACT_CUDA_CORES 1
 
 #define RIDG_IMAGE_P 1 /* classical image, Eq. imageP */
 #define RIDG_IMAGE_Q 2 /* characteristic image, Eq. imageQ */

@@ -13,14 +13,19 @@ static cudaError_t launch_step_w(const StepArgs<real>& a, cudaStream_t st) {
   int64_t blocks = (a.slot_hi - a.slot_lo) / (32 / W);
   if (blocks <= 0) return cudaSuccess;
   if constexpr (std::is_same<real, float>::value) {
-    // FP32: element products on tensor cores (TF32 three-term split)
-    constexpr size_t smem = SmemTc<N, W>::bytes;
-    // set once per process (thread-safe initialisation: shot servers launch from several threads)
-    static const cudaError_t configured =
-        cudaFuncSetAttribute(dg_step_kernel_tc<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (configured != cudaSuccess) return configured;
-    dg_step_kernel_tc<N, W><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a);
-  } else {
+    if (!a.cuda_cores) {
+      // FP32: element products on tensor cores (TF32 three-term split)
+      constexpr size_t smem = SmemTc<N, W>::bytes;
+      // set once per process (thread-safe initialisation: shot servers launch from several threads)
+      static const cudaError_t configured =
+          cudaFuncSetAttribute(dg_step_kernel_tc<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+      if (configured != cudaSuccess) return configured;
+      dg_step_kernel_tc<N, W><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a);
+      return cudaGetLastError();
+    }
+  }
+  {
+    // FP64, or FP32 on CUDA cores
     constexpr size_t smem = step_smem_bytes<N, real, W>();
     static const cudaError_t configured =
         cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -215,6 +215,9 @@ class Engine final : public ridg_solver {
     double cfl = opt.cfl > 0 ? opt.cfl : 0.15;
     int nlm = opt.n_levels_max > 0 ? opt.n_levels_max : 3;
     tau_scale_ = opt.tau_scale > 0 ? opt.tau_scale : 1.0;
+    if (opt.contraction != RIDG_CONTRACT_TENSOR && opt.contraction != RIDG_CONTRACT_CUDA_CORES)
+      throw Error{RIDG_E_INVALID_ARG, "contraction must be RIDG_CONTRACT_TENSOR or RIDG_CONTRACT_CUDA_CORES"};
+    cuda_cores_ = std::is_same<real, float>::value && opt.contraction == RIDG_CONTRACT_CUDA_CORES;
     image_mode_ = ((opt.image_mask & RIDG_IMAGE_P) || !(opt.image_mask & 3) ? kModeImageP : 0) |
                   ((opt.image_mask & RIDG_IMAGE_Q) || !(opt.image_mask & 3) ? kModeImageQ : 0);
     if (nlm > kMaxLevels) throw Error{RIDG_E_INVALID_ARG, "n_levels_max too large"};
@@ -884,9 +887,8 @@ class Engine final : public ridg_solver {
     size_t need = dispatch_order(N_, [&](auto NC) {
       constexpr int NN = decltype(NC)::value;
       if constexpr (std::is_same<real, float>::value)
-        return std::max(SmemTc<NN, 1>::bytes, SmemTc<NN, 2>::bytes);
-      else
-        return std::max(step_smem_bytes<NN, real, 1>(), step_smem_bytes<NN, real, 2>());
+        if (!cuda_cores_) return std::max(SmemTc<NN, 1>::bytes, SmemTc<NN, 2>::bytes);
+      return std::max(step_smem_bytes<NN, real, 1>(), step_smem_bytes<NN, real, 2>());
     });
     if (need > size_t(optin))
       throw Error{RIDG_E_INVALID_ARG, "order " + std::to_string(N_) + " in this precision needs " +
@@ -1151,6 +1153,7 @@ class Engine final : public ridg_solver {
     a.fmask = dptr<const int>(fmask_d_);
     a.perm = dptr<const int>(perm_d_);
     a.afrag = dptr<const uint32_t>(afrag_d_);
+    a.cuda_cores = cuda_cores_ ? 1 : 0;
     a.e_up[2] = real(-1);
     return a;
   }
@@ -1302,6 +1305,7 @@ class Engine final : public ridg_solver {
   DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
   DBuf afrag_d_, gtab_d_[2], pos_d_;
   double tau_scale_ = 1.0;
+  bool cuda_cores_ = false;  // FP32 element products on CUDA cores instead of tensor cores
   int image_mode_ = kModeImage;
   std::vector<int> pos_of_;  // device position of each reference node
   DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_;

@@ -115,6 +115,7 @@ struct StepArgs {
   real* rhs_out;         // kModeRhsOnly: q-sized
   const uint32_t* afrag; // tensor-core variant: operator fragments (TF32 hi/lo), see step_kernel_tc.cuh
   const float* gtab;     // tensor-core variant: per-element coefficients [n_slots][kGtab] (this tau sign)
+  int cuda_cores;        // FP32: 1 runs the CUDA-core kernel instead of the tensor-core one
 };
 
 template <int N>
@@ -246,7 +247,9 @@ template <int N, typename real, int W>
 struct Smem {
   using O = Order<N>;
   static constexpr int Np = O::Np, Nfp = O::Nfp;
-  static constexpr int CS = ColStride<real>::value;  // padded column rows (face-node gathers)
+  // padded column rows (face-node gathers); unpadded for FP64 at N = 6, whose tile would not fit
+  // in a block's shared memory with the padding
+  static constexpr int CS = (sizeof(real) == 8 && N >= 6) ? 32 : ColStride<real>::value;
   static constexpr int RS = 32;                      // ring rows: read by their owner thread only
   static constexpr int XS = 33;                      // exterior-trace staging rows
   static constexpr int NG = 49;                      // per-element coefficients (odd: conflict-free)

@@ -41,10 +41,11 @@ class RidgError(RuntimeError):
 
 class Options(C.Structure):
     _fields_ = [("dtype", C.c_int32), ("cfl", C.c_double), ("n_levels_max", C.c_int32), ("image_mask", C.c_int32),
-                ("tau_scale", C.c_double), ("reserved", C.c_int32 * 4)]
+                ("tau_scale", C.c_double), ("contraction", C.c_int32), ("reserved", C.c_int32 * 3)]
 
 
 IMAGE_P, IMAGE_Q = 1, 2
+CONTRACT_TENSOR, CONTRACT_CUDA_CORES = 0, 1
 SRC_RICKER, SRC_SAMPLED = 0, 1
 
 
@@ -205,12 +206,12 @@ class Mesh:
 
 class Solver:
     def __init__(self, mesh: Mesh, N: int, c, rho, dtype="f32", cfl=0.15, n_levels_max=3, stream=0, tau_scale=1.0,
-                 image_mask=IMAGE_P | IMAGE_Q):
+                 image_mask=IMAGE_P | IMAGE_Q, contraction=CONTRACT_TENSOR):
         self.mesh = mesh
         c = _f64(c)
         rho = _f64(rho)
         opt = Options(F64 if dtype == "f64" else F32, float(cfl), int(n_levels_max), int(image_mask),
-                      float(tau_scale))
+                      float(tau_scale), int(contraction))
         h = C.c_void_p()
         _check(lib().ridg_solver_create(mesh._h, int(N), _ptr(c), _ptr(rho), C.byref(opt), int(stream), C.byref(h)))
         self._h = h

@@ -28,4 +28,6 @@ from .workloads import (  # noqa: F401
     adjoint_box,
     adjoint_box_small,
     adjoint_observed_velocity,
+    serving_model,
+    serving_requests,
 )

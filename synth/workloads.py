@@ -156,6 +156,39 @@ def adjoint_box_small() -> Workload:
     return w
 
 
+def serving_model(size: str, seed=6) -> Workload:
+    """One of the three models of the shot-serving stream: a 2 x 2 x 1 km box with three layers
+    (1500, 2000, 2500 m/s; interface depths drawn with ``seed``), the surface refined 8x in depth and
+    2x around each interface (three rate levels), transparent boundaries.  ``size``: "50k" (N = 3),
+    "200k" (N = 4) or "800k" (N = 5) elements, approximately."""
+    h, N = {"50k": (100.0, 3), "200k": (2000.0 / 36, 4), "800k": (100.0 / 3, 5)}[size]
+    rng = np.random.default_rng(seed)
+    z1 = float(rng.uniform(250.0, 450.0))
+    z2 = float(rng.uniform(550.0, 800.0))
+    zb = [(0.0, h, 2), (0.0, h / 2, 2), (0.0, h / 4, 2), (z1 - h, z1 + h, 2), (z2 - h, z2 + h, 2)]
+    g = HexGrid(graded_axis(0.0, 2000.0, h), graded_axis(0.0, 2000.0, h), graded_axis(0.0, 1000.0, h, zb))
+    xyz, tets = g.mesh()
+    zc = xyz[tets][:, :, 2].mean(axis=1)
+    c = np.where(zc < z1, 1500.0, np.where(zc < z2, 2000.0, 2500.0))
+    return Workload(f"serving_{size}_N{N}", xyz, tets, c, np.full(tets.shape[0], 1000.0), N=N,
+                    default_bc=BC_TRANSPARENT, cfl=0.15, n_levels_max=3, dtype="f32", f0=10.0,
+                    t_peak=0.1127 * 12.0 / 10.0)
+
+
+def serving_requests(n, seed=5):
+    """Request stream of the serving benchmark: per request the model index (0..2), a surface source
+    position and a receiver line (101..401 receivers at y = 1000 m, z = 10 m)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n):
+        m = int(rng.integers(0, 3))
+        src = (float(rng.uniform(200.0, 1800.0)), float(rng.uniform(200.0, 1800.0)), 8.0)
+        nr = int(rng.integers(101, 402))
+        rec = np.stack([np.linspace(0.0, 2000.0, nr), np.full(nr, 1000.0), np.full(nr, 10.0)], axis=1)
+        out.append((m, src, rec))
+    return out
+
+
 def tiny_layered_rtm(N=3, t_final=0.03) -> Workload:
     """200 x 200 x 100 m, two layers (interface at 50 m), refined bands around the source:
     three rate levels on 1440 tetrahedra.  Small enough for the oracle to run a whole shot."""

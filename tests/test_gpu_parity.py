@@ -50,12 +50,6 @@ def test_rhs_parity_mixed_boundaries(dtype, N):
     two-material, three-level mesh: several CTAs and a ragged last block."""
     w = tiny_layered_rtm(N=N)
     fb = mixed_bc(w)
-    if N == 6 and dtype == "f64":
-        # the FP64 tile of order 6 does not fit the shared memory of one block: refused up front
-        with pytest.raises(ridg.RidgError) as e:
-            _gpu(w, dtype, face_bc=fb)
-        assert e.value.code == -1
-        return
     prob = _oracle_problem(w, face_bc=fb)
     s = _gpu(w, dtype, face_bc=fb)
     q = random_state(w.K, s.Np, seed=11)
@@ -101,8 +95,6 @@ def test_config1_standing_mode_fp64():
 def test_mrab_three_levels_parity(dtype, N):
     """Multi-rate stepping with half-step traces on three levels: 4 global steps from a seeded
     state and history (orders 5 and 6 run the tensor-core kernel with rolled k-steps)."""
-    if N == 6 and dtype == "f64":
-        pytest.skip("the FP64 tile of order 6 does not fit one block's shared memory (refused, tested above)")
     w = tiny_layered_rtm(N=N)
     fb = mixed_bc(w)
     prob = _oracle_problem(w, face_bc=fb)
@@ -293,3 +285,26 @@ def test_device_state_round_trip(dtype):
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), q_host)
     assert np.array_equal(s.get_state(), q_host)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_rhs_parity_fp32_cuda_cores(N):
+    """FP32 with the element products as plain FMAs on CUDA cores (the reference the tensor-core
+    split is measured against): right-hand side with every boundary condition."""
+    w = tiny_layered_rtm(N=N)
+    fb = mixed_bc(w)
+    prob = _oracle_problem(w, face_bc=fb)
+    s = _gpu(w, "f32", face_bc=fb, contraction=ridg.CONTRACT_CUDA_CORES)
+    q = random_state(w.K, s.Np, seed=11)
+    g = prob.geo
+    r_ref = rhs(np.arange(g.K), q, traces(q, g), g)
+    assert rel_l2(s.eval_rhs(q), r_ref) < TOL["f32"]
+
+
+def test_rtm_shot_parity_fp32_cuda_cores():
+    w, ref = _oracle_shot(4)
+    s = _gpu(w, "f32", contraction=ridg.CONTRACT_CUDA_CORES)
+    tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
+    assert rel_l2(tr, ref.traces) < TOL["f32"]
+    assert rel_l2(ip, ref.image_p) < 10 * TOL["f32"]
+    assert rel_l2(iq, ref.image_q) < 10 * TOL["f32"]

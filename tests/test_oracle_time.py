@@ -253,3 +253,18 @@ def test_mrab_energy_non_increasing_three_levels():
         st.global_step()
         e.append(energy(st.q, g))
     assert max(e) <= e[0] * (1 + 1e-6) and e[-1] < e[0]
+
+
+def test_serving_models_have_three_levels():
+    """The shot-serving models use three rate levels (the smallest is checked here with the
+    oracle's level rule; the larger ones use the same bands at a finer spacing)."""
+    from oracle.dg_rhs import attach_media
+    from oracle.mesh_geometry import MeshGeometry
+    from oracle.mrab import assign_levels
+    from oracle.reference_element import reference_element
+    from synth import serving_model
+
+    w = serving_model("50k")
+    g = attach_media(MeshGeometry(w.xyz, w.tets, reference_element(1), default_bc=2), w.c, w.rho)
+    lev, nl, _ = assign_levels(g, w.N, w.c, w.cfl, w.n_levels_max)
+    assert nl == 3 and all(np.bincount(lev)[1:] > 0)
