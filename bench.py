@@ -578,6 +578,37 @@ def serving_stream(n_req, t_rec=0.01):
     return 0
 
 
+def gradient_bench(dtype="f64", n_checkpoints=16):
+    """Misfit gradient on the 648-element adjoint box (N = 3, one rate level, 0.5 s record, 25
+    receivers, observed data from a model with a 5 % Gaussian velocity bump): time of the forward
+    run with checkpoints and of the adjoint sweep.  One JSON line."""
+    from paper_1506_00907_gb300 import ridg
+    from synth import adjoint_box, adjoint_observed_velocity
+
+    w = adjoint_box()
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=1)
+    n_t = s.trace_len(w.t_final)
+    s.set_velocity(adjoint_observed_velocity(w))
+    _, obs = s.misfit_forward(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, np.zeros((25, n_t)))
+    s.set_velocity(w.c)
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        J, _ = s.misfit_forward(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, obs, n_checkpoints)
+        t1 = time.perf_counter()
+        g = s.misfit_backward()
+        t2 = time.perf_counter()
+        times.append((t1 - t0, t2 - t1))
+    fw, bw = min(t[0] for t in times), min(t[1] for t in times)
+    print(json.dumps({"workload": "adjoint box: 648 tets, N=3, one level, 0.5 s record, 25 receivers",
+                      "dtype": dtype, "steps": n_t - 1, "checkpoints": n_checkpoints, "misfit": J,
+                      "grad_norm": float(np.linalg.norm(g)), "forward_s": fw, "backward_s": bw,
+                      "gradient_s": fw + bw, "forward_us_per_step": 1e6 * fw / (n_t - 1),
+                      "backward_us_per_step": 1e6 * bw / (n_t - 1)}), flush=True)
+    return 0
+
+
 def _kernel_hash():
     import hashlib
 
@@ -602,7 +633,13 @@ def main():
                     help="comma-separated orders: FP64 / FP32 tensor-core / FP32 CUDA-core shots of the bench model")
     ap.add_argument("--serving-stream", type=int, default=0,
                     help="run the three-model shot-serving stream with this many requests and exit")
+    ap.add_argument("--gradient", action="store_true", help="time the misfit gradient on the adjoint box and exit")
     args = ap.parse_args()
+    if args.gradient:
+        from paper_1506_00907_gb300.build import build
+
+        build()
+        return gradient_bench()
     if args.serving_stream > 0:
         from paper_1506_00907_gb300.build import build
 

@@ -86,7 +86,9 @@ static T* dptr(const DBuf& b) {
 
 template <typename T>
 static void upload(DBuf& b, const std::vector<T>& v, cudaStream_t st) {
-  b.alloc(v.size() * sizeof(T));
+  // grow-only: a shot's tables change size with its receivers, and freeing device memory would
+  // synchronise the whole device (and so stall the shots of other streams)
+  b.reserve(v.size() * sizeof(T));
   if (!v.empty()) RIDG_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
 }
 
