@@ -141,3 +141,16 @@ def test_gradient_errors():
     assert e.value.code == -1
     with pytest.raises(ridg.RidgError):
         s.set_velocity(-w.c)
+
+
+def test_fp32_gradient_follows_fp64(box):
+    """The adjoint kernels in FP32 (CUDA cores for A^T, tensor cores for the forward steps) give the
+    FP64 gradient to FP32 accuracy, relative to the gradient's size."""
+    w, s64, obs = box
+    s64.misfit_forward(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, obs)
+    g64 = s64.misfit_backward()
+    s32 = _solver(w, dtype="f32")
+    J32, _ = s32.misfit_forward(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, obs)
+    g32 = s32.misfit_backward()
+    assert J32 > 0
+    assert rel_l2(g32, g64) < 1e-3
