@@ -52,13 +52,15 @@ def _forward_then_backward(prob, q0, n_global, replay):
 
 
 def test_replayed_boundary_traces_reconstruct_the_source_wavefield():
-    """Recorded forward traces as the exterior state of boundary faces: the backward run
-    returns to the initial state within a few percent, better than without the replay."""
+    """Recorded forward traces as the exterior state of boundary faces: after 200 global steps
+    (28 ms: the pulse has reached the transparent faces 50 m away), the backward run returns
+    to the initial state within a few percent; without the replay the waves that left do not come
+    back and the error is an order of magnitude larger."""
     prob, q0 = _pulse_problem()
-    e_replay = _forward_then_backward(prob, q0, 40, True)
-    e_plain = _forward_then_backward(prob, q0, 40, False)
-    assert e_replay < 3e-2
-    assert e_replay < e_plain
+    e_replay = _forward_then_backward(prob, q0, 200, True)
+    e_plain = _forward_then_backward(prob, q0, 200, False)
+    assert e_replay < 4e-2
+    assert e_plain > 5 * e_replay
 
 
 def test_tiny_shot_runs():
