@@ -308,3 +308,14 @@ def test_rtm_shot_parity_fp32_cuda_cores():
     assert rel_l2(tr, ref.traces) < TOL["f32"]
     assert rel_l2(ip, ref.image_p) < 10 * TOL["f32"]
     assert rel_l2(iq, ref.image_q) < 10 * TOL["f32"]
+
+
+def test_blow_up_is_reported_as_unstable():
+    """A time step far beyond the AB3 stability bound (cfl = 3) makes the fields overflow; the shot
+    reports RIDG_E_UNSTABLE instead of returning non-finite images."""
+    w = tiny_layered_rtm(N=3, t_final=0.02)
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=3.0, n_levels_max=w.n_levels_max)
+    with pytest.raises(ridg.RidgError) as e:
+        s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1e6, w.receivers, w.t_final)
+    assert e.value.code == -5
