@@ -463,7 +463,8 @@ def profile_shot(t_final):
 
 def precision_sweep(orders, t_final=0.01):
     """Per order: the bench model's shot over a short record in FP64, in FP32 with the element
-    products on tensor cores (three-term TF32 split) and in FP32 with them on CUDA cores; throughput,
+    products on tensor cores (three-term TF32 split, or BF16 hi + lo split) and in FP32 with them on
+    CUDA cores; throughput,
     fused-kernel times and the relative L2 error of traces and images against the FP64 shot.  One
     JSON line per order."""
     from paper_1506_00907_gb300 import ridg
@@ -479,6 +480,7 @@ def precision_sweep(orders, t_final=0.01):
         res = {}
         for name, dtype, contraction in (("f64", "f64", ridg.CONTRACT_TENSOR),
                                          ("f32_tensor_tf32x3", "f32", ridg.CONTRACT_TENSOR),
+                                         ("f32_tensor_bf16x3", "f32", ridg.CONTRACT_TENSOR_BF16),
                                          ("f32_cuda_cores", "f32", ridg.CONTRACT_CUDA_CORES)):
             try:
                 s = ridg.Solver(mesh, N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=w.n_levels_max,
@@ -498,7 +500,7 @@ def precision_sweep(orders, t_final=0.01):
                          "backward_full_launch_ms": st.prof_backward_ms / max(1, st.prof_backward_launches)}
             s.close()
         if "f64" in res:
-            for name in ("f32_tensor_tf32x3", "f32_cuda_cores"):
+            for name in ("f32_tensor_tf32x3", "f32_tensor_bf16x3", "f32_cuda_cores"):
                 if name in res:
                     out[name].update({k: rel(a, b) for k, a, b in zip(("traces_rel_l2", "image_p_rel_l2",
                                                                       "image_q_rel_l2"), res[name], res["f64"])})

@@ -98,11 +98,14 @@ typedef struct ridg_options {
                            upwind fluxes (Sec. 3.1, Eqs. weakFormP/V); <= 0 selects 1 (upwind) */
   int32_t contraction;  /* RIDG_F32 only: RIDG_CONTRACT_TENSOR (0, default) runs the D_r/D_s/D_t and
                            LIFT products on tensor cores (three-term TF32 split, FP32 accumulation);
-                           RIDG_CONTRACT_CUDA_CORES runs them as plain FP32 FMAs */
+                           RIDG_CONTRACT_CUDA_CORES runs them as plain FP32 FMAs;
+                           RIDG_CONTRACT_TENSOR_BF16 on tensor cores as a BF16 hi + lo split (three
+                           m16n8k16 products, FP32 accumulation: about 2^-16 relative per product) */
   int32_t reserved[3];
 } ridg_options;
 #define RIDG_CONTRACT_TENSOR 0
 #define RIDG_CONTRACT_CUDA_CORES 1
+#define RIDG_CONTRACT_TENSOR_BF16 2
 
 #define RIDG_IMAGE_P 1 /* classical image, Eq. imageP */
 #define RIDG_IMAGE_Q 2 /* characteristic image, Eq. imageQ */

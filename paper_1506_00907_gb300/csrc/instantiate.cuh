@@ -1,4 +1,6 @@
 // Explicit instantiation of the kernels of one order (RIDG_ORDER), included by kernels_n<N>.cu.
+#include "ridg.h"
+
 #include "adjoint_kernels.cuh"
 #include "aux_kernels.cuh"
 #include "dispatch.hpp"
@@ -8,30 +10,32 @@
 
 namespace ridg {
 
+// FP32 on tensor cores with the split format KIND
+template <int N, int W, int KIND>
+static cudaError_t launch_step_tc(const StepArgs<float>& a, int64_t blocks, cudaStream_t st) {
+  constexpr size_t smem = SmemTc<N, W>::bytes;
+  // set once per process (thread-safe initialisation: shot servers launch from several threads)
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(dg_step_kernel_tc<N, W, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (configured != cudaSuccess) return configured;
+  dg_step_kernel_tc<N, W, KIND><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int N, typename real, int W>
 static cudaError_t launch_step_w(const StepArgs<real>& a, cudaStream_t st) {
   int64_t blocks = (a.slot_hi - a.slot_lo) / (32 / W);
   if (blocks <= 0) return cudaSuccess;
   if constexpr (std::is_same<real, float>::value) {
-    if (!a.cuda_cores) {
-      // FP32: element products on tensor cores (TF32 three-term split)
-      constexpr size_t smem = SmemTc<N, W>::bytes;
-      // set once per process (thread-safe initialisation: shot servers launch from several threads)
-      static const cudaError_t configured =
-          cudaFuncSetAttribute(dg_step_kernel_tc<N, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-      if (configured != cudaSuccess) return configured;
-      dg_step_kernel_tc<N, W><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a);
-      return cudaGetLastError();
-    }
+    if (a.contraction == RIDG_CONTRACT_TENSOR) return launch_step_tc<N, W, kSplitTf32>(a, blocks, st);
+    if (a.contraction == RIDG_CONTRACT_TENSOR_BF16) return launch_step_tc<N, W, kSplitBf16>(a, blocks, st);
   }
-  {
-    // FP64, or FP32 on CUDA cores
-    constexpr size_t smem = step_smem_bytes<N, real, W>();
-    static const cudaError_t configured =
-        cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    if (configured != cudaSuccess) return configured;
-    dg_step_kernel<N, real, W><<<dim3(unsigned(blocks)), Order<N>::NT, smem, st>>>(a);
-  }
+  // FP64, or FP32 on CUDA cores
+  constexpr size_t smem = step_smem_bytes<N, real, W>();
+  static const cudaError_t configured =
+      cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (configured != cudaSuccess) return configured;
+  dg_step_kernel<N, real, W><<<dim3(unsigned(blocks)), Order<N>::NT, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -217,9 +217,10 @@ class Engine final : public ridg_solver {
     double cfl = opt.cfl > 0 ? opt.cfl : 0.15;
     int nlm = opt.n_levels_max > 0 ? opt.n_levels_max : 3;
     tau_scale_ = opt.tau_scale > 0 ? opt.tau_scale : 1.0;
-    if (opt.contraction != RIDG_CONTRACT_TENSOR && opt.contraction != RIDG_CONTRACT_CUDA_CORES)
-      throw Error{RIDG_E_INVALID_ARG, "contraction must be RIDG_CONTRACT_TENSOR or RIDG_CONTRACT_CUDA_CORES"};
-    cuda_cores_ = std::is_same<real, float>::value && opt.contraction == RIDG_CONTRACT_CUDA_CORES;
+    if (opt.contraction != RIDG_CONTRACT_TENSOR && opt.contraction != RIDG_CONTRACT_CUDA_CORES &&
+        opt.contraction != RIDG_CONTRACT_TENSOR_BF16)
+      throw Error{RIDG_E_INVALID_ARG, "contraction must be one of RIDG_CONTRACT_TENSOR, _CUDA_CORES, _TENSOR_BF16"};
+    contraction_ = std::is_same<real, float>::value ? opt.contraction : RIDG_CONTRACT_CUDA_CORES;
     image_mode_ = ((opt.image_mask & RIDG_IMAGE_P) || !(opt.image_mask & 3) ? kModeImageP : 0) |
                   ((opt.image_mask & RIDG_IMAGE_Q) || !(opt.image_mask & 3) ? kModeImageQ : 0);
     if (nlm > kMaxLevels) throw Error{RIDG_E_INVALID_ARG, "n_levels_max too large"};
@@ -889,7 +890,7 @@ class Engine final : public ridg_solver {
     size_t need = dispatch_order(N_, [&](auto NC) {
       constexpr int NN = decltype(NC)::value;
       if constexpr (std::is_same<real, float>::value)
-        if (!cuda_cores_) return std::max(SmemTc<NN, 1>::bytes, SmemTc<NN, 2>::bytes);
+        if (contraction_ != RIDG_CONTRACT_CUDA_CORES) return std::max(SmemTc<NN, 1>::bytes, SmemTc<NN, 2>::bytes);
       return std::max(step_smem_bytes<NN, real, 1>(), step_smem_bytes<NN, real, 2>());
     });
     if (need > size_t(optin))
@@ -975,7 +976,8 @@ class Engine final : public ridg_solver {
       for (int n = 0; n < Np_; ++n) Lt[fm * NPa_ + n] = real(ref_.LIFT(n, fm));
     upload(Dt_d_, Dt, st_);
     upload(Lt_d_, Lt, st_);
-    if (std::is_same<real, float>::value) upload(afrag_d_, operator_fragments(), st_);
+    if (contraction_ == RIDG_CONTRACT_TENSOR || contraction_ == RIDG_CONTRACT_TENSOR_BF16)
+      upload(afrag_d_, operator_fragments(contraction_ == RIDG_CONTRACT_TENSOR_BF16), st_);
     std::vector<int> fm(128, 0), pm(192, 0);
     for (int f = 0; f < 4; ++f)
       for (int j = 0; j < Nfp_; ++j) fm[f * 32 + j] = ref_.fmask[f][j];
@@ -1060,41 +1062,73 @@ class Engine final : public ridg_solver {
   // columns t, t+4) for D_r, D_s, D_t and the four LIFT blocks, tiles of 16 nodes x 8 nodes,
   // each value split into TF32 hi and lo (hi + lo = the FP64 operator to ~2^-22).  One stream
   // per node tile mt, in the order the kernel consumes them: D_jd k-steps, then LIFT blocks.
-  std::vector<uint32_t> operator_fragments() const {
-    const int MT = (Np_ + 15) / 16, KSD = (Np_ + 7) / 8, KSF = (Nfp_ + 7) / 8;
+  // BF16 rounding (round to nearest even) of an FP32 value, as the 16 high bits
+  static uint32_t bf16_bits(float x) {
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return u >> 16;
+    u += 0x7fffu + ((u >> 16) & 1u);
+    return u >> 16;
+  }
+  // Operator fragments for the tensor-core products, one stream per node tile mt, in the order the
+  // kernel consumes them: D_jd k-steps, then LIFT blocks; each value split into hi and lo
+  // (hi + lo = the FP64 operator to ~2^-22 in TF32, ~2^-16 in BF16).
+  //  TF32 (mma.m16n8k8, A 16 x 8 row major): lane (g, t) holds rows g, g+8 and columns t, t+4.
+  //  BF16 (mma.m16n8k16, A 16 x 16 row major): lane (g, t) holds rows g, g+8 and fragment columns
+  //  2t, 2t+1 (register 0/1) and 2t+8, 2t+9 (register 2/3), two values per register, lower column
+  //  in the low half; fragment columns 2t, 2t+1, 2t+8, 2t+9 are the step's nodes t, t+4, t+8, t+12
+  //  (the kernel loads B in the same order).
+  std::vector<uint32_t> operator_fragments(bool bf16) const {
+    const int KS = bf16 ? 16 : 8;
+    const int MT = (Np_ + 15) / 16, KSD = (Np_ + KS - 1) / KS, KSF = (Nfp_ + KS - 1) / KS;
     const int NSTEP = 3 * KSD + 4 * KSF;
     std::vector<uint32_t> out(size_t(MT * NSTEP) * 256, 0u);
-    auto put = [&](size_t tile, int lane, int q, double v) {
-      float hf = float(v);
-      uint32_t hi = tf32_bits(hf);
-      float hiv;
-      std::memcpy(&hiv, &hi, 4);
-      uint32_t lo = tf32_bits(float(v - double(hiv)));
-      out[tile * 256 + lane * 8 + q] = hi;
-      out[tile * 256 + lane * 8 + 4 + q] = lo;
+    // op(r, c): the operator value of row r, column c of step (matrix, k-step kb)
+    auto tile = [&](size_t step, int mt, int kb, int ncol, auto&& op) {
+      for (int lane = 0; lane < 32; ++lane) {
+        const int g = lane >> 2, t = lane & 3;
+        auto val = [&](int r, int c) { return (r < Np_ && c < ncol) ? op(r, c) : 0.0; };
+        for (int q = 0; q < 4; ++q) {
+          const int r = mt * 16 + g + 8 * (q & 1);
+          uint32_t hi, lo;
+          if (!bf16) {
+            const int c = kb * 8 + t + 4 * (q >> 1);
+            const double v = val(r, c);
+            hi = tf32_bits(float(v));
+            float hv;
+            std::memcpy(&hv, &hi, 4);
+            lo = tf32_bits(float(v - double(hv)));
+          } else {
+            const int c0 = kb * 16 + t + 8 * (q >> 1), c1 = c0 + 4;  // fragment columns 2t(+8), 2t+1(+8)
+            uint32_t h2[2], l2[2];
+            const double v2[2] = {val(r, c0), val(r, c1)};
+            for (int i = 0; i < 2; ++i) {
+              h2[i] = bf16_bits(float(v2[i]));
+              const uint32_t hb = h2[i] << 16;
+              float hv;
+              std::memcpy(&hv, &hb, 4);
+              l2[i] = bf16_bits(float(v2[i] - double(hv)));
+            }
+            hi = h2[0] | (h2[1] << 16);
+            lo = l2[0] | (l2[1] << 16);
+          }
+          out[step * 256 + lane * 8 + q] = hi;
+          out[step * 256 + lane * 8 + 4 + q] = lo;
+        }
+      }
     };
-    for (int lane = 0; lane < 32; ++lane) {
-      const int g = lane >> 2, t = lane & 3;
-      const int rr[4] = {g, g + 8, g, g + 8}, cc[4] = {t, t, t + 4, t + 4};
+    for (int mt = 0; mt < MT; ++mt) {
       for (int jd = 0; jd < 3; ++jd)
-        for (int mt = 0; mt < MT; ++mt)
-          for (int kb = 0; kb < KSD; ++kb)
-            for (int q = 0; q < 4; ++q) {
-              int r = mt * 16 + rr[q], c = kb * 8 + cc[q];
-              double v = (r < Np_ && c < Np_) ? ref_.D[jd](r, c) : 0.0;
-              put(size_t(mt * NSTEP + jd * KSD + kb), lane, q, v);
-            }
+        for (int kb = 0; kb < KSD; ++kb)
+          tile(size_t(mt * NSTEP + jd * KSD + kb), mt, kb, Np_, [&](int r, int c) { return ref_.D[jd](r, c); });
       for (int f = 0; f < 4; ++f)
-        for (int mt = 0; mt < MT; ++mt)
-          for (int kb = 0; kb < KSF; ++kb)
-            for (int q = 0; q < 4; ++q) {
-              int r = mt * 16 + rr[q], c = kb * 8 + cc[q];
-              double v = (r < Np_ && c < Nfp_) ? ref_.LIFT(r, f * Nfp_ + c) : 0.0;
-              put(size_t(mt * NSTEP + 3 * KSD + f * KSF + kb), lane, q, v);
-            }
+        for (int kb = 0; kb < KSF; ++kb)
+          tile(size_t(mt * NSTEP + 3 * KSD + f * KSF + kb), mt, kb, Nfp_,
+               [&](int r, int c) { return ref_.LIFT(r, f * Nfp_ + c); });
     }
     return out;
   }
+
 
   void alloc_wave(Wave<real>& w) {
     if (w.q.p) return;
@@ -1155,7 +1189,7 @@ class Engine final : public ridg_solver {
     a.fmask = dptr<const int>(fmask_d_);
     a.perm = dptr<const int>(perm_d_);
     a.afrag = dptr<const uint32_t>(afrag_d_);
-    a.cuda_cores = cuda_cores_ ? 1 : 0;
+    a.contraction = contraction_;
     a.e_up[2] = real(-1);
     return a;
   }
@@ -1307,7 +1341,7 @@ class Engine final : public ridg_solver {
   DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
   DBuf afrag_d_, gtab_d_[2], pos_d_;
   double tau_scale_ = 1.0;
-  bool cuda_cores_ = false;  // FP32 element products on CUDA cores instead of tensor cores
+  int contraction_ = RIDG_CONTRACT_TENSOR;  // how the FP32 element products run (FP64: CUDA cores)
   int image_mode_ = kModeImage;
   std::vector<int> pos_of_;  // device position of each reference node
   DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_;

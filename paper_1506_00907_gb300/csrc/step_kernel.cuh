@@ -115,7 +115,7 @@ struct StepArgs {
   real* rhs_out;         // kModeRhsOnly: q-sized
   const uint32_t* afrag; // tensor-core variant: operator fragments (TF32 hi/lo), see step_kernel_tc.cuh
   const float* gtab;     // tensor-core variant: per-element coefficients [n_slots][kGtab] (this tau sign)
-  int cuda_cores;        // FP32: 1 runs the CUDA-core kernel instead of the tensor-core one
+  int contraction;       // FP32 element products: RIDG_CONTRACT_TENSOR / _CUDA_CORES / _TENSOR_BF16
 };
 
 template <int N>

@@ -18,16 +18,23 @@
 // memory; the update then runs with a thread per (node, element), so that every global store is
 // 32 (or 2 x 16) consecutive columns.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "step_kernel.cuh"
 
 namespace ridg {
-template <int N>
+// Split formats of the tensor-core products: TF32 hi + lo with m16n8k8 (k-steps of 8 nodes), or
+// BF16 hi + lo with m16n8k16 (k-steps of 16 nodes, half the instructions, 16 significand bits).
+constexpr int kSplitTf32 = 0, kSplitBf16 = 1;
+
+template <int N, int KIND = kSplitTf32>
 struct TcOrder {
   using O = Order<N>;
   static constexpr int Np = O::Np, Nfp = O::Nfp;
   static constexpr int MT = (Np + 15) / 16;  // 16-node tiles
-  static constexpr int KSD = (Np + 7) / 8;   // k-steps over the nodes
-  static constexpr int KSF = (Nfp + 7) / 8;  // k-steps over the nodes of one face
+  static constexpr int KS = KIND == kSplitBf16 ? 16 : 8;  // nodes per k-step
+  static constexpr int KSD = (Np + KS - 1) / KS;   // k-steps over the nodes
+  static constexpr int KSF = (Nfp + KS - 1) / KS;  // k-steps over the nodes of one face
   static constexpr int NWARP = 2 * MT;
   static constexpr int NT = 32 * NWARP;
   // operator fragments, one contiguous stream per node tile: [MT][NSTEP][32 lanes][8], 8 = 4 hi +
@@ -71,6 +78,38 @@ __device__ __forceinline__ void load_b(const float* X, int row0, int kvalid_rel,
   split_tf32(x1, bh[1], bl[1]);
 }
 
+// m16n8k16 BF16 product with FP32 accumulation (A 16 x 16 row major, B 16 x 8 column major).
+__device__ __forceinline__ void mma_bf16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Two values as BF16 hi + lo pairs (round to nearest even): hi = bf16(x), lo = bf16(x - hi); the
+// value with the lower k index goes to the low half of each register.
+__device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(x0, x1);
+  const __nv_bfloat162 l = __floats2bfloat162_rn(x0 - __low2float(h), x1 - __high2float(h));
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// B fragment of a BF16 k-step (16 x 8, column major).  The k index is permuted inside the step so
+// that lane (g, t) reads rows t, t + 4, t + 8, t + 12 (the conflict-free rows of the TF32 loads):
+// fragment positions 2t, 2t+1, 2t+8, 2t+9 hold rows t, t+4, t+8, t+12; the host orders the operator
+// columns of each step the same way, so the product is unchanged.
+template <int CS>
+__device__ __forceinline__ void load_b16(const float* X, int row0, int kvalid_rel, int t, int col, uint32_t bh[2],
+                                         uint32_t bl[2]) {
+  float x[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) x[i] = (t + 4 * i < kvalid_rel) ? X[(row0 + t + 4 * i) * CS + col] : 0.f;
+  split_bf16x2(x[0], x[1], bh[0], bl[0]);
+  split_bf16x2(x[2], x[3], bh[1], bl[1]);
+}
+
 __device__ __forceinline__ void load_a(const uint32_t* frag, int lane, FragA& a) {
   const uint4* p = reinterpret_cast<const uint4*>(frag + lane * 8);
   uint4 h = __ldg(p), l = __ldg(p + 1);
@@ -108,10 +147,24 @@ struct SmemTc {
   static_assert(4 * Np * CS <= 2 * ST + UX, "right-hand-side staging must fit in the penalty/U region");
 };
 
-template <int N, int W>
+template <int N, int W, int KIND>
 __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kernel_tc(const StepArgs<float> A) {
   using O = Order<N>;
-  using T = TcOrder<N>;
+  using T = TcOrder<N, KIND>;
+  constexpr int KS = T::KS;
+  // one k-step of the split product: B pieces from shared memory, and the MMA of the split format
+  auto load_bk = [](const float* X, int row0, int kv, int t, int col, uint32_t bh[2], uint32_t bl[2]) {
+    if constexpr (KIND == kSplitBf16)
+      load_b16<SmemTc<N, W>::CS>(X, row0, kv, t, col, bh, bl);
+    else
+      load_b<SmemTc<N, W>::CS>(X, row0, kv, t, col, bh, bl);
+  };
+  auto mma = [](float c[4], const uint32_t a[4], const uint32_t b[2]) {
+    if constexpr (KIND == kSplitBf16)
+      mma_bf16(c, a, b);
+    else
+      mma_tf32(c, a, b);
+  };
   using SM = SmemTc<N, W>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NT = T::NT, NFPP = O::NFPP;
   constexpr int CS = SM::CS, EPB = SM::EPB, GS = SM::GS;
@@ -430,28 +483,28 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
 #pragma unroll(KUNROLL)
       for (int kb = 0; kb < KSD; ++kb) {
         const FragA F3 = next(jd * KSD + kb);
-        const int kv = Np - kb * 8;
+        const int kv = Np - kb * KS;
         uint32_t ph[2][2], pl[2][2], uh[2][2], ul[2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          load_b<CS>(sQ, kb * 8, kv, t4, colb[b], ph[b], pl[b]);
-          load_b<CS>(Ub, kb * 8, kv, t4, colb[b], uh[b], ul[b]);
+          load_bk(sQ, kb * KS, kv, t4, colb[b], ph[b], pl[b]);
+          load_bk(Ub, kb * KS, kv, t4, colb[b], uh[b], ul[b]);
         }
         // the three split terms of four independent accumulators, interleaved
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(acc[b], F0.l, ph[b]);
-          mma_tf32(rp[b], F0.l, uh[b]);
+          mma(acc[b], F0.l, ph[b]);
+          mma(rp[b], F0.l, uh[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(acc[b], F0.h, pl[b]);
-          mma_tf32(rp[b], F0.h, ul[b]);
+          mma(acc[b], F0.h, pl[b]);
+          mma(rp[b], F0.h, ul[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(acc[b], F0.h, ph[b]);
-          mma_tf32(rp[b], F0.h, uh[b]);
+          mma(acc[b], F0.h, ph[b]);
+          mma(rp[b], F0.h, uh[b]);
         }
         F0 = F1;
         F1 = F2;
@@ -479,27 +532,27 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
 #pragma unroll(KUNROLL)
       for (int kb = 0; kb < KSF; ++kb) {
         const FragA F3 = next(3 * KSD + f * KSF + kb);
-        const int kv = Nfp - kb * 8;
+        const int kv = Nfp - kb * KS;
         uint32_t th[2][2], tl[2][2], sh[2][2], sl[2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          load_b<CS>(sT, f * Nfp + kb * 8, kv, t4, colb[b], th[b], tl[b]);
-          load_b<CS>(sS, f * Nfp + kb * 8, kv, t4, colb[b], sh[b], sl[b]);
+          load_bk(sT, f * Nfp + kb * KS, kv, t4, colb[b], th[b], tl[b]);
+          load_bk(sS, f * Nfp + kb * KS, kv, t4, colb[b], sh[b], sl[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(rp[b], F0.l, th[b]);
-          mma_tf32(acc[b], F0.l, sh[b]);
+          mma(rp[b], F0.l, th[b]);
+          mma(acc[b], F0.l, sh[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(rp[b], F0.h, tl[b]);
-          mma_tf32(acc[b], F0.h, sl[b]);
+          mma(rp[b], F0.h, tl[b]);
+          mma(acc[b], F0.h, sl[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          mma_tf32(rp[b], F0.h, th[b]);
-          mma_tf32(acc[b], F0.h, sh[b]);
+          mma(rp[b], F0.h, th[b]);
+          mma(acc[b], F0.h, sh[b]);
         }
         F0 = F1;
         F1 = F2;

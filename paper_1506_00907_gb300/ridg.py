@@ -45,7 +45,7 @@ class Options(C.Structure):
 
 
 IMAGE_P, IMAGE_Q = 1, 2
-CONTRACT_TENSOR, CONTRACT_CUDA_CORES = 0, 1
+CONTRACT_TENSOR, CONTRACT_CUDA_CORES, CONTRACT_TENSOR_BF16 = 0, 1, 2
 SRC_RICKER, SRC_SAMPLED = 0, 1
 
 

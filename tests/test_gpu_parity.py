@@ -319,3 +319,34 @@ def test_blow_up_is_reported_as_unstable():
     with pytest.raises(ridg.RidgError) as e:
         s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1e6, w.receivers, w.t_final)
     assert e.value.code == -5
+
+
+# the BF16 hi + lo split keeps about 16 significand bits per product (2^-17 relative): its stated
+# tolerance against the FP64 oracle is 1e-4
+TOL_BF16 = 1e-4
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_rhs_parity_bf16_split(N):
+    """FP32 with the element products on tensor cores as a BF16 hi + lo split (m16n8k16): right-hand
+    side with every boundary condition, several blocks and a ragged tail."""
+    w = tiny_layered_rtm(N=N)
+    fb = mixed_bc(w)
+    prob = _oracle_problem(w, face_bc=fb)
+    s = _gpu(w, "f32", face_bc=fb, contraction=ridg.CONTRACT_TENSOR_BF16)
+    q = random_state(w.K, s.Np, seed=11)
+    g = prob.geo
+    r_ref = rhs(np.arange(g.K), q, traces(q, g), g)
+    r = s.eval_rhs(q)
+    assert rel_l2(r, r_ref) < TOL_BF16
+    # the split is the only difference from the TF32 path: its error is above FP32 rounding
+    assert rel_l2(r, r_ref) > 1e-7
+
+
+def test_rtm_shot_parity_bf16_split():
+    w, ref = _oracle_shot(4)
+    s = _gpu(w, "f32", contraction=ridg.CONTRACT_TENSOR_BF16)
+    tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
+    assert rel_l2(tr, ref.traces) < TOL_BF16
+    assert rel_l2(ip, ref.image_p) < 10 * TOL_BF16
+    assert rel_l2(iq, ref.image_q) < 10 * TOL_BF16
