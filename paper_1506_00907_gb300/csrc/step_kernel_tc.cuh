@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   constexpr int CS = SM::CS, EPB = SM::EPB, GS = SM::GS;
   constexpr bool RING = SM::ring_in_smem;
   constexpr int MT = T::MT, KSD = T::KSD, KSF = T::KSF, NSTEP = T::NSTEP;
-  // the k-steps are unrolled where the registers allow it (the two highest orders keep them rolled)
-  constexpr int KUNROLL = N <= 4 ? 16 : 1;
+  // the k-steps are unrolled (the fragment registers then rotate by renaming)
+  constexpr int KUNROLL = 16;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* sQ = reinterpret_cast<float*>(smem_raw);  // [4][Np][CS]
