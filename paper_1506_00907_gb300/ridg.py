@@ -341,9 +341,10 @@ class Solver:
         return traces, ip, iq
 
     def rtm_shot_device(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0,
-                        observed=None, traces=None, image_p=None, image_q=None, e_up=(0.0, 0.0, -1.0)):
+                        observed=None, traces=None, image_p=None, image_q=None, e_up=(0.0, 0.0, -1.0),
+                        wavelet=None, wavelet_dt=None):
         """Device-buffer shot (torch CUDA float64 tensors or None); returns after enqueueing."""
-        src, _keep = _source(source_xyz, f0, t_peak, amplitude)
+        src, _keep = _source(source_xyz, f0, t_peak, amplitude, wavelet, wavelet_dt)
         rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
         eu = _f64(e_up)
         _check(lib().ridg_rtm_shot_device(self._h, C.byref(src), _ptr(rec), rec.shape[0], float(t_final),
