@@ -511,29 +511,32 @@ def precision_sweep(orders, t_final=0.01):
     return 0
 
 
-def serving_stream(n_req, t_rec=0.01):
-    """Shot-serving stream over three models (about 5e4 / 2e5 / 8e5 elements at N = 3 / 4 / 5,
-    three layers, three rate levels): n_req requests (model, surface source, 101-401 receivers;
-    seed 5) with Poisson arrivals (seed 5) at 0.8x and 1.5x the measured sequential rate, served
-    with one and with two slots per model.  Prints one JSON line."""
+def serving_stream(n_req, t_rec=0.01, sizes=("50k", "200k", "800k"), slot_counts=(1, 2), contraction="tf32"):
+    """Shot-serving stream over the serving models (about 5e4 / 2e5 / 8e5 elements at N = 3 / 4 / 5,
+    three layers, three rate levels; ``sizes`` picks a subset): n_req requests (model, surface
+    source, 101-401 receivers; seed 5) with Poisson arrivals (seed 5) at 0.8x and 1.5x the measured
+    sequential rate, served with each number of slots per model in ``slot_counts``; FP32 with the
+    TF32 or BF16 split.  Prints one JSON line."""
     import torch
 
     from paper_1506_00907_gb300 import ridg
     from synth import serving_model, serving_requests
 
-    sizes = ("50k", "200k", "800k")
+    nm = len(sizes)
+    kmax = max(slot_counts)
     models = [serving_model(sz) for sz in sizes]
     meshes = [ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc) for w in models]
+    ctr = ridg.CONTRACT_TENSOR_BF16 if contraction == "bf16" else ridg.CONTRACT_TENSOR
     streams, slots = [], {}
     for m, (w, mesh) in enumerate(zip(models, meshes)):
         slots[m] = []
-        for _ in range(2):
+        for _ in range(kmax):
             st = torch.cuda.Stream()
             streams.append(st)
             slots[m].append(ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max,
-                                        stream=st.cuda_stream))
-    reqs = serving_requests(n_req)
-    out = {"requests": n_req, "record_s": t_rec,
+                                        stream=st.cuda_stream, contraction=ctr))
+    reqs = [(m % nm, src, rec) for m, src, rec in serving_requests(n_req)]
+    out = {"requests": n_req, "record_s": t_rec, "contraction": contraction,
            "models": [{"elements": int(w.K), "order": w.N, "levels": s[0].info.n_levels} for w, s in
                       zip(models, slots.values())],
            "arrivals": "Poisson (seed 5) at 0.8x and 1.5x the sequential rate; model, source and receiver count "
@@ -545,11 +548,11 @@ def serving_stream(n_req, t_rec=0.01):
         return sv.submit(src, w.f0, w.t_peak, 1.0, rec, t_rec, model=m)
 
     def server(k):
-        sl = [slots[m][i] for m in range(3) for i in range(k)]
-        return ridg.Server(sl, max_queued=n_req, models=[m for m in range(3) for _ in range(k)])
+        sl = [slots[m][i] for m in range(nm) for i in range(k)]
+        return ridg.Server(sl, max_queued=n_req, models=[m for m in range(nm) for _ in range(k)])
 
-    with server(2) as sv:  # buffers of every slot in place
-        for t in [submit(sv, (m, (1000.0, 1000.0, 8.0), reqs[0][2])) for m in range(3) for _ in range(2)]:
+    with server(kmax) as sv:  # buffers of every slot in place
+        for t in [submit(sv, (m, (1000.0, 1000.0, 8.0), reqs[0][2])) for m in range(nm) for _ in range(kmax)]:
             sv.wait(t)
     n_seq = min(n_req, 24)
     with server(1) as sv:
@@ -558,7 +561,7 @@ def serving_stream(n_req, t_rec=0.01):
             sv.wait(submit(sv, r))
         seq = n_seq / (time.perf_counter() - t0)
     out["sequential_shots_per_s"] = seq
-    for k in (1, 2):
+    for k in slot_counts:
         for factor in (0.8, 1.5):
             gaps = np.random.default_rng(5).exponential(1.0 / (factor * seq), n_req)
             with server(k) as sv:
@@ -635,6 +638,9 @@ def main():
                     help="comma-separated orders: FP64 / FP32 tensor-core / FP32 CUDA-core shots of the bench model")
     ap.add_argument("--serving-stream", type=int, default=0,
                     help="run the three-model shot-serving stream with this many requests and exit")
+    ap.add_argument("--serving-sizes", default="50k,200k,800k", help="serving models (subset of 50k,200k,800k)")
+    ap.add_argument("--serving-slots", default="1,2", help="slots per model to compare")
+    ap.add_argument("--serving-contraction", default="tf32", choices=["tf32", "bf16"])
     ap.add_argument("--gradient", action="store_true", help="time the misfit gradient on the adjoint box and exit")
     args = ap.parse_args()
     if args.gradient:
@@ -646,7 +652,9 @@ def main():
         from paper_1506_00907_gb300.build import build
 
         build()
-        return serving_stream(args.serving_stream)
+        return serving_stream(args.serving_stream, sizes=tuple(args.serving_sizes.split(",")),
+                              slot_counts=tuple(int(x) for x in args.serving_slots.split(",")),
+                              contraction=args.serving_contraction)
     if args.precision_sweep:
         from paper_1506_00907_gb300.build import build
 
