@@ -80,6 +80,15 @@ void ridg_mesh_destroy(ridg_mesh* mesh);
 /* Number of boundary faces, interior faces of the mesh (host only). */
 int ridg_mesh_counts(const ridg_mesh* mesh, int64_t* n_boundary_faces, int64_t* n_interior_faces);
 
+/* Point location (host only): for each of the n points xyz[3*i..3*i+2] the element that contains
+ * it (barycentric coordinates >= -1e-12; the lowest element index when the point lies on a face,
+ * edge or vertex shared by several) in elem_out[i], or -1 outside the mesh, and its reference
+ * coordinates (r, s, t) on the reference tetrahedron with vertices (-1,-1,-1), (1,-1,-1), (-1,1,-1),
+ * (-1,-1,1) in rst_out[3*i..] (may be NULL).  Sources and receivers are placed with this rule
+ * (Eq. sourceTerm, receiver interpolation).  A uniform grid index is built on the first call and
+ * kept with the mesh.  Errors: RIDG_E_INVALID_ARG. */
+int ridg_mesh_locate(ridg_mesh* mesh, const double* xyz, int64_t n, int64_t* elem_out, double* rst_out);
+
 /* ------------------------------------------------------------------ reference element (host only)
  * Operators of the reference tetrahedron of order N (Sec. 3.1 and the appendix), computed by the
  * library's own setup code.  Any output pointer may be NULL.

@@ -634,19 +634,87 @@ Ordering build_ordering(const Levels& lv, int64_t K) {
   return o;
 }
 
-int64_t locate_point(const MeshData& m, const Geometry& g, const double x[3], double rst[3]) {
-  (void)g;
-  for (int64_t k = 0; k < m.K; ++k) {
+PointLocator build_locator(const MeshData& m) {
+  PointLocator L;
+  if (m.K == 0) {
+    L.start.assign(2, 0);
+    return L;
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t v = 0; v < m.n_vert; ++v)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], m.xyz[3 * v + d]);
+      hi[d] = std::max(hi[d], m.xyz[3 * v + d]);
+    }
+  // about two elements per cell on average
+  const double vol = std::max((hi[0] - lo[0]) * (hi[1] - lo[1]) * (hi[2] - lo[2]), 1e-300);
+  const double cell = std::cbrt(2.0 * vol / double(m.K));
+  int64_t cells = 1;
+  for (int d = 0; d < 3; ++d) {
+    const double ext = hi[d] - lo[d];
+    L.n[d] = int(std::min<double>(std::max(1.0, std::ceil(ext / cell)), 1024.0));
+    L.lo[d] = lo[d];
+    L.h[d] = ext > 0 ? ext / L.n[d] : 1.0;
+    cells *= L.n[d];
+  }
+  const double tol = 1e-9 * std::max({hi[0] - lo[0], hi[1] - lo[1], hi[2] - lo[2], 1e-300});
+  auto range = [&](int64_t k, int d, int& c0, int& c1) {
+    double a = 1e300, b = -1e300;
+    for (int v = 0; v < 4; ++v) {
+      const double x = m.xyz[3 * m.tet[4 * k + v] + d];
+      a = std::min(a, x);
+      b = std::max(b, x);
+    }
+    c0 = std::max(0, std::min(L.n[d] - 1, int(std::floor((a - tol - L.lo[d]) / L.h[d]))));
+    c1 = std::max(0, std::min(L.n[d] - 1, int(std::floor((b + tol - L.lo[d]) / L.h[d]))));
+  };
+  std::vector<int64_t> count(cells + 1, 0);
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int64_t> fill;
+    if (pass == 1) {
+      L.start.assign(cells + 1, 0);
+      for (int64_t c = 0; c < cells; ++c) L.start[c + 1] = L.start[c] + count[c];
+      L.items.assign(L.start[cells], 0);
+      fill.assign(L.start.begin(), L.start.end() - 1);
+    }
+    for (int64_t k = 0; k < m.K; ++k) {  // increasing k: every cell's list comes out sorted
+      int c0[3], c1[3];
+      for (int d = 0; d < 3; ++d) range(k, d, c0[d], c1[d]);
+      for (int z = c0[2]; z <= c1[2]; ++z)
+        for (int y = c0[1]; y <= c1[1]; ++y)
+          for (int x = c0[0]; x <= c1[0]; ++x) {
+            const int64_t c = (int64_t(z) * L.n[1] + y) * L.n[0] + x;
+            if (pass == 0)
+              ++count[c];
+            else
+              L.items[fill[c]++] = k;
+          }
+    }
+  }
+  return L;
+}
+
+int64_t locate_point(const MeshData& m, const PointLocator& L, const double x[3], double rst[3]) {
+  if (m.K == 0 || L.start.empty()) return -1;
+  int c[3];
+  for (int d = 0; d < 3; ++d) {
+    const double u = (x[d] - L.lo[d]) / L.h[d];
+    if (!(u >= -1e-6 && u <= L.n[d] + 1e-6)) return -1;  // outside the bounding box (or NaN)
+    c[d] = std::max(0, std::min(L.n[d] - 1, int(std::floor(u))));
+  }
+  const int64_t cell = (int64_t(c[2]) * L.n[1] + c[1]) * L.n[0] + c[0];
+  for (int64_t i = L.start[cell]; i < L.start[cell + 1]; ++i) {
+    const int64_t k = L.items[i];
     double A[3][3], Ai[3][3], det;
     element_jacobian(m, k, A);
     inv3(A, Ai, det);
     const double* P0 = &m.xyz[3 * m.tet[4 * k]];
     double d[3] = {x[0] - P0[0], x[1] - P0[1], x[2] - P0[2]};
     double r1[3];  // r + 1
-    for (int i = 0; i < 3; ++i) r1[i] = Ai[i][0] * d[0] + Ai[i][1] * d[1] + Ai[i][2] * d[2];
+    for (int q = 0; q < 3; ++q) r1[q] = Ai[q][0] * d[0] + Ai[q][1] * d[1] + Ai[q][2] * d[2];
     double lam[4] = {1.0 - 0.5 * (r1[0] + r1[1] + r1[2]), 0.5 * r1[0], 0.5 * r1[1], 0.5 * r1[2]};
     if (lam[0] >= -1e-12 && lam[1] >= -1e-12 && lam[2] >= -1e-12 && lam[3] >= -1e-12) {
-      for (int i = 0; i < 3; ++i) rst[i] = r1[i] - 1.0;
+      for (int q = 0; q < 3; ++q) rst[q] = r1[q] - 1.0;
       return k;
     }
   }

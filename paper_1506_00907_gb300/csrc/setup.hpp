@@ -105,6 +105,17 @@ struct Ordering {
 Ordering build_ordering(const Levels& lv, int64_t K);
 
 // Point location: lowest element index whose barycentrics are all >= -1e-12; returns -1 if none.
-int64_t locate_point(const MeshData& m, const Geometry& g, const double x[3], double rst[3]);
+// Uniform grid over the mesh's bounding box; each cell lists (in increasing order) the elements
+// whose bounding box, widened by a relative 1e-9, meets the cell.
+struct PointLocator {
+  double lo[3] = {0, 0, 0}, h[3] = {1, 1, 1};
+  int n[3] = {1, 1, 1};
+  std::vector<int64_t> start;  // [cells + 1]
+  std::vector<int64_t> items;  // element ids per cell
+};
+PointLocator build_locator(const MeshData& m);
+// Element containing x (barycentric coordinates >= -1e-12) with the lowest index, and the reference
+// coordinates of x in it; -1 if no element contains x.
+int64_t locate_point(const MeshData& m, const PointLocator& L, const double x[3], double rst[3]);
 
 }  // namespace ridg

@@ -144,6 +144,7 @@ struct Wavelet {
 
 struct ridg_mesh {
   ridg::MeshData m;
+  std::unique_ptr<ridg::PointLocator> loc;  // built on the first ridg_mesh_locate
 };
 
 struct ridg_solver {
@@ -208,6 +209,7 @@ class Engine final : public ridg_solver {
     NFPP_ = Nfp_ <= 16 ? 16 : 32;
     NPa_ = 2 * ((Np_ + 1) / 2);
     geo_ = build_geometry(mesh_);
+    loc_ = build_locator(mesh_);
     c_.assign(c, c + mesh_.K);
     c_ref_ = c_;
     rho_.assign(rho, rho + mesh_.K);
@@ -404,7 +406,7 @@ class Engine final : public ridg_solver {
     const int64_t n_t = n_global + 1;
     stats_.n_global = n_global;
     double rst[3];
-    const int64_t ks = locate_point(mesh_, geo_, src.xyz, rst);
+    const int64_t ks = locate_point(mesh_, loc_, src.xyz, rst);
     if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
     {
       std::vector<int2> range(n_slots_, make_int2(0, 0));
@@ -416,7 +418,7 @@ class Engine final : public ridg_solver {
     std::vector<int64_t> rslot(std::max<int64_t>(nrec, 1), 0);
     std::vector<real> rrow(std::max<int64_t>(nrec, 1) * Np_, real(0));
     for (int64_t r = 0; r < nrec; ++r) {
-      const int64_t kr = locate_point(mesh_, geo_, rec + 3 * r, rst);
+      const int64_t kr = locate_point(mesh_, loc_, rec + 3 * r, rst);
       if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
       rslot[r] = ord_.slot_of[kr];
       std::vector<double> l = ref_.lagrange_at({rst[0], rst[1], rst[2]});
@@ -502,7 +504,7 @@ class Engine final : public ridg_solver {
     adj_.n_ck = (n_global + adj_.seg - 1) / adj_.seg;
     adj_.nrec = nrec;
     double rst[3];
-    const int64_t ks = locate_point(mesh_, geo_, src.xyz, rst);
+    const int64_t ks = locate_point(mesh_, loc_, src.xyz, rst);
     if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
     adj_.src_slot = ord_.slot_of[ks];
     const std::vector<real> w_src = projected_dirac(ks, rst);
@@ -517,7 +519,7 @@ class Engine final : public ridg_solver {
     std::vector<int64_t> rslot(nrec, 0);
     std::vector<real> rrow(nrec * Np_, real(0));
     for (int64_t r = 0; r < nrec; ++r) {
-      const int64_t kr = locate_point(mesh_, geo_, rec + 3 * r, rst);
+      const int64_t kr = locate_point(mesh_, loc_, rec + 3 * r, rst);
       if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
       rslot[r] = ord_.slot_of[kr];
       std::vector<double> l = ref_.lagrange_at({rst[0], rst[1], rst[2]});
@@ -684,7 +686,7 @@ class Engine final : public ridg_solver {
     stats_.n_global = n_global;
     // ---- source and receivers
     double rst[3];
-    int64_t ks = locate_point(mesh_, geo_, src.xyz, rst);
+    int64_t ks = locate_point(mesh_, loc_, src.xyz, rst);
     if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
     std::vector<real> w_src = projected_dirac(ks, rst);
     const Wavelet wav = Wavelet::of(src);
@@ -695,7 +697,7 @@ class Engine final : public ridg_solver {
     };
     std::vector<Rec> recs(nrec);
     for (int64_t r = 0; r < nrec; ++r) {
-      int64_t kr = locate_point(mesh_, geo_, rec + 3 * r, rst);
+      int64_t kr = locate_point(mesh_, loc_, rec + 3 * r, rst);
       if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
       recs[r].slot = ord_.slot_of[kr];
       std::array<double, 3> p = {rst[0], rst[1], rst[2]};
@@ -1322,6 +1324,7 @@ class Engine final : public ridg_solver {
   cudaStream_t st_;
   RefElem ref_;
   Geometry geo_;
+  PointLocator loc_;
   Levels lv_;
   Ordering ord_;
   std::vector<double> c_, c_ref_, rho_, xnodes_;
@@ -1618,6 +1621,20 @@ int ridg_mesh_counts(const ridg_mesh* mesh, int64_t* nb, int64_t* ni) {
     if (!mesh) throw Error{RIDG_E_INVALID_ARG, "mesh is null"};
     if (nb) *nb = mesh->m.n_boundary;
     if (ni) *ni = mesh->m.n_interior;
+  });
+}
+
+int ridg_mesh_locate(ridg_mesh* mesh, const double* xyz, int64_t n, int64_t* elem_out, double* rst_out) {
+  return guarded([&] {
+    if (!mesh || (n > 0 && (!xyz || !elem_out))) throw Error{RIDG_E_INVALID_ARG, "null argument"};
+    if (n < 0) throw Error{RIDG_E_INVALID_ARG, "n must be >= 0"};
+    if (!mesh->loc) mesh->loc = std::make_unique<ridg::PointLocator>(ridg::build_locator(mesh->m));
+    for (int64_t i = 0; i < n; ++i) {
+      double rst[3] = {0, 0, 0};
+      elem_out[i] = ridg::locate_point(mesh->m, *mesh->loc, xyz + 3 * i, rst);
+      if (rst_out)
+        for (int d = 0; d < 3; ++d) rst_out[3 * i + d] = rst[d];
+    }
   });
 }
 

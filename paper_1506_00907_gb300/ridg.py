@@ -29,7 +29,7 @@ EXPORTED = [
     "ridg_get_state", "ridg_energy", "ridg_trace_len", "ridg_rtm_shot", "ridg_rtm_shot_device",
     "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc", "ridg_server_create", "ridg_server_create_slots", "ridg_server_submit",
     "ridg_server_wait", "ridg_server_destroy", "ridg_forward", "ridg_set_state_device", "ridg_get_state_device",
-    "ridg_set_velocity", "ridg_eval_adjoint_rhs", "ridg_misfit_forward", "ridg_misfit_backward",
+    "ridg_set_velocity", "ridg_eval_adjoint_rhs", "ridg_misfit_forward", "ridg_misfit_backward", "ridg_mesh_locate",
 ]
 
 
@@ -124,6 +124,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_set_state_device": (C.c_int, [P, P]),
         "ridg_get_state_device": (C.c_int, [P, P]),
         "ridg_set_velocity": (C.c_int, [P, P]),
+        "ridg_mesh_locate": (C.c_int, [P, P, C.c_int64, P, P]),
         "ridg_eval_adjoint_rhs": (C.c_int, [P, P, P]),
         "ridg_misfit_forward": (C.c_int, [P, P, P, C.c_int64, C.c_double, P, C.c_int32, P, P]),
         "ridg_misfit_backward": (C.c_int, [P, P]),
@@ -197,6 +198,14 @@ class Mesh:
         nb, ni = C.c_int64(), C.c_int64()
         _check(lib().ridg_mesh_counts(self._h, C.byref(nb), C.byref(ni)))
         return nb.value, ni.value
+
+    def locate(self, xyz):
+        """(element [n], reference coordinates [n, 3]) of the points xyz [n, 3]; element -1 outside."""
+        x = _f64(np.atleast_2d(xyz))
+        elem = np.zeros(x.shape[0], dtype=np.int64)
+        rst = np.zeros((x.shape[0], 3))
+        _check(lib().ridg_mesh_locate(self._h, _ptr(x), x.shape[0], _ptr(elem), _ptr(rst)))
+        return elem, rst
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -73,3 +73,34 @@ def test_layered_mesh_boundary_faces():
     m = ridg.Mesh(w.xyz, w.tets, default_bc=2)
     nb, ni = m.counts()
     assert nb > 0 and 2 * ni + nb == 4 * w.K
+
+
+def test_point_location_matches_the_oracle():
+    """Host point location (grid index) against the oracle's brute-force rule: the lowest element
+    index whose barycentric coordinates are all >= -1e-12, and the reference coordinates in it; at
+    random points, at mesh vertices, edge midpoints and face centroids (points on several elements)
+    and outside the mesh."""
+    from oracle.mesh_geometry import MeshGeometry
+    from oracle.reference_element import reference_element
+
+    w = tiny_layered_rtm(N=1)
+    m = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    g = MeshGeometry(w.xyz, w.tets, reference_element(1), default_bc=w.default_bc)
+    rng = np.random.default_rng(7)
+    lo, hi = w.xyz.min(axis=0), w.xyz.max(axis=0)
+    pts = [lo + (hi - lo) * rng.uniform(size=3) for _ in range(60)]
+    tets = w.tets[rng.choice(len(w.tets), 20, replace=False)]
+    for t in tets:
+        v = w.xyz[t]
+        pts += [v[0], 0.5 * (v[0] + v[1]), v[:3].mean(axis=0)]
+    pts += [hi + 1.0, lo - np.array([0.0, 0.0, 5.0]), np.array([np.nan, 0.0, 0.0])]
+    pts = np.array(pts)
+    elem, rst = m.locate(pts)
+    for x, k, r in zip(pts, elem, rst):
+        if not np.all(np.isfinite(x)):
+            assert k == -1
+            continue
+        k_ref, r_ref = g.locate(x)
+        assert k == k_ref
+        if k >= 0:
+            assert np.allclose(r, r_ref, atol=1e-10)
