@@ -346,7 +346,12 @@ def run_ridg(args):
         return e0.elapsed_time(e1) / 1e3, wall, launches, clocks
 
     sec, wall, launches, clocks = timed_region()
-    if _rejected(clocks):
+    redo = _rejected(clocks)
+    if dist is not None:  # every rank takes the same decision (the timed region holds a barrier)
+        flag = torch.tensor([1.0 if redo else 0.0], dtype=torch.float64, device=dev)
+        dist.all_reduce(flag, op=dist.ReduceOp.MAX)
+        redo = bool(flag.item() > 0)
+    if redo:
         sec, wall, launches, clocks = timed_region()
     stats = s.shot_stats()
     dof_shot = stats.dof_updates_forward + stats.dof_updates_backward
@@ -381,6 +386,10 @@ def run_ridg(args):
     tr_h, ip_h, iq_h = s.rtm_shot(src_x, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start,
                                   observed=obs_host)
     e2e_sec = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_sec], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_sec = float(t.item())
     e2e = {"value": world * dof_shot / e2e_sec, "unit": UNIT, "h2d_bytes_per_step": int(obs_host.nbytes),
            "d2h_bytes_per_step": int(tr_h.nbytes + ip_h.nbytes + iq_h.nbytes), "shots_per_s": world / e2e_sec}
 
