@@ -21,7 +21,12 @@ Galerkin simulations for reverse-time migration on GPU clusters"):
   the classical (Eq. imageP) and characteristic (Eqs. imageQ, charact) conditions.
 * ``rtm`` -- one RTM shot: forward run with boundary-trace recording, backward
   source re-simulation with replay, backward receiver run, image accumulation
-  (Sec. 2, Sec. 4.3).
+  (Sec. 2, Sec. 4.3); forward modelling alone.
+* ``wavelet`` -- the Ricker pulse, sampled source signals and the cubic interpolation of
+  receiver data in time.
+* ``adjoint`` -- the least-squares trace misfit and its gradient with respect to the
+  per-element velocity (discrete adjoint of the single-rate scheme; the operator is
+  assembled from ``dg_rhs`` and transposed as a sparse matrix).
 
 Every function is FP64 and follows the paper's steps in the paper's order; matrix
 products from numpy serve as single steps.  Readings of places where the paper is
