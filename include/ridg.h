@@ -285,7 +285,9 @@ int ridg_misfit_forward(ridg_solver* s, const ridg_source* src, const double* re
  *   lambda^m = lambda^{m+1} + Dt A^T sum_s a_s lambda^{m+1+s} - Dt sum_r (y_r^m - d_r^m) l(x_r),
  * run backward from m = n_t-1, recomputing the forward states segment by segment from the
  * checkpoints, with dJ/dc_k = -(2/c_k) sum_n lambda^{n+1}_p,k . (A (q^{n+1} - q^n source-free))_p,k.
- * RIDG_E_INVALID_ARG without a valid forward run (none yet, or the velocity changed since). */
+ * Leaves the solver's fields at the first checkpoint's segment (set the state again before stepping).
+ * May be called again for the same forward run.  RIDG_E_INVALID_ARG without a valid forward run
+ * (none yet, or the velocity changed since). */
 int ridg_misfit_backward(ridg_solver* s, double* grad);
 
 /* ------------------------------------------------------------------ shot server
