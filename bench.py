@@ -592,20 +592,32 @@ def serving_stream(n_req, t_rec=0.01, sizes=("50k", "200k", "800k"), slot_counts
     return 0
 
 
-def gradient_bench(dtype="f64", n_checkpoints=16):
-    """Misfit gradient on the 648-element adjoint box (N = 3, one rate level, 0.5 s record, 25
-    receivers, observed data from a model with a 5 % Gaussian velocity bump): time of the forward
-    run with checkpoints and of the adjoint sweep.  One JSON line."""
+def gradient_bench(dtype="f64", n_checkpoints=16, model="box"):
+    """Misfit gradient: on the 648-element adjoint box (N = 3, one rate level, 0.5 s record, 25
+    receivers, observed data from a model with a 5 % Gaussian velocity bump), or with ``model ==
+    "bench"`` on the bench mesh (190,608 elements, N = 4, FP32, one rate level, 0.005 s record, 201
+    receivers, observed data zero): time of the forward run with checkpoints and of the adjoint
+    sweep.  One JSON line."""
     from paper_1506_00907_gb300 import ridg
     from synth import adjoint_box, adjoint_observed_velocity
 
-    w = adjoint_box()
+    if model == "bench":
+        w = _workload()
+        dtype, t_final = "f32", 0.005
+    else:
+        w = adjoint_box()
+        t_final = w.t_final
+    w.t_final = t_final
     mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
     s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=1)
     n_t = s.trace_len(w.t_final)
-    s.set_velocity(adjoint_observed_velocity(w))
-    _, obs = s.misfit_forward(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, np.zeros((25, n_t)))
-    s.set_velocity(w.c)
+    nrec = len(w.receivers)
+    if model == "bench":
+        obs = np.zeros((nrec, n_t))
+    else:
+        s.set_velocity(adjoint_observed_velocity(w))
+        _, obs = s.misfit_forward(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, np.zeros((nrec, n_t)))
+        s.set_velocity(w.c)
     times = []
     for _ in range(3):
         t0 = time.perf_counter()
@@ -615,7 +627,9 @@ def gradient_bench(dtype="f64", n_checkpoints=16):
         t2 = time.perf_counter()
         times.append((t1 - t0, t2 - t1))
     fw, bw = min(t[0] for t in times), min(t[1] for t in times)
-    print(json.dumps({"workload": "adjoint box: 648 tets, N=3, one level, 0.5 s record, 25 receivers",
+    label = ("bench mesh: 190608 tets, N=4, FP32, one level, 0.005 s record, 201 receivers" if model == "bench"
+             else "adjoint box: 648 tets, N=3, one level, 0.5 s record, 25 receivers")
+    print(json.dumps({"workload": label, "elements": int(w.K),
                       "dtype": dtype, "steps": n_t - 1, "checkpoints": n_checkpoints, "misfit": J,
                       "grad_norm": float(np.linalg.norm(g)), "forward_s": fw, "backward_s": bw,
                       "gradient_s": fw + bw, "forward_us_per_step": 1e6 * fw / (n_t - 1),
@@ -650,13 +664,14 @@ def main():
     ap.add_argument("--serving-sizes", default="50k,200k,800k", help="serving models (subset of 50k,200k,800k)")
     ap.add_argument("--serving-slots", default="1,2", help="slots per model to compare")
     ap.add_argument("--serving-contraction", default="tf32", choices=["tf32", "bf16"])
-    ap.add_argument("--gradient", action="store_true", help="time the misfit gradient on the adjoint box and exit")
+    ap.add_argument("--gradient", default="", nargs="?", const="box", choices=["", "box", "bench"],
+                    help="time the misfit gradient (on the adjoint box, or on the bench mesh) and exit")
     args = ap.parse_args()
     if args.gradient:
         from paper_1506_00907_gb300.build import build
 
         build()
-        return gradient_bench()
+        return gradient_bench(model=args.gradient)
     if args.serving_stream > 0:
         from paper_1506_00907_gb300.build import build
 

@@ -7,14 +7,15 @@
 // with alpha_f = -Fs_f rho c^2 / 2, beta_f = -Fs_f / (2 rho), jp = p+ - p-, jv = vn+ - vn-.
 // Its transpose applied to lambda, element by element:
 //   volume:  (A^T l)_v_i = -rho c^2 sum_j g_ij D_j^T l_p,  (A^T l)_p = -(1/rho) sum_ij g_ij D_j^T l_v_i
-//   faces:   adjoint traces at = alpha_f L_f^T l_p, bt = beta_f L_f^T (n_f . l_v) (adj_traces_kernel);
+//   faces:   adjoint traces at = alpha_f L_f^T l_p, bt = beta_f L_f^T (n_f . l_v) (adj_traces_kernel,
+//            which also pushes them into the neighbour's inbox);
 //            the flux depends on jp with weight (-tau_p at + bt) and on jv with weight (at - tau_v bt),
 //            so the interior traces (p-, vn-) of the element receive minus these weights and, through
 //            jp, jv of the neighbour's flux, the neighbour's weights (its vn+ is minus this element's
 //            n.v); boundary ghosts fold p+ and vn+ into p- and vn- (free: jp = -2p-, jv = 0;
 //            transparent: jp = -p-, jv = -vn-; rigid: jp = 0, jv = -2vn-).
 // Layouts are the solver's: fields [K/32][4][Np][32] in the device node numbering, adjoint traces
-// [slot][4 faces][2][NFPP].
+// and inboxes [slot][4 faces][2][NFPP].
 #pragma once
 #include <cuda_runtime.h>
 
@@ -22,98 +23,167 @@
 
 namespace ridg {
 
+// One block per 32 element slots (one column block of the field layout).  The block's lambda tile
+// is staged in shared memory, [4][Np][32]: thread (row, column c) reads row entries of consecutive
+// columns (no bank conflicts), and the operator rows it multiplies by are the same for the whole
+// warp (broadcast loads).
 template <int N, typename real>
-__global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict__ adjt, int64_t n_slots,
-                                  const double* __restrict__ geo, const real* __restrict__ mat,
-                                  const int* __restrict__ meta, const real* __restrict__ Lt, int NPa) {
+__device__ __forceinline__ void load_lambda_tile(const real* __restrict__ lam, real* sL, int64_t blk) {
   using O = Order<N>;
-  constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n_slots * 4 * Nfp) return;
-  const int64_t s = i / (4 * Nfp);
-  const int r = int(i - s * 4 * Nfp);
-  const int f = r / Nfp, j = r - f * Nfp;
-  real* out = adjt + s * (8 * NFPP) + f * 2 * NFPP;
-  if (!(meta[s] & kMetaValid)) {
-    out[j] = real(0);
-    out[NFPP + j] = real(0);
-    return;
-  }
-  const int64_t blk = s >> 5;
-  const int lane = int(s & 31);
-  const double* g = geo + s * kGeo;
-  const real* m = mat + s * kMat;
-  const double nx = g[9 + 3 * f], ny = g[10 + 3 * f], nz = g[11 + 3 * f], fs = g[21 + f];
-  const real* row = Lt + int64_t(f * Nfp + j) * NPa;
-  auto at = [&](int fld, int n) { return lam[((blk * 4 + fld) * Np + n) * 32 + lane]; };
-  real ap = 0, av = 0;
-  for (int n = 0; n < Np; ++n) {
-    const real l = row[n];
-    ap += l * at(0, n);
-    av += l * (real(nx) * at(1, n) + real(ny) * at(2, n) + real(nz) * at(3, n));
-  }
-  out[j] = real(-0.5 * fs) * m[0] * ap;
-  out[NFPP + j] = real(-0.5 * fs) * m[1] * av;
+  constexpr int Np = O::Np;
+  const real* src = lam + blk * 4 * Np * 32;
+  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) sL[i] = src[i];
 }
 
+// Adjoint traces of every face of the block's elements (at = alpha_f L_f^T l_p, bt = beta_f L_f^T
+// (n_f . l_v)), written to the element's own rows and, for interior faces, pushed into the
+// neighbour's inbox at the neighbour's face-node index of each node (the correspondence codes of
+// the two sides are mutually inverse).
 template <int N, typename real>
-__global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restrict__ adjt, real* __restrict__ out,
-                               int64_t n_slots, const double* __restrict__ geo, const real* __restrict__ mat,
-                               const int* __restrict__ meta, const real* __restrict__ Dt, int NPa,
-                               const int* __restrict__ fmask, const int* __restrict__ nbr,
-                               const uint8_t* __restrict__ finfo, const int* __restrict__ perm) {
+__global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict__ own, real* __restrict__ inbox,
+                                  int64_t n_slots, const double* __restrict__ geo, const real* __restrict__ mat,
+                                  const int* __restrict__ meta, const real* __restrict__ Lt, int NPa,
+                                  const int* __restrict__ nbr, const uint8_t* __restrict__ finfo,
+                                  const int* __restrict__ perm) {
   using O = Order<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n_slots * Np) return;
-  const int64_t s = i / Np;
-  const int mnode = int(i - s * Np);
-  const int64_t blk = s >> 5;
-  const int lane = int(s & 31);
-  auto idx = [&](int fld) { return ((blk * 4 + fld) * Np + mnode) * 32 + lane; };
-  if (!(meta[s] & kMetaValid)) {
-    for (int fld = 0; fld < 4; ++fld) out[idx(fld)] = real(0);
-    return;
+  extern __shared__ __align__(16) unsigned char smem_adj[];
+  real* sL = reinterpret_cast<real*>(smem_adj);  // [4][Np][32]
+  real* sV = sL + 4 * Np * 32;                   // [4 faces][Np][32]: n_f . lambda_v
+  const int64_t blk = blockIdx.x;
+  load_lambda_tile<N, real>(lam, sL, blk);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) {
+    const int f = i / (Np * 32), r = i - f * (Np * 32), n = r >> 5, c = r & 31;
+    const double* g = geo + (blk * 32 + c) * kGeo + 9 + 3 * f;
+    sV[i] = real(g[0]) * sL[(1 * Np + n) * 32 + c] + real(g[1]) * sL[(2 * Np + n) * 32 + c] +
+            real(g[2]) * sL[(3 * Np + n) * 32 + c];
   }
-  auto at = [&](int fld, int n) { return lam[((blk * 4 + fld) * Np + n) * 32 + lane]; };
-  const double* g = geo + s * kGeo;
-  const real* m = mat + s * kMat;
-  // D_j^T applied to lambda_p and to each lambda_v_i at node mnode
-  real dp[3] = {0, 0, 0}, dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-  for (int j = 0; j < 3; ++j) {
-    const real* row = Dt + int64_t(j * Np + mnode) * NPa;
+  __syncthreads();
+  // half-warp per (face, column) item, lanes over the face's nodes: the element's own rows and the
+  // neighbour's inbox row are written as one 64-byte segment each
+  constexpr int NJ = (Nfp + 15) / 16;
+  const int hw = threadIdx.x >> 4, lane16 = threadIdx.x & 15, nhw = blockDim.x >> 4;
+  for (int item = hw; item < 4 * 32; item += nhw) {
+    const int f = item >> 5, c = item & 31;
+    const int64_t s = blk * 32 + c;
+    real* out = own + s * (8 * NFPP) + f * 2 * NFPP;
+    const bool valid = (meta[s] & kMetaValid) != 0;
+    const double* g = geo + s * kGeo;
+    const real* m = mat + s * kMat;
+    const uint8_t info = finfo[s * 4 + f];
+    const real* vf = sV + f * Np * 32;
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) {
+      const int j = lane16 + 16 * t;
+      if (j >= Nfp) continue;
+      if (!valid) {
+        out[j] = real(0);
+        out[NFPP + j] = real(0);
+        continue;
+      }
+      const real* row = Lt + int64_t(f * Nfp + j) * NPa;
+      real ap = 0, av = 0;
+#pragma unroll 4
+      for (int n = 0; n < Np; ++n) {
+        const real l = row[n];
+        ap += l * sL[(0 * Np + n) * 32 + c];
+        av += l * vf[n * 32 + c];
+      }
+      const real a = real(-0.5 * g[21 + f]) * m[0] * ap, b = real(-0.5 * g[21 + f]) * m[1] * av;
+      out[j] = a;
+      out[NFPP + j] = b;
+      if (finfo_bc(info) == 0) {
+        const int64_t s2 = nbr[s * 4 + f];
+        const int j2 = perm[finfo_perm(info) * 32 + j];
+        real* x = inbox + s2 * (8 * NFPP) + finfo_face(info) * 2 * NFPP;
+        x[j2] = a;
+        x[NFPP + j2] = b;
+      }
+    }
+  }
+}
+
+// A^T lambda for the block's elements: the transposed volume terms (D_j^T rows, broadcast over the
+// warp) and, at each face node, the weights of the jumps from the element's own adjoint traces and
+// from the neighbour's (its inbox), with the boundary ghosts folded in.
+template <int N, typename real>
+__global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restrict__ own,
+                               const real* __restrict__ inbox, real* __restrict__ out, int64_t n_slots,
+                               const double* __restrict__ geo, const real* __restrict__ mat,
+                               const int* __restrict__ meta, const real* __restrict__ Dt, int NPa,
+                               const int* __restrict__ fmask, const uint8_t* __restrict__ finfo) {
+  using O = Order<N>;
+  constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
+  constexpr int OS = 8 * NFPP + 1;  // trace rows of one slot, padded: column-wise reads hit distinct banks
+  extern __shared__ __align__(16) unsigned char smem_adj[];
+  real* sL = reinterpret_cast<real*>(smem_adj);  // [4][Np][32]
+  real* sOwn = sL + 4 * Np * 32;                 // [32][OS]
+  real* sIn = sOwn + 32 * OS;                    // [32][OS]
+  int* sInv = reinterpret_cast<int*>(sIn + 32 * OS);  // [Np][3]: f * 32 + jf of the faces holding node m
+  const int64_t blk = blockIdx.x;
+  load_lambda_tile<N, real>(lam, sL, blk);
+  for (int i = threadIdx.x; i < 32 * 8 * NFPP; i += blockDim.x) {
+    const int c = i / (8 * NFPP), r = i - c * (8 * NFPP);
+    sOwn[c * OS + r] = own[(blk * 32) * (8 * NFPP) + i];
+    sIn[c * OS + r] = inbox[(blk * 32) * (8 * NFPP) + i];
+  }
+  for (int m = threadIdx.x; m < Np; m += blockDim.x) {
+    int cnt = 0;
+    for (int f = 0; f < 4; ++f)
+      for (int jf = 0; jf < Nfp; ++jf)
+        if (fmask[f * 32 + jf] == m && cnt < 3) sInv[m * 3 + cnt++] = f * 32 + jf;
+    for (; cnt < 3; ++cnt) sInv[m * 3 + cnt] = -1;
+  }
+  __syncthreads();
+  for (int item = threadIdx.x; item < Np * 32; item += blockDim.x) {
+    const int mnode = item >> 5, c = item & 31;  // warp: one node row of 32 columns
+    const int64_t s = blk * 32 + c;
+    auto idx = [&](int fld) { return ((blk * 4 + fld) * Np + mnode) * 32 + c; };
+    if (!(meta[s] & kMetaValid)) {
+      for (int fld = 0; fld < 4; ++fld) out[idx(fld)] = real(0);
+      continue;
+    }
+    const double* g = geo + s * kGeo;
+    const real* m = mat + s * kMat;
+    real dp[3] = {0, 0, 0}, dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const real* r0 = Dt + int64_t(0 * Np + mnode) * NPa;
+    const real* r1 = Dt + int64_t(1 * Np + mnode) * NPa;
+    const real* r2 = Dt + int64_t(2 * Np + mnode) * NPa;
+#pragma unroll 4
     for (int n = 0; n < Np; ++n) {
-      const real d = row[n];
-      dp[j] += d * at(0, n);
-      for (int c = 0; c < 3; ++c) dv[c][j] += d * at(1 + c, n);
+      const real d[3] = {r0[n], r1[n], r2[n]};
+      const real lp = sL[(0 * Np + n) * 32 + c];
+      const real lv[3] = {sL[(1 * Np + n) * 32 + c], sL[(2 * Np + n) * 32 + c], sL[(3 * Np + n) * 32 + c]};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dp[j] += d[j] * lp;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dv[i][j] += d[j] * lv[i];
+      }
     }
-  }
-  real op = 0, ov[3] = {0, 0, 0};
-  for (int c = 0; c < 3; ++c)
-    for (int j = 0; j < 3; ++j) {
-      const real gij = real(g[3 * c + j]);
-      op -= m[1] * gij * dv[c][j];
-      ov[c] -= m[0] * gij * dp[j];
-    }
-  // faces that hold this node
-  for (int f = 0; f < 4; ++f) {
-    for (int jf = 0; jf < Nfp; ++jf) {
-      if (fmask[f * 32 + jf] != mnode) continue;
-      const real* t = adjt + s * (8 * NFPP) + f * 2 * NFPP;
-      const real a = t[jf], b = t[NFPP + jf];
+    real op = 0, ov[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const real gij = real(g[3 * i + j]);
+        op -= m[1] * gij * dv[i][j];
+        ov[i] -= m[0] * gij * dp[j];
+      }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int e = sInv[mnode * 3 + k];
+      if (e < 0) break;
+      const int f = e >> 5, jf = e & 31;
+      const real a = sOwn[c * OS + f * 2 * NFPP + jf], b = sOwn[c * OS + f * 2 * NFPP + NFPP + jf];
       const real taup = m[3 + f], tauv = m[7 + f];
-      const uint8_t info = finfo[s * 4 + f];
-      const int bc = finfo_bc(info);
+      const int bc = finfo_bc(finfo[s * 4 + f]);
       real sp = 0, sv = 0;
       if (bc == 0) {
-        sp = taup * a - b;
-        sv = tauv * b - a;
-        const int64_t s2 = nbr[s * 4 + f];
-        const int j2 = perm[finfo_perm(info) * 32 + jf];
-        const real* t2 = adjt + s2 * (8 * NFPP) + finfo_face(info) * 2 * NFPP;
-        const real a2 = t2[j2], b2 = t2[NFPP + j2];
-        sp += b2 - taup * a2;
-        sv += tauv * b2 - a2;
+        const real a2 = sIn[c * OS + f * 2 * NFPP + jf], b2 = sIn[c * OS + f * 2 * NFPP + NFPP + jf];
+        sp = taup * a - b + b2 - taup * a2;
+        sv = tauv * b - a + tauv * b2 - a2;
       } else if (bc == 1) {  // free surface
         sp = real(2) * (taup * a - b);
       } else if (bc == 2) {  // transparent
@@ -123,11 +193,24 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
         sv = real(2) * (tauv * b - a);
       }
       op += sp;
-      for (int c = 0; c < 3; ++c) ov[c] += real(g[9 + 3 * f + c]) * sv;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ov[i] += real(g[9 + 3 * f + i]) * sv;
     }
+    out[idx(0)] = op;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) out[idx(1 + i)] = ov[i];
   }
-  out[idx(0)] = op;
-  for (int c = 0; c < 3; ++c) out[idx(1 + c)] = ov[c];
+}
+
+// shared memory of the two kernels
+template <int N, typename real>
+constexpr size_t adj_traces_smem() {
+  return size_t(8) * Order<N>::Np * 32 * sizeof(real);
+}
+template <int N, typename real>
+constexpr size_t adj_rhs_smem() {
+  return size_t(4) * Order<N>::Np * 32 * sizeof(real) + size_t(2) * 32 * (8 * Order<N>::NFPP + 1) * sizeof(real) +
+         size_t(Order<N>::Np) * 3 * sizeof(int);
 }
 
 // lambda += h (a1 s0 + a2 s1 + a3 s2), elementwise over the whole field array
@@ -139,39 +222,43 @@ __global__ void adj_update_kernel(real* __restrict__ lam, const real* __restrict
   lam[i] += real(h) * (real(AB::a1) * s0[i] + real(AB::a2) * s1[i] + real(AB::a3) * s2[i]);
 }
 
-// lambda_p -= coef res_r(col) l(x_r) for every receiver (receivers taken in order: deterministic)
+// lambda_p -= coef res_r(col) l(x_r): block g handles the receivers rec_sorted[grp[g] .. grp[g+1])
+// (all in one element slot), taken in order, threads over the nodes: deterministic
 template <int N, typename real>
-__global__ void adj_inject_kernel(real* __restrict__ lam, const int64_t* __restrict__ rec_slot,
-                                  const real* __restrict__ rec_row, int nrec, const double* __restrict__ res,
-                                  int64_t n_time, int64_t col, double coef) {
+__global__ void adj_inject_kernel(real* __restrict__ lam, const int* __restrict__ grp, const int* __restrict__ rec_sorted,
+                                  const int64_t* __restrict__ rec_slot, const real* __restrict__ rec_row,
+                                  const double* __restrict__ res, int64_t n_time, int64_t col, double coef) {
   using O = Order<N>;
   constexpr int Np = O::Np;
-  for (int n = threadIdx.x; n < Np; n += blockDim.x)
-    for (int r = 0; r < nrec; ++r) {
-      const int64_t s = rec_slot[r];
-      const int64_t at = ((s >> 5) * 4 * Np + n) * 32 + (s & 31);
-      lam[at] -= real(coef * res[int64_t(r) * n_time + col]) * rec_row[int64_t(r) * Np + n];
+  const int g0 = grp[blockIdx.x], g1 = grp[blockIdx.x + 1];
+  const int64_t s = rec_slot[rec_sorted[g0]];
+  for (int n = threadIdx.x; n < Np; n += blockDim.x) {
+    const int64_t at = ((s >> 5) * 4 * Np + n) * 32 + (s & 31);
+    real v = lam[at];
+    for (int i = g0; i < g1; ++i) {
+      const int r = rec_sorted[i];
+      v -= real(coef * res[int64_t(r) * n_time + col]) * rec_row[int64_t(r) * Np + n];
     }
+    lam[at] = v;
+  }
 }
 
-// acc[s] += sum_m lambda_p[m] (q1_p[m] - q0_p[m] - F w[m]) (w on the source slot only)
+// acc[node] += lambda_p (q1_p - q0_p - F w) for every pressure node (acc laid out like the pressure
+// field, [n_slots/32][Np][32]; w on the source slot only); the per-element sums are taken at the end
 template <int N, typename real>
 __global__ void adj_grad_kernel(const real* __restrict__ lam, const real* __restrict__ q1, const real* __restrict__ q0,
-                                int64_t n_slots, const int* __restrict__ meta, int64_t src_slot,
-                                const real* __restrict__ w_src, double F, double* __restrict__ acc) {
+                                int64_t n_slots, int64_t src_slot, const real* __restrict__ w_src, double F,
+                                double* __restrict__ acc) {
   using O = Order<N>;
   constexpr int Np = O::Np;
-  const int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (s >= n_slots || !(meta[s] & kMetaValid)) return;
-  const int64_t base = (s >> 5) * 4 * Np * 32 + (s & 31);
-  double sum = 0.0;
-  for (int m = 0; m < Np; ++m) {
-    const int64_t at = base + int64_t(m) * 32;
-    double dq = double(q1[at]) - double(q0[at]);
-    if (s == src_slot) dq -= F * double(w_src[m]);
-    sum += double(lam[at]) * dq;
-  }
-  acc[s] += sum;
+  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // (block, node, lane)
+  if (i >= n_slots * Np) return;
+  const int64_t blk = i / (Np * 32);
+  const int r = int(i - blk * Np * 32), m = r >> 5, lane = r & 31;
+  const int64_t at = (blk * 4 * Np + m) * 32 + lane;  // pressure row of the field layout
+  double dq = double(q1[at]) - double(q0[at]);
+  if (blk * 32 + lane == src_slot) dq -= F * double(w_src[m]);
+  acc[i] += double(lam[at]) * dq;
 }
 
 }  // namespace ridg

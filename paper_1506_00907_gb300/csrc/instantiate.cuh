@@ -91,15 +91,25 @@ cudaError_t Launch<N, real>::state_io(bool to_slots, const double* q_abi_in, dou
 }
 
 template <int N, typename real>
-cudaError_t Launch<N, real>::adj_rhs(const real* lam, real* adjt, real* out, int64_t n_slots, const double* geo,
-                                     const real* mat, const int* meta, const real* Dt, const real* Lt, int NPa,
-                                     const int* fmask, const int* nbr, const uint8_t* finfo, const int* perm,
-                                     cudaStream_t st) {
-  const int64_t nt = n_slots * 4 * Order<N>::Nfp, nn = n_slots * Order<N>::Np;
-  if (nn <= 0) return cudaSuccess;
-  adj_traces_kernel<N, real><<<unsigned((nt + 127) / 128), 128, 0, st>>>(lam, adjt, n_slots, geo, mat, meta, Lt, NPa);
-  adj_rhs_kernel<N, real><<<unsigned((nn + 127) / 128), 128, 0, st>>>(lam, adjt, out, n_slots, geo, mat, meta, Dt, NPa,
-                                                                       fmask, nbr, finfo, perm);
+cudaError_t Launch<N, real>::adj_rhs(const real* lam, real* own, real* inbox, real* out, int64_t n_slots,
+                                     const double* geo, const real* mat, const int* meta, const real* Dt,
+                                     const real* Lt, int NPa, const int* fmask, const int* nbr, const uint8_t* finfo,
+                                     const int* perm, cudaStream_t st) {
+  const int64_t blocks = n_slots / 32;
+  if (blocks <= 0) return cudaSuccess;
+  constexpr size_t sm_t = adj_traces_smem<N, real>(), sm_r = adj_rhs_smem<N, real>();
+  static const cudaError_t configured = [] {
+    cudaError_t e =
+        cudaFuncSetAttribute(adj_traces_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_t));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(adj_rhs_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_r));
+    return e;
+  }();
+  if (configured != cudaSuccess) return configured;
+  adj_traces_kernel<N, real><<<unsigned(blocks), 256, sm_t, st>>>(lam, own, inbox, n_slots, geo, mat, meta, Lt, NPa,
+                                                                   nbr, finfo, perm);
+  adj_rhs_kernel<N, real><<<unsigned(blocks), 256, sm_r, st>>>(lam, own, inbox, out, n_slots, geo, mat, meta, Dt, NPa,
+                                                                fmask, finfo);
   return cudaGetLastError();
 }
 
@@ -112,20 +122,21 @@ cudaError_t Launch<N, real>::adj_update(real* lam, const real* s0, const real* s
 }
 
 template <int N, typename real>
-cudaError_t Launch<N, real>::adj_inject(real* lam, const int64_t* rec_slot, const real* rec_row, int nrec,
-                                        const double* res, int64_t n_time, int64_t col, double coef, cudaStream_t st) {
-  if (nrec <= 0) return cudaSuccess;
-  adj_inject_kernel<N, real><<<1, 128, 0, st>>>(lam, rec_slot, rec_row, nrec, res, n_time, col, coef);
+cudaError_t Launch<N, real>::adj_inject(real* lam, const int* grp, const int* rec_sorted, int n_groups,
+                                        const int64_t* rec_slot, const real* rec_row, const double* res,
+                                        int64_t n_time, int64_t col, double coef, cudaStream_t st) {
+  if (n_groups <= 0) return cudaSuccess;
+  adj_inject_kernel<N, real><<<unsigned(n_groups), 64, 0, st>>>(lam, grp, rec_sorted, rec_slot, rec_row, res, n_time,
+                                                                 col, coef);
   return cudaGetLastError();
 }
 
 template <int N, typename real>
 cudaError_t Launch<N, real>::adj_grad(const real* lam, const real* q1, const real* q0, int64_t n_slots,
-                                      const int* meta, int64_t src_slot, const real* w_src, double F, double* acc,
-                                      cudaStream_t st) {
-  if (n_slots <= 0) return cudaSuccess;
-  adj_grad_kernel<N, real><<<unsigned((n_slots + 127) / 128), 128, 0, st>>>(lam, q1, q0, n_slots, meta, src_slot,
-                                                                           w_src, F, acc);
+                                      int64_t src_slot, const real* w_src, double F, double* acc, cudaStream_t st) {
+  const int64_t n = n_slots * Order<N>::Np;
+  if (n <= 0) return cudaSuccess;
+  adj_grad_kernel<N, real><<<unsigned((n + 255) / 256), 256, 0, st>>>(lam, q1, q0, n_slots, src_slot, w_src, F, acc);
   return cudaGetLastError();
 }
 

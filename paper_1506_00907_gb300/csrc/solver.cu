@@ -455,10 +455,11 @@ class Engine final : public ridg_solver {
     RIDG_CUDA(cudaStreamSynchronize(st_));
   }
 
+  // out = A^T lam; adjt: scratch for the adjoint traces and their inboxes (2 trace slots)
   void adjoint_rhs_into(const real* lam, real* out, real* adjt) {
     cudaError_t e = dispatch_order(N_, [&](auto NC) {
       return Launch<decltype(NC)::value, real>::adj_rhs(
-          lam, adjt, out, n_slots_, dptr<const double>(geo_d_), dptr<const real>(mat_d_), dptr<const int>(meta_d_),
+          lam, adjt, adjt + trace_slot_elems(), out, n_slots_, dptr<const double>(geo_d_), dptr<const real>(mat_d_), dptr<const int>(meta_d_),
           dptr<const real>(Dt_d_), dptr<const real>(Lt_d_), NPa_, dptr<const int>(fmask_d_), dptr<const int>(nbr_d_),
           dptr<const uint8_t>(finfo_d_), dptr<const int>(perm_d_), st_);
     });
@@ -470,7 +471,7 @@ class Engine final : public ridg_solver {
     DBuf l, o, t;
     l.alloc(qsize() * sizeof(real));
     o.alloc(qsize() * sizeof(real));
-    t.alloc(trace_slot_elems() * sizeof(real));
+    t.alloc(2 * trace_slot_elems() * sizeof(real));
     std::vector<real> h = to_slots(lam);
     RIDG_CUDA(cudaMemcpyAsync(l.p, h.data(), h.size() * sizeof(real), cudaMemcpyHostToDevice, st_));
     adjoint_rhs_into(dptr<real>(l), dptr<real>(o), dptr<real>(t));
@@ -529,6 +530,19 @@ class Engine final : public ridg_solver {
     upload(rec_row_, rrow, st_);
     upload(adj_rec_slot_, rslot, st_);
     upload(adj_rec_row_, rrow, st_);
+    {
+      // receivers grouped by element slot (stable: each group keeps the receivers' order)
+      std::vector<int> order(nrec);
+      for (int64_t r = 0; r < nrec; ++r) order[r] = int(r);
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rslot[x] < rslot[y]; });
+      std::vector<int> grp{0};
+      for (int64_t i = 1; i < nrec; ++i)
+        if (rslot[order[i]] != rslot[order[i - 1]]) grp.push_back(int(i));
+      grp.push_back(int(nrec));
+      adj_.n_groups = int64_t(grp.size()) - 1;
+      upload(adj_grp_, grp, st_);
+      upload(adj_rec_sorted_, order, st_);
+    }
     adj_.amp.assign(n_global + 1, 0.0);
     for (int64_t n = 0; n <= n_global; ++n) adj_.amp[n] = double(real(adj_.wav(double(n) * dt)));
     const size_t qb = qsize() * sizeof(real), tb = 3 * trace_slot_elems() * sizeof(real);
@@ -588,9 +602,9 @@ class Engine final : public ridg_solver {
     DBuf lam, sring, adjt, seg, acc;
     lam.alloc(qb);
     sring.alloc(3 * qb);
-    adjt.alloc(trace_slot_elems() * sizeof(real));
+    adjt.alloc(2 * trace_slot_elems() * sizeof(real));
     seg.alloc(size_t(adj_.seg + 1) * qb);
-    acc.alloc(size_t(n_slots_) * sizeof(double));
+    acc.alloc(size_t(n_slots_) * Np_ * sizeof(double));  // per pressure node, summed per element at the end
     RIDG_CUDA(cudaMemsetAsync(lam.p, 0, lam.bytes, st_));
     RIDG_CUDA(cudaMemsetAsync(sring.p, 0, sring.bytes, st_));
     RIDG_CUDA(cudaMemsetAsync(acc.p, 0, acc.bytes, st_));
@@ -624,20 +638,26 @@ class Engine final : public ridg_solver {
           using LN = Launch<decltype(NC)::value, real>;
           cudaError_t e2 = LN::adj_update(L, sr(m + 1), sr(m + 2), sr(m + 3), h, int64_t(qn), st_);
           if (e2 == cudaSuccess)
-            e2 = LN::adj_inject(L, dptr<const int64_t>(adj_rec_slot_), dptr<const real>(adj_rec_row_), int(adj_.nrec),
+            e2 = LN::adj_inject(L, dptr<const int>(adj_grp_), dptr<const int>(adj_rec_sorted_), int(adj_.n_groups),
+                                dptr<const int64_t>(adj_rec_slot_), dptr<const real>(adj_rec_row_),
                                 dptr<const double>(adj_res_), n_t, m, h, st_);
           if (e2 == cudaSuccess)
-            e2 = LN::adj_grad(L, sg(m - a0), sg(m - 1 - a0), n_slots_, dptr<const int>(meta_d_), adj_.src_slot,
-                              dptr<const real>(adj_w_), F, dptr<double>(acc), st_);
+            e2 = LN::adj_grad(L, sg(m - a0), sg(m - 1 - a0), n_slots_, adj_.src_slot, dptr<const real>(adj_w_), F,
+                              dptr<double>(acc), st_);
           return e2;
         });
         if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
       }
     }
-    std::vector<double> sums(n_slots_);
-    RIDG_CUDA(cudaMemcpyAsync(sums.data(), acc.p, acc.bytes, cudaMemcpyDeviceToHost, st_));
+    std::vector<double> nodes(size_t(n_slots_) * Np_);
+    RIDG_CUDA(cudaMemcpyAsync(nodes.data(), acc.p, acc.bytes, cudaMemcpyDeviceToHost, st_));
     RIDG_CUDA(cudaStreamSynchronize(st_));
-    for (int64_t k = 0; k < mesh_.K; ++k) grad[k] = -2.0 / c_[k] * sums[ord_.slot_of[k]];
+    for (int64_t k = 0; k < mesh_.K; ++k) {
+      const int64_t sl = ord_.slot_of[k];
+      double sum = 0.0;
+      for (int m = 0; m < Np_; ++m) sum += nodes[((sl >> 5) * Np_ + m) * 32 + (sl & 31)];
+      grad[k] = -2.0 / c_[k] * sum;
+    }
     for (int64_t k = 0; k < mesh_.K; ++k)
       if (!std::isfinite(grad[k])) throw Error{RIDG_E_UNSTABLE, "non-finite gradient"};
   }
@@ -1332,11 +1352,11 @@ class Engine final : public ridg_solver {
   struct AdjointRun {
     bool ready = false;
     Wavelet wav;
-    int64_t n_global = 0, seg = 1, n_ck = 0, nrec = 0, src_slot = 0;
+    int64_t n_global = 0, seg = 1, n_ck = 0, nrec = 0, src_slot = 0, n_groups = 0;
     std::vector<int64_t> ck_tau, ck_count;
     std::vector<double> amp;
   } adj_;
-  DBuf ck_q_, ck_ring_, ck_trace_, adj_res_, adj_w_, adj_rec_slot_, adj_rec_row_;
+  DBuf ck_q_, ck_ring_, ck_trace_, adj_res_, adj_w_, adj_rec_slot_, adj_rec_row_, adj_grp_, adj_rec_sorted_;
   int64_t n_slots_ = 0, NL_ = 1, n_bfaces_ = 0;
   int L_ = 1;
   std::vector<int> bface_host_;
