@@ -35,6 +35,22 @@ __device__ __forceinline__ void load_lambda_tile(const real* __restrict__ lam, r
   for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) sL[i] = src[i];
 }
 
+// shared memory of the two kernels (the LIFT^T columns are staged where they still fit)
+template <int N, typename real>
+constexpr bool adj_traces_stage_lt() {
+  return (size_t(8) * Order<N>::Np * 32 + size_t(4) * Order<N>::Nfp * Order<N>::Np) * sizeof(real) <= 227 * 1024;
+}
+template <int N, typename real>
+constexpr size_t adj_traces_smem() {
+  return (size_t(8) * Order<N>::Np * 32 + (adj_traces_stage_lt<N, real>() ? size_t(4) * Order<N>::Nfp * Order<N>::Np : 0)) *
+         sizeof(real);
+}
+template <int N, typename real>
+constexpr size_t adj_rhs_smem() {
+  return size_t(4) * Order<N>::Np * 32 * sizeof(real) + size_t(2) * 32 * (8 * Order<N>::NFPP + 1) * sizeof(real) +
+         size_t(Order<N>::Np) * 3 * sizeof(int);
+}
+
 // Adjoint traces of every face of the block's elements (at = alpha_f L_f^T l_p, bt = beta_f L_f^T
 // (n_f . l_v)), written to the element's own rows and, for interior faces, pushed into the
 // neighbour's inbox at the neighbour's face-node index of each node (the correspondence codes of
@@ -47,11 +63,18 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
                                   const int* __restrict__ perm) {
   using O = Order<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
+  constexpr bool STAGE_LT = adj_traces_stage_lt<N, real>();
   extern __shared__ __align__(16) unsigned char smem_adj[];
   real* sL = reinterpret_cast<real*>(smem_adj);  // [4][Np][32]
   real* sV = sL + 4 * Np * 32;                   // [4 faces][Np][32]: n_f . lambda_v
+  real* sLt = sV + 4 * Np * 32;                  // [Np][4 Nfp]: LIFT^T columns, lanes read consecutive entries
   const int64_t blk = blockIdx.x;
   load_lambda_tile<N, real>(lam, sL, blk);
+  if constexpr (STAGE_LT)
+    for (int i = threadIdx.x; i < 4 * Nfp * Np; i += blockDim.x) {
+      const int fj = i / Np, n = i - fj * Np;
+      sLt[n * (4 * Nfp) + fj] = Lt[int64_t(fj) * NPa + n];
+    }
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) {
     const int f = i / (Np * 32), r = i - f * (Np * 32), n = r >> 5, c = r & 31;
@@ -86,7 +109,7 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
       real ap = 0, av = 0;
 #pragma unroll 4
       for (int n = 0; n < Np; ++n) {
-        const real l = row[n];
+        const real l = STAGE_LT ? sLt[n * (4 * Nfp) + f * Nfp + j] : row[n];
         ap += l * sL[(0 * Np + n) * 32 + c];
         av += l * vf[n * 32 + c];
       }
@@ -200,17 +223,6 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
 #pragma unroll
     for (int i = 0; i < 3; ++i) out[idx(1 + i)] = ov[i];
   }
-}
-
-// shared memory of the two kernels
-template <int N, typename real>
-constexpr size_t adj_traces_smem() {
-  return size_t(8) * Order<N>::Np * 32 * sizeof(real);
-}
-template <int N, typename real>
-constexpr size_t adj_rhs_smem() {
-  return size_t(4) * Order<N>::Np * 32 * sizeof(real) + size_t(2) * 32 * (8 * Order<N>::NFPP + 1) * sizeof(real) +
-         size_t(Order<N>::Np) * 3 * sizeof(int);
 }
 
 // lambda += h (a1 s0 + a2 s1 + a3 s2), elementwise over the whole field array
