@@ -35,20 +35,30 @@ __device__ __forceinline__ void load_lambda_tile(const real* __restrict__ lam, r
   for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) sL[i] = src[i];
 }
 
+// per-column coefficients staged in shared memory, [k][32]: lanes of consecutive columns read
+// consecutive words.  Traces: normals (12) and the face factors alpha_f, beta_f (8).  A^T: rx (9),
+// normals (12), rho c^2, 1/rho, tau_p[4], tau_v[4]; the boundary kinds follow as ints [4][32].
+constexpr int kAdjTc = 20;
+constexpr int kAdjRc = 31;
+
 // shared memory of the two kernels (the LIFT^T columns are staged where they still fit)
 template <int N, typename real>
 constexpr bool adj_traces_stage_lt() {
-  return (size_t(8) * Order<N>::Np * 32 + size_t(4) * Order<N>::Nfp * Order<N>::Np) * sizeof(real) <= 227 * 1024;
+  return (size_t(8) * Order<N>::Np * 32 + size_t(kAdjTc) * 32 + size_t(4) * Order<N>::Nfp * Order<N>::Np) *
+             sizeof(real) <=
+         227 * 1024;
 }
 template <int N, typename real>
 constexpr size_t adj_traces_smem() {
-  return (size_t(8) * Order<N>::Np * 32 + (adj_traces_stage_lt<N, real>() ? size_t(4) * Order<N>::Nfp * Order<N>::Np : 0)) *
+  return (size_t(8) * Order<N>::Np * 32 + size_t(kAdjTc) * 32 +
+          (adj_traces_stage_lt<N, real>() ? size_t(4) * Order<N>::Nfp * Order<N>::Np : 0)) *
          sizeof(real);
 }
 template <int N, typename real>
 constexpr size_t adj_rhs_smem() {
-  return size_t(4) * Order<N>::Np * 32 * sizeof(real) + size_t(2) * 32 * (8 * Order<N>::NFPP + 1) * sizeof(real) +
-         size_t(Order<N>::Np) * 3 * sizeof(int);
+  return (size_t(4) * Order<N>::Np * 32 + size_t(2) * 32 * (8 * Order<N>::NFPP + 1) + size_t(kAdjRc) * 32) *
+             sizeof(real) +
+         (size_t(Order<N>::Np) * 3 + size_t(4) * 32) * sizeof(int);
 }
 
 // Adjoint traces of every face of the block's elements (at = alpha_f L_f^T l_p, bt = beta_f L_f^T
@@ -67,7 +77,8 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
   extern __shared__ __align__(16) unsigned char smem_adj[];
   real* sL = reinterpret_cast<real*>(smem_adj);  // [4][Np][32]
   real* sV = sL + 4 * Np * 32;                   // [4 faces][Np][32]: n_f . lambda_v
-  real* sLt = sV + 4 * Np * 32;                  // [Np][4 Nfp]: LIFT^T columns, lanes read consecutive entries
+  real* sC = sV + 4 * Np * 32;                   // [kAdjTc][32]: normals, alpha_f, beta_f
+  real* sLt = sC + kAdjTc * 32;                  // [Np][4 Nfp]: LIFT^T columns, lanes read consecutive entries
   const int64_t blk = blockIdx.x;
   load_lambda_tile<N, real>(lam, sL, blk);
   if constexpr (STAGE_LT)
@@ -75,12 +86,17 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
       const int fj = i / Np, n = i - fj * Np;
       sLt[n * (4 * Nfp) + fj] = Lt[int64_t(fj) * NPa + n];
     }
+  for (int i = threadIdx.x; i < kAdjTc * 32; i += blockDim.x) {
+    const int k = i >> 5, c = i & 31;
+    const int64_t s = blk * 32 + c;
+    const double* g = geo + s * kGeo;
+    sC[i] = k < 12 ? real(g[9 + k]) : real(-0.5 * g[21 + (k & 3)]) * mat[s * kMat + (k < 16 ? 0 : 1)];
+  }
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) {
     const int f = i / (Np * 32), r = i - f * (Np * 32), n = r >> 5, c = r & 31;
-    const double* g = geo + (blk * 32 + c) * kGeo + 9 + 3 * f;
-    sV[i] = real(g[0]) * sL[(1 * Np + n) * 32 + c] + real(g[1]) * sL[(2 * Np + n) * 32 + c] +
-            real(g[2]) * sL[(3 * Np + n) * 32 + c];
+    const real* nf = sC + 3 * f * 32 + c;
+    sV[i] = nf[0] * sL[(1 * Np + n) * 32 + c] + nf[32] * sL[(2 * Np + n) * 32 + c] + nf[64] * sL[(3 * Np + n) * 32 + c];
   }
   __syncthreads();
   // half-warp per (face, column) item, lanes over the face's nodes: the element's own rows and the
@@ -92,8 +108,7 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
     const int64_t s = blk * 32 + c;
     real* out = own + s * (8 * NFPP) + f * 2 * NFPP;
     const bool valid = (meta[s] & kMetaValid) != 0;
-    const double* g = geo + s * kGeo;
-    const real* m = mat + s * kMat;
+    const real alpha = sC[(12 + f) * 32 + c], beta = sC[(16 + f) * 32 + c];
     const uint8_t info = finfo[s * 4 + f];
     const real* vf = sV + f * Np * 32;
 #pragma unroll
@@ -113,7 +128,7 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
         ap += l * sL[(0 * Np + n) * 32 + c];
         av += l * vf[n * 32 + c];
       }
-      const real a = real(-0.5 * g[21 + f]) * m[0] * ap, b = real(-0.5 * g[21 + f]) * m[1] * av;
+      const real a = alpha * ap, b = beta * av;
       out[j] = a;
       out[NFPP + j] = b;
       if (finfo_bc(info) == 0) {
@@ -143,9 +158,18 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
   real* sL = reinterpret_cast<real*>(smem_adj);  // [4][Np][32]
   real* sOwn = sL + 4 * Np * 32;                 // [32][OS]
   real* sIn = sOwn + 32 * OS;                    // [32][OS]
-  int* sInv = reinterpret_cast<int*>(sIn + 32 * OS);  // [Np][3]: f * 32 + jf of the faces holding node m
+  real* sC = sIn + 32 * OS;                      // [kAdjRc][32]: rx, normals, rho c^2, 1/rho, tau_p, tau_v
+  int* sInv = reinterpret_cast<int*>(sC + kAdjRc * 32);  // [Np][3]: f * 32 + jf of the faces holding node m
+  int* sBc = sInv + Np * 3;                              // [4][32]: boundary kind of each face
   const int64_t blk = blockIdx.x;
   load_lambda_tile<N, real>(lam, sL, blk);
+  for (int i = threadIdx.x; i < kAdjRc * 32; i += blockDim.x) {
+    const int k = i >> 5, c = i & 31;
+    const int64_t s = blk * 32 + c;
+    // geo[0..20] are rx and the normals; mat[0], mat[1] and mat[3..10] follow at 21..30
+    sC[i] = k < 21 ? real(geo[s * kGeo + k]) : mat[s * kMat + (k < 23 ? k - 21 : k - 20)];
+  }
+  for (int i = threadIdx.x; i < 4 * 32; i += blockDim.x) sBc[i] = finfo_bc(finfo[(blk * 32 + (i & 31)) * 4 + (i >> 5)]);
   for (int i = threadIdx.x; i < 32 * 8 * NFPP; i += blockDim.x) {
     const int c = i / (8 * NFPP), r = i - c * (8 * NFPP);
     sOwn[c * OS + r] = own[(blk * 32) * (8 * NFPP) + i];
@@ -167,8 +191,7 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
       for (int fld = 0; fld < 4; ++fld) out[idx(fld)] = real(0);
       continue;
     }
-    const double* g = geo + s * kGeo;
-    const real* m = mat + s * kMat;
+    const real* cc = sC + c;  // coefficient k of this column at cc[32 k]
     real dp[3] = {0, 0, 0}, dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     const real* r0 = Dt + int64_t(0 * Np + mnode) * NPa;
     const real* r1 = Dt + int64_t(1 * Np + mnode) * NPa;
@@ -190,9 +213,9 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const real gij = real(g[3 * i + j]);
-        op -= m[1] * gij * dv[i][j];
-        ov[i] -= m[0] * gij * dp[j];
+        const real gij = cc[32 * (3 * i + j)];
+        op -= cc[32 * 22] * gij * dv[i][j];
+        ov[i] -= cc[32 * 21] * gij * dp[j];
       }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -200,8 +223,8 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
       if (e < 0) break;
       const int f = e >> 5, jf = e & 31;
       const real a = sOwn[c * OS + f * 2 * NFPP + jf], b = sOwn[c * OS + f * 2 * NFPP + NFPP + jf];
-      const real taup = m[3 + f], tauv = m[7 + f];
-      const int bc = finfo_bc(finfo[s * 4 + f]);
+      const real taup = cc[32 * (23 + f)], tauv = cc[32 * (27 + f)];
+      const int bc = sBc[f * 32 + c];
       real sp = 0, sv = 0;
       if (bc == 0) {
         const real a2 = sIn[c * OS + f * 2 * NFPP + jf], b2 = sIn[c * OS + f * 2 * NFPP + NFPP + jf];
@@ -217,7 +240,7 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
       }
       op += sp;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) ov[i] += real(g[9 + 3 * f + i]) * sv;
+      for (int i = 0; i < 3; ++i) ov[i] += cc[32 * (9 + 3 * f + i)] * sv;
     }
     out[idx(0)] = op;
 #pragma unroll

@@ -98,6 +98,7 @@ cudaError_t Launch<N, real>::adj_rhs(const real* lam, real* own, real* inbox, re
   const int64_t blocks = n_slots / 32;
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t sm_t = adj_traces_smem<N, real>(), sm_r = adj_rhs_smem<N, real>();
+  static_assert(sm_t <= 227 * 1024 && sm_r <= 227 * 1024, "adjoint kernels exceed the shared memory of a block");
   static const cudaError_t configured = [] {
     cudaError_t e =
         cudaFuncSetAttribute(adj_traces_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_t));
