@@ -15,7 +15,8 @@
 //            n.v); boundary ghosts fold p+ and vn+ into p- and vn- (free: jp = -2p-, jv = 0;
 //            transparent: jp = -p-, jv = -vn-; rigid: jp = 0, jv = -2vn-).
 // Layouts are the solver's: fields [K/32][4][Np][32] in the device node numbering, adjoint traces
-// and inboxes [slot][4 faces][2][NFPP].
+// and inboxes [slot][4 faces][2][NFPP]; the derivative matrices interleaved, Dt4 [Np][Np][4] with
+// (D_0, D_1, D_2, 0)[n][m] at (m, n), so that one vector load brings the three entries a node needs.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -142,15 +143,32 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
   }
 }
 
+// the three derivative entries at Dt4 + 4 (m Np + n)
+__device__ __forceinline__ void load_d3(const float* p, float d[3]) {
+  const float4 v = *reinterpret_cast<const float4*>(p);
+  d[0] = v.x;
+  d[1] = v.y;
+  d[2] = v.z;
+}
+__device__ __forceinline__ void load_d3(const double* p, double d[3]) {
+  const double2 v = *reinterpret_cast<const double2*>(p);
+  d[0] = v.x;
+  d[1] = v.y;
+  d[2] = p[2];
+}
+
 // A^T lambda for the block's elements: the transposed volume terms (D_j^T rows, broadcast over the
 // warp) and, at each face node, the weights of the jumps from the element's own adjoint traces and
-// from the neighbour's (its inbox), with the boundary ghosts folded in.
+// from the neighbour's (its inbox), with the boundary ghosts folded in.  With s1 != null the block
+// then applies the adjoint Adams-Bashforth update to its own lambda tile, in place (no other block
+// reads it): lam += h (a1 A^T lam + a2 s1 + a3 s2).
 template <int N, typename real>
-__global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restrict__ own,
-                               const real* __restrict__ inbox, real* __restrict__ out, int64_t n_slots,
-                               const double* __restrict__ geo, const real* __restrict__ mat,
-                               const int* __restrict__ meta, const real* __restrict__ Dt, int NPa,
-                               const int* __restrict__ fmask, const uint8_t* __restrict__ finfo) {
+__global__ void adj_rhs_kernel(real* lam, const real* __restrict__ own, const real* __restrict__ inbox,
+                               real* __restrict__ out, int64_t n_slots, const double* __restrict__ geo,
+                               const real* __restrict__ mat, const int* __restrict__ meta,
+                               const real* __restrict__ Dt4, const int* __restrict__ fmask,
+                               const uint8_t* __restrict__ finfo, const real* __restrict__ s1,
+                               const real* __restrict__ s2, real h) {
   using O = Order<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
   constexpr int OS = 8 * NFPP + 1;  // trace rows of one slot, padded: column-wise reads hit distinct banks
@@ -187,18 +205,28 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
     const int mnode = item >> 5, c = item & 31;  // warp: one node row of 32 columns
     const int64_t s = blk * 32 + c;
     auto idx = [&](int fld) { return ((blk * 4 + fld) * Np + mnode) * 32 + c; };
+    // out = r and, with s1, lam += h (a1 r + a2 s1 + a3 s2) for the four fields of node mnode; the
+    // older terms are loaded first, so that their latency hides behind the contraction
+    real older[4] = {0, 0, 0, 0};
+    if (s1)
+#pragma unroll
+      for (int fld = 0; fld < 4; ++fld) older[fld] = real(AB::a2) * s1[idx(fld)] + real(AB::a3) * s2[idx(fld)];
+    auto store = [&](int fld, real r) {
+      const int64_t at = idx(fld);
+      out[at] = r;
+      if (s1) lam[at] = sL[(fld * Np + mnode) * 32 + c] + h * (real(AB::a1) * r + older[fld]);
+    };
     if (!(meta[s] & kMetaValid)) {
-      for (int fld = 0; fld < 4; ++fld) out[idx(fld)] = real(0);
+      for (int fld = 0; fld < 4; ++fld) store(fld, real(0));
       continue;
     }
     const real* cc = sC + c;  // coefficient k of this column at cc[32 k]
     real dp[3] = {0, 0, 0}, dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    const real* r0 = Dt + int64_t(0 * Np + mnode) * NPa;
-    const real* r1 = Dt + int64_t(1 * Np + mnode) * NPa;
-    const real* r2 = Dt + int64_t(2 * Np + mnode) * NPa;
+    const real* dm = Dt4 + int64_t(mnode) * Np * 4;
 #pragma unroll 4
     for (int n = 0; n < Np; ++n) {
-      const real d[3] = {r0[n], r1[n], r2[n]};
+      real d[3];
+      load_d3(dm + 4 * n, d);
       const real lp = sL[(0 * Np + n) * 32 + c];
       const real lv[3] = {sL[(1 * Np + n) * 32 + c], sL[(2 * Np + n) * 32 + c], sL[(3 * Np + n) * 32 + c]};
 #pragma unroll
@@ -242,19 +270,10 @@ __global__ void adj_rhs_kernel(const real* __restrict__ lam, const real* __restr
 #pragma unroll
       for (int i = 0; i < 3; ++i) ov[i] += cc[32 * (9 + 3 * f + i)] * sv;
     }
-    out[idx(0)] = op;
+    store(0, op);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) out[idx(1 + i)] = ov[i];
+    for (int i = 0; i < 3; ++i) store(1 + i, ov[i]);
   }
-}
-
-// lambda += h (a1 s0 + a2 s1 + a3 s2), elementwise over the whole field array
-template <typename real>
-__global__ void adj_update_kernel(real* __restrict__ lam, const real* __restrict__ s0, const real* __restrict__ s1,
-                                  const real* __restrict__ s2, double h, int64_t n) {
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  lam[i] += real(h) * (real(AB::a1) * s0[i] + real(AB::a2) * s1[i] + real(AB::a3) * s2[i]);
 }
 
 // lambda_p -= coef res_r(col) l(x_r): block g handles the receivers rec_sorted[grp[g] .. grp[g+1])
@@ -278,22 +297,36 @@ __global__ void adj_inject_kernel(real* __restrict__ lam, const int* __restrict_
   }
 }
 
-// acc[node] += lambda_p (q1_p - q0_p - F w) for every pressure node (acc laid out like the pressure
-// field, [n_slots/32][Np][32]; w on the source slot only); the per-element sums are taken at the end
+// acc[slot] += sum_m lambda_p (q1_p - q0_p - F w)_m over the pressure nodes m of the slot (w on the
+// source slot only).  One block per 32 slots: warp w takes the rows w, w + 8, ..., lane = slot, in
+// the working precision (FP64 arithmetic is slow on this part), and the eight partial sums are
+// added in FP64 in a fixed order (deterministic).
 template <int N, typename real>
 __global__ void adj_grad_kernel(const real* __restrict__ lam, const real* __restrict__ q1, const real* __restrict__ q0,
                                 int64_t n_slots, int64_t src_slot, const real* __restrict__ w_src, double F,
                                 double* __restrict__ acc) {
   using O = Order<N>;
   constexpr int Np = O::Np;
-  const int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;  // (block, node, lane)
-  if (i >= n_slots * Np) return;
-  const int64_t blk = i / (Np * 32);
-  const int r = int(i - blk * Np * 32), m = r >> 5, lane = r & 31;
-  const int64_t at = (blk * 4 * Np + m) * 32 + lane;  // pressure row of the field layout
-  double dq = double(q1[at]) - double(q0[at]);
-  if (blk * 32 + lane == src_slot) dq -= F * double(w_src[m]);
-  acc[i] += double(lam[at]) * dq;
+  __shared__ double part[8][32];
+  const int64_t blk = blockIdx.x;
+  const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool src = blk * 32 + lane == src_slot;
+  real sum = 0;
+#pragma unroll 4
+  for (int m = wp; m < Np; m += 8) {
+    const int64_t at = (blk * 4 * Np + m) * 32 + lane;  // pressure row of the field layout
+    real dq = q1[at] - q0[at];
+    if (src) dq -= real(F) * w_src[m];
+    sum += lam[at] * dq;
+  }
+  part[wp][lane] = double(sum);
+  __syncthreads();
+  if (wp == 0) {
+    double t = part[0][lane];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) t += part[k][lane];
+    acc[blk * 32 + lane] += t;
+  }
 }
 
 }  // namespace ridg

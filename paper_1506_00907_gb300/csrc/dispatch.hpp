@@ -21,15 +21,17 @@ struct Launch {
   static cudaError_t image_out(const double* img, const int64_t* slot_of, const int* pos_of, int64_t K, double* out,
                                cudaStream_t st);
   // discrete adjoint (adjoint_kernels.cuh)
-  // out = A^T lam; own, inbox: scratch adjoint traces [n_slots][4][2][NFPP] each
-  static cudaError_t adj_rhs(const real* lam, real* own, real* inbox, real* out, int64_t n_slots, const double* geo,
-                             const real* mat, const int* meta, const real* Dt, const real* Lt, int NPa, const int* fmask,
-                             const int* nbr, const uint8_t* finfo, const int* perm, cudaStream_t st);
-  static cudaError_t adj_update(real* lam, const real* s0, const real* s1, const real* s2, double h, int64_t n,
-                                cudaStream_t st);
+  // out = A^T lam; own, inbox: scratch adjoint traces [n_slots][4][2][NFPP] each; Dt4: [Np][Np][4]
+  // (D_0, D_1, D_2, 0)[n][m] at (m, n).  With s1 != null the adjoint Adams-Bashforth update
+  // lam += h (a1 out + a2 s1 + a3 s2) is applied in place as well.
+  static cudaError_t adj_rhs(real* lam, real* own, real* inbox, real* out, int64_t n_slots, const double* geo,
+                             const real* mat, const int* meta, const real* Dt4, const real* Lt, int NPa, const int* fmask,
+                             const int* nbr, const uint8_t* finfo, const int* perm, const real* s1, const real* s2,
+                             double h, cudaStream_t st);
   static cudaError_t adj_inject(real* lam, const int* grp, const int* rec_sorted, int n_groups, const int64_t* rec_slot,
                                 const real* rec_row, const double* res, int64_t n_time, int64_t col, double coef,
                                 cudaStream_t st);
+  // acc[slot] += sum over the pressure nodes of lam_p (q1_p - q0_p - F w), per element slot
   static cudaError_t adj_grad(const real* lam, const real* q1, const real* q0, int64_t n_slots, int64_t src_slot,
                               const real* w_src, double F, double* acc, cudaStream_t st);
 };

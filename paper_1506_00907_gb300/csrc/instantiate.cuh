@@ -91,10 +91,10 @@ cudaError_t Launch<N, real>::state_io(bool to_slots, const double* q_abi_in, dou
 }
 
 template <int N, typename real>
-cudaError_t Launch<N, real>::adj_rhs(const real* lam, real* own, real* inbox, real* out, int64_t n_slots,
-                                     const double* geo, const real* mat, const int* meta, const real* Dt,
-                                     const real* Lt, int NPa, const int* fmask, const int* nbr, const uint8_t* finfo,
-                                     const int* perm, cudaStream_t st) {
+cudaError_t Launch<N, real>::adj_rhs(real* lam, real* own, real* inbox, real* out, int64_t n_slots, const double* geo,
+                                     const real* mat, const int* meta, const real* Dt4, const real* Lt, int NPa,
+                                     const int* fmask, const int* nbr, const uint8_t* finfo, const int* perm,
+                                     const real* s1, const real* s2, double h, cudaStream_t st) {
   const int64_t blocks = n_slots / 32;
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t sm_t = adj_traces_smem<N, real>(), sm_r = adj_rhs_smem<N, real>();
@@ -109,16 +109,8 @@ cudaError_t Launch<N, real>::adj_rhs(const real* lam, real* own, real* inbox, re
   if (configured != cudaSuccess) return configured;
   adj_traces_kernel<N, real><<<unsigned(blocks), 256, sm_t, st>>>(lam, own, inbox, n_slots, geo, mat, meta, Lt, NPa,
                                                                    nbr, finfo, perm);
-  adj_rhs_kernel<N, real><<<unsigned(blocks), 256, sm_r, st>>>(lam, own, inbox, out, n_slots, geo, mat, meta, Dt, NPa,
-                                                                fmask, finfo);
-  return cudaGetLastError();
-}
-
-template <int N, typename real>
-cudaError_t Launch<N, real>::adj_update(real* lam, const real* s0, const real* s1, const real* s2, double h, int64_t n,
-                                        cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  adj_update_kernel<real><<<unsigned((n + 255) / 256), 256, 0, st>>>(lam, s0, s1, s2, h, n);
+  adj_rhs_kernel<N, real><<<unsigned(blocks), 256, sm_r, st>>>(lam, own, inbox, out, n_slots, geo, mat, meta, Dt4,
+                                                                fmask, finfo, s1, s2, real(h));
   return cudaGetLastError();
 }
 
@@ -135,9 +127,9 @@ cudaError_t Launch<N, real>::adj_inject(real* lam, const int* grp, const int* re
 template <int N, typename real>
 cudaError_t Launch<N, real>::adj_grad(const real* lam, const real* q1, const real* q0, int64_t n_slots,
                                       int64_t src_slot, const real* w_src, double F, double* acc, cudaStream_t st) {
-  const int64_t n = n_slots * Order<N>::Np;
-  if (n <= 0) return cudaSuccess;
-  adj_grad_kernel<N, real><<<unsigned((n + 255) / 256), 256, 0, st>>>(lam, q1, q0, n_slots, src_slot, w_src, F, acc);
+  const int64_t blocks = n_slots / 32;
+  if (blocks <= 0) return cudaSuccess;
+  adj_grad_kernel<N, real><<<unsigned(blocks), 256, 0, st>>>(lam, q1, q0, n_slots, src_slot, w_src, F, acc);
   return cudaGetLastError();
 }
 

@@ -455,13 +455,15 @@ class Engine final : public ridg_solver {
     RIDG_CUDA(cudaStreamSynchronize(st_));
   }
 
-  // out = A^T lam; adjt: scratch for the adjoint traces and their inboxes (2 trace slots)
-  void adjoint_rhs_into(const real* lam, real* out, real* adjt) {
+  // out = A^T lam; adjt: scratch for the adjoint traces and their inboxes (2 trace slots).  With s1,
+  // lam += h (a1 out + a2 s1 + a3 s2) in the same pass (the adjoint Adams-Bashforth update).
+  void adjoint_rhs_into(real* lam, real* out, real* adjt, const real* s1 = nullptr, const real* s2 = nullptr,
+                        double h = 0.0) {
     cudaError_t e = dispatch_order(N_, [&](auto NC) {
       return Launch<decltype(NC)::value, real>::adj_rhs(
-          lam, adjt, adjt + trace_slot_elems(), out, n_slots_, dptr<const double>(geo_d_), dptr<const real>(mat_d_), dptr<const int>(meta_d_),
-          dptr<const real>(Dt_d_), dptr<const real>(Lt_d_), NPa_, dptr<const int>(fmask_d_), dptr<const int>(nbr_d_),
-          dptr<const uint8_t>(finfo_d_), dptr<const int>(perm_d_), st_);
+          lam, adjt, adjt + trace_slot_elems(), out, n_slots_, dptr<const double>(geo_d_), dptr<const real>(mat_d_),
+          dptr<const int>(meta_d_), dptr<const real>(Dt4_d_), dptr<const real>(Lt_d_), NPa_, dptr<const int>(fmask_d_),
+          dptr<const int>(nbr_d_), dptr<const uint8_t>(finfo_d_), dptr<const int>(perm_d_), s1, s2, h, st_);
     });
     if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
   }
@@ -604,7 +606,7 @@ class Engine final : public ridg_solver {
     sring.alloc(3 * qb);
     adjt.alloc(2 * trace_slot_elems() * sizeof(real));
     seg.alloc(size_t(adj_.seg + 1) * qb);
-    acc.alloc(size_t(n_slots_) * Np_ * sizeof(double));  // per pressure node, summed per element at the end
+    acc.alloc(size_t(n_slots_) * sizeof(double));  // per element slot
     RIDG_CUDA(cudaMemsetAsync(lam.p, 0, lam.bytes, st_));
     RIDG_CUDA(cudaMemsetAsync(sring.p, 0, sring.bytes, st_));
     RIDG_CUDA(cudaMemsetAsync(acc.p, 0, acc.bytes, st_));
@@ -630,15 +632,14 @@ class Engine final : public ridg_solver {
       }
       // adjoint steps m = b0 .. a0 + 1: lambda^m = lambda^{m+1} + h sum_s a_s A^T lambda^{m+1+s} - g^m
       for (int64_t m = b0; m > a0; --m) {
-        adjoint_rhs_into(L, sr(m + 1), dptr<real>(adjt));
+        // A^T lambda^{m+1} into the ring and the update of lambda with it, in one pass
+        adjoint_rhs_into(L, sr(m + 1), dptr<real>(adjt), sr(m + 2), sr(m + 3), h);
         double F = 0.0;  // source part of q^m - q^{m-1}
         for (int s = 0; s < 3; ++s)
           if (m - 1 - s >= 0) F += h * a[s] * adj_.amp[m - 1 - s];
         cudaError_t e = dispatch_order(N_, [&](auto NC) {
           using LN = Launch<decltype(NC)::value, real>;
-          cudaError_t e2 = LN::adj_update(L, sr(m + 1), sr(m + 2), sr(m + 3), h, int64_t(qn), st_);
-          if (e2 == cudaSuccess)
-            e2 = LN::adj_inject(L, dptr<const int>(adj_grp_), dptr<const int>(adj_rec_sorted_), int(adj_.n_groups),
+          cudaError_t e2 = LN::adj_inject(L, dptr<const int>(adj_grp_), dptr<const int>(adj_rec_sorted_), int(adj_.n_groups),
                                 dptr<const int64_t>(adj_rec_slot_), dptr<const real>(adj_rec_row_),
                                 dptr<const double>(adj_res_), n_t, m, h, st_);
           if (e2 == cudaSuccess)
@@ -649,15 +650,10 @@ class Engine final : public ridg_solver {
         if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
       }
     }
-    std::vector<double> nodes(size_t(n_slots_) * Np_);
-    RIDG_CUDA(cudaMemcpyAsync(nodes.data(), acc.p, acc.bytes, cudaMemcpyDeviceToHost, st_));
+    std::vector<double> per_slot(static_cast<size_t>(n_slots_));
+    RIDG_CUDA(cudaMemcpyAsync(per_slot.data(), acc.p, acc.bytes, cudaMemcpyDeviceToHost, st_));
     RIDG_CUDA(cudaStreamSynchronize(st_));
-    for (int64_t k = 0; k < mesh_.K; ++k) {
-      const int64_t sl = ord_.slot_of[k];
-      double sum = 0.0;
-      for (int m = 0; m < Np_; ++m) sum += nodes[((sl >> 5) * Np_ + m) * 32 + (sl & 31)];
-      grad[k] = -2.0 / c_[k] * sum;
-    }
+    for (int64_t k = 0; k < mesh_.K; ++k) grad[k] = -2.0 / c_[k] * per_slot[ord_.slot_of[k]];
     for (int64_t k = 0; k < mesh_.K; ++k)
       if (!std::isfinite(grad[k])) throw Error{RIDG_E_UNSTABLE, "non-finite gradient"};
   }
@@ -864,7 +860,7 @@ class Engine final : public ridg_solver {
   size_t trace_slot_elems() const { return size_t(n_slots_) * 8 * NFPP_; }
   size_t device_bytes() const {
     size_t b = 0;
-    const DBuf* all[] = {&geo_d_, &J_d_, &mat_d_, &nbr_d_, &finfo_d_, &bface_d_, &meta_d_, &Dt_d_, &Lt_d_,
+    const DBuf* all[] = {&geo_d_, &J_d_, &mat_d_, &nbr_d_, &finfo_d_, &bface_d_, &meta_d_, &Dt_d_, &Dt4_d_, &Lt_d_,
                          &fmask_d_, &perm_d_, &M_d_, &slot_of_d_, &q_snap_, &ring_snap_, &img_p_, &img_q_, &arena_,
                          &afrag_d_, &gtab_d_[0], &gtab_d_[1]};
     for (auto* x : all) b += x->bytes;
@@ -996,7 +992,12 @@ class Engine final : public ridg_solver {
         for (int n = 0; n < Np_; ++n) Dt[(j * Np_ + m) * NPa_ + n] = real(ref_.D[j](n, m));
     for (int fm = 0; fm < 4 * Nfp_; ++fm)
       for (int n = 0; n < Np_; ++n) Lt[fm * NPa_ + n] = real(ref_.LIFT(n, fm));
+    std::vector<real> Dt4(size_t(Np_) * Np_ * 4, real(0));  // (D_0, D_1, D_2, 0)[n][m] at (m, n)
+    for (int m = 0; m < Np_; ++m)
+      for (int n = 0; n < Np_; ++n)
+        for (int j = 0; j < 3; ++j) Dt4[(size_t(m) * Np_ + n) * 4 + j] = real(ref_.D[j](n, m));
     upload(Dt_d_, Dt, st_);
+    upload(Dt4_d_, Dt4, st_);
     upload(Lt_d_, Lt, st_);
     if (contraction_ == RIDG_CONTRACT_TENSOR || contraction_ == RIDG_CONTRACT_TENSOR_BF16)
       upload(afrag_d_, operator_fragments(contraction_ == RIDG_CONTRACT_TENSOR_BF16), st_);
@@ -1361,7 +1362,7 @@ class Engine final : public ridg_solver {
   int L_ = 1;
   std::vector<int> bface_host_;
   std::vector<int64_t> level_count_;
-  DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
+  DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Dt4_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
   DBuf afrag_d_, gtab_d_[2], pos_d_;
   double tau_scale_ = 1.0;
   int contraction_ = RIDG_CONTRACT_TENSOR;  // how the FP32 element products run (FP64: CUDA cores)
