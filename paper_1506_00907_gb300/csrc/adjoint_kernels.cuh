@@ -163,7 +163,7 @@ __device__ __forceinline__ void load_d3(const double* p, double d[3]) {
 // then applies the adjoint Adams-Bashforth update to its own lambda tile, in place (no other block
 // reads it): lam += h (a1 A^T lam + a2 s1 + a3 s2).
 template <int N, typename real>
-__global__ void adj_rhs_kernel(real* lam, const real* __restrict__ own, const real* __restrict__ inbox,
+__global__ void __launch_bounds__(256, N <= 4 ? 4 : 2) adj_rhs_kernel(real* lam, const real* __restrict__ own, const real* __restrict__ inbox,
                                real* __restrict__ out, int64_t n_slots, const double* __restrict__ geo,
                                const real* __restrict__ mat, const int* __restrict__ meta,
                                const real* __restrict__ Dt4, const int* __restrict__ fmask,
@@ -201,78 +201,107 @@ __global__ void adj_rhs_kernel(real* lam, const real* __restrict__ own, const re
     for (; cnt < 3; ++cnt) sInv[m * 3 + cnt] = -1;
   }
   __syncthreads();
-  for (int item = threadIdx.x; item < Np * 32; item += blockDim.x) {
-    const int mnode = item >> 5, c = item & 31;  // warp: one node row of 32 columns
+  // thread per (row pair, column): the rows r and r + H of one column share every lambda value they
+  // read (FP32; FP64 takes one row per thread, for its registers)
+  constexpr int RT = sizeof(real) == 4 ? 2 : 1;
+  constexpr int H = (Np + RT - 1) / RT;
+  for (int item = threadIdx.x; item < H * 32; item += blockDim.x) {
+    const int r = item >> 5, c = item & 31;  // warp: one row (pair) of 32 columns
     const int64_t s = blk * 32 + c;
-    auto idx = [&](int fld) { return ((blk * 4 + fld) * Np + mnode) * 32 + c; };
-    // out = r and, with s1, lam += h (a1 r + a2 s1 + a3 s2) for the four fields of node mnode; the
+    const bool valid = (meta[s] & kMetaValid) != 0;
+    auto idx = [&](int fld, int mnode) { return ((blk * 4 + fld) * Np + mnode) * 32 + c; };
+    // out = r and, with s1, lam += h (a1 r + a2 s1 + a3 s2) for the four fields of each row; the
     // older terms are loaded first, so that their latency hides behind the contraction
-    real older[4] = {0, 0, 0, 0};
-    if (s1)
+    real older[RT][4];
 #pragma unroll
-      for (int fld = 0; fld < 4; ++fld) older[fld] = real(AB::a2) * s1[idx(fld)] + real(AB::a3) * s2[idx(fld)];
-    auto store = [&](int fld, real r) {
-      const int64_t at = idx(fld);
-      out[at] = r;
-      if (s1) lam[at] = sL[(fld * Np + mnode) * 32 + c] + h * (real(AB::a1) * r + older[fld]);
-    };
-    if (!(meta[s] & kMetaValid)) {
-      for (int fld = 0; fld < 4; ++fld) store(fld, real(0));
-      continue;
+    for (int t = 0; t < RT; ++t) {
+      const int mnode = r + t * H < Np ? r + t * H : Np - 1;
+#pragma unroll
+      for (int fld = 0; fld < 4; ++fld)
+        older[t][fld] = s1 ? real(AB::a2) * s1[idx(fld, mnode)] + real(AB::a3) * s2[idx(fld, mnode)] : real(0);
+    }
+    real dp[RT][3], dv[RT][3][3];
+#pragma unroll
+    for (int t = 0; t < RT; ++t)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dp[t][j] = 0;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dv[t][i][j] = 0;
+      }
+    if (valid) {
+      const real* dm[RT];
+#pragma unroll
+      for (int t = 0; t < RT; ++t) dm[t] = Dt4 + int64_t(r + t * H < Np ? r + t * H : Np - 1) * Np * 4;
+#pragma unroll 4
+      for (int n = 0; n < Np; ++n) {
+        const real lp = sL[(0 * Np + n) * 32 + c];
+        const real lv[3] = {sL[(1 * Np + n) * 32 + c], sL[(2 * Np + n) * 32 + c], sL[(3 * Np + n) * 32 + c]};
+#pragma unroll
+        for (int t = 0; t < RT; ++t) {
+          real d[3];
+          load_d3(dm[t] + 4 * n, d);
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            dp[t][j] += d[j] * lp;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) dv[t][i][j] += d[j] * lv[i];
+          }
+        }
+      }
     }
     const real* cc = sC + c;  // coefficient k of this column at cc[32 k]
-    real dp[3] = {0, 0, 0}, dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    const real* dm = Dt4 + int64_t(mnode) * Np * 4;
-#pragma unroll 4
-    for (int n = 0; n < Np; ++n) {
-      real d[3];
-      load_d3(dm + 4 * n, d);
-      const real lp = sL[(0 * Np + n) * 32 + c];
-      const real lv[3] = {sL[(1 * Np + n) * 32 + c], sL[(2 * Np + n) * 32 + c], sL[(3 * Np + n) * 32 + c]};
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        dp[j] += d[j] * lp;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) dv[i][j] += d[j] * lv[i];
+    for (int t = 0; t < RT; ++t) {
+      const int mnode = r + t * H;
+      if (mnode >= Np) break;
+      auto store = [&](int fld, real v) {
+        const int64_t at = idx(fld, mnode);
+        out[at] = v;
+        if (s1) lam[at] = sL[(fld * Np + mnode) * 32 + c] + h * (real(AB::a1) * v + older[t][fld]);
+      };
+      if (!valid) {
+        for (int fld = 0; fld < 4; ++fld) store(fld, real(0));
+        continue;
       }
+      real op = 0, ov[3] = {0, 0, 0};
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          const real gij = cc[32 * (3 * i + j)];
+          op -= cc[32 * 22] * gij * dv[t][i][j];
+          ov[i] -= cc[32 * 21] * gij * dp[t][j];
+        }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const int e = sInv[mnode * 3 + k];
+        if (e < 0) break;
+        const int f = e >> 5, jf = e & 31;
+        const real a = sOwn[c * OS + f * 2 * NFPP + jf], b = sOwn[c * OS + f * 2 * NFPP + NFPP + jf];
+        const real taup = cc[32 * (23 + f)], tauv = cc[32 * (27 + f)];
+        const int bc = sBc[f * 32 + c];
+        real sp = 0, sv = 0;
+        if (bc == 0) {
+          const real a2 = sIn[c * OS + f * 2 * NFPP + jf], b2 = sIn[c * OS + f * 2 * NFPP + NFPP + jf];
+          sp = taup * a - b + b2 - taup * a2;
+          sv = tauv * b - a + tauv * b2 - a2;
+        } else if (bc == 1) {  // free surface
+          sp = real(2) * (taup * a - b);
+        } else if (bc == 2) {  // transparent
+          sp = taup * a - b;
+          sv = tauv * b - a;
+        } else {  // rigid wall
+          sv = real(2) * (tauv * b - a);
+        }
+        op += sp;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) ov[i] += cc[32 * (9 + 3 * f + i)] * sv;
+      }
+      store(0, op);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) store(1 + i, ov[i]);
     }
-    real op = 0, ov[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const real gij = cc[32 * (3 * i + j)];
-        op -= cc[32 * 22] * gij * dv[i][j];
-        ov[i] -= cc[32 * 21] * gij * dp[j];
-      }
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      const int e = sInv[mnode * 3 + k];
-      if (e < 0) break;
-      const int f = e >> 5, jf = e & 31;
-      const real a = sOwn[c * OS + f * 2 * NFPP + jf], b = sOwn[c * OS + f * 2 * NFPP + NFPP + jf];
-      const real taup = cc[32 * (23 + f)], tauv = cc[32 * (27 + f)];
-      const int bc = sBc[f * 32 + c];
-      real sp = 0, sv = 0;
-      if (bc == 0) {
-        const real a2 = sIn[c * OS + f * 2 * NFPP + jf], b2 = sIn[c * OS + f * 2 * NFPP + NFPP + jf];
-        sp = taup * a - b + b2 - taup * a2;
-        sv = tauv * b - a + tauv * b2 - a2;
-      } else if (bc == 1) {  // free surface
-        sp = real(2) * (taup * a - b);
-      } else if (bc == 2) {  // transparent
-        sp = taup * a - b;
-        sv = tauv * b - a;
-      } else {  // rigid wall
-        sv = real(2) * (tauv * b - a);
-      }
-      op += sp;
-#pragma unroll
-      for (int i = 0; i < 3; ++i) ov[i] += cc[32 * (9 + 3 * f + i)] * sv;
-    }
-    store(0, op);
-#pragma unroll
-    for (int i = 0; i < 3; ++i) store(1 + i, ov[i]);
   }
 }
 
