@@ -62,6 +62,22 @@ constexpr size_t adj_rhs_smem() {
          (size_t(Order<N>::Np) * 3 + size_t(4) * 32) * sizeof(int);
 }
 
+// four consecutive entries (16-byte aligned for float, two 16-byte loads for double)
+__device__ __forceinline__ void load4(const float* p, float v[4]) {
+  const float4 x = *reinterpret_cast<const float4*>(p);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = x.z;
+  v[3] = x.w;
+}
+__device__ __forceinline__ void load4(const double* p, double v[4]) {
+  const double2 x = *reinterpret_cast<const double2*>(p), y = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = x.x;
+  v[1] = x.y;
+  v[2] = y.x;
+  v[3] = y.y;
+}
+
 // Adjoint traces of every face of the block's elements (at = alpha_f L_f^T l_p, bt = beta_f L_f^T
 // (n_f . l_v)), written to the element's own rows and, for interior faces, pushed into the
 // neighbour's inbox at the neighbour's face-node index of each node (the correspondence codes of
@@ -100,44 +116,52 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
     sV[i] = nf[0] * sL[(1 * Np + n) * 32 + c] + nf[32] * sL[(2 * Np + n) * 32 + c] + nf[64] * sL[(3 * Np + n) * 32 + c];
   }
   __syncthreads();
-  // half-warp per (face, column) item, lanes over the face's nodes: the element's own rows and the
-  // neighbour's inbox row are written as one 64-byte segment each
+  // half-warp per (face, group of four columns) item, lanes over the face's nodes: each LIFT^T entry
+  // a lane reads serves four columns, whose lambda values come in one vector load per node; the
+  // element's own rows and the neighbour's inbox row are written as one 64-byte segment each
   constexpr int NJ = (Nfp + 15) / 16;
   const int hw = threadIdx.x >> 4, lane16 = threadIdx.x & 15, nhw = blockDim.x >> 4;
-  for (int item = hw; item < 4 * 32; item += nhw) {
-    const int f = item >> 5, c = item & 31;
-    const int64_t s = blk * 32 + c;
-    real* out = own + s * (8 * NFPP) + f * 2 * NFPP;
-    const bool valid = (meta[s] & kMetaValid) != 0;
-    const real alpha = sC[(12 + f) * 32 + c], beta = sC[(16 + f) * 32 + c];
-    const uint8_t info = finfo[s * 4 + f];
+  for (int item = hw; item < 4 * 8; item += nhw) {
+    const int f = item >> 3, c0 = (item & 7) * 4;
     const real* vf = sV + f * Np * 32;
 #pragma unroll
     for (int t = 0; t < NJ; ++t) {
       const int j = lane16 + 16 * t;
       if (j >= Nfp) continue;
-      if (!valid) {
-        out[j] = real(0);
-        out[NFPP + j] = real(0);
-        continue;
-      }
-      const real* row = Lt + int64_t(f * Nfp + j) * NPa;
-      real ap = 0, av = 0;
+      real ap[4] = {0, 0, 0, 0}, av[4] = {0, 0, 0, 0};
 #pragma unroll 4
       for (int n = 0; n < Np; ++n) {
-        const real l = STAGE_LT ? sLt[n * (4 * Nfp) + f * Nfp + j] : row[n];
-        ap += l * sL[(0 * Np + n) * 32 + c];
-        av += l * vf[n * 32 + c];
+        const real l = STAGE_LT ? sLt[n * (4 * Nfp) + f * Nfp + j] : Lt[int64_t(f * Nfp + j) * NPa + n];
+        real lp[4], lv[4];
+        load4(sL + n * 32 + c0, lp);
+        load4(vf + n * 32 + c0, lv);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ap[u] += l * lp[u];
+          av[u] += l * lv[u];
+        }
       }
-      const real a = alpha * ap, b = beta * av;
-      out[j] = a;
-      out[NFPP + j] = b;
-      if (finfo_bc(info) == 0) {
-        const int64_t s2 = nbr[s * 4 + f];
-        const int j2 = perm[finfo_perm(info) * 32 + j];
-        real* x = inbox + s2 * (8 * NFPP) + finfo_face(info) * 2 * NFPP;
-        x[j2] = a;
-        x[NFPP + j2] = b;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u;
+        const int64_t s = blk * 32 + c;
+        real* out = own + s * (8 * NFPP) + f * 2 * NFPP;
+        if (!(meta[s] & kMetaValid)) {
+          out[j] = real(0);
+          out[NFPP + j] = real(0);
+          continue;
+        }
+        const real a = sC[(12 + f) * 32 + c] * ap[u], b = sC[(16 + f) * 32 + c] * av[u];
+        out[j] = a;
+        out[NFPP + j] = b;
+        const uint8_t info = finfo[s * 4 + f];
+        if (finfo_bc(info) == 0) {
+          const int64_t s2 = nbr[s * 4 + f];
+          const int j2 = perm[finfo_perm(info) * 32 + j];
+          real* x = inbox + s2 * (8 * NFPP) + finfo_face(info) * 2 * NFPP;
+          x[j2] = a;
+          x[NFPP + j2] = b;
+        }
       }
     }
   }
