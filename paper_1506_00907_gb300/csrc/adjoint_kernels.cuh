@@ -27,13 +27,15 @@ namespace ridg {
 // One block per 32 element slots (one column block of the field layout).  The block's lambda tile
 // is staged in shared memory, [4][Np][32]: thread (row, column c) reads row entries of consecutive
 // columns (no bank conflicts), and the operator rows it multiplies by are the same for the whole
-// warp (broadcast loads).
+// warp (broadcast loads).  The tiles are fetched with asynchronous copies (global to shared
+// without a register round trip, all in flight at once); the caller commits and waits for them.
 template <int N, typename real>
 __device__ __forceinline__ void load_lambda_tile(const real* __restrict__ lam, real* sL, int64_t blk) {
   using O = Order<N>;
-  constexpr int Np = O::Np;
-  const real* src = lam + blk * 4 * Np * 32;
-  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) sL[i] = src[i];
+  constexpr int CH = 4 * O::Np * 32 * int(sizeof(real)) / 16;  // 16-byte chunks of the contiguous tile
+  const char* src = reinterpret_cast<const char*>(lam + blk * 4 * O::Np * 32);
+  char* dst = reinterpret_cast<char*>(sL);
+  for (int i = threadIdx.x; i < CH; i += blockDim.x) cp_async_bytes16(dst + 16 * i, src + 16 * i);
 }
 
 // per-column coefficients staged in shared memory, [k][32]: lanes of consecutive columns read
@@ -101,14 +103,16 @@ __global__ void adj_traces_kernel(const real* __restrict__ lam, real* __restrict
   if constexpr (STAGE_LT)
     for (int i = threadIdx.x; i < 4 * Nfp * Np; i += blockDim.x) {
       const int fj = i / Np, n = i - fj * Np;
-      sLt[n * (4 * Nfp) + fj] = Lt[int64_t(fj) * NPa + n];
+      cp_async_small<sizeof(real)>(sLt + n * (4 * Nfp) + fj, Lt + int64_t(fj) * NPa + n);
     }
+  cp_async_commit();
   for (int i = threadIdx.x; i < kAdjTc * 32; i += blockDim.x) {
     const int k = i >> 5, c = i & 31;
     const int64_t s = blk * 32 + c;
     const double* g = geo + s * kGeo;
     sC[i] = k < 12 ? real(g[9 + k]) : real(-0.5 * g[21 + (k & 3)]) * mat[s * kMat + (k < 16 ? 0 : 1)];
   }
+  cp_async_wait_all();
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) {
     const int f = i / (Np * 32), r = i - f * (Np * 32), n = r >> 5, c = r & 31;
@@ -205,6 +209,12 @@ __global__ void __launch_bounds__(256, N <= 4 ? 4 : 2) adj_rhs_kernel(real* lam,
   int* sBc = sInv + Np * 3;                              // [4][32]: boundary kind of each face
   const int64_t blk = blockIdx.x;
   load_lambda_tile<N, real>(lam, sL, blk);
+  for (int i = threadIdx.x; i < 32 * 8 * NFPP; i += blockDim.x) {
+    const int c = i / (8 * NFPP), r = i - c * (8 * NFPP);
+    cp_async_small<sizeof(real)>(sOwn + c * OS + r, own + (blk * 32) * (8 * NFPP) + i);
+    cp_async_small<sizeof(real)>(sIn + c * OS + r, inbox + (blk * 32) * (8 * NFPP) + i);
+  }
+  cp_async_commit();
   for (int i = threadIdx.x; i < kAdjRc * 32; i += blockDim.x) {
     const int k = i >> 5, c = i & 31;
     const int64_t s = blk * 32 + c;
@@ -212,11 +222,6 @@ __global__ void __launch_bounds__(256, N <= 4 ? 4 : 2) adj_rhs_kernel(real* lam,
     sC[i] = k < 21 ? real(geo[s * kGeo + k]) : mat[s * kMat + (k < 23 ? k - 21 : k - 20)];
   }
   for (int i = threadIdx.x; i < 4 * 32; i += blockDim.x) sBc[i] = finfo_bc(finfo[(blk * 32 + (i & 31)) * 4 + (i >> 5)]);
-  for (int i = threadIdx.x; i < 32 * 8 * NFPP; i += blockDim.x) {
-    const int c = i / (8 * NFPP), r = i - c * (8 * NFPP);
-    sOwn[c * OS + r] = own[(blk * 32) * (8 * NFPP) + i];
-    sIn[c * OS + r] = inbox[(blk * 32) * (8 * NFPP) + i];
-  }
   for (int m = threadIdx.x; m < Np; m += blockDim.x) {
     int cnt = 0;
     for (int f = 0; f < 4; ++f)
@@ -224,6 +229,7 @@ __global__ void __launch_bounds__(256, N <= 4 ? 4 : 2) adj_rhs_kernel(real* lam,
         if (fmask[f * 32 + jf] == m && cnt < 3) sInv[m * 3 + cnt++] = f * 32 + jf;
     for (; cnt < 3; ++cnt) sInv[m * 3 + cnt] = -1;
   }
+  cp_async_wait_all();
   __syncthreads();
   // thread per (row pair, column): the rows r and r + H of one column share every lambda value they
   // read (FP32; FP64 takes one row per thread, for its registers)
