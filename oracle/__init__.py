@@ -26,7 +26,9 @@ Galerkin simulations for reverse-time migration on GPU clusters"):
   receiver data in time.
 * ``adjoint`` -- the least-squares trace misfit and its gradient with respect to the
   per-element velocity (discrete adjoint of the single-rate scheme; the operator is
-  assembled from ``dg_rhs`` and transposed as a sparse matrix).
+  assembled from ``dg_rhs`` and transposed as a sparse matrix; with several rate levels,
+  reverse accumulation over the fine steps of Algorithm 1, their matrices assembled from
+  ``mrab``).
 
 Every function is FP64 and follows the paper's steps in the paper's order; matrix
 products from numpy serve as single steps.  Readings of places where the paper is

@@ -25,6 +25,19 @@ discrete adjoint.  Readings (the paper has no gradient, so each is a definition)
 
 The operator A is assembled column by column from this package's own right-hand side
 (``dg_rhs.rhs``) and A^T is its sparse transpose: no transposed operator is derived by hand.
+
+Several rate levels (``misfit_gradient_levels``): the scheme is Algorithm 1 with the levels
+frozen as well.  One fine step of it (right-hand sides of the active elements, Eq. updateAB for
+the levels that finish, Eq. updateABcoarse traces for their coarse neighbours) is an affine map
+Z' = F_tau Z + (source) of the full state Z = (fields q, stored face traces, three right-hand-side
+histories); F_tau depends on tau only through tau mod 2^{L-1}.  Its matrix is assembled column
+by column from ``MRAB.fine_step`` itself, and so is B_tau, the response of Z' to the pressure
+right-hand side computed in the step.  Velocity enters a fine step only through the pressure rows
+of that right-hand side, (A q)_p of element k scaling with c_k^2, so reverse accumulation gives
+    mu_T = dJ/dZ_T,   mu_tau = F_tau^T mu_{tau+1} + dJ/dZ_tau,
+    dJ/dc_k = sum_tau (2/c_k) (B_tau^T mu_{tau+1})_{p,k} . (A q_tau)_{p,k}   (k active at tau),
+with dJ/dZ nonzero at the global steps only.  With one level this is the recursion above, written
+over the state instead of q alone.
 """
 
 from __future__ import annotations
@@ -108,16 +121,15 @@ def _receivers(geo, rec_xyz):
 
 
 def shot_misfit(prob, c, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, observed, keep_states=False):
-    """Forward single-rate run with velocity c (frozen tau, level and step) and its misfit."""
-    if prob.n_levels != 1:
-        raise ValueError("the gradient is defined for one rate level")
+    """Forward run (Algorithm 1 with the problem's levels) with velocity c (frozen tau, levels and
+    step) and its misfit; ``keep_states`` keeps q at the global steps."""
     geo = frozen_geometry(prob.geo, c)
     n_global = int(np.ceil(t_final / prob.dt_global - 1e-9))
     ks, rs = geo.locate(source_xyz)
     if ks < 0:
         raise ValueError("source outside the mesh")
     rec = _receivers(geo, rec_xyz)
-    S = MRAB(geo, prob.levels, 1, prob.dt_local, +1)
+    S = MRAB(geo, prob.levels, prob.n_levels, prob.dt_local, +1)
     S.injections = [(ks, geo.source_weights(ks, rs),
                      lambda tau: float(ricker(tau * prob.dt_local, f0, t_peak, amplitude)))]
     tr = np.zeros((len(rec), n_global + 1))
@@ -133,7 +145,9 @@ def shot_misfit(prob, c, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, ob
 
 
 def misfit_gradient(prob, c, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, observed):
-    """(J, dJ/dc [K]) by the discrete adjoint above."""
+    """(J, dJ/dc [K]) by the discrete adjoint above (one rate level)."""
+    if prob.n_levels != 1:
+        raise ValueError("misfit_gradient is the single-rate adjoint; use misfit_gradient_levels")
     fwd = shot_misfit(prob, c, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, observed, keep_states=True)
     geo = frozen_geometry(prob.geo, c)
     K, Np = geo.K, geo.ref.Np
@@ -174,3 +188,99 @@ def misfit_gradient(prob, c, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final
         prod = (lam[n + 1] * dAq).reshape(K, 4, Np)[:, 0].sum(axis=1)
         grad -= (2.0 / geo.c) * prod
     return fwd.misfit, grad
+
+
+# ---------------------------------------------------------------- several rate levels
+def _get_state(S: MRAB) -> np.ndarray:
+    return np.concatenate([S.q.ravel(), S.qf.ravel(), S.hist.ravel()])
+
+
+def _set_state(S: MRAB, z: np.ndarray) -> None:
+    nq, nf = S.q.size, S.qf.size
+    S.q = z[:nq].reshape(S.q.shape).copy()
+    S.qf = z[nq:nq + nf].reshape(S.qf.shape).copy()
+    S.hist = z[nq + nf:].reshape(S.hist.shape).copy()
+
+
+def _fine_step_matrices(geo, prob, tau):
+    """F (state to state) and B (pressure right-hand side of the active elements to state) of the
+    source-free fine step at tau, both assembled from MRAB.fine_step on unit vectors; ``cols``
+    lists the (element, node) of each column of B."""
+    S = MRAB(geo, prob.levels, prob.n_levels, prob.dt_local, +1)
+    n = _get_state(S).size
+    F = np.zeros((n, n))
+    for i in range(n):
+        z = np.zeros(n)
+        z[i] = 1.0
+        _set_state(S, z)
+        S.tau = tau
+        S.fine_step()
+        F[:, i] = _get_state(S)
+    active = S.active(tau)
+    Np = geo.ref.Np
+    cols = [(int(k), j) for k in active for j in range(Np)]
+    B = np.zeros((n, len(cols)))
+    for ci, (k, j) in enumerate(cols):
+        _set_state(S, np.zeros(n))
+        S.tau = tau
+        w = np.zeros(Np)
+        w[j] = 1.0
+        S.injections = [(k, w, lambda t: 1.0)]
+        S.fine_step()
+        B[:, ci] = _get_state(S)
+    S.injections = []
+    return sp.csr_matrix(F), sp.csr_matrix(B), cols
+
+
+def misfit_gradient_levels(prob, c, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, observed):
+    """(J, dJ/dc [K]) for any number of rate levels, by reverse accumulation over the fine steps
+    of Algorithm 1 (module docstring).  The state matrices are dense during assembly: for small
+    meshes only."""
+    geo = frozen_geometry(prob.geo, c)
+    K, Np = geo.K, geo.ref.Np
+    nl = 2 ** (prob.n_levels - 1)
+    n_global = int(np.ceil(t_final / prob.dt_global - 1e-9))
+    T = n_global * nl
+    ks, rs = geo.locate(source_xyz)
+    if ks < 0:
+        raise ValueError("source outside the mesh")
+    rec = _receivers(geo, rec_xyz)
+    # forward run, keeping each fine step's state and the source-free pressure right-hand side
+    S = MRAB(geo, prob.levels, prob.n_levels, prob.dt_local, +1)
+    S.injections = [(ks, geo.source_weights(ks, rs),
+                     lambda tau: float(ricker(tau * prob.dt_local, f0, t_peak, amplitude)))]
+    Z, R = [], []
+    tr = np.zeros((len(rec), n_global + 1))
+    tr[:, 0] = [row @ S.q[k, 0] for k, row in rec]
+    for tau in range(T):
+        Z.append(_get_state(S))
+        act = S.active(tau)
+        R.append((act, rhs(act, S.q, S.qf, geo)[:, 0].copy() if len(act) else None))
+        S.fine_step()
+        if (tau + 1) % nl == 0:
+            tr[:, (tau + 1) // nl] = [row @ S.q[k, 0] for k, row in rec]
+    J = 0.5 * prob.dt_global * float(np.sum((tr - observed) ** 2))
+    res = tr - observed
+    n = Z[0].size
+
+    def dJdZ(tau):
+        out = np.zeros(n)
+        if tau % nl == 0:
+            q = out[:K * 4 * Np].reshape(K, 4, Np)
+            for r, (k, row) in enumerate(rec):
+                q[k, 0] += prob.dt_global * res[r, tau // nl] * row
+        return out
+
+    mats = {p: _fine_step_matrices(geo, prob, p) for p in range(nl)}
+    grad = np.zeros(K)
+    mu = dJdZ(T)
+    for tau in range(T - 1, -1, -1):
+        F, B, cols = mats[tau % nl]
+        act, r = R[tau]
+        if r is not None:
+            v = B.T @ mu
+            pos = {int(k): i for i, k in enumerate(act)}
+            for ci, (k, j) in enumerate(cols):
+                grad[k] += (2.0 / geo.c[k]) * v[ci] * r[pos[k], j]
+        mu = F.T @ mu + dJdZ(tau)
+    return J, grad

@@ -27,6 +27,7 @@ from .workloads import (  # noqa: F401
     tiny_layered_rtm,
     adjoint_box,
     adjoint_box_small,
+    adjoint_box_two_level,
     adjoint_observed_velocity,
     serving_model,
     serving_requests,
