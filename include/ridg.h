@@ -277,14 +277,19 @@ int ridg_eval_adjoint_rhs(ridg_solver* s, const double* lam, double* out);
  * (n = 0 .. n_t-1, n_t from ridg_trace_len) and the misfit
  *   J = 1/2 Dt sum_n sum_r (y_r^n - observed_r^n)^2      (observed: host double [nrec][n_t], nrec >= 1).
  * Keeps n_checkpoints (<= 0 selects 16) snapshots of the state for ridg_misfit_backward.
- * traces_out (host double [nrec][n_t]) may be NULL.  Errors: RIDG_E_INVALID_ARG (more than one rate
- * level, missing receivers or data), RIDG_E_NOT_FOUND, RIDG_E_UNSTABLE. */
+ * traces_out (host double [nrec][n_t]) may be NULL.  Any number of rate levels (Algorithm 1; the
+ * global step is Dt).  Errors: RIDG_E_INVALID_ARG (missing receivers or data), RIDG_E_NOT_FOUND,
+ * RIDG_E_UNSTABLE. */
 int ridg_misfit_forward(ridg_solver* s, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
                         const double* observed, int32_t n_checkpoints, double* misfit, double* traces_out);
 /* grad (host double [K]) = dJ/dc of the last ridg_misfit_forward: the adjoint recursion
  *   lambda^m = lambda^{m+1} + Dt A^T sum_s a_s lambda^{m+1+s} - Dt sum_r (y_r^m - d_r^m) l(x_r),
  * run backward from m = n_t-1, recomputing the forward states segment by segment from the
  * checkpoints, with dJ/dc_k = -(2/c_k) sum_n lambda^{n+1}_p,k . (A (q^{n+1} - q^n source-free))_p,k.
+ * With several rate levels the same gradient comes from reverse accumulation over the fine steps of
+ * Algorithm 1 (the transposed trace pushes, updates and right-hand sides of each fine step; the
+ * levels, the time step and tau stay frozen); each segment's right-hand sides are kept on the device
+ * (segment length x NL field arrays).
  * Leaves the solver's fields at the first checkpoint's segment (set the state again before stepping).
  * May be called again for the same forward run.  RIDG_E_INVALID_ARG without a valid forward run
  * (none yet, or the velocity changed since). */

@@ -1,0 +1,268 @@
+// Discrete adjoint of the multi-rate scheme as the library runs it (reverse accumulation).
+//
+// Forward fine step tau (Algorithm 1 in the library's fused form), for every element k of an
+// active level l (stride d, step h = d dt):
+//   r = A_k(q_k, x_k)              x_k: the element's inbox slot tau mod 3 (its neighbours' traces)
+//   ring: r_new <- r (the two older right-hand sides r1, r2 stay)
+//   q_k <- q_k + h (a1 r + a2 r1 + a3 r2)                       (Eq. updateAB, at the step's start)
+//   traces of q_k pushed into the neighbours' inbox slot (tau + d) mod 3, and, for elements with a
+//   finer neighbour, traces of q_k + h (b1 r + b2 r1 + b3 r2) into slot (tau + d/2) mod 3
+//   (Eq. updateABcoarse).
+// Its reverse, per fine step from the last to the first, with mu = dJ/d(state):
+//   pull:    the adjoint of each pushed trace is taken (and cleared) from the neighbour's inbox
+//            adjoint; mu_q' = mu_q + T^T g_full, mu_h = T^T g_half; mu_q <- mu_q' + mu_h and the
+//            ring adjoints gain h (a_s mu_q' + b_s mu_h) (adjml_pull_kernel);
+//   rhs:     mu_r = the ring adjoint of r_new (then cleared); the volume transposes and the
+//            element's own face traces go to mu_q, and the weights of the neighbour's traces to the
+//            element's inbox adjoint at slot tau mod 3 (adjml_traces_kernel, adjml_rhs_kernel);
+//   gradient: dJ/dc_k += (2/c_k) mu_r,p . (A q)_p, with A q the saved right-hand side less the
+//            source term (in adjml_rhs_kernel).
+// Every entry has one writer per pass: an element writes its own rows and clears only the inbox
+// entries it filled in the forward run.  Layouts are the solver's (fields [K/32][4][Np][32], ring
+// [3][fields], inboxes [3 slots][n_slots][4 faces][2][NFPP]); the face terms are those of the
+// single-rate kernels (adjoint_kernels.cuh).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "adjoint_kernels.cuh"
+#include "dispatch.hpp"
+
+namespace ridg {
+
+
+template <typename real>
+__device__ __forceinline__ int adjml_level(const AdjMrArgs<real>& A, int64_t slot0) {
+  int lev = 0;
+  for (int l = 0; l < A.n_levels; ++l)
+    if (slot0 >= A.level_begin[l]) lev = l;
+  return lev;
+}
+
+// faces holding each node: sInv[m * 3 + i] = f * 32 + jf (or -1)
+template <int N>
+__device__ __forceinline__ void adjml_inverse_fmask(const int* __restrict__ fmask, int* sInv) {
+  using O = Order<N>;
+  for (int m = threadIdx.x; m < O::Np; m += blockDim.x) {
+    int cnt = 0;
+    for (int f = 0; f < 4; ++f)
+      for (int jf = 0; jf < O::Nfp; ++jf)
+        if (fmask[f * 32 + jf] == m && cnt < 3) sInv[m * 3 + cnt++] = f * 32 + jf;
+    for (; cnt < 3; ++cnt) sInv[m * 3 + cnt] = -1;
+  }
+}
+
+// Reverse of the trace pushes and of the update: thread per (node, column) of the block's slots.
+template <int N, typename real>
+__global__ void adjml_pull_kernel(AdjMrArgs<real> A) {
+  using O = Order<N>;
+  constexpr int Np = O::Np, NFPP = O::NFPP;
+  __shared__ int sInv[Np * 3];
+  const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * 32;
+  const int64_t blk = slot0 >> 5;
+  const int lev = adjml_level(A, slot0);
+  const real h = A.h[lev];
+  const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
+  const int64_t tsz = A.n_slots * (8 * NFPP);
+  real* rn = A.mu_ring + A.ring_new[lev] * qsize;
+  real* r1 = A.mu_ring + A.ring_old1[lev] * qsize;
+  real* r2 = A.mu_ring + A.ring_old2[lev] * qsize;
+  real* xfull = A.mu_in + A.slot_full[lev] * tsz;
+  real* xhalf = A.mu_in + A.slot_half[lev] * tsz;
+  adjml_inverse_fmask<N>(A.fmask, sInv);
+  __syncthreads();
+  for (int item = threadIdx.x; item < Np * 32; item += blockDim.x) {
+    const int m = item >> 5, c = item & 31;
+    const int64_t s = slot0 + c;
+    const int meta = A.meta[s];
+    if (!(meta & kMetaValid)) continue;
+    const bool half = (meta & kMetaHalf) != 0;
+    const double* g = A.geo + s * kGeo;
+    real gq[4] = {0, 0, 0, 0}, hq[4] = {0, 0, 0, 0};
+    for (int k = 0; k < 3; ++k) {
+      const int e = sInv[m * 3 + k];
+      if (e < 0) break;
+      const int f = e >> 5, jf = e & 31;
+      const uint8_t info = A.finfo[s * 4 + f];
+      if (finfo_bc(info) != 0) continue;  // boundary faces push nothing
+      const int64_t s2 = A.nbr[s * 4 + f];
+      const int j2 = A.perm[finfo_perm(info) * 32 + jf];
+      const int64_t at = s2 * (8 * NFPP) + finfo_face(info) * 2 * NFPP;
+      // the pushed pair is (p, -n.v) in this element's normal: its adjoint goes to p and to v
+      const real gp = xfull[at + j2], gv = xfull[at + NFPP + j2];
+      xfull[at + j2] = real(0);
+      xfull[at + NFPP + j2] = real(0);
+      gq[0] += gp;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) gq[1 + i] -= real(g[9 + 3 * f + i]) * gv;
+      if (half) {
+        const real hp = xhalf[at + j2], hv = xhalf[at + NFPP + j2];
+        xhalf[at + j2] = real(0);
+        xhalf[at + NFPP + j2] = real(0);
+        hq[0] += hp;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) hq[1 + i] -= real(g[9 + 3 * f + i]) * hv;
+      }
+    }
+#pragma unroll
+    for (int fld = 0; fld < 4; ++fld) {
+      const int64_t at = ((blk * 4 + fld) * Np + m) * 32 + c;
+      const real mq = A.mu[at] + gq[fld], mh = hq[fld];
+      A.mu[at] = mq + mh;
+      rn[at] += h * (real(AB::a1) * mq + real(AB::b1) * mh);
+      r1[at] += h * (real(AB::a2) * mq + real(AB::b2) * mh);
+      r2[at] += h * (real(AB::a3) * mq + real(AB::b3) * mh);
+    }
+  }
+}
+
+// Adjoint traces of mu_r (the ring adjoint of this step's right-hand side): per face node the
+// weights of the jumps, w_p = -tau_p at + bt and w_v = at - tau_v bt with at = alpha_f L_f^T mu_r,p
+// and bt = beta_f L_f^T (n_f . mu_r,v).  The neighbour's traces receive (w_p, w_v) in the element's
+// inbox adjoint; the element's own traces receive minus them, with the boundary ghosts folded in,
+// in the scratch rows (thread per (face, node, column)).
+template <int N, typename real>
+__global__ void adjml_traces_kernel(AdjMrArgs<real> A) {
+  using O = Order<N>;
+  constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
+  extern __shared__ __align__(16) unsigned char smem_adjml[];
+  real* sL = reinterpret_cast<real*>(smem_adjml);  // [4][Np][32]
+  const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * 32;
+  const int64_t blk = slot0 >> 5;
+  const int lev = adjml_level(A, slot0);
+  const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
+  const real* src = A.mu_ring + A.ring_new[lev] * qsize + blk * 4 * Np * 32;
+  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) sL[i] = src[i];
+  __syncthreads();
+  real* xin = A.mu_in + int64_t(A.slot_read) * A.n_slots * (8 * NFPP);
+  for (int item = threadIdx.x; item < 4 * Nfp * 32; item += blockDim.x) {
+    const int c = item & 31, fj = item >> 5, f = fj / Nfp, j = fj - f * Nfp;
+    const int64_t s = slot0 + c;
+    real* ow = A.own + s * (8 * NFPP) + f * 2 * NFPP;
+    if (!(A.meta[s] & kMetaValid)) {
+      ow[j] = real(0);
+      ow[NFPP + j] = real(0);
+      continue;
+    }
+    const double* g = A.geo + s * kGeo;
+    const real* mt = A.mat + s * kMat;
+    const real* row = A.Lt + int64_t(fj) * A.NPa;
+    const real n0 = real(g[9 + 3 * f]), n1 = real(g[10 + 3 * f]), n2 = real(g[11 + 3 * f]);
+    real ap = 0, av = 0;
+    for (int n = 0; n < Np; ++n) {
+      const real l = row[n];
+      ap += l * sL[(0 * Np + n) * 32 + c];
+      av += l * (n0 * sL[(1 * Np + n) * 32 + c] + n1 * sL[(2 * Np + n) * 32 + c] + n2 * sL[(3 * Np + n) * 32 + c]);
+    }
+    const real a = real(-0.5 * g[21 + f]) * mt[0] * ap, b = real(-0.5 * g[21 + f]) * mt[1] * av;
+    const real taup = mt[3 + f], tauv = mt[7 + f];
+    const real wp = -taup * a + b, wv = a - tauv * b;
+    const int bc = finfo_bc(A.finfo[s * 4 + f]);
+    real op = 0, ov = 0;
+    if (bc == 0) {
+      op = -wp;
+      ov = -wv;
+      real* x = xin + s * (8 * NFPP) + f * 2 * NFPP;
+      x[j] += wp;
+      x[NFPP + j] += wv;
+    } else if (bc == 1) {  // free surface: jp = -2 p-, jv = 0
+      op = real(-2) * wp;
+    } else if (bc == 2) {  // transparent: jp = -p-, jv = -vn-
+      op = -wp;
+      ov = -wv;
+    } else {  // rigid wall: jp = 0, jv = -2 vn-
+      ov = real(-2) * wv;
+    }
+    ow[j] = op;
+    ow[NFPP + j] = ov;
+  }
+}
+
+// mu_q += (volume transposes) mu_r + the own-trace weights at the face nodes; the ring adjoint of
+// this step's right-hand side is cleared (thread per (node, column); with 256 threads a thread
+// keeps one column).  acc[slot] += sum_m mu_r,p (r_p - F w)_m, the source-free right-hand side,
+// summed in a fixed order (eight warp partial sums, added in FP64).
+template <int N, typename real>
+__global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
+  using O = Order<N>;
+  constexpr int Np = O::Np, NFPP = O::NFPP;
+  extern __shared__ __align__(16) unsigned char smem_adjml[];
+  real* sL = reinterpret_cast<real*>(smem_adjml);  // [4][Np][32]
+  int* sInv = reinterpret_cast<int*>(sL + 4 * Np * 32);
+  const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * 32;
+  const int64_t blk = slot0 >> 5;
+  const int lev = adjml_level(A, slot0);
+  const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
+  real* rnew = A.mu_ring + A.ring_new[lev] * qsize + blk * 4 * Np * 32;
+  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) sL[i] = rnew[i];
+  adjml_inverse_fmask<N>(A.fmask, sInv);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) rnew[i] = real(0);
+  __shared__ double part[8][32];
+  real gsum = 0;
+  for (int item = threadIdx.x; item < Np * 32; item += blockDim.x) {
+    const int m = item >> 5, c = item & 31;
+    const int64_t s = slot0 + c;
+    if (!(A.meta[s] & kMetaValid)) continue;
+    {
+      real r = A.rsaved[((blk * 4 + 0) * Np + m) * 32 + c];
+      if (s == A.src_slot) r -= A.F * A.w_src[m];
+      gsum += sL[(0 * Np + m) * 32 + c] * r;
+    }
+    const double* g = A.geo + s * kGeo;
+    const real* mt = A.mat + s * kMat;
+    real dp[3] = {0, 0, 0}, dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+    const real* dm = A.Dt4 + int64_t(m) * Np * 4;
+    for (int n = 0; n < Np; ++n) {
+      real d[3];
+      load_d3(dm + 4 * n, d);
+      const real lp = sL[(0 * Np + n) * 32 + c];
+      const real lv[3] = {sL[(1 * Np + n) * 32 + c], sL[(2 * Np + n) * 32 + c], sL[(3 * Np + n) * 32 + c]};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        dp[j] += d[j] * lp;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) dv[i][j] += d[j] * lv[i];
+      }
+    }
+    real op = 0, ov[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const real gij = real(g[3 * i + j]);
+        op -= mt[1] * gij * dv[i][j];
+        ov[i] -= mt[0] * gij * dp[j];
+      }
+    for (int k = 0; k < 3; ++k) {
+      const int e = sInv[m * 3 + k];
+      if (e < 0) break;
+      const int f = e >> 5, jf = e & 31;
+      const real* ow = A.own + s * (8 * NFPP) + f * 2 * NFPP;
+      op += ow[jf];
+#pragma unroll
+      for (int i = 0; i < 3; ++i) ov[i] += real(g[9 + 3 * f + i]) * ow[NFPP + jf];
+    }
+    A.mu[((blk * 4 + 0) * Np + m) * 32 + c] += op;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) A.mu[((blk * 4 + 1 + i) * Np + m) * 32 + c] += ov[i];
+  }
+  part[threadIdx.x >> 5][threadIdx.x & 31] = double(gsum);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = part[0][threadIdx.x];
+#pragma unroll
+    for (int k = 1; k < 8; ++k) t += part[k][threadIdx.x];
+    A.acc[slot0 + threadIdx.x] += t;
+  }
+}
+
+template <int N, typename real>
+constexpr size_t adjml_traces_smem() {
+  return size_t(4) * Order<N>::Np * 32 * sizeof(real);
+}
+template <int N, typename real>
+constexpr size_t adjml_rhs_smem() {
+  return size_t(4) * Order<N>::Np * 32 * sizeof(real) + size_t(Order<N>::Np) * 3 * sizeof(int);
+}
+
+}  // namespace ridg

@@ -6,6 +6,40 @@
 
 namespace ridg {
 
+// Arguments of one reverse fine step of the multi-rate adjoint (adjoint_mr_kernels.cuh): the
+// adjoint state, the active slots and each level's ring and trace-slot indices at that step.
+template <typename real>
+struct AdjMrArgs {
+  real* mu;        // [fields]
+  real* mu_ring;   // [3][fields]
+  real* mu_in;     // [3][n_slots][8 NFPP]
+  real* own;       // [n_slots][8 NFPP] scratch: the element's own-trace weights of this step
+  int64_t slot_lo, n_slots;
+  int64_t level_begin[kMaxLevels + 1];
+  int n_levels;
+  int ring_new[kMaxLevels], ring_old1[kMaxLevels], ring_old2[kMaxLevels];
+  real h[kMaxLevels];
+  int slot_read;
+  int slot_full[kMaxLevels], slot_half[kMaxLevels];
+  const double* geo;
+  const real* mat;
+  const int* meta;
+  const real* Dt4;
+  const real* Lt;
+  int NPa;
+  const int* fmask;
+  const int* nbr;
+  const uint8_t* finfo;
+  const int* perm;
+  // gradient: the forward right-hand side of this step (saved, source included), the source slot,
+  // its projected Dirac and amplitude at this step, and the per-slot sums
+  const real* rsaved;
+  int64_t src_slot;
+  const real* w_src;
+  real F;
+  double* acc;
+};
+
 template <int N, typename real>
 struct Launch {
   static cudaError_t step(const StepArgs<real>& a, int W, cudaStream_t st);
@@ -31,6 +65,8 @@ struct Launch {
   static cudaError_t adj_inject(real* lam, const int* grp, const int* rec_sorted, int n_groups, const int64_t* rec_slot,
                                 const real* rec_row, const double* res, int64_t n_time, int64_t col, double coef,
                                 cudaStream_t st);
+  // one reverse fine step of the multi-rate adjoint over the active slots [a.slot_lo, a.n_slots)
+  static cudaError_t adjml_step(const AdjMrArgs<real>& a, cudaStream_t st);
   // acc[slot] += sum over the pressure nodes of lam_p (q1_p - q0_p - F w), per element slot
   static cudaError_t adj_grad(const real* lam, const real* q1, const real* q0, int64_t n_slots, int64_t src_slot,
                               const real* w_src, double F, double* acc, cudaStream_t st);

@@ -2,6 +2,7 @@
 #include "ridg.h"
 
 #include "adjoint_kernels.cuh"
+#include "adjoint_mr_kernels.cuh"
 #include "aux_kernels.cuh"
 #include "dispatch.hpp"
 #include "step_kernel_tc.cuh"
@@ -121,6 +122,26 @@ cudaError_t Launch<N, real>::adj_inject(real* lam, const int* grp, const int* re
   if (n_groups <= 0) return cudaSuccess;
   adj_inject_kernel<N, real><<<unsigned(n_groups), 64, 0, st>>>(lam, grp, rec_sorted, rec_slot, rec_row, res, n_time,
                                                                  col, coef);
+  return cudaGetLastError();
+}
+
+template <int N, typename real>
+cudaError_t Launch<N, real>::adjml_step(const AdjMrArgs<real>& a, cudaStream_t st) {
+  const int64_t blocks = (a.n_slots - a.slot_lo) / 32;
+  if (blocks <= 0) return cudaSuccess;
+  constexpr size_t sm_t = adjml_traces_smem<N, real>(), sm_r = adjml_rhs_smem<N, real>();
+  static_assert(sm_t <= 227 * 1024 && sm_r <= 227 * 1024, "multi-rate adjoint kernels exceed the shared memory");
+  static const cudaError_t configured = [] {
+    cudaError_t e =
+        cudaFuncSetAttribute(adjml_traces_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_t));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(adjml_rhs_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_r));
+    return e;
+  }();
+  if (configured != cudaSuccess) return configured;
+  adjml_pull_kernel<N, real><<<unsigned(blocks), 256, 0, st>>>(a);
+  adjml_traces_kernel<N, real><<<unsigned(blocks), 256, sm_t, st>>>(a);
+  adjml_rhs_kernel<N, real><<<unsigned(blocks), 256, sm_r, st>>>(a);
   return cudaGetLastError();
 }
 

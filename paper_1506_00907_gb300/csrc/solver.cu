@@ -493,13 +493,11 @@ class Engine final : public ridg_solver {
 
   double misfit_forward(const ridg_source& src, const double* rec, int64_t nrec, double t_final,
                         const double* observed, int n_ckpt, double* traces_host) override {
-    if (L_ != 1)
-      throw Error{RIDG_E_INVALID_ARG, "the misfit gradient needs one rate level (create the solver with n_levels_max = 1)"};
     if (!(t_final > 0.0)) throw Error{RIDG_E_INVALID_ARG, "t_final must be > 0"};
     if (nrec < 1 || !rec || !observed) throw Error{RIDG_E_INVALID_ARG, "receivers and observed traces are required"};
     adj_.ready = false;
     adj_.wav = Wavelet::of(src);
-    const double dt = lv_.dt_local;
+    const double dtl = lv_.dt_local, dt = dtl * double(NL_);  // fine and global step
     const int64_t n_global = int64_t(std::ceil(t_final / dt - 1e-9)), n_t = n_global + 1;
     const int64_t n_ck_max = n_ckpt > 0 ? n_ckpt : 16;
     adj_.n_global = n_global;
@@ -545,14 +543,15 @@ class Engine final : public ridg_solver {
       upload(adj_grp_, grp, st_);
       upload(adj_rec_sorted_, order, st_);
     }
-    adj_.amp.assign(n_global + 1, 0.0);
-    for (int64_t n = 0; n <= n_global; ++n) adj_.amp[n] = double(real(adj_.wav(double(n) * dt)));
+    // the wavelet at every fine step, as the step kernel injects it
+    adj_.amp.assign(n_global * NL_ + 1, 0.0);
+    for (int64_t n = 0; n <= n_global * NL_; ++n) adj_.amp[n] = double(real(adj_.wav(double(n) * dtl)));
     const size_t qb = qsize() * sizeof(real), tb = 3 * trace_slot_elems() * sizeof(real);
     ck_q_.reserve(size_t(adj_.n_ck) * qb);
     ck_ring_.reserve(size_t(adj_.n_ck) * 3 * qb);
     ck_trace_.reserve(size_t(adj_.n_ck) * tb);
     adj_.ck_tau.assign(adj_.n_ck, 0);
-    adj_.ck_count.assign(adj_.n_ck, 0);
+    adj_.ck_count.assign(size_t(adj_.n_ck) * L_, 0);
     DBuf y;
     y.alloc(size_t(nrec) * n_t * sizeof(double));
     zero_wave(w_[0]);
@@ -570,9 +569,9 @@ class Engine final : public ridg_solver {
         RIDG_CUDA(cudaMemcpyAsync(cr, w_[0].ring.p, 3 * qb, cudaMemcpyDeviceToDevice, st_));
         RIDG_CUDA(cudaMemcpyAsync(ct, w_[0].trace.p, tb, cudaMemcpyDeviceToDevice, st_));
         adj_.ck_tau[j] = tau_;
-        adj_.ck_count[j] = ring_count_[0];
+        for (int l = 0; l < L_; ++l) adj_.ck_count[size_t(j) * L_ + l] = ring_count_[l];
       }
-      misfit_step(adj_.wav);
+      for (int64_t sub = 0; sub < NL_; ++sub) misfit_step(adj_.wav);
       sample(dptr<double>(y), n_t, g + 1, nrec);
     }
     stats_.dof_updates_forward = dof_;
@@ -598,6 +597,7 @@ class Engine final : public ridg_solver {
   void misfit_backward(double* grad) override {
     if (!adj_.ready) throw Error{RIDG_E_INVALID_ARG, "no misfit forward run to differentiate (or the velocity changed)"};
     if (!grad) throw Error{RIDG_E_INVALID_ARG, "grad is null"};
+    if (L_ > 1) return misfit_backward_levels(grad);
     const double h = lv_.dt_local;
     const size_t qn = qsize(), qb = qn * sizeof(real), tb = 3 * trace_slot_elems() * sizeof(real);
     const int64_t n_t = adj_.n_global + 1;
@@ -624,7 +624,7 @@ class Engine final : public ridg_solver {
       RIDG_CUDA(cudaMemcpyAsync(w_[0].trace.p, static_cast<char*>(ck_trace_.p) + size_t(j) * tb, tb,
                                 cudaMemcpyDeviceToDevice, st_));
       tau_ = adj_.ck_tau[j];
-      ring_count_[0] = int(adj_.ck_count[j]);
+      ring_count_[0] = int(adj_.ck_count[size_t(j)]);
       RIDG_CUDA(cudaMemcpyAsync(sg(0), w_[0].q.p, qb, cudaMemcpyDeviceToDevice, st_));
       for (int64_t n = a0; n < b0; ++n) {
         misfit_step(adj_.wav);
@@ -654,6 +654,106 @@ class Engine final : public ridg_solver {
     RIDG_CUDA(cudaMemcpyAsync(per_slot.data(), acc.p, acc.bytes, cudaMemcpyDeviceToHost, st_));
     RIDG_CUDA(cudaStreamSynchronize(st_));
     for (int64_t k = 0; k < mesh_.K; ++k) grad[k] = -2.0 / c_[k] * per_slot[ord_.slot_of[k]];
+    for (int64_t k = 0; k < mesh_.K; ++k)
+      if (!std::isfinite(grad[k])) throw Error{RIDG_E_UNSTABLE, "non-finite gradient"};
+  }
+
+  // The gradient on several rate levels: reverse accumulation over the fine steps of the library's
+  // multi-rate scheme (adjoint_mr_kernels.cuh), segment by segment from the checkpoints.  Each
+  // segment is recomputed first, keeping every fine step's new right-hand sides; then its fine
+  // steps are reversed, the receiver residuals entering at the global steps.
+  void misfit_backward_levels(double* grad) {
+    const size_t qn = qsize(), qb = qn * sizeof(real), tsz = trace_slot_elems();
+    const size_t tb = 3 * tsz * sizeof(real);
+    const int64_t n_t = adj_.n_global + 1;
+    const double dtl = lv_.dt_local, dtg = dtl * double(NL_);
+    const int64_t fseg = adj_.seg * NL_;  // fine steps per segment
+    DBuf mu, mring, min, own, rsav, acc;
+    mu.alloc(qb);
+    mring.alloc(3 * qb);
+    min.alloc(3 * tsz * sizeof(real));
+    own.alloc(tsz * sizeof(real));
+    rsav.alloc(size_t(fseg) * qb);
+    acc.alloc(size_t(n_slots_) * sizeof(double));
+    for (DBuf* b : {&mu, &mring, &min, &own, &rsav, &acc}) RIDG_CUDA(cudaMemsetAsync(b->p, 0, b->bytes, st_));
+    AdjMrArgs<real> a{};
+    a.mu = dptr<real>(mu);
+    a.mu_ring = dptr<real>(mring);
+    a.mu_in = dptr<real>(min);
+    a.own = dptr<real>(own);
+    a.n_slots = n_slots_;
+    a.n_levels = L_;
+    for (int l = 0; l <= L_; ++l) a.level_begin[l] = ord_.level_begin[l];
+    a.geo = dptr<const double>(geo_d_);
+    a.mat = dptr<const real>(mat_d_);
+    a.meta = dptr<const int>(meta_d_);
+    a.Dt4 = dptr<const real>(Dt4_d_);
+    a.Lt = dptr<const real>(Lt_d_);
+    a.NPa = NPa_;
+    a.fmask = dptr<const int>(fmask_d_);
+    a.nbr = dptr<const int>(nbr_d_);
+    a.finfo = dptr<const uint8_t>(finfo_d_);
+    a.perm = dptr<const int>(perm_d_);
+    a.src_slot = adj_.src_slot;
+    a.w_src = dptr<const real>(adj_w_);
+    a.acc = dptr<double>(acc);
+    std::vector<int> cnt(size_t(fseg) * L_);  // each level's ring count before each fine step
+    for (int64_t j = adj_.n_ck - 1; j >= 0; --j) {
+      const int64_t g0 = j * adj_.seg, g1 = std::min(g0 + adj_.seg, adj_.n_global);
+      const int64_t t0 = g0 * NL_, t1 = g1 * NL_;
+      RIDG_CUDA(cudaMemcpyAsync(w_[0].q.p, static_cast<char*>(ck_q_.p) + size_t(j) * qb, qb, cudaMemcpyDeviceToDevice,
+                                st_));
+      RIDG_CUDA(cudaMemcpyAsync(w_[0].ring.p, static_cast<char*>(ck_ring_.p) + size_t(j) * 3 * qb, 3 * qb,
+                                cudaMemcpyDeviceToDevice, st_));
+      RIDG_CUDA(cudaMemcpyAsync(w_[0].trace.p, static_cast<char*>(ck_trace_.p) + size_t(j) * tb, tb,
+                                cudaMemcpyDeviceToDevice, st_));
+      tau_ = adj_.ck_tau[j];
+      for (int l = 0; l < L_; ++l) ring_count_[l] = int(adj_.ck_count[size_t(j) * L_ + l]);
+      for (int64_t t = t0; t < t1; ++t) {
+        const int l0 = first_active_level(t);
+        for (int l = 0; l < L_; ++l) cnt[size_t(t - t0) * L_ + l] = ring_count_[l];
+        misfit_step(adj_.wav);
+        for (int l = l0; l <= L_; ++l) {  // the new right-hand sides of the active levels
+          const int64_t b0 = ord_.level_begin[l - 1] / 32, b1 = ord_.level_begin[l] / 32;
+          if (b1 <= b0) continue;
+          const size_t off = size_t(b0) * 4 * Np_ * 32, len = size_t(b1 - b0) * 4 * Np_ * 32;
+          const int rn = cnt[size_t(t - t0) * L_ + (l - 1)] % 3;
+          RIDG_CUDA(cudaMemcpyAsync(dptr<real>(rsav) + size_t(t - t0) * qn + off, dptr<real>(w_[0].ring) + rn * qn + off,
+                                    len * sizeof(real), cudaMemcpyDeviceToDevice, st_));
+        }
+      }
+      for (int64_t t = t1 - 1; t >= t0; --t) {
+        cudaError_t e = dispatch_order(N_, [&](auto NC) {
+          using LN = Launch<decltype(NC)::value, real>;
+          cudaError_t e2 = cudaSuccess;
+          if ((t + 1) % NL_ == 0)  // mu_q += Dt (y - d) l(x_r) at the global step t + 1
+            e2 = LN::adj_inject(dptr<real>(mu), dptr<const int>(adj_grp_), dptr<const int>(adj_rec_sorted_),
+                                int(adj_.n_groups), dptr<const int64_t>(adj_rec_slot_), dptr<const real>(adj_rec_row_),
+                                dptr<const double>(adj_res_), n_t, (t + 1) / NL_, -dtg, st_);
+          if (e2 != cudaSuccess) return e2;
+          a.slot_lo = ord_.level_begin[first_active_level(t) - 1];
+          a.slot_read = mod3(t);
+          for (int l = 1; l <= L_; ++l) {
+            const int64_t d = int64_t(1) << (L_ - l);
+            const int c = cnt[size_t(t - t0) * L_ + (l - 1)];
+            a.ring_new[l - 1] = c % 3;
+            a.ring_old1[l - 1] = (c + 2) % 3;
+            a.ring_old2[l - 1] = (c + 1) % 3;
+            a.h[l - 1] = real(double(d) * dtl);
+            a.slot_full[l - 1] = mod3(t + d);
+            a.slot_half[l - 1] = d >= 2 ? mod3(t + d / 2) : mod3(t + 2);
+          }
+          a.rsaved = dptr<const real>(rsav) + size_t(t - t0) * qn;
+          a.F = real(adj_.amp[t]);
+          return LN::adjml_step(a, st_);
+        });
+        if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
+      }
+    }
+    std::vector<double> per_slot(static_cast<size_t>(n_slots_));
+    RIDG_CUDA(cudaMemcpyAsync(per_slot.data(), acc.p, acc.bytes, cudaMemcpyDeviceToHost, st_));
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    for (int64_t k = 0; k < mesh_.K; ++k) grad[k] = 2.0 / c_[k] * per_slot[ord_.slot_of[k]];
     for (int64_t k = 0; k < mesh_.K; ++k)
       if (!std::isfinite(grad[k])) throw Error{RIDG_E_UNSTABLE, "non-finite gradient"};
   }

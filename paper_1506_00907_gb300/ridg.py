@@ -309,7 +309,7 @@ class Solver:
     def misfit_forward(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, observed, n_checkpoints=16,
                        wavelet=None, wavelet_dt=None):
         """(J, traces) of a forward run against observed traces [nrec, n_t]; keeps checkpoints for
-        ``misfit_backward`` (one rate level only)."""
+        ``misfit_backward`` (any number of rate levels)."""
         src, _keep = _source(source_xyz, f0, t_peak, amplitude, wavelet, wavelet_dt)
         rec = _f64(np.atleast_2d(rec_xyz))
         n_t = self.trace_len(t_final)
