@@ -596,12 +596,13 @@ def gradient_bench(dtype="f64", n_checkpoints=16, model="box"):
     """Misfit gradient: on the 648-element adjoint box (N = 3, one rate level, 0.5 s record, 25
     receivers, observed data from a model with a 5 % Gaussian velocity bump), or with ``model ==
     "bench"`` on the bench mesh (190,608 elements, N = 4, FP32, one rate level, 0.005 s record, 201
-    receivers, observed data zero): time of the forward run with checkpoints and of the adjoint
-    sweep.  One JSON line."""
+    receivers, observed data zero), or with ``model == "bench3"`` on the bench mesh with its three
+    rate levels: time of the forward run with checkpoints and of the adjoint sweep.  One JSON line."""
     from paper_1506_00907_gb300 import ridg
     from synth import adjoint_box, adjoint_observed_velocity
 
-    if model == "bench":
+    levels = 3 if model == "bench3" else 1
+    if model in ("bench", "bench3"):
         w = _workload()
         dtype, t_final = "f32", 0.005
     else:
@@ -609,10 +610,10 @@ def gradient_bench(dtype="f64", n_checkpoints=16, model="box"):
         t_final = w.t_final
     w.t_final = t_final
     mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
-    s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=1)
+    s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=levels)
     n_t = s.trace_len(w.t_final)
     nrec = len(w.receivers)
-    if model == "bench":
+    if model in ("bench", "bench3"):
         obs = np.zeros((nrec, n_t))
     else:
         s.set_velocity(adjoint_observed_velocity(w))
@@ -627,8 +628,9 @@ def gradient_bench(dtype="f64", n_checkpoints=16, model="box"):
         t2 = time.perf_counter()
         times.append((t1 - t0, t2 - t1))
     fw, bw = min(t[0] for t in times), min(t[1] for t in times)
-    label = ("bench mesh: 190608 tets, N=4, FP32, one level, 0.005 s record, 201 receivers" if model == "bench"
-             else "adjoint box: 648 tets, N=3, one level, 0.5 s record, 25 receivers")
+    label = {"bench": "bench mesh: 190608 tets, N=4, FP32, one level, 0.005 s record, 201 receivers",
+             "bench3": "bench mesh: 190608 tets, N=4, FP32, three levels, 0.005 s record, 201 receivers"}.get(
+                 model, "adjoint box: 648 tets, N=3, one level, 0.5 s record, 25 receivers")
     print(json.dumps({"workload": label, "elements": int(w.K),
                       "dtype": dtype, "steps": n_t - 1, "checkpoints": n_checkpoints, "misfit": J,
                       "grad_norm": float(np.linalg.norm(g)), "forward_s": fw, "backward_s": bw,
@@ -664,8 +666,8 @@ def main():
     ap.add_argument("--serving-sizes", default="50k,200k,800k", help="serving models (subset of 50k,200k,800k)")
     ap.add_argument("--serving-slots", default="1,2", help="slots per model to compare")
     ap.add_argument("--serving-contraction", default="tf32", choices=["tf32", "bf16"])
-    ap.add_argument("--gradient", default="", nargs="?", const="box", choices=["", "box", "bench"],
-                    help="time the misfit gradient (on the adjoint box, or on the bench mesh) and exit")
+    ap.add_argument("--gradient", default="", nargs="?", const="box", choices=["", "box", "bench", "bench3"],
+                    help="time the misfit gradient (on the adjoint box, or on the bench mesh with one or three levels) and exit")
     args = ap.parse_args()
     if args.gradient:
         from paper_1506_00907_gb300.build import build
