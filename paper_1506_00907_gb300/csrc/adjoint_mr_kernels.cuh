@@ -30,6 +30,12 @@
 namespace ridg {
 
 
+// per-column coefficients staged in shared memory, [k][32] (lanes of consecutive columns read
+// consecutive words): traces: normals (12), alpha_f, beta_f, tau_p, tau_v (4 each); rhs: rx (9),
+// normals (12), rho c^2, 1/rho
+constexpr int kAdjMlTc = 28;
+constexpr int kAdjMlRc = 23;
+
 template <typename real>
 __device__ __forceinline__ int adjml_level(const AdjMrArgs<real>& A, int64_t slot0) {
   int lev = 0;
@@ -126,37 +132,49 @@ __global__ void adjml_traces_kernel(AdjMrArgs<real> A) {
   constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
   extern __shared__ __align__(16) unsigned char smem_adjml[];
   real* sL = reinterpret_cast<real*>(smem_adjml);  // [4][Np][32]
+  real* sC = sL + 4 * Np * 32;                     // [kAdjMlTc][32]: normals, alpha_f, beta_f, tau_p, tau_v
+  int* sI = reinterpret_cast<int*>(sC + kAdjMlTc * 32);  // [4][32] boundary kinds, then [32] valid flags
   const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * 32;
   const int64_t blk = slot0 >> 5;
   const int lev = adjml_level(A, slot0);
   const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
-  const real* src = A.mu_ring + A.ring_new[lev] * qsize + blk * 4 * Np * 32;
-  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) sL[i] = src[i];
+  load_lambda_tile<N, real>(A.mu_ring + A.ring_new[lev] * qsize, sL, blk);
+  cp_async_commit();
+  for (int i = threadIdx.x; i < kAdjMlTc * 32; i += blockDim.x) {
+    const int k = i >> 5, c = i & 31;
+    const int64_t s = slot0 + c;
+    const double* g = A.geo + s * kGeo;
+    const real* mt = A.mat + s * kMat;
+    sC[i] = k < 12 ? real(g[9 + k]) : k < 20 ? real(-0.5 * g[21 + (k & 3)]) * mt[k < 16 ? 0 : 1] : mt[k - 17];
+  }
+  for (int i = threadIdx.x; i < 5 * 32; i += blockDim.x)
+    sI[i] = i < 128 ? finfo_bc(A.finfo[(slot0 + (i & 31)) * 4 + (i >> 5)])
+                    : int((A.meta[slot0 + (i & 31)] & kMetaValid) != 0);
+  cp_async_wait_all();
   __syncthreads();
   real* xin = A.mu_in + int64_t(A.slot_read) * A.n_slots * (8 * NFPP);
   for (int item = threadIdx.x; item < 4 * Nfp * 32; item += blockDim.x) {
     const int c = item & 31, fj = item >> 5, f = fj / Nfp, j = fj - f * Nfp;
     const int64_t s = slot0 + c;
     real* ow = A.own + s * (8 * NFPP) + f * 2 * NFPP;
-    if (!(A.meta[s] & kMetaValid)) {
+    if (!sI[128 + c]) {
       ow[j] = real(0);
       ow[NFPP + j] = real(0);
       continue;
     }
-    const double* g = A.geo + s * kGeo;
-    const real* mt = A.mat + s * kMat;
+    const real* cc = sC + c;  // coefficient k of this column at cc[32 k]
     const real* row = A.Lt + int64_t(fj) * A.NPa;
-    const real n0 = real(g[9 + 3 * f]), n1 = real(g[10 + 3 * f]), n2 = real(g[11 + 3 * f]);
+    const real n0 = cc[32 * (3 * f)], n1 = cc[32 * (3 * f + 1)], n2 = cc[32 * (3 * f + 2)];
     real ap = 0, av = 0;
     for (int n = 0; n < Np; ++n) {
       const real l = row[n];
       ap += l * sL[(0 * Np + n) * 32 + c];
       av += l * (n0 * sL[(1 * Np + n) * 32 + c] + n1 * sL[(2 * Np + n) * 32 + c] + n2 * sL[(3 * Np + n) * 32 + c]);
     }
-    const real a = real(-0.5 * g[21 + f]) * mt[0] * ap, b = real(-0.5 * g[21 + f]) * mt[1] * av;
-    const real taup = mt[3 + f], tauv = mt[7 + f];
+    const real a = cc[32 * (12 + f)] * ap, b = cc[32 * (16 + f)] * av;
+    const real taup = cc[32 * (20 + f)], tauv = cc[32 * (24 + f)];
     const real wp = -taup * a + b, wv = a - tauv * b;
-    const int bc = finfo_bc(A.finfo[s * 4 + f]);
+    const int bc = sI[f * 32 + c];
     real op = 0, ov = 0;
     if (bc == 0) {
       op = -wp;
@@ -187,14 +205,24 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
   constexpr int Np = O::Np, NFPP = O::NFPP;
   extern __shared__ __align__(16) unsigned char smem_adjml[];
   real* sL = reinterpret_cast<real*>(smem_adjml);  // [4][Np][32]
-  int* sInv = reinterpret_cast<int*>(sL + 4 * Np * 32);
+  real* sC = sL + 4 * Np * 32;                     // [kAdjMlRc][32]: rx, normals, rho c^2, 1/rho
+  int* sInv = reinterpret_cast<int*>(sC + kAdjMlRc * 32);  // [Np][3]
+  int* sValid = sInv + Np * 3;                             // [32]
   const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * 32;
   const int64_t blk = slot0 >> 5;
   const int lev = adjml_level(A, slot0);
   const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
   real* rnew = A.mu_ring + A.ring_new[lev] * qsize + blk * 4 * Np * 32;
-  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) sL[i] = rnew[i];
+  load_lambda_tile<N, real>(A.mu_ring + A.ring_new[lev] * qsize, sL, blk);
+  cp_async_commit();
+  for (int i = threadIdx.x; i < kAdjMlRc * 32; i += blockDim.x) {
+    const int k = i >> 5, c = i & 31;
+    const int64_t s = slot0 + c;
+    sC[i] = k < 21 ? real(A.geo[s * kGeo + k]) : A.mat[s * kMat + (k - 21)];
+  }
+  for (int i = threadIdx.x; i < 32; i += blockDim.x) sValid[i] = (A.meta[slot0 + i] & kMetaValid) != 0;
   adjml_inverse_fmask<N>(A.fmask, sInv);
+  cp_async_wait_all();
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) rnew[i] = real(0);
   __shared__ double part[8][32];
@@ -202,14 +230,13 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
   for (int item = threadIdx.x; item < Np * 32; item += blockDim.x) {
     const int m = item >> 5, c = item & 31;
     const int64_t s = slot0 + c;
-    if (!(A.meta[s] & kMetaValid)) continue;
+    if (!sValid[c]) continue;
     {
       real r = A.rsaved[((blk * 4 + 0) * Np + m) * 32 + c];
       if (s == A.src_slot) r -= A.F * A.w_src[m];
       gsum += sL[(0 * Np + m) * 32 + c] * r;
     }
-    const double* g = A.geo + s * kGeo;
-    const real* mt = A.mat + s * kMat;
+    const real* cc = sC + c;  // coefficient k of this column at cc[32 k]
     real dp[3] = {0, 0, 0}, dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
     const real* dm = A.Dt4 + int64_t(m) * Np * 4;
     for (int n = 0; n < Np; ++n) {
@@ -229,9 +256,9 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
     for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
-        const real gij = real(g[3 * i + j]);
-        op -= mt[1] * gij * dv[i][j];
-        ov[i] -= mt[0] * gij * dp[j];
+        const real gij = cc[32 * (3 * i + j)];
+        op -= cc[32 * 22] * gij * dv[i][j];
+        ov[i] -= cc[32 * 21] * gij * dp[j];
       }
     for (int k = 0; k < 3; ++k) {
       const int e = sInv[m * 3 + k];
@@ -240,7 +267,7 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
       const real* ow = A.own + s * (8 * NFPP) + f * 2 * NFPP;
       op += ow[jf];
 #pragma unroll
-      for (int i = 0; i < 3; ++i) ov[i] += real(g[9 + 3 * f + i]) * ow[NFPP + jf];
+      for (int i = 0; i < 3; ++i) ov[i] += cc[32 * (9 + 3 * f + i)] * ow[NFPP + jf];
     }
     A.mu[((blk * 4 + 0) * Np + m) * 32 + c] += op;
 #pragma unroll
@@ -258,11 +285,12 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
 
 template <int N, typename real>
 constexpr size_t adjml_traces_smem() {
-  return size_t(4) * Order<N>::Np * 32 * sizeof(real);
+  return (size_t(4) * Order<N>::Np * 32 + size_t(kAdjMlTc) * 32) * sizeof(real) + size_t(5) * 32 * sizeof(int);
 }
 template <int N, typename real>
 constexpr size_t adjml_rhs_smem() {
-  return size_t(4) * Order<N>::Np * 32 * sizeof(real) + size_t(Order<N>::Np) * 3 * sizeof(int);
+  return (size_t(4) * Order<N>::Np * 32 + size_t(kAdjMlRc) * 32) * sizeof(real) +
+         (size_t(Order<N>::Np) * 3 + 32) * sizeof(int);
 }
 
 }  // namespace ridg
