@@ -262,9 +262,9 @@ int ridg_set_profiling(ridg_solver* s, int32_t every);
 /* ------------------------------------------------------------------ velocity gradient
  * The paper migrates with the imaging condition; these calls give the gradient of a least-squares
  * trace misfit with respect to the per-element velocity, as the exact discrete adjoint of the
- * single-rate scheme (Sec. 3.1 right-hand side, Sec. 3.2 AB3 on one rate level: create the solver
- * with n_levels_max = 1).  The velocity enters through rho c^2 in the pressure equation; the time
- * step, the level and the penalty parameters tau_p, tau_v (and the impedance of I_Q) keep the
+ * library's scheme (Sec. 3.1 right-hand side, Sec. 3.2 AB3; with several rate levels Algorithm 1
+ * with its half-step traces).  The velocity enters through rho c^2 in the pressure equation; the
+ * time step, the levels and the penalty parameters tau_p, tau_v (and the impedance of I_Q) keep the
  * values of the model the solver was created with. */
 
 /* Velocity per element (host double [K], > 0) in rho c^2; see above for what stays frozen.

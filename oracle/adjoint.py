@@ -2,14 +2,15 @@
 (oracle, FP64, test infrastructure).
 
 The paper migrates with the imaging condition alone; the gradient here extends its forward
-scheme (Sec. 3.1 right-hand side, Sec. 3.2 Adams-Bashforth with one rate level) with its exact
-discrete adjoint.  Readings (the paper has no gradient, so each is a definition):
+scheme (Sec. 3.1 right-hand side, Sec. 3.2 Adams-Bashforth; ``misfit_gradient`` with one rate
+level, ``misfit_gradient_levels`` with any number) with its exact discrete adjoint.  Readings (the
+paper has no gradient, so each is a definition):
 
 * Model parameter: the velocity c_k of each element where it enters the pressure equation,
   through rho_k c_k^2 (Eq. dgLocalSchemeP).  The time step, the rate level and the penalty
   parameters tau_p, tau_v (Sec. 3.1) stay those of the reference model the problem was built
-  with: they are frozen, so the discrete scheme is a smooth function of c.  Only one rate level
-  is used (single-rate AB3).
+  with: they are frozen, so the discrete scheme is a smooth function of c.  The recursion below
+  is that of one rate level (single-rate AB3); several levels follow at the end.
 * Misfit: J(c) = 1/2 Dt sum_{n=0}^{Nt} sum_r (y_r^n - d_r^n)^2 with the traces
   y_r^n = l(x_r) . p^n_{k_r} of the forward run at the global steps t_n = n Dt (Sec. 2) and the
   observed data d.
