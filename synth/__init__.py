@@ -28,6 +28,7 @@ from .workloads import (  # noqa: F401
     adjoint_box,
     adjoint_box_small,
     adjoint_box_two_level,
+    adjoint_box_three_level,
     adjoint_observed_velocity,
     serving_model,
     serving_requests,

@@ -170,6 +170,22 @@ def adjoint_box_two_level() -> Workload:
     return v
 
 
+def adjoint_box_three_level() -> Workload:
+    """The 24-tetrahedron box at N = 1 with three velocity zones (about 1500 m/s for x < 100 m,
+    3400 m/s for x > 100 m and y < 100 m, 7200 m/s elsewhere, each varied by up to 10 % per
+    element), so that the elements fall on three rate levels; for checks of the oracle's
+    multi-rate gradient."""
+    w = adjoint_box_small()
+    cen = w.xyz[w.tets].mean(axis=1)
+    c = np.where(cen[:, 0] < 100.0, 1500.0, np.where(cen[:, 1] < 100.0, 3400.0, 7200.0))
+    c = c * (1.0 + 0.1 * np.random.default_rng(1).uniform(size=w.K))
+    v = Workload("box24_N1_three_level", w.xyz, w.tets, c, w.rho.copy(), N=1, default_bc=w.default_bc, cfl=w.cfl,
+                 n_levels_max=3, dtype="f64", source_xyz=w.source_xyz, f0=w.f0, t_peak=w.t_peak,
+                 receivers=w.receivers, t_final=w.t_final)
+    v.c_observed = adjoint_observed_velocity(v, sigma=60.0)
+    return v
+
+
 def serving_model(size: str, seed=6) -> Workload:
     """One of the three models of the shot-serving stream: a 2 x 2 x 1 km box with three layers
     (1500, 2000, 2500 m/s; interface depths drawn with ``seed``), the surface refined 8x in depth and

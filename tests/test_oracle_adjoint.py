@@ -2,7 +2,7 @@
 tau, level and time step frozen): the assembled operator reproduces the right-hand side, and the
 adjoint gradient matches central finite differences of the oracle's own forward misfit.  The
 multi-rate gradient (reverse accumulation over the fine steps of Algorithm 1) matches the
-single-rate adjoint on one level and central finite differences on two."""
+single-rate adjoint on one level and central finite differences on two and three."""
 
 import numpy as np
 
@@ -11,7 +11,7 @@ import pytest
 from oracle.adjoint import assemble_operator, frozen_geometry, misfit_gradient, misfit_gradient_levels, shot_misfit
 from oracle.dg_rhs import rhs, traces
 from oracle.rtm import make_problem
-from synth import adjoint_box_small, adjoint_box_two_level
+from synth import adjoint_box_small, adjoint_box_three_level, adjoint_box_two_level
 
 
 def _case():
@@ -88,3 +88,23 @@ def test_single_rate_adjoint_refuses_several_levels():
     w, prob, args, obs = _two_level_case(2)
     with pytest.raises(ValueError):
         misfit_gradient(prob, w.c, *args, obs)
+
+
+def test_multirate_gradient_matches_finite_differences_on_three_levels():
+    """Three levels (10 + 8 + 6 elements): nested half steps and the coupling of the two finer
+    levels; central differences on elements of every level."""
+    w = adjoint_box_three_level()
+    prob = make_problem(w.xyz, w.tets, w.c, w.rho, w.N, default_bc=w.default_bc, cfl=w.cfl, n_levels_max=3)
+    assert prob.n_levels == 3
+    args = (w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
+    obs = shot_misfit(prob, w.c_observed, *args, 0.0).traces
+    J, grad = misfit_gradient_levels(prob, w.c, *args, obs)
+    assert J > 0 and np.all(np.isfinite(grad))
+    ks = [int(np.nonzero(prob.levels == l)[0][0]) for l in (1, 2, 3)] + [5, 15]
+    for k in ks:
+        d = 1e-4 * w.c[k]
+        cp, cm = w.c.copy(), w.c.copy()
+        cp[k] += d
+        cm[k] -= d
+        fd = (shot_misfit(prob, cp, *args, obs).misfit - shot_misfit(prob, cm, *args, obs).misfit) / (2 * d)
+        assert abs(fd - grad[k]) < 1e-5 * abs(grad[k]) + 1e-9 * np.abs(grad).max(), (k, fd, grad[k])
