@@ -115,7 +115,10 @@ def forward(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, 
 
 
 def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0,
-             observed=None, e_up=(0.0, 0.0, -1.0), wavelet=None, wavelet_dt=None) -> ShotResult:
+             observed=None, e_up=(0.0, 0.0, -1.0), wavelet=None, wavelet_dt=None, observe=None) -> ShotResult:
+    """``observe`` (tests only): called as observe(tau, q_S, q_R) with the backward source and
+    receiver fields at t = tau Delta t_local, once at tau_f and after every fine step of the
+    backward sweep down to tau_i; it lets a test integrate the imaging conditions on its own."""
     geo = prob.geo
     K, Np = geo.K, geo.ref.Np
     nl = prob.n_local
@@ -194,6 +197,8 @@ def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final,
         rqR = [characteristic(R.hist[s][E, 0], R.hist[s][E, 1:4], ZE, e_up, +1.0) for s in range(3)]
         I_q[E] -= step_increment(h, qS, rqS, qR, rqR)
 
+    if observe is not None:
+        observe(Sb.tau, Sb.q.copy(), R.q.copy())
     while Sb.tau > tau_i:
         Sb.phase_rhs()
         R.phase_rhs()
@@ -207,4 +212,6 @@ def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final,
         R.phase_halfstep(updated)
         Sb.tau -= 1
         R.tau -= 1
+        if observe is not None:
+            observe(Sb.tau, Sb.q.copy(), R.q.copy())
     return ShotResult(tr, I_p, I_q, q_tf, Sb.q.copy(), q_ti, S.dof_updates + Sb.dof_updates + R.dof_updates, n_global)
