@@ -12,14 +12,16 @@
 * on two rate levels the misfit and the gradient equal the oracle's multi-rate gradient (reverse
   accumulation over the fine steps of Algorithm 1), independently of the number of checkpoints."""
 
+import functools
+
 import numpy as np
 import pytest
 
 from oracle.adjoint import assemble_operator, frozen_geometry, misfit_gradient, misfit_gradient_levels, shot_misfit
 from oracle.rtm import make_problem
 from paper_1506_00907_gb300 import ridg
-from synth import (adjoint_box, adjoint_box_small, adjoint_box_two_level, adjoint_observed_velocity, random_state,
-                   tiny_layered_rtm)
+from synth import (adjoint_box, adjoint_box_small, adjoint_box_three_level, adjoint_box_two_level,
+                   adjoint_observed_velocity, random_state, tiny_layered_rtm)
 from tests.parity_cases import TOL, mixed_bc, rel_l2
 
 pytestmark = pytest.mark.gpu
@@ -159,19 +161,27 @@ def test_fp32_gradient_follows_fp64(box):
     assert rel_l2(g32, g64) < 1e-3
 
 
-def test_multirate_gradient_matches_the_oracle():
-    """Two rate levels (24 elements, N = 1, FP64): the library's reverse accumulation over its fine
-    steps (pull of the pushed traces, the update and right-hand-side transposes) against the
-    oracle's, which assembles each fine step's matrix from its own Algorithm 1; and the same
-    gradient bit for bit with 1, 3 and 16 checkpoints."""
-    w = adjoint_box_two_level()
-    prob = make_problem(w.xyz, w.tets, w.c, w.rho, w.N, default_bc=w.default_bc, cfl=w.cfl, n_levels_max=2)
-    assert prob.n_levels == 2
+@functools.lru_cache(maxsize=None)
+def _multirate_reference(n_levels, N):
+    w = (adjoint_box_two_level if n_levels == 2 else adjoint_box_three_level)()
+    prob = make_problem(w.xyz, w.tets, w.c, w.rho, N, default_bc=w.default_bc, cfl=w.cfl, n_levels_max=n_levels)
+    assert prob.n_levels == n_levels
     args = (w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
     obs = shot_misfit(prob, w.c_observed, *args, 0.0).traces
     J_ref, g_ref = misfit_gradient_levels(prob, w.c, *args, obs)
-    s = _solver(w, n_levels_max=2)
-    assert s.info.n_levels == 2
+    return w, args, obs, J_ref, g_ref
+
+
+@pytest.mark.parametrize("n_levels,N", [(2, 1), (3, 1), (3, 2)])
+def test_multirate_gradient_matches_the_oracle(n_levels, N):
+    """Two and three rate levels (24 elements, FP64; three levels use the mod-3 reuse of the inbox
+    slots with a coarsest stride of 4, N = 2 the face-node paths of several nodes per face): the
+    library's reverse accumulation over its fine steps (pull of the pushed traces, the update and
+    right-hand-side transposes) against the oracle's, which assembles each fine step's matrix from
+    its own Algorithm 1; and the same gradient bit for bit with 1, 3 and 16 checkpoints."""
+    w, args, obs, J_ref, g_ref = _multirate_reference(n_levels, N)
+    s = _solver(w, N=N, n_levels_max=n_levels)
+    assert s.info.n_levels == n_levels
     grads = []
     for n_ck in (16, 3, 1):
         J, _ = s.misfit_forward(*args, obs, n_checkpoints=n_ck)
@@ -179,3 +189,15 @@ def test_multirate_gradient_matches_the_oracle():
         grads.append(s.misfit_backward())
     assert rel_l2(grads[0], g_ref) < 1e-9
     assert np.array_equal(grads[0], grads[1]) and np.array_equal(grads[0], grads[2])
+
+
+def test_multirate_gradient_fp32_follows_the_oracle():
+    """The same three-level reverse sweep in FP32 (the precision of the bench): misfit and gradient
+    against the FP64 oracle within 1e-3 relative (FP32 rounding accumulated over the forward run
+    and the reverse sweep, as for the single-rate FP32 gradient)."""
+    w, args, obs, J_ref, g_ref = _multirate_reference(3, 2)
+    s = _solver(w, dtype="f32", N=2, n_levels_max=3)
+    J, _ = s.misfit_forward(*args, obs, n_checkpoints=4)
+    g = s.misfit_backward()
+    assert abs(J - J_ref) < 1e-3 * J_ref
+    assert rel_l2(g, g_ref) < 1e-3

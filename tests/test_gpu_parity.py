@@ -7,7 +7,7 @@ import functools
 import numpy as np
 import pytest
 
-from oracle.dg_rhs import attach_media, rhs, traces
+from oracle.dg_rhs import attach_media, energy, rhs, traces
 from oracle.mesh_geometry import MeshGeometry
 from oracle.mrab import MRAB, assign_levels
 from oracle.reference_element import reference_element
@@ -86,8 +86,7 @@ def test_config1_standing_mode_fp64():
     qe = sm(w.n_steps * dt)
     err = rel_l2(q_gpu[:, 0], qe[:, 0])
     assert err < 2e-2
-    e = s.energy()
-    assert np.isfinite(e) and e > 0
+    assert rel_l2(s.energy(), energy(st.q, g)) < 1e-10
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -133,8 +132,8 @@ def test_rtm_shot_parity(dtype, N):
     tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
     assert tr.shape == ref.traces.shape
     assert rel_l2(tr, ref.traces) < TOL[dtype]
-    assert rel_l2(ip, ref.image_p) < (10 * TOL[dtype] if dtype == "f32" else TOL[dtype])
-    assert rel_l2(iq, ref.image_q) < (10 * TOL[dtype] if dtype == "f32" else TOL[dtype])
+    assert rel_l2(ip, ref.image_p) < TOL[dtype]
+    assert rel_l2(iq, ref.image_q) < TOL[dtype]
     st = s.shot_stats()
     assert st.n_global == ref.n_global
     assert st.dof_updates_forward + st.dof_updates_backward > 0
@@ -173,8 +172,8 @@ def test_rtm_shot_variants_parity(dtype, variant):
     s = _gpu(w, dtype, face_bc=fb)
     tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, rec, w.t_final, t_i, observed=obs)
     assert rel_l2(tr, ref.traces) < TOL[dtype]
-    assert rel_l2(ip, ref.image_p) < (10 * TOL[dtype] if dtype == "f32" else TOL[dtype])
-    assert rel_l2(iq, ref.image_q) < (10 * TOL[dtype] if dtype == "f32" else TOL[dtype])
+    assert rel_l2(ip, ref.image_p) < TOL[dtype]
+    assert rel_l2(iq, ref.image_q) < TOL[dtype]
 
 
 def test_rtm_edge_cases():
@@ -203,6 +202,21 @@ def test_single_element_mesh():
     q = random_state(1, s.Np, seed=9)
     g = attach_media(MeshGeometry(xyz, tets, reference_element(3), default_bc=1), [2.0], [1.5])
     assert rel_l2(s.eval_rhs(q), rhs(np.arange(1), q, traces(q, g), g)) < TOL["f64"]
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_energy_matches_oracle(dtype):
+    """The discrete energy of the solver's fields (FP64 accumulation on the device) against the
+    oracle's, on a two-material mesh with several blocks; in FP32 mode the oracle takes the same
+    fields rounded to FP32, so both sides add the same terms in FP64."""
+    w = tiny_layered_rtm(N=4)
+    prob = _oracle_problem(w)
+    s = _gpu(w, dtype)
+    q = random_state(w.K, s.Np, seed=41)
+    s.set_state(q)
+    q_ref = q.astype(np.float32).astype(np.float64) if dtype == "f32" else q
+    e_ref = energy(q_ref, prob.geo)
+    assert abs(s.energy() - e_ref) <= 1e-12 * e_ref
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
@@ -306,8 +320,8 @@ def test_rtm_shot_parity_fp32_cuda_cores():
     s = _gpu(w, "f32", contraction=ridg.CONTRACT_CUDA_CORES)
     tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
     assert rel_l2(tr, ref.traces) < TOL["f32"]
-    assert rel_l2(ip, ref.image_p) < 10 * TOL["f32"]
-    assert rel_l2(iq, ref.image_q) < 10 * TOL["f32"]
+    assert rel_l2(ip, ref.image_p) < TOL["f32"]
+    assert rel_l2(iq, ref.image_q) < TOL["f32"]
 
 
 def test_blow_up_is_reported_as_unstable():
@@ -348,5 +362,5 @@ def test_rtm_shot_parity_bf16_split():
     s = _gpu(w, "f32", contraction=ridg.CONTRACT_TENSOR_BF16)
     tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
     assert rel_l2(tr, ref.traces) < TOL_BF16
-    assert rel_l2(ip, ref.image_p) < 10 * TOL_BF16
-    assert rel_l2(iq, ref.image_q) < 10 * TOL_BF16
+    assert rel_l2(ip, ref.image_p) < TOL_BF16
+    assert rel_l2(iq, ref.image_q) < TOL_BF16
