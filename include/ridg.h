@@ -171,9 +171,10 @@ int ridg_get_state(ridg_solver* s, double* q_out);
 int ridg_energy(ridg_solver* s, double* energy);
 
 /* The same energy of the solver's current fields, for callers that cannot allocate device memory
- * when they need it (for instance while a stream is being captured into a CUDA graph, or inside a
- * loop that must not touch the allocator).  The paper has no counterpart: this is an interface
- * variant of ridg_energy.
+ * when they need it: a host application that gives the library a fixed device-memory budget and
+ * owns every allocation, or a time-critical stepping loop in which cudaMalloc/cudaFree must not run
+ * (they can block the host and synchronise the device).  The paper has no counterpart: this is an
+ * interface variant of ridg_energy.
  *   energy_dev  device double[1] owned by the caller; written asynchronously on the solver's stream.
  * Allocates no device memory: its scratch (per-block partial sums) is a fixed 32 KiB device array
  * that every GPU loading the library keeps until exit.  Solvers with more than 1,048,576 element
@@ -268,7 +269,11 @@ int ridg_set_profiling(ridg_solver* s, int32_t every);
  * values of the model the solver was created with. */
 
 /* Velocity per element (host double [K], > 0) in rho c^2; see above for what stays frozen.
- * Invalidates the last misfit forward run. */
+ * Invalidates the last misfit forward run.  Because the time step and the levels stay those of the
+ * creation model, an element's Courant number on its level's step, Dt_l (N+1)^2 c_k / l_k (l_k its
+ * smallest height), may not exceed 4/3 of the solver's CFL constant (0.2 at the default 0.15; AB3
+ * with this step rule was measured stable up to 0.22 and unstable at 0.25): a faster element is
+ * rejected with RIDG_E_INVALID_ARG, naming it, instead of silently running an unstable scheme. */
 int ridg_set_velocity(ridg_solver* s, const double* c);
 /* out = A^T lam, the transposed right-hand-side operator (no source), host double [K][4][Np] each
  * in the reference node numbering.  The parity check of the adjoint kernels. */

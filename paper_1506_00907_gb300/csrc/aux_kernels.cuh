@@ -54,32 +54,38 @@ __global__ void sample_receivers_kernel(const real* __restrict__ q, const int64_
   out[int64_t(r) * n_time + col] = acc;
 }
 
+// Discrete energy of the element in slot s (a valid slot): J/2 (p^T M p / (rho c^2) + rho v^T M v),
+// with FP64 products and sums.  Shared by energy_kernel and the allocation-free variant.
+template <int N, typename real>
+__device__ __forceinline__ double slot_energy(const real* __restrict__ q, int64_t s, const double* __restrict__ Jdet,
+                                              const real* __restrict__ mat, const double* __restrict__ M) {
+  constexpr int Np = Order<N>::Np;
+  const int64_t blk = s >> 5;
+  const int lane = int(s & 31);
+  const double rc2 = double(mat[s * kMat + 0]), irho = double(mat[s * kMat + 1]);
+  double e = 0.0;
+  for (int fld = 0; fld < 4; ++fld) {
+    double acc = 0.0;
+    for (int a = 0; a < Np; ++a) {
+      const double xa = double(q[((blk * 4 + fld) * Np + a) * 32 + lane]);
+      double row = 0.0;
+      for (int b = 0; b < Np; ++b) row += M[a * Np + b] * double(q[((blk * 4 + fld) * Np + b) * 32 + lane]);
+      acc += xa * row;
+    }
+    e += (fld == 0 ? acc / rc2 : acc / irho);
+  }
+  return 0.5 * Jdet[s] * e;
+}
+
 // Discrete energy sum_k J_k/2 (p^T M p / (rho c^2) + rho v^T M v), FP64 accumulation.
 template <int N, typename real>
 __global__ void energy_kernel(const real* __restrict__ q, int64_t n_slots, const double* __restrict__ Jdet,
                               const real* __restrict__ mat, const int* __restrict__ meta, const double* __restrict__ M,
                               double* __restrict__ out) {
-  using O = Order<N>;
-  constexpr int Np = O::Np;
   __shared__ double red[256];
   int64_t s = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   double e = 0.0;
-  if (s < n_slots && (meta[s] & kMetaValid)) {
-    int64_t blk = s >> 5;
-    int lane = int(s & 31);
-    double rc2 = double(mat[s * kMat + 0]), irho = double(mat[s * kMat + 1]);
-    for (int fld = 0; fld < 4; ++fld) {
-      double acc = 0.0;
-      for (int a = 0; a < Np; ++a) {
-        double xa = double(q[((blk * 4 + fld) * Np + a) * 32 + lane]);
-        double row = 0.0;
-        for (int b = 0; b < Np; ++b) row += M[a * Np + b] * double(q[((blk * 4 + fld) * Np + b) * 32 + lane]);
-        acc += xa * row;
-      }
-      e += (fld == 0 ? acc / rc2 : acc / irho);
-    }
-    e *= 0.5 * Jdet[s];
-  }
+  if (s < n_slots && (meta[s] & kMetaValid)) e = slot_energy<N, real>(q, s, Jdet, mat, M);
   red[threadIdx.x] = e;
   __syncthreads();
   for (int w = blockDim.x / 2; w > 0; w >>= 1) {

@@ -2,9 +2,38 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
+#include <mutex>
+
 #include "step_kernel.cuh"
 
 namespace ridg {
+
+// Kernel attributes (the dynamic shared-memory limit) belong to each device's context: they are set
+// once per device, with that device current, the first time a kernel is launched there.  Launches
+// come from several host threads (shot-server slots), so the set-up is serialised and its outcome
+// kept per device.
+struct PerDeviceSetup {
+  static constexpr int kMaxDevices = 64;
+  std::atomic<bool> done[kMaxDevices] = {};
+  cudaError_t result[kMaxDevices] = {};
+  std::mutex m;
+
+  template <typename F>
+  cudaError_t run(F&& configure) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    if (done[dev].load(std::memory_order_acquire)) return result[dev];
+    std::lock_guard<std::mutex> lock(m);
+    if (!done[dev].load(std::memory_order_relaxed)) {
+      result[dev] = configure();
+      done[dev].store(true, std::memory_order_release);
+    }
+    return result[dev];
+  }
+};
 
 // Arguments of one reverse fine step of the multi-rate adjoint (adjoint_mr_kernels.cuh): the
 // adjoint state, the active slots and each level's ring and trace-slot indices at that step.

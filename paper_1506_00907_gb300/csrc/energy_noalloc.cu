@@ -1,24 +1,27 @@
 // Discrete energy without any device allocation, for callers that cannot call cudaMalloc.
 //
-// Some callers cannot allocate device memory at the time they need the energy check: code that
-// runs while a stream is being captured into a CUDA graph (allocation calls are not allowed there),
-// code that must not touch the allocator inside a time-critical loop, or hosts whose memory is
-// managed by another pool.  This variant of the energy reduction keeps its per-block partial sums in
-// a file-scope device array instead of a per-call allocation and writes the result to device memory
-// the caller owns.
+// Some callers of this library cannot allocate device memory at the moment they want the energy
+// check: a host application that hands the library a fixed device-memory budget up front and owns
+// every allocation itself, a time-critical stepping loop in which cudaMalloc/cudaFree must not run
+// because they can block the host and synchronise the device, or a caller on a thread that must
+// never enter the CUDA allocator.  This variant of the energy reduction keeps its per-block partial
+// sums in a file-scope device array instead of a per-call allocation and writes the result to
+// device memory the caller owns.
 //
 // The scratch array holds kMaxBlocks partial sums (32 KiB); every device that loads the library
 // keeps it until the process exits.  Solvers with more than kMaxBlocks * 256 element slots are
-// rejected.  Every call on a device shares the array, and the array keeps the last call's
-// contents: pass 1 overwrites every entry that pass 2 reads, so nothing needs clearing, but calls
-// that overlap on the GPU (different streams, or different solvers on one device without
-// ordering) race on it.
+// rejected.  The first call on a device looks up the array's device address with that device
+// current (the host-side name of a __device__ array is only a stand-in); make that first call
+// before any stream capture.  Every call on a device shares the array, and the array keeps the
+// last call's contents: pass 1 overwrites every entry that pass 2 reads, so nothing needs
+// clearing, but calls that overlap on the GPU (different streams, or different solvers on one
+// device without ordering) race on it.
 #include <cuda_runtime.h>
 
 #include <mutex>
 
 #include "energy_noalloc.hpp"
-#include "step_kernel.cuh"
+#include "aux_kernels.cuh"
 
 namespace ridg {
 
@@ -38,25 +41,10 @@ template <int N, typename real>
 __global__ void energy_partials_kernel(const real* __restrict__ q, int64_t n_slots, const double* __restrict__ Jdet,
                                        const real* __restrict__ mat, const int* __restrict__ meta,
                                        const double* __restrict__ M, double* __restrict__ partials) {
-  constexpr int Np = Order<N>::Np;
   __shared__ double red[kThreads];
   const int64_t s = int64_t(blockIdx.x) * kThreads + threadIdx.x;
   double e = 0.0;
-  if (s < n_slots && (meta[s] & kMetaValid)) {
-    const int64_t blk = s >> 5;
-    const int lane = int(s & 31);
-    const double rc2 = double(mat[s * kMat + 0]), irho = double(mat[s * kMat + 1]);
-    for (int fld = 0; fld < 4; ++fld) {
-      double acc = 0.0;
-      for (int a = 0; a < Np; ++a) {
-        double row = 0.0;
-        for (int b = 0; b < Np; ++b) row += M[a * Np + b] * double(q[((blk * 4 + fld) * Np + b) * 32 + lane]);
-        acc += double(q[((blk * 4 + fld) * Np + a) * 32 + lane]) * row;
-      }
-      e += fld == 0 ? acc / rc2 : acc / irho;
-    }
-    e *= 0.5 * Jdet[s];
-  }
+  if (s < n_slots && (meta[s] & kMetaValid)) e = slot_energy<N, real>(q, s, Jdet, mat, M);
   red[threadIdx.x] = e;
   __syncthreads();
   for (int w = kThreads / 2; w > 0; w >>= 1) {

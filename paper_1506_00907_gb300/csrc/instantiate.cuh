@@ -15,9 +15,10 @@ namespace ridg {
 template <int N, int W, int KIND>
 static cudaError_t launch_step_tc(const StepArgs<float>& a, int64_t blocks, cudaStream_t st) {
   constexpr size_t smem = SmemTc<N, W>::bytes;
-  // set once per process (thread-safe initialisation: shot servers launch from several threads)
-  static const cudaError_t configured =
-      cudaFuncSetAttribute(dg_step_kernel_tc<N, W, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  static PerDeviceSetup setup;
+  const cudaError_t configured = setup.run([] {
+    return cudaFuncSetAttribute(dg_step_kernel_tc<N, W, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  });
   if (configured != cudaSuccess) return configured;
   dg_step_kernel_tc<N, W, KIND><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a);
   return cudaGetLastError();
@@ -33,8 +34,10 @@ static cudaError_t launch_step_w(const StepArgs<real>& a, cudaStream_t st) {
   }
   // FP64, or FP32 on CUDA cores
   constexpr size_t smem = step_smem_bytes<N, real, W>();
-  static const cudaError_t configured =
-      cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  static PerDeviceSetup setup;
+  const cudaError_t configured = setup.run([] {
+    return cudaFuncSetAttribute(dg_step_kernel<N, real, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  });
   if (configured != cudaSuccess) return configured;
   dg_step_kernel<N, real, W><<<dim3(unsigned(blocks)), Order<N>::NT, smem, st>>>(a);
   return cudaGetLastError();
@@ -100,13 +103,14 @@ cudaError_t Launch<N, real>::adj_rhs(real* lam, real* own, real* inbox, real* ou
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t sm_t = adj_traces_smem<N, real>(), sm_r = adj_rhs_smem<N, real>();
   static_assert(sm_t <= 227 * 1024 && sm_r <= 227 * 1024, "adjoint kernels exceed the shared memory of a block");
-  static const cudaError_t configured = [] {
+  static PerDeviceSetup setup;
+  const cudaError_t configured = setup.run([] {
     cudaError_t e =
         cudaFuncSetAttribute(adj_traces_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_t));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(adj_rhs_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_r));
     return e;
-  }();
+  });
   if (configured != cudaSuccess) return configured;
   adj_traces_kernel<N, real><<<unsigned(blocks), 256, sm_t, st>>>(lam, own, inbox, n_slots, geo, mat, meta, Lt, NPa,
                                                                    nbr, finfo, perm);
@@ -131,13 +135,14 @@ cudaError_t Launch<N, real>::adjml_step(const AdjMrArgs<real>& a, cudaStream_t s
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t sm_t = adjml_traces_smem<N, real>(), sm_r = adjml_rhs_smem<N, real>();
   static_assert(sm_t <= 227 * 1024 && sm_r <= 227 * 1024, "multi-rate adjoint kernels exceed the shared memory");
-  static const cudaError_t configured = [] {
+  static PerDeviceSetup setup;
+  const cudaError_t configured = setup.run([] {
     cudaError_t e =
         cudaFuncSetAttribute(adjml_traces_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_t));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(adjml_rhs_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_r));
     return e;
-  }();
+  });
   if (configured != cudaSuccess) return configured;
   adjml_pull_kernel<N, real><<<unsigned(blocks), 256, 0, st>>>(a);
   adjml_traces_kernel<N, real><<<unsigned(blocks), 256, sm_t, st>>>(a);

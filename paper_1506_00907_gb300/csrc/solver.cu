@@ -217,6 +217,7 @@ class Engine final : public ridg_solver {
       if (!(rho_[k] > 0.0) || !(c_[k] > 0.0) || !std::isfinite(rho_[k]) || !std::isfinite(c_[k]))
         throw Error{RIDG_E_INVALID_ARG, "c and rho must be positive and finite"};
     double cfl = opt.cfl > 0 ? opt.cfl : 0.15;
+    cfl_ = cfl;
     int nlm = opt.n_levels_max > 0 ? opt.n_levels_max : 3;
     tau_scale_ = opt.tau_scale > 0 ? opt.tau_scale : 1.0;
     if (opt.contraction != RIDG_CONTRACT_TENSOR && opt.contraction != RIDG_CONTRACT_CUDA_CORES &&
@@ -449,6 +450,18 @@ class Engine final : public ridg_solver {
     if (!c) throw Error{RIDG_E_INVALID_ARG, "c is null"};
     for (int64_t k = 0; k < mesh_.K; ++k)
       if (!(c[k] > 0.0) || !std::isfinite(c[k])) throw Error{RIDG_E_INVALID_ARG, "c must be positive and finite"};
+    // the time step and levels stay those of the creation model: an element may speed up only while
+    // its Courant number on its level's step stays within kVelocityCflMargin x the solver's CFL
+    // constant (AB3 with this step rule measured stable to C = 0.22, unstable at 0.25)
+    for (int64_t k = 0; k < mesh_.K; ++k) {
+      const double dt_l = lv_.dt_local * double(int64_t(1) << (L_ - lv_.level[k]));
+      const double courant = dt_l * (N_ + 1.0) * (N_ + 1.0) * c[k] / geo_.lmin[k];
+      if (courant > kVelocityCflMargin * cfl_ * (1.0 + 1e-12))
+        throw Error{RIDG_E_INVALID_ARG, "velocity of element " + std::to_string(k) + " (" + std::to_string(c[k]) +
+                                            " m/s) exceeds the stability bound of its frozen time step: Courant " +
+                                            std::to_string(courant) + " > " +
+                                            std::to_string(kVelocityCflMargin * cfl_)};
+    }
     c_.assign(c, c + mesh_.K);
     upload_material();
     adj_.ready = false;
@@ -1465,6 +1478,8 @@ class Engine final : public ridg_solver {
   DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Dt4_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
   DBuf afrag_d_, gtab_d_[2], pos_d_;
   double tau_scale_ = 1.0;
+  double cfl_ = 0.15;
+  static constexpr double kVelocityCflMargin = 4.0 / 3.0;
   int contraction_ = RIDG_CONTRACT_TENSOR;  // how the FP32 element products run (FP64: CUDA cores)
   int image_mode_ = kModeImage;
   std::vector<int> pos_of_;  // device position of each reference node
