@@ -151,14 +151,22 @@ class MRAB:
         self.dof_updates += len(E) * 4 * self.geo.ref.Np
         return E
 
-    def phase_halfstep(self, updated_mask):
-        """Eq. updateABcoarse for elements not updated at this step that are coarse
-        neighbours of updated elements."""
+    def halfstep_elements(self, updated_mask):
+        """Elements not updated at this step that are coarse neighbours of updated elements."""
         geo = self.geo
         inter = geo.nbr >= 0
         nb = np.maximum(geo.nbr, 0)
         coarse_nbr = np.any(inter & updated_mask[nb] & (self.lev[nb] > self.lev[:, None]), axis=1)
-        H = np.nonzero(coarse_nbr & ~updated_mask)[0]
+        return np.nonzero(coarse_nbr & ~updated_mask)[0]
+
+    def phase_halfstep(self, updated_mask):
+        """Eq. updateABcoarse for elements not updated at this step that are coarse
+        neighbours of updated elements."""
+        return self.apply_halfstep(self.halfstep_elements(updated_mask))
+
+    def apply_halfstep(self, H):
+        """Traces of the elements H set to their fields at the middle of their own step."""
+        geo = self.geo
         if len(H) == 0:
             return H
         b = self.b

@@ -115,10 +115,13 @@ def forward(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, 
 
 
 def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0,
-             observed=None, e_up=(0.0, 0.0, -1.0), wavelet=None, wavelet_dt=None, observe=None) -> ShotResult:
+             observed=None, e_up=(0.0, 0.0, -1.0), wavelet=None, wavelet_dt=None, observe=None,
+             stepper=MRAB) -> ShotResult:
     """``observe`` (tests only): called as observe(tau, q_S, q_R) with the backward source and
     receiver fields at t = tau Delta t_local, once at tau_f and after every fine step of the
-    backward sweep down to tau_i; it lets a test integrate the imaging conditions on its own."""
+    backward sweep down to tau_i; it lets a test integrate the imaging conditions on its own.
+    ``stepper``: the class that advances each wavefield (Algorithm 1); ``oracle.partition`` gives one
+    that advances a single part of a partitioned mesh and exchanges interface traces (Sec. 4.2)."""
     geo = prob.geo
     K, Np = geo.K, geo.ref.Np
     nl = prob.n_local
@@ -137,7 +140,7 @@ def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final,
         return np.array([row @ q[k, 0] for k, row, _ in rec])
 
     # ---------------------------------------------------------------- forward
-    S = MRAB(geo, prob.levels, prob.n_levels, dtl, direction=+1, tau0=0)
+    S = stepper(geo, prob.levels, prob.n_levels, dtl, direction=+1, tau0=0)
     S.injections = [(ks, w_src, src_amp)]
     S.record = {}
     tr = np.zeros((len(rec), n_global + 1))
@@ -166,7 +169,7 @@ def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final,
     saved[1] = (S.hist[1][E].copy(), S.hist[0][E].copy())
 
     # ---------------------------------------------------------------- backward
-    Sb = MRAB(geo, prob.levels, prob.n_levels, dtl, direction=-1, tau0=tau_f)
+    Sb = stepper(geo, prob.levels, prob.n_levels, dtl, direction=-1, tau0=tau_f)
     Sb.set_state(q_tf)
     for l, (r1, r2) in saved.items():
         E = Sb.level_elems[l]
@@ -175,7 +178,7 @@ def rtm_shot(prob: Problem, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final,
     Sb.injections = [(ks, w_src, src_amp)]
     Sb.replay = record
     data = tr if observed is None else np.asarray(observed, dtype=np.float64)
-    R = MRAB(geo, prob.levels, prob.n_levels, dtl, direction=-1, tau0=tau_f)
+    R = stepper(geo, prob.levels, prob.n_levels, dtl, direction=-1, tau0=tau_f)
     R.injections = [(kr, wr, (lambda tau, d=data[i]: interpolate_trace(d, tau, nl))) for i, (kr, _, wr) in enumerate(rec)]
     I_p = np.zeros((K, Np))
     I_q = np.zeros((K, Np))

@@ -30,6 +30,7 @@ from .workloads import (  # noqa: F401
     adjoint_box_two_level,
     adjoint_box_three_level,
     adjoint_observed_velocity,
+    inclusion_box,
     serving_model,
     serving_requests,
 )

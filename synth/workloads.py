@@ -131,6 +131,30 @@ def adjoint_box(seed=0) -> Workload:
                     f0=10.0, t_peak=0.13524, receivers=rec, t_final=0.5)
 
 
+def inclusion_box(seed=3, n_fast=3) -> Workload:
+    """The 648-tetrahedron box (6x6x3 hexahedra, 600 x 600 x 300 m) at 1500 m/s with ``n_fast``
+    isolated elements (seeded, none sharing a vertex) at 6000 m/s, N = 2: the fast elements are
+    the only ones of the finest of three rate levels, as in the paper's survey where the finest
+    elements are few and isolated; for checks of the domain decomposition."""
+    ax = np.linspace(0.0, 600.0, 7)
+    g = HexGrid(ax, ax.copy(), np.linspace(0.0, 300.0, 4))
+    xyz, tets = g.mesh()
+    K = tets.shape[0]
+    rng = np.random.default_rng(seed)
+    fast = []
+    for k in rng.permutation(K):
+        if all(not (set(tets[k]) & set(tets[j])) for j in fast):
+            fast.append(int(k))
+        if len(fast) == n_fast:
+            break
+    c = np.full(K, 1500.0)
+    c[fast] = 6000.0
+    rec = np.stack([np.linspace(50.0, 550.0, 11), np.full(11, 300.0), np.full(11, 10.0)], axis=1)
+    return Workload("box648_N2_inclusions", xyz, tets, c, np.full(K, 1000.0), N=2, default_bc=BC_TRANSPARENT,
+                    cfl=0.15, n_levels_max=3, dtype="f64", source_xyz=(300.0, 300.0, 8.0), f0=25.0,
+                    t_peak=0.1127 * 12.0 / 25.0, receivers=rec, t_final=0.004)
+
+
 def adjoint_observed_velocity(w: Workload, amplitude=0.05, sigma=100.0) -> np.ndarray:
     """Velocity of the observed data: c (1 + amplitude g), g a Gaussian bump of width sigma at the
     centre of the box."""
