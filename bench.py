@@ -146,48 +146,83 @@ def _traffic():
 
 
 # --------------------------------------------------------------------------- CPU oracle leg
-ORACLE_SAMPLE = r"""
-import json, os, sys, time
-sys.path.insert(0, {root!r})
-import numpy as np
-from synth import config2_layered_rtm
-from oracle.rtm import make_problem
-from oracle.mrab import MRAB
-from oracle.wavelet import ricker
-w = config2_layered_rtm()
-prob = make_problem(w.xyz, w.tets, w.c, w.rho, w.N, default_bc=w.default_bc, cfl=w.cfl, n_levels_max=w.n_levels_max)
-g = prob.geo
-ks, rs = g.locate(w.source_xyz)
-S = MRAB(g, prob.levels, prob.n_levels, prob.dt_local, +1)
-S.injections = [(ks, g.source_weights(ks, rs), lambda tau: float(ricker(tau * prob.dt_local, w.f0, w.t_peak)))]
-steps = {steps}
-out = []
-for i in range(steps):
+ORACLE_BYTES_PER_PROCESS = 3.5e9  # peak resident memory of one oracle instance of the bench mesh (measured 3.1 GB)
+
+
+def _oracle_replica(root, warm, timed, barrier, queue):
+    """One oracle instance (FP64 numpy, one thread): builds the bench problem, waits at the barrier so
+    that every replica steps at the same time, then runs warm + timed global MRAB steps of the forward
+    source run; reports (DOF updates of the timed steps, wall start and end of the timed steps)."""
+    sys.path.insert(0, root)
+    from oracle.mrab import MRAB
+    from oracle.rtm import make_problem
+    from oracle.wavelet import ricker
+    from synth import config2_layered_rtm
+
+    w = config2_layered_rtm()
+    prob = make_problem(w.xyz, w.tets, w.c, w.rho, w.N, default_bc=w.default_bc, cfl=w.cfl,
+                        n_levels_max=w.n_levels_max)
+    g = prob.geo
+    ks, rs = g.locate(w.source_xyz)
+    S = MRAB(g, prob.levels, prob.n_levels, prob.dt_local, +1)
+    S.injections = [(ks, g.source_weights(ks, rs), lambda tau: float(ricker(tau * prob.dt_local, w.f0, w.t_peak)))]
+    barrier.wait(timeout=1200)
+    for _ in range(warm):
+        S.global_step()
     d0 = S.dof_updates
-    t0 = time.perf_counter()
-    S.global_step()
-    out.append((S.dof_updates - d0, time.perf_counter() - t0))
-print(json.dumps(out))
-"""
+    t0 = time.time()
+    for _ in range(timed):
+        S.global_step()
+    queue.put((S.dof_updates - d0, t0, time.time()))
 
 
-def run_oracle_steps(steps, timeout=1800):
-    env = dict(os.environ)
+def _replica_count():
+    """Host cores, bounded so that the replicas take at most half of the available memory."""
+    n = os.cpu_count() or 1
+    try:
+        avail = [int(l.split()[1]) * 1024 for l in open("/proc/meminfo") if l.startswith("MemAvailable:")][0]
+        n = min(n, max(1, int(0.5 * avail // ORACLE_BYTES_PER_PROCESS)))
+    except (OSError, IndexError, ValueError):
+        n = 1
+    return max(1, n)
+
+
+def run_oracle_replicas(n_proc, warm, timed, timeout=3600):
+    """n_proc independent oracle instances (spawned processes, one thread each: independent shots, the
+    data-parallel form of the method) stepping at the same time.  Returns (DOF updates of the timed
+    steps over all replicas, seconds from the first start to the last end of the timed steps)."""
+    import multiprocessing as mp
+
     for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[v] = "1"
-    r = subprocess.run([sys.executable, "-c", ORACLE_SAMPLE.format(root=ROOT, steps=steps)], capture_output=True,
-                       text=True, env=env, timeout=timeout)
-    if r.returncode != 0:
-        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
-    return json.loads(r.stdout.strip().splitlines()[-1])
+        os.environ[v] = "1"
+    ctx = mp.get_context("spawn")
+    barrier, queue = ctx.Barrier(n_proc), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_replica, args=(ROOT, warm, timed, barrier, queue)) for _ in range(n_proc)]
+    for p in procs:
+        p.start()
+    try:
+        res = [queue.get(timeout=timeout) for _ in range(n_proc)]
+    finally:
+        for p in procs:
+            p.join(timeout=60)
+            if p.is_alive():
+                p.kill()
+    dof = sum(r[0] for r in res)
+    return dof, max(r[2] for r in res) - min(r[1] for r in res)
 
 
 def cpu_baseline_line():
-    res = run_oracle_steps(1)
-    dof, sec = res[-1]
-    return {"value": dof / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"1 global MRAB step (4 steps of the finest level, source on) of the same 190608-tet N=4 "
-                      f"mesh in the FP64 numpy oracle, 1 thread: {dof} DOF updates in {sec:.2f} s"}
+    """The oracle on the host cores, after the GPU work: one global MRAB step of the bench mesh on one
+    thread, then one step in each of P replicas stepping together (P = host cores, memory allowing)."""
+    dof1, sec1 = run_oracle_replicas(1, 0, 1)
+    n = _replica_count()
+    dofn, secn = run_oracle_replicas(n, 0, 1) if n > 1 else (dof1, sec1)
+    return {"value": dofn / secn, "unit": UNIT, "cores": n, "kind": "oracle",
+            "one_thread": {"value": dof1 / sec1, "cores": 1, "seconds": sec1},
+            "sample": f"1 global MRAB step (4 steps of the finest level, source on) of the same 190608-tet N=4 mesh "
+                      f"in the FP64 numpy oracle: {n} independent single-threaded instances stepping together "
+                      f"({dofn} DOF updates in {secn:.2f} s; value = all of them / wall time) and one instance alone "
+                      f"({dof1} in {sec1:.2f} s)"}
 
 
 # --------------------------------------------------------------------------- reference arm
@@ -196,18 +231,17 @@ def run_reference(args):
     if rank != 0:
         return 0
     w = _workload()
-    res = run_oracle_steps(args.warmup + args.steps)
-    timed = res[args.warmup:]
-    dof = sum(d for d, _ in timed)
-    sec = sum(s for _, s in timed)
+    n = _replica_count()
+    dof, sec = run_oracle_replicas(n, args.warmup, args.steps)
     value = dof / sec
+    sample = (f"{n} independent oracle instances (FP64 numpy, one thread each) stepping together: {args.steps} global "
+              f"MRAB steps each after {args.warmup} warm-up steps")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config(w, {"reference_step": "one global MRAB step of the forward source run"}),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} global MRAB steps after {args.warmup} warm-up steps, FP64 numpy, 1 thread"},
+        "config": _config(w, {"reference_step": "one global MRAB step of the forward source run per instance"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -279,14 +313,6 @@ def run_ridg(args):
 
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
-    # the oracle CPU baseline runs in its own process; start it before the GPU work (rank 0, N = 1)
-    cpu_future = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        import concurrent.futures as cf
-
-        cpu_pool = cf.ThreadPoolExecutor(max_workers=1)
-        cpu_future = cpu_pool.submit(cpu_baseline_line)
-
     from paper_1506_00907_gb300 import ridg
 
     w = _workload()
@@ -441,11 +467,14 @@ def run_ridg(args):
             "gpu_launches": int(launches),
             "clocks": clocks,
         }
-        if cpu_future is not None:
+        # the oracle CPU baseline (rank 0, N = 1) runs after every GPU leg, so it shares no host cores
+        # with the GPU measurement
+        if world == 1 and not args.no_cpu_baseline:
+            torch.cuda.synchronize()
             try:
-                line["cpu_baseline"] = cpu_future.result(timeout=1800)
+                line["cpu_baseline"] = cpu_baseline_line()
             except Exception as exc:  # noqa: BLE001
-                line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
                                         "sample": f"failed: {exc}"}
         print(json.dumps(line), flush=True)
     if dist is not None:

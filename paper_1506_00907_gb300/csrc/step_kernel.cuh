@@ -73,6 +73,7 @@ struct WaveArgs {
   int amp_mode;           // 0 none, 1 constant amplitude, 2 interpolated data rows
   real amp;               // amp_mode 1
   const double* data;     // amp_mode 2: [rows][n_time]
+  const double* data_scale;  // amp_mode 2: the rows are injected times *data_scale (a power of two), or null
   int n_time;
 };
 
@@ -618,6 +619,7 @@ __global__ void __launch_bounds__(Order<N>::NT) dg_step_kernel(const StepArgs<re
               int nt = A.interp_n0 + t;
               if (nt >= 0 && nt < wa.n_time) acc += A.interp_w[t] * wa.data[int64_t(row) * wa.n_time + nt];
             }
+            if (wa.data_scale) acc *= *wa.data_scale;
             amp = real(acc);
           }
           r[0][k] += amp * wa.inj_w[int64_t(q) * Np + n];

@@ -636,6 +636,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
               const int nt = A.interp_n0 + tt;
               if (nt >= 0 && nt < wa.n_time) acc += A.interp_w[tt] * wa.data[int64_t(row) * wa.n_time + nt];
             }
+            if (wa.data_scale) acc *= *wa.data_scale;
             amp = float(acc);
           }
           r[w][0] += amp * wa.inj_w[int64_t(qq) * Np + n];

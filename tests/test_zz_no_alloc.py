@@ -31,13 +31,15 @@ def test_energy_noalloc_matches_energy_on_two_calls(dtype):
         q = random_state(w.K, s.Np, seed=seed)
         s.set_state(q)
         e_ref = s.energy()
-        # both entry points against the oracle's energy of the same (working-precision) fields
+        # both entry points against the oracle's energy of the same (working-precision) fields; the
+        # FP32 solver's material factors are FP32 too (2^-24 each), hence 1e-6 there
         e_oracle = energy(q.astype(np.float32).astype(np.float64) if dtype == "f32" else q, geo)
-        assert abs(e_ref - e_oracle) <= 1e-12 * e_oracle
+        tol = 1e-6 if dtype == "f32" else 1e-12
+        assert abs(e_ref - e_oracle) <= tol * e_oracle
         s.energy_noalloc(out[seed - 21:])
         torch.cuda.synchronize()
         e_new = float(out[seed - 21].item())
         assert np.isfinite(e_new) and e_ref > 0
         # same FP64 accumulation, different summation order
         assert abs(e_new - e_ref) <= 1e-12 * abs(e_ref)
-        assert abs(e_new - e_oracle) <= 1e-12 * e_oracle
+        assert abs(e_new - e_oracle) <= tol * e_oracle
