@@ -364,6 +364,61 @@ int ridg_server_wait(ridg_server* sv, int64_t ticket, double timeout_s, ridg_req
  * the server; the solvers can be used again afterwards. */
 int ridg_server_destroy(ridg_server* sv);
 
+/* ------------------------------------------------------------------ domain decomposition (Sec. 4.2)
+ * One shot on a mesh split into parts, each part advanced by its own solver (on its own device, or
+ * several parts on one device), as the paper runs one part per device of a cluster.  After every
+ * fine step the traces (p, n.v) that a part's elements pushed across faces to elements of another
+ * part are copied into that part's face inboxes; only the elements advanced at that step have
+ * pushed, and with the lumping below the steps that advance the finest level only copy nothing.
+ * Both backward wavefields use the same partition, so the images need no transfer (Sec. 4.2).  The
+ * union of the parts' traces and images is the shot of one solver over the whole mesh. */
+#define RIDG_MAX_PARTS 64
+typedef struct ridg_group ridg_group;
+
+/* part_out (host int32 [K]): the part of each element, for n_parts parts (1..RIDG_MAX_PARTS).
+ * Weights 2^(l-1) per element of level l (l = 1 coarsest: its right-hand-side evaluations per
+ * global step), levels as ridg_solver_create assigns them (opt: cfl, n_levels_max; NULL for the
+ * defaults) for order N and velocity c (host double [K]); every finest element, or connected group
+ * of them, is lumped with its face neighbours and kept in one part unless the lump outweighs half a
+ * part's share; the lumps are split by weighted recursive coordinate bisection of their weighted
+ * vertex centroids (across the longest extent, at the weighted median; the paper uses METIS with
+ * the same weights and lumping).  Host only.  Errors: RIDG_E_INVALID_ARG. */
+int ridg_partition(const ridg_mesh* mesh, int N, const double* c, const ridg_options* opt, int32_t n_parts,
+                   int32_t* part_out);
+
+typedef struct ridg_group_info {
+  int32_t n_parts;
+  int32_t reserved;
+  int64_t elements[RIDG_MAX_PARTS];        /* elements each part advances */
+  int64_t ghosts[RIDG_MAX_PARTS];          /* elements of other parts next to them */
+  int64_t interface_faces[RIDG_MAX_PARTS]; /* faces across which each part pushes to another part */
+  /* the last shot: */
+  int64_t dof_updates;     /* all parts, both phases */
+  int64_t transfer_steps;  /* fine steps (of all wavefield runs) after which traces were copied */
+  int64_t silent_steps;    /* fine steps that needed no copy (finest level only, lumping held) */
+  int64_t transfer_bytes;  /* bytes copied between parts */
+} ridg_group_info;
+
+/* A group of n_parts solvers for the parts part[K] (host int32, values 0..n_parts-1, each part
+ * non-empty) of mesh, with the media, order and options of ridg_solver_create; part i lives on CUDA
+ * device devices[i] (host int32 [n_parts]; NULL: all on the current device) with a stream of its
+ * own.  Parts on different devices copy traces between devices (peer copies).  The levels and time
+ * step are those of the whole mesh.  Errors: RIDG_E_INVALID_ARG, RIDG_E_BAD_MESH, RIDG_E_OOM,
+ * RIDG_E_CUDA. */
+int ridg_group_create(const ridg_mesh* mesh, int N, const double* c, const double* rho, const ridg_options* opt,
+                      const int32_t* part, int32_t n_parts, const int32_t* devices, ridg_group** out);
+/* One RTM shot over the whole mesh with the arguments and host buffers of ridg_rtm_shot (traces_out
+ * [nrec][n_t], image_p / image_q [K][Np], any of them NULL).  One host thread per part drives it;
+ * the call returns when every part has finished.  A source or receiver belongs to the part of the
+ * element that contains it.  Errors as ridg_rtm_shot. */
+int ridg_group_rtm_shot(ridg_group* g, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                        double t_image_start, const double* observed, double* traces_out, double* image_p,
+                        double* image_q, const double* e_up);
+int ridg_group_info_get(const ridg_group* g, ridg_group_info* out);
+/* n_t of a record of t_final seconds (as ridg_trace_len); Np through np_out (may be NULL). */
+int64_t ridg_group_trace_len(const ridg_group* g, double t_final, int32_t* np_out);
+void ridg_group_destroy(ridg_group* g);
+
 #ifdef __cplusplus
 }
 #endif

@@ -47,6 +47,7 @@ __global__ void sample_receivers_kernel(const real* __restrict__ q, const int64_
   int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= nrec) return;
   int64_t s = rec_slot[r];
+  if (s < 0) return;  // a receiver another part of a partitioned mesh samples
   int64_t blk = s >> 5;
   int lane = int(s & 31);
   double acc = 0.0;
@@ -95,10 +96,12 @@ __global__ void energy_kernel(const real* __restrict__ q, int64_t n_slots, const
   if (threadIdx.x == 0) atomicAdd(out, red[0]);
 }
 
-// Image from the slot layout [n_slots/32][Np][32] to element order [K][Np].
+// Image from the slot layout [n_slots/32][Np][32] to element order [K][Np], times *inv_scale (a power
+// of two; null = 1).
 template <int N>
 __global__ void image_to_elements_kernel(const double* __restrict__ img, const int64_t* __restrict__ slot_of,
-                                         const int* __restrict__ pos_of, int64_t K, double* __restrict__ out) {
+                                         const int* __restrict__ pos_of, int64_t K, const double* __restrict__ inv_scale,
+                                         double* __restrict__ out) {
   using O = Order<N>;
   constexpr int Np = O::Np;
   int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -106,7 +109,12 @@ __global__ void image_to_elements_kernel(const double* __restrict__ img, const i
   int64_t k = i / Np;
   int n = int(i - k * Np);  // reference numbering; pos_of[n] is the node's place in the slot layout
   int64_t s = slot_of[k];
-  out[i] = img[((s >> 5) * Np + pos_of[n]) * 32 + (s & 31)];
+  if (s < 0) {  // an element another part of a partitioned mesh images
+    out[i] = 0.0;
+    return;
+  }
+  const double v = img[((s >> 5) * Np + pos_of[n]) * 32 + (s & 31)];
+  out[i] = inv_scale ? v * *inv_scale : v;
 }
 
 // Fields between the C-ABI layout [K][4][Np] (double, reference node numbering) and the slot
@@ -120,6 +128,7 @@ __global__ void state_from_abi_kernel(const double* __restrict__ q_abi, const in
   int64_t k = i / (4 * Np);
   int r = int(i - k * 4 * Np), fld = r / Np, n = r - fld * Np;
   int64_t s = slot_of[k];
+  if (s < 0) return;
   q[(((s >> 5) * 4 + fld) * Np + pos_of[n]) * 32 + (s & 31)] = real(q_abi[i]);
 }
 template <int N, typename real>
@@ -131,7 +140,7 @@ __global__ void state_to_abi_kernel(const real* __restrict__ q, const int64_t* _
   int64_t k = i / (4 * Np);
   int r = int(i - k * 4 * Np), fld = r / Np, n = r - fld * Np;
   int64_t s = slot_of[k];
-  q_abi[i] = double(q[(((s >> 5) * 4 + fld) * Np + pos_of[n]) * 32 + (s & 31)]);
+  q_abi[i] = s < 0 ? 0.0 : double(q[(((s >> 5) * 4 + fld) * Np + pos_of[n]) * 32 + (s & 31)]);
 }
 
 }  // namespace ridg

@@ -81,8 +81,8 @@ struct Launch {
                             const double* M, double* out, cudaStream_t st);
   static cudaError_t state_io(bool to_slots, const double* q_abi_in, double* q_abi_out, real* q,
                               const int64_t* slot_of, const int* pos_of, int64_t K, cudaStream_t st);
-  static cudaError_t image_out(const double* img, const int64_t* slot_of, const int* pos_of, int64_t K, double* out,
-                               cudaStream_t st);
+  static cudaError_t image_out(const double* img, const int64_t* slot_of, const int* pos_of, int64_t K,
+                               const double* inv_scale, double* out, cudaStream_t st);
   // discrete adjoint (adjoint_kernels.cuh)
   // out = A^T lam; own, inbox: scratch adjoint traces [n_slots][4][2][NFPP] each; Dt4: [Np][Np][4]
   // (D_0, D_1, D_2, 0)[n][m] at (m, n).  With s1 != null the adjoint Adams-Bashforth update

@@ -76,9 +76,9 @@ cudaError_t Launch<N, real>::energy(const real* q, int64_t n_slots, const double
 
 template <int N, typename real>
 cudaError_t Launch<N, real>::image_out(const double* img, const int64_t* slot_of, const int* pos_of, int64_t K,
-                                       double* out, cudaStream_t st) {
+                                       const double* inv_scale, double* out, cudaStream_t st) {
   int64_t n = K * Order<N>::Np;
-  image_to_elements_kernel<N><<<unsigned((n + 255) / 256), 256, 0, st>>>(img, slot_of, pos_of, K, out);
+  image_to_elements_kernel<N><<<unsigned((n + 255) / 256), 256, 0, st>>>(img, slot_of, pos_of, K, inv_scale, out);
   return cudaGetLastError();
 }
 

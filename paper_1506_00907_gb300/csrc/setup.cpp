@@ -9,6 +9,7 @@
 #include "setup.hpp"
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <numeric>
 
@@ -629,9 +630,141 @@ Ordering build_ordering(const Levels& lv, int64_t K) {
   }
   o.level_begin[lv.n_levels] = slot;
   o.n_slots = slot;
+  o.owned_end = slot;
   o.elem_of.assign(slot, -1);
   for (int64_t k = 0; k < K; ++k) o.elem_of[o.slot_of[k]] = k;
   return o;
+}
+
+Ordering build_part_ordering(const Levels& lv, const MeshData& m, const int32_t* part, int32_t rank) {
+  const int64_t K = m.K;
+  Ordering o;
+  o.slot_of.assign(K, -1);
+  o.level_begin.assign(lv.n_levels + 1, 0);
+  int64_t slot = 0;
+  for (int l = 1; l <= lv.n_levels; ++l) {
+    o.level_begin[l - 1] = slot;
+    for (int64_t k = 0; k < K; ++k)
+      if (part[k] == rank && lv.level[k] == l) o.slot_of[k] = slot++;
+    slot = (slot + 31) / 32 * 32;
+  }
+  o.level_begin[lv.n_levels] = slot;
+  o.owned_end = slot;
+  std::vector<char> ghost(K, 0);
+  for (int64_t k = 0; k < K; ++k)
+    if (part[k] == rank)
+      for (int f = 0; f < 4; ++f) {
+        const int64_t k2 = m.nbr[4 * k + f];
+        if (k2 >= 0 && part[k2] != rank) ghost[k2] = 1;
+      }
+  for (int64_t k = 0; k < K; ++k)
+    if (ghost[k]) o.slot_of[k] = slot++;
+  slot = (slot + 31) / 32 * 32;
+  o.n_slots = slot;
+  o.elem_of.assign(slot, -1);
+  for (int64_t k = 0; k < K; ++k)
+    if (o.slot_of[k] >= 0) o.elem_of[o.slot_of[k]] = k;
+  return o;
+}
+
+namespace {
+
+// weighted recursive coordinate bisection of points (part index per point)
+void rcb_split(const std::vector<std::array<double, 3>>& pt, const std::vector<double>& w, std::vector<int64_t> idx,
+               int32_t first, int32_t n, std::vector<int32_t>& out) {
+  if (n == 1 || idx.empty()) {
+    for (int64_t i : idx) out[i] = first;
+    return;
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int64_t i : idx)
+    for (int d = 0; d < 3; ++d) {
+      lo[d] = std::min(lo[d], pt[i][d]);
+      hi[d] = std::max(hi[d], pt[i][d]);
+    }
+  int axis = 0;
+  for (int d = 1; d < 3; ++d)
+    if (hi[d] - lo[d] > hi[axis] - lo[axis]) axis = d;
+  std::stable_sort(idx.begin(), idx.end(), [&](int64_t a, int64_t b) {
+    return pt[a][axis] < pt[b][axis] || (pt[a][axis] == pt[b][axis] && a < b);
+  });
+  const int32_t n_left = n / 2;
+  std::vector<double> cw(idx.size());
+  double acc = 0.0;
+  for (size_t i = 0; i < idx.size(); ++i) cw[i] = (acc += w[idx[i]]);
+  const double target = cw.back() * double(n_left) / double(n);
+  int64_t cut = std::lower_bound(cw.begin(), cw.end(), target) - cw.begin();
+  if (idx.size() > 1)
+    cut = std::min<int64_t>(std::max<int64_t>(cut, 1), int64_t(idx.size()) - 1);
+  else
+    cut = int64_t(idx.size());
+  rcb_split(pt, w, std::vector<int64_t>(idx.begin(), idx.begin() + cut), first, n_left, out);
+  rcb_split(pt, w, std::vector<int64_t>(idx.begin() + cut, idx.end()), first + n_left, n - n_left, out);
+}
+
+int64_t uf_find(std::vector<int64_t>& parent, int64_t a) {
+  int64_t root = a;
+  while (parent[root] != root) root = parent[root];
+  while (parent[a] != root) {
+    const int64_t next = parent[a];
+    parent[a] = root;
+    a = next;
+  }
+  return root;
+}
+
+}  // namespace
+
+std::vector<int32_t> partition_mesh(const MeshData& m, const Levels& lv, int32_t n_parts) {
+  const int64_t K = m.K;
+  if (n_parts < 1) throw Error{RIDG_E_INVALID_ARG, "n_parts must be >= 1"};
+  std::vector<double> w(K);
+  double total = 0.0;
+  for (int64_t k = 0; k < K; ++k) total += (w[k] = double(int64_t(1) << (lv.level[k] - 1)));
+  // lumps: each finest element joined with its face neighbours
+  std::vector<int64_t> parent(K);
+  for (int64_t k = 0; k < K; ++k) parent[k] = k;
+  if (lv.n_levels >= 2)
+    for (int64_t k = 0; k < K; ++k)
+      if (lv.level[k] == lv.n_levels)
+        for (int f = 0; f < 4; ++f) {
+          const int64_t k2 = m.nbr[4 * k + f];
+          if (k2 < 0) continue;
+          const int64_t ra = uf_find(parent, k), rb = uf_find(parent, k2);
+          if (ra != rb) parent[std::max(ra, rb)] = std::min(ra, rb);
+        }
+  // unit number per element: lumps in the order of their smallest element; the elements of lumps
+  // too heavy to keep whole become units of their own, numbered after every kept lump
+  std::vector<int64_t> root(K);
+  for (int64_t k = 0; k < K; ++k) root[k] = uf_find(parent, k);
+  std::vector<double> rw(K, 0.0);
+  for (int64_t k = 0; k < K; ++k) rw[root[k]] += w[k];
+  std::vector<int64_t> key(K);
+  for (int64_t k = 0; k < K; ++k) key[k] = rw[root[k]] > 0.5 * total / double(n_parts) ? K + k : root[k];
+  std::vector<int64_t> sorted = key;
+  std::sort(sorted.begin(), sorted.end());
+  sorted.erase(std::unique(sorted.begin(), sorted.end()), sorted.end());
+  std::vector<int64_t> unit(K);
+  for (int64_t k = 0; k < K; ++k) unit[k] = std::lower_bound(sorted.begin(), sorted.end(), key[k]) - sorted.begin();
+  const int64_t n_units = int64_t(sorted.size());
+  std::vector<double> uw(n_units, 0.0);
+  std::vector<std::array<double, 3>> uc(n_units, {0.0, 0.0, 0.0});
+  for (int64_t k = 0; k < K; ++k) uw[unit[k]] += w[k];
+  for (int d = 0; d < 3; ++d)
+    for (int64_t k = 0; k < K; ++k) {
+      double cen = 0.0;
+      for (int v = 0; v < 4; ++v) cen += m.xyz[3 * m.tet[4 * k + v] + d];
+      uc[unit[k]][d] += w[k] * (cen / 4.0);
+    }
+  for (int64_t u = 0; u < n_units; ++u)
+    for (int d = 0; d < 3; ++d) uc[u][d] /= uw[u];
+  std::vector<int32_t> upart(n_units, 0);
+  std::vector<int64_t> all(n_units);
+  for (int64_t u = 0; u < n_units; ++u) all[u] = u;
+  rcb_split(uc, uw, all, 0, n_parts, upart);
+  std::vector<int32_t> out(K);
+  for (int64_t k = 0; k < K; ++k) out[k] = upart[unit[k]];
+  return out;
 }
 
 PointLocator build_locator(const MeshData& m) {

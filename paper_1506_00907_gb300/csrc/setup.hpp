@@ -96,13 +96,26 @@ struct Levels {
 Levels assign_levels(const MeshData& m, const Geometry& g, int N, const double* c, double cfl, int n_levels_max);
 
 // Element order on the device: levels coarse -> fine, each level padded to a multiple of 32.
+// Slots [0, owned_end) are the elements the solver advances.  A solver for one part of a partitioned
+// mesh (Sec. 4.2) places after them, in slots [owned_end, n_slots), the ghosts: elements of other
+// parts that share a face with one of its own; they are never advanced, but their face inboxes
+// receive the traces this part pushes across the interface (which the other part then takes).
 struct Ordering {
   int64_t n_slots = 0;
-  std::vector<int64_t> slot_of;      // [K]
+  int64_t owned_end = 0;
+  std::vector<int64_t> slot_of;      // [K], -1 for elements of other parts that are not ghosts
   std::vector<int64_t> elem_of;      // [n_slots], -1 for padding
   std::vector<int64_t> level_begin;  // [n_levels+1] slot ranges per level (multiples of 32)
 };
 Ordering build_ordering(const Levels& lv, int64_t K);
+// The elements with part[k] == rank by level, then their ghosts (padded to a multiple of 32).
+Ordering build_part_ordering(const Levels& lv, const MeshData& m, const int32_t* part, int32_t rank);
+
+// Partition of the elements into n_parts (Sec. 4.2): weights 2^(l-1) per element; every element of
+// the finest level, or connected group of them, lumped with its face neighbours and kept in one part
+// unless the lump weighs more than half of one part's share; weighted recursive coordinate bisection
+// of the lumps' weighted vertex centroids (split across the longest extent at the weighted median).
+std::vector<int32_t> partition_mesh(const MeshData& m, const Levels& lv, int32_t n_parts);
 
 // Point location: lowest element index whose barycentrics are all >= -1e-12; returns -1 if none.
 // Uniform grid over the mesh's bounding box; each cell lists (in increasing order) the elements

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
@@ -19,7 +20,9 @@
 
 #include "ridg.h"
 #include "dispatch.hpp"
+#include "data_scale.hpp"
 #include "energy_noalloc.hpp"
+#include "exchange.hpp"
 #include "setup.hpp"
 #include "step_kernel_tc.cuh"
 
@@ -182,6 +185,16 @@ struct ridg_solver {
   virtual void misfit_backward(double* grad) = 0;
 };
 
+// A shot on a partitioned mesh, one solver per part (ridg_group_*).
+struct ridg_group {
+  virtual ~ridg_group() = default;
+  virtual void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i,
+                    const double* observed, double* traces_out, double* image_p, double* image_q,
+                    const double* e_up) = 0;
+  virtual void info(ridg_group_info* out) const = 0;
+  virtual int64_t trace_len(double t_final, int32_t* np_out) const = 0;
+};
+
 namespace ridg {
 
 template <typename real>
@@ -190,10 +203,32 @@ struct Wave {
   DBuf inj_range, inj_w, inj_row;
 };
 
+// What a solver for one part of a partitioned mesh (Sec. 4.2) asks of the group that drives the
+// parts: after each fine step (and after the traces are initialised) the interface traces its
+// elements pushed into their ghosts' inboxes go to the parts that own those ghosts, and the data
+// scale of the receiver run is taken over the data of every part.
+template <typename real>
+class Engine;
+template <typename real>
+struct PartHook {
+  virtual ~PartHook() = default;
+  // pushers: levels >= first_level pushed traces at this step; waves: bit w = wavefield w
+  virtual void exchange(Engine<real>& e, int first_level, int waves) = 0;
+  // work: the engine's data-scale work buffer, holding this part's max |data| bits
+  virtual void combine_data_scale(Engine<real>& e, void* work) = 0;
+};
+
+template <typename real>
+class Group;
+
 template <typename real>
 class Engine final : public ridg_solver {
+  template <typename R>
+  friend class Group;
+
  public:
-  Engine(const MeshData& mesh, int N, const double* c, const double* rho, const ridg_options& opt, cudaStream_t st)
+  Engine(const MeshData& mesh, int N, const double* c, const double* rho, const ridg_options& opt, cudaStream_t st,
+         const int32_t* part = nullptr, int32_t rank = 0)
       : mesh_(mesh), N_(N), st_(st) {
     {
       // the device numbers the element's nodes so that face-node gathers spread over the banks;
@@ -228,7 +263,11 @@ class Engine final : public ridg_solver {
                   ((opt.image_mask & RIDG_IMAGE_Q) || !(opt.image_mask & 3) ? kModeImageQ : 0);
     if (nlm > kMaxLevels) throw Error{RIDG_E_INVALID_ARG, "n_levels_max too large"};
     lv_ = assign_levels(mesh_, geo_, N, c_.data(), cfl, nlm);
-    ord_ = build_ordering(lv_, mesh_.K);
+    if (part) {
+      part_.assign(part, part + mesh_.K);
+      rank_ = rank;
+    }
+    ord_ = part ? build_part_ordering(lv_, mesh_, part, rank) : build_ordering(lv_, mesh_.K);
     n_slots_ = ord_.n_slots;
     L_ = lv_.n_levels;
     NL_ = int64_t(1) << (L_ - 1);
@@ -333,7 +372,7 @@ class Engine final : public ridg_solver {
     a.wave[0] = wave_args(tmp);
     a.wave[0].amp_mode = 0;
     a.slot_lo = 0;
-    a.slot_hi = n_slots_;
+    a.slot_hi = ord_.owned_end;
     a.trace_read = 0;
     a.tau_sign = real(1);
     a.mode = kModeRhsOnly;
@@ -411,7 +450,7 @@ class Engine final : public ridg_solver {
     if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
     {
       std::vector<int2> range(n_slots_, make_int2(0, 0));
-      range[ord_.slot_of[ks]] = make_int2(0, 1);
+      if (owned(ks)) range[ord_.slot_of[ks]] = make_int2(0, 1);
       upload(w_[0].inj_range, range, st_);
       upload(w_[0].inj_w, projected_dirac(ks, rst), st_);
       upload(w_[0].inj_row, std::vector<int>{0}, st_);
@@ -421,7 +460,7 @@ class Engine final : public ridg_solver {
     for (int64_t r = 0; r < nrec; ++r) {
       const int64_t kr = locate_point(mesh_, loc_, rec + 3 * r, rst);
       if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
-      rslot[r] = ord_.slot_of[kr];
+      rslot[r] = owned(kr) ? ord_.slot_of[kr] : -1;
       std::vector<double> l = ref_.lagrange_at({rst[0], rst[1], rst[2]});
       for (int m = 0; m < Np_; ++m) rrow[r * Np_ + m] = real(l[m]);
     }
@@ -535,7 +574,7 @@ class Engine final : public ridg_solver {
     for (int64_t r = 0; r < nrec; ++r) {
       const int64_t kr = locate_point(mesh_, loc_, rec + 3 * r, rst);
       if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
-      rslot[r] = ord_.slot_of[kr];
+      rslot[r] = owned(kr) ? ord_.slot_of[kr] : -1;
       std::vector<double> l = ref_.lagrange_at({rst[0], rst[1], rst[2]});
       for (int m = 0; m < Np_; ++m) rrow[r * Np_ + m] = real(l[m]);
     }
@@ -819,6 +858,7 @@ class Engine final : public ridg_solver {
     if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
     std::vector<real> w_src = projected_dirac(ks, rst);
     const Wavelet wav = Wavelet::of(src);
+    const bool src_here = owned(ks);
     struct Rec {
       int64_t slot;
       std::vector<real> row, w;
@@ -828,7 +868,7 @@ class Engine final : public ridg_solver {
     for (int64_t r = 0; r < nrec; ++r) {
       int64_t kr = locate_point(mesh_, loc_, rec + 3 * r, rst);
       if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
-      recs[r].slot = ord_.slot_of[kr];
+      recs[r].slot = owned(kr) ? ord_.slot_of[kr] : -1;  // -1: another part samples and injects it
       std::array<double, 3> p = {rst[0], rst[1], rst[2]};
       std::vector<double> l = ref_.lagrange_at(p);
       recs[r].row.assign(l.begin(), l.end());
@@ -838,7 +878,7 @@ class Engine final : public ridg_solver {
     // source injection table (wavefield 0)
     {
       std::vector<int2> range(n_slots_, make_int2(0, 0));
-      range[ord_.slot_of[ks]] = make_int2(0, 1);
+      if (src_here) range[ord_.slot_of[ks]] = make_int2(0, 1);
       upload(w_[0].inj_range, range, st_);
       upload(w_[0].inj_w, w_src, st_);
       upload(w_[0].inj_row, std::vector<int>{0}, st_);
@@ -846,7 +886,9 @@ class Engine final : public ridg_solver {
     alloc_wave(w_[1]);
     {
       // receiver injections grouped by slot (wavefield 1)
-      std::vector<Rec> sorted = recs;
+      std::vector<Rec> sorted;
+      for (const Rec& r : recs)
+        if (r.slot >= 0) sorted.push_back(r);
       std::stable_sort(sorted.begin(), sorted.end(), [](const Rec& a, const Rec& b) { return a.slot < b.slot; });
       std::vector<int2> range(n_slots_, make_int2(0, 0));
       std::vector<real> wv;
@@ -931,7 +973,22 @@ class Engine final : public ridg_solver {
     tau_ = tau_f;
     RIDG_CUDA(cudaMemsetAsync(w_[0].trace.p, 0, w_[0].trace.bytes, st_));
     init_traces(w_[0], mod3(tau_));
+    if (hook_) hook_->exchange(*this, 1, 1);
     const double* data = obs_dev ? obs_dev : traces;
+    // the receiver run injects the data times a power of two that brings max |data| into [1, 2), so
+    // that the image products of small-amplitude shots stay inside the FP32 range; the images are
+    // divided by it on the way out (both steps exact)
+    const double* dscale = nullptr;
+    const double* dscale_inv = nullptr;
+    if (nrec > 0) {
+      scale_d_.reserve(kDataScaleWorkBytes);
+      cudaError_t e = data_scale(data, nrec * n_t, scale_d_.p, st_);
+      if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("data scale: ") + cudaGetErrorString(e)};
+      if (hook_) hook_->combine_data_scale(*this, scale_d_.p);
+      stats_.kernel_launches += 2;
+      dscale = dptr<const double>(scale_d_) + 1;
+      dscale_inv = dptr<const double>(scale_d_) + 2;
+    }
     int64_t dof_before = dof_;
     while (tau_ > tau_i) {
       StepArgs<real> a = fine_args(-1, 2, kModeReplay | image_mode_);
@@ -941,6 +998,7 @@ class Engine final : public ridg_solver {
       a.wave[1] = wave_args(w_[1]);
       a.wave[1].amp_mode = nrec > 0 ? 2 : 0;
       a.wave[1].data = data;
+      a.wave[1].data_scale = dscale;
       a.wave[1].n_time = int(n_t);
       int64_t n_lo = tau_ / NL_;
       double u = double(tau_ - n_lo * NL_) / double(NL_);
@@ -962,8 +1020,8 @@ class Engine final : public ridg_solver {
       launch_fine(a, -1, 2);
     }
     stats_.dof_updates_backward = dof_ - dof_before;
-    if (imgp_dev) image_out(dptr<double>(img_p_), imgp_dev);
-    if (imgq_dev) image_out(dptr<double>(img_q_), imgq_dev);
+    if (imgp_dev) image_out(dptr<double>(img_p_), dscale_inv, imgp_dev);
+    if (imgq_dev) image_out(dptr<double>(img_q_), dscale_inv, imgq_dev);
     RIDG_CUDA(cudaGetLastError());
   }
 
@@ -999,6 +1057,7 @@ class Engine final : public ridg_solver {
     std::vector<real> h(qsize(), real(0));
     for (int64_t k = 0; k < mesh_.K; ++k) {
       int64_t s = ord_.slot_of[k];
+      if (!owned(k)) continue;
       for (int f = 0; f < 4; ++f)
         for (int n = 0; n < Np_; ++n)
           h[(((s >> 5) * 4 + f) * Np_ + pos_of_[n]) * 32 + (s & 31)] = real(q[(k * 4 + f) * Np_ + n]);
@@ -1010,7 +1069,7 @@ class Engine final : public ridg_solver {
       int64_t s = ord_.slot_of[k];
       for (int f = 0; f < 4; ++f)
         for (int n = 0; n < Np_; ++n)
-          q[(k * 4 + f) * Np_ + n] = double(h[(((s >> 5) * 4 + f) * Np_ + pos_of_[n]) * 32 + (s & 31)]);
+          q[(k * 4 + f) * Np_ + n] = owned(k) ? double(h[(((s >> 5) * 4 + f) * Np_ + pos_of_[n]) * 32 + (s & 31)]) : 0.0;
     }
   }
 
@@ -1072,7 +1131,7 @@ class Engine final : public ridg_solver {
     for (int64_t s = 0; s < S; ++s) {
       bface[s] = int(nb);
       int64_t k = ord_.elem_of[s];
-      if (k < 0) continue;
+      if (k < 0 || s >= ord_.owned_end) continue;  // padding, or a ghost of another part
       meta[s] = kMetaValid;
       for (int i = 0; i < 9; ++i) geo[s * kGeo + i] = geo_.rx[9 * k + i];
       for (int i = 0; i < 12; ++i) geo[s * kGeo + 9 + i] = geo_.normal[12 * k + i];
@@ -1125,7 +1184,8 @@ class Engine final : public ridg_solver {
     upload(pos_d_, pos_of_, st_);
     upload(slot_of_d_, ord_.slot_of, st_);
     level_count_.assign(L_, 0);
-    for (int64_t k = 0; k < mesh_.K; ++k) level_count_[lv_.level[k] - 1]++;
+    for (int64_t k = 0; k < mesh_.K; ++k)
+      if (owned(k)) level_count_[lv_.level[k] - 1]++;
   }
 
   // Per-element coefficients of the FP32 tensor-core kernel for penalty sign `sigma` (Eq. penaltyFlux
@@ -1336,7 +1396,7 @@ class Engine final : public ridg_solver {
     StepArgs<real> a = base_args();
     int l0 = first_active_level(tau_);
     a.slot_lo = ord_.level_begin[l0 - 1];
-    a.slot_hi = n_slots_;
+    a.slot_hi = ord_.owned_end;
     a.trace_read = mod3(tau_);
     for (int l = 1; l <= L_; ++l) {
       int64_t d = int64_t(1) << (L_ - l);
@@ -1382,6 +1442,7 @@ class Engine final : public ridg_solver {
       RIDG_CUDA(cudaEventRecord(prof_ev_[2 * prof_used_ + 1], st_));
       ++prof_used_;
     }
+    if (hook_) hook_->exchange(*this, l0, W == 2 ? 3 : 1);
     for (int l = l0; l <= L_; ++l) {
       ring_count_[l - 1] += 1;
       dof_ += level_count_[l - 1] * 4 * Np_ * W;
@@ -1428,10 +1489,10 @@ class Engine final : public ridg_solver {
                               cudaMemcpyDeviceToDevice, st_));
   }
 
-  void image_out(const double* img, double* out) {
+  void image_out(const double* img, const double* inv_scale, double* out) {
     cudaError_t e = dispatch_order(N_, [&](auto NC) {
       return Launch<decltype(NC)::value, real>::image_out(img, dptr<const int64_t>(slot_of_d_), dptr<const int>(pos_d_),
-                                                           mesh_.K, out, st_);
+                                                           mesh_.K, inv_scale, out, st_);
     });
     if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
     ++stats_.kernel_launches;
@@ -1453,7 +1514,13 @@ class Engine final : public ridg_solver {
     return v;
   }
 
+  // this solver advances element k (the whole mesh, or its part of a partitioned mesh)
+  bool owned(int64_t k) const { return ord_.slot_of[k] >= 0 && ord_.slot_of[k] < ord_.owned_end; }
+
   MeshData mesh_;
+  std::vector<int32_t> part_;  // part per element of a partitioned mesh (empty: the whole mesh)
+  int32_t rank_ = 0;
+  PartHook<real>* hook_ = nullptr;
   int N_, Np_ = 0, Nfp_ = 0, NFPP_ = 16, NPa_ = 0;
   cudaStream_t st_;
   RefElem ref_;
@@ -1483,7 +1550,7 @@ class Engine final : public ridg_solver {
   int contraction_ = RIDG_CONTRACT_TENSOR;  // how the FP32 element products run (FP64: CUDA cores)
   int image_mode_ = kModeImage;
   std::vector<int> pos_of_;  // device position of each reference node
-  DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_;
+  DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_, scale_d_;
   Wave<real> w_[2];
   int64_t tau_ = 0, dof_ = 0;
   std::vector<int> ring_count_;
@@ -1493,6 +1560,339 @@ class Engine final : public ridg_solver {
   std::vector<cudaEvent_t> prof_ev_;
   std::vector<int> prof_w_;
   int64_t n_half_ = 0;
+};
+
+
+// ------------------------------------------------------------------ domain decomposition (Sec. 4.2)
+// A host barrier for the threads that drive the parts of a group; a part that fails releases the
+// others (their wait then throws) so that no thread waits for a part that will not arrive.
+class PartBarrier {
+ public:
+  void reset(int n) {
+    std::lock_guard<std::mutex> l(m_);
+    n_ = n;
+    count_ = 0;
+    aborted_ = false;
+  }
+  void wait() {
+    std::unique_lock<std::mutex> l(m_);
+    if (aborted_) throw Error{RIDG_E_CUDA, "another part of the group failed"};
+    const int64_t gen = gen_;
+    if (++count_ == n_) {
+      count_ = 0;
+      ++gen_;
+      cv_.notify_all();
+      return;
+    }
+    cv_.wait(l, [&] { return gen_ != gen || aborted_; });
+    if (gen_ == gen) throw Error{RIDG_E_CUDA, "another part of the group failed"};
+  }
+  void abort() {
+    std::lock_guard<std::mutex> l(m_);
+    aborted_ = true;
+    cv_.notify_all();
+  }
+
+ private:
+  std::mutex m_;
+  std::condition_variable cv_;
+  int n_ = 1, count_ = 0;
+  int64_t gen_ = 0;
+  bool aborted_ = false;
+};
+
+// One solver per part.  Part p's elements push their traces across an interface face into the inbox
+// of p's ghost copy of the neighbour (an element of part q); after a fine step those rows (all three
+// time slots) go to q, into the inbox of q's own element: gathered on p's stream into a send buffer
+// (two, used in turn), copied on q's stream once p's gather has run, and scattered.  A send buffer
+// is gathered into again only after q's copy from it two transfers earlier has run.  The rows of
+// one ordered pair of parts are sorted by the level of the pushing element, finest first, so the
+// rows pushed at a step whose coarsest advanced level is l0 are a prefix.  Each part's thread runs
+// the unchanged single-solver shot; the solver calls exchange() after every fine step.
+template <typename real>
+class Group final : public ridg_group, public PartHook<real> {
+  struct Pair {
+    int from = 0, to = 0;
+    int64_t n = 0;
+    std::vector<int64_t> prefix;  // [L + 2]: rows pushed by levels >= l0
+    DBuf src_rows, dst_rows;      // on from's and to's device
+    DBuf send[2], recv;           // [2 wavefields][n][3][row_len]
+    cudaEvent_t copied[2] = {nullptr, nullptr};  // recorded on to's stream after each copy
+  };
+  struct Part {
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    std::unique_ptr<Engine<real>> e;
+    cudaEvent_t packed[2] = {nullptr, nullptr};
+    int64_t parity = 0, transfer_steps = 0, silent_steps = 0, bytes = 0;
+    unsigned long long max_bits = 0, global_bits = 0;
+    std::vector<int> out_pairs, in_pairs;
+    DBuf traces, obs, img_p, img_q;
+  };
+
+ public:
+  Group(const MeshData& mesh, int N, const double* c, const double* rho, const ridg_options& opt,
+        const int32_t* part, int32_t n_parts, const int32_t* devices)
+      : K_(mesh.K), parts_(checked_parts(n_parts)) {
+    std::vector<int64_t> count(n_parts, 0);
+    for (int64_t k = 0; k < mesh.K; ++k) {
+      if (part[k] < 0 || part[k] >= n_parts) throw Error{RIDG_E_INVALID_ARG, "part index out of range"};
+      ++count[part[k]];
+    }
+    for (int p = 0; p < n_parts; ++p)
+      if (count[p] == 0) throw Error{RIDG_E_INVALID_ARG, "part " + std::to_string(p) + " has no elements"};
+    int dev0 = 0;
+    RIDG_CUDA(cudaGetDevice(&dev0));
+    for (int p = 0; p < n_parts; ++p) {
+      Part& P = parts_[p];
+      P.dev = devices ? devices[p] : dev0;
+      RIDG_CUDA(cudaSetDevice(P.dev));
+      RIDG_CUDA(cudaStreamCreateWithFlags(&P.st, cudaStreamNonBlocking));
+      P.e.reset(new Engine<real>(mesh, N, c, rho, opt, P.st, part, p));
+      P.e->hook_ = this;
+      for (int i = 0; i < 2; ++i) RIDG_CUDA(cudaEventCreateWithFlags(&P.packed[i], cudaEventDisableTiming));
+    }
+    const Engine<real>& e0 = *parts_[0].e;
+    L_ = e0.L_;
+    row_len_ = 2 * e0.NFPP_;
+    // interface rows of every ordered pair of parts
+    std::map<std::pair<int, int>, std::vector<std::array<int64_t, 5>>> rows;  // (-level, g, f, src, dst)
+    for (int p = 0; p < n_parts; ++p) {
+      const Engine<real>& ep = *parts_[p].e;
+      for (int64_t sl = ep.ord_.owned_end; sl < ep.ord_.n_slots; ++sl) {
+        const int64_t g = ep.ord_.elem_of[sl];
+        if (g < 0) continue;
+        const int q = part[g];
+        for (int f = 0; f < 4; ++f) {
+          const int64_t el = mesh.nbr[4 * g + f];
+          if (el < 0 || part[el] != p) continue;
+          const int64_t dst = parts_[q].e->ord_.slot_of[g];
+          rows[{p, q}].push_back({-int64_t(e0.lv_.level[el]), g, f, sl * 4 + f, dst * 4 + f});
+        }
+      }
+    }
+    for (auto& kv : rows) {
+      auto& v = kv.second;
+      std::sort(v.begin(), v.end());
+      auto pr = std::make_unique<Pair>();
+      pr->from = kv.first.first;
+      pr->to = kv.first.second;
+      pr->n = int64_t(v.size());
+      pr->prefix.assign(L_ + 2, 0);
+      for (int l0 = 1; l0 <= L_; ++l0)
+        for (const auto& r : v)
+          if (-r[0] >= l0) ++pr->prefix[l0];
+      std::vector<int64_t> src(v.size()), dst(v.size());
+      for (size_t i = 0; i < v.size(); ++i) {
+        src[i] = v[i][3];
+        dst[i] = v[i][4];
+      }
+      const size_t buf = size_t(2) * pr->n * 3 * row_len_ * sizeof(real);
+      Part& F = parts_[pr->from];
+      Part& T = parts_[pr->to];
+      RIDG_CUDA(cudaSetDevice(F.dev));
+      upload(pr->src_rows, src, F.st);
+      pr->send[0].alloc(buf);
+      pr->send[1].alloc(buf);
+      RIDG_CUDA(cudaStreamSynchronize(F.st));
+      RIDG_CUDA(cudaSetDevice(T.dev));
+      upload(pr->dst_rows, dst, T.st);
+      pr->recv.alloc(buf);
+      for (int i = 0; i < 2; ++i) RIDG_CUDA(cudaEventCreateWithFlags(&pr->copied[i], cudaEventDisableTiming));
+      RIDG_CUDA(cudaStreamSynchronize(T.st));
+      F.out_pairs.push_back(int(pairs_.size()));
+      T.in_pairs.push_back(int(pairs_.size()));
+      pairs_.push_back(std::move(pr));
+    }
+    any_.assign(L_ + 2, false);
+    for (int l0 = 1; l0 <= L_; ++l0)
+      for (const auto& pr : pairs_) any_[l0] = any_[l0] || pr->prefix[l0] > 0;
+    RIDG_CUDA(cudaSetDevice(dev0));
+  }
+
+  ~Group() override {
+    for (auto& pr : pairs_) {
+      cudaSetDevice(parts_[pr->to].dev);
+      for (auto ev : pr->copied)
+        if (ev) cudaEventDestroy(ev);
+    }
+    pairs_.clear();
+    for (auto& P : parts_) {
+      cudaSetDevice(P.dev);
+      if (P.st) cudaStreamSynchronize(P.st);
+      P.e.reset();
+      P.traces.release();
+      P.obs.release();
+      P.img_p.release();
+      P.img_q.release();
+      for (auto ev : P.packed)
+        if (ev) cudaEventDestroy(ev);
+      if (P.st) cudaStreamDestroy(P.st);
+    }
+  }
+
+  // ---- PartHook (called from the part's own thread, its device current)
+  void exchange(Engine<real>& e, int l0, int waves) override {
+    Part& P = parts_[e.rank_];
+    if (!any_[l0]) {
+      ++P.silent_steps;  // nothing pushed across an interface (finest level only, lumping held)
+      return;
+    }
+    ++P.transfer_steps;
+    const int par = int(P.parity++ & 1);
+    for (int i : P.out_pairs) {
+      Pair& pr = *pairs_[i];
+      const int64_t n = pr.prefix[l0];
+      if (n == 0) continue;
+      RIDG_CUDA(cudaStreamWaitEvent(P.st, pr.copied[par], 0));  // the copy out of this buffer two transfers ago
+      for (int w = 0; w < 2; ++w)
+        if (waves & (1 << w)) check(pack_face_rows<real>(dptr<const real>(e.w_[w].trace), e.n_slots_, row_len_,
+                                                         dptr<const int64_t>(pr.src_rows), n,
+                                                         dptr<real>(pr.send[par]) + size_t(w) * pr.n * 3 * row_len_, P.st));
+    }
+    RIDG_CUDA(cudaEventRecord(P.packed[par], P.st));
+    barrier_.wait();
+    for (int i : P.in_pairs) {
+      Pair& pr = *pairs_[i];
+      const int64_t n = pr.prefix[l0];
+      if (n == 0) continue;
+      const Part& F = parts_[pr.from];
+      RIDG_CUDA(cudaStreamWaitEvent(P.st, F.packed[par], 0));
+      for (int w = 0; w < 2; ++w)
+        if (waves & (1 << w)) {
+          const size_t off = size_t(w) * pr.n * 3 * row_len_, bytes = size_t(n) * 3 * row_len_ * sizeof(real);
+          RIDG_CUDA(cudaMemcpyPeerAsync(dptr<real>(pr.recv) + off, P.dev, dptr<const real>(pr.send[par]) + off, F.dev,
+                                        bytes, P.st));
+          P.bytes += int64_t(bytes);
+        }
+      RIDG_CUDA(cudaEventRecord(pr.copied[par], P.st));
+      for (int w = 0; w < 2; ++w)
+        if (waves & (1 << w)) check(unpack_face_rows<real>(dptr<real>(e.w_[w].trace), e.n_slots_, row_len_,
+                                                           dptr<const int64_t>(pr.dst_rows), n,
+                                                           dptr<const real>(pr.recv) + size_t(w) * pr.n * 3 * row_len_, P.st));
+    }
+  }
+
+  void combine_data_scale(Engine<real>& e, void* work) override {
+    Part& P = parts_[e.rank_];
+    RIDG_CUDA(cudaMemcpyAsync(&P.max_bits, work, sizeof(P.max_bits), cudaMemcpyDeviceToHost, P.st));
+    RIDG_CUDA(cudaStreamSynchronize(P.st));
+    barrier_.wait();
+    P.global_bits = 0;
+    for (const Part& Q : parts_) P.global_bits = std::max(P.global_bits, Q.max_bits);
+    barrier_.wait();
+    RIDG_CUDA(cudaMemcpyAsync(work, &P.global_bits, sizeof(P.global_bits), cudaMemcpyHostToDevice, P.st));
+    check(data_scale_finish(work, P.st));
+    RIDG_CUDA(cudaStreamSynchronize(P.st));
+  }
+
+  // ---- the shot
+  void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i, const double* observed,
+            double* traces_out, double* image_p, double* image_q, const double* e_up) override {
+    if (nrec < 0 || (nrec > 0 && !rec)) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
+    const int64_t n_t = parts_[0].e->trace_len(t_final);
+    const int Np = parts_[0].e->Np_;
+    const size_t tb = size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double), ib = size_t(K_) * Np * sizeof(double);
+    for (Part& P : parts_) {
+      RIDG_CUDA(cudaSetDevice(P.dev));
+      P.traces.reserve(tb);
+      P.img_p.reserve(ib);
+      P.img_q.reserve(ib);
+      if (observed) {
+        P.obs.reserve(tb);
+        RIDG_CUDA(cudaMemcpyAsync(P.obs.p, observed, size_t(nrec) * n_t * sizeof(double), cudaMemcpyHostToDevice, P.st));
+      }
+      P.parity = P.transfer_steps = P.silent_steps = P.bytes = 0;
+    }
+    barrier_.reset(int(parts_.size()));
+    std::vector<std::string> err(parts_.size());
+    std::vector<int> code(parts_.size(), 0);
+    std::vector<std::thread> th;
+    for (size_t p = 0; p < parts_.size(); ++p)
+      th.emplace_back([&, p] {
+        Part& P = parts_[p];
+        try {
+          RIDG_CUDA(cudaSetDevice(P.dev));
+          P.e->shot(src, rec, nrec, t_final, t_i, observed ? dptr<const double>(P.obs) : nullptr, dptr<double>(P.traces),
+                    dptr<double>(P.img_p), dptr<double>(P.img_q), e_up);
+          RIDG_CUDA(cudaStreamSynchronize(P.st));
+        } catch (const Error& x) {
+          code[p] = x.code;
+          err[p] = x.msg;
+          barrier_.abort();
+        } catch (const std::exception& x) {
+          code[p] = RIDG_E_CUDA;
+          err[p] = x.what();
+          barrier_.abort();
+        }
+      });
+    for (auto& t : th) t.join();
+    // the first failure that is not another part's release
+    for (size_t p = 0; p < parts_.size(); ++p)
+      if (code[p] != 0 && err[p] != "another part of the group failed")
+        throw Error{code[p], "part " + std::to_string(p) + ": " + err[p]};
+    for (size_t p = 0; p < parts_.size(); ++p)
+      if (code[p] != 0) throw Error{code[p], "part " + std::to_string(p) + ": " + err[p]};
+    // the union of the parts: traces and images of the other parts read zero in each
+    std::vector<double> buf;
+    auto gather = [&](DBuf Part::*member, double* out, size_t n) {
+      if (!out) return;
+      std::fill(out, out + n, 0.0);
+      buf.resize(n);
+      for (Part& P : parts_) {
+        RIDG_CUDA(cudaSetDevice(P.dev));
+        RIDG_CUDA(cudaMemcpy(buf.data(), (P.*member).p, n * sizeof(double), cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < n; ++i) out[i] += buf[i];
+      }
+    };
+    gather(&Part::traces, traces_out, size_t(nrec) * n_t);
+    gather(&Part::img_p, image_p, size_t(K_) * Np);
+    gather(&Part::img_q, image_q, size_t(K_) * Np);
+    dof_ = 0;
+    for (Part& P : parts_) {
+      RIDG_CUDA(cudaSetDevice(P.dev));
+      const ridg_shot_stats& st = P.e->stats();
+      dof_ += st.dof_updates_forward + st.dof_updates_backward;
+    }
+  }
+
+  int64_t trace_len(double t_final, int32_t* np_out) const override {
+    if (np_out) *np_out = parts_[0].e->Np_;
+    return parts_[0].e->trace_len(t_final);
+  }
+
+  void info(ridg_group_info* out) const override {
+    std::memset(out, 0, sizeof(*out));
+    out->n_parts = int32_t(parts_.size());
+    for (size_t p = 0; p < parts_.size(); ++p) {
+      const Engine<real>& e = *parts_[p].e;
+      out->elements[p] = std::count_if(e.ord_.elem_of.begin(), e.ord_.elem_of.begin() + e.ord_.owned_end,
+                                       [](int64_t k) { return k >= 0; });
+      out->ghosts[p] = std::count_if(e.ord_.elem_of.begin() + e.ord_.owned_end, e.ord_.elem_of.end(),
+                                     [](int64_t k) { return k >= 0; });
+      for (int i : parts_[p].out_pairs) out->interface_faces[p] += pairs_[i]->n;
+      out->transfer_bytes += parts_[p].bytes;
+    }
+    out->dof_updates = dof_;
+    out->transfer_steps = parts_[0].transfer_steps;
+    out->silent_steps = parts_[0].silent_steps;
+  }
+
+ private:
+  static void check(cudaError_t e) {
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("interface transfer: ") + cudaGetErrorString(e)};
+  }
+  static size_t checked_parts(int32_t n) {
+    if (n < 1 || n > RIDG_MAX_PARTS) throw Error{RIDG_E_INVALID_ARG, "n_parts must be in 1..64"};
+    return size_t(n);
+  }
+
+  int64_t K_ = 0, dof_ = 0;
+  int L_ = 1, row_len_ = 32;
+  std::vector<Part> parts_;
+  std::vector<std::unique_ptr<Pair>> pairs_;
+  std::vector<bool> any_;
+  PartBarrier barrier_;
 };
 
 }  // namespace ridg
@@ -2117,5 +2517,65 @@ int ridg_server_destroy(ridg_server* sv) {
     delete sv;
   });
 }
+
+
+int ridg_partition(const ridg_mesh* mesh, int N, const double* c, const ridg_options* opt, int32_t n_parts,
+                   int32_t* part_out) {
+  return guarded([&] {
+    if (!mesh || !c || !part_out) throw Error{RIDG_E_INVALID_ARG, "null mesh, c or part_out"};
+    if (N < 1 || N > 6) throw Error{RIDG_E_INVALID_ARG, "order N must be in 1..6"};
+    if (n_parts < 1 || n_parts > RIDG_MAX_PARTS) throw Error{RIDG_E_INVALID_ARG, "n_parts must be in 1..64"};
+    for (int64_t k = 0; k < mesh->m.K; ++k)
+      if (!(c[k] > 0.0) || !std::isfinite(c[k])) throw Error{RIDG_E_INVALID_ARG, "c must be positive and finite"};
+    ridg_options o{};
+    if (opt) o = *opt;
+    const double cfl = o.cfl > 0 ? o.cfl : 0.15;
+    const int nlm = o.n_levels_max > 0 ? o.n_levels_max : 3;
+    if (nlm > ridg::kMaxLevels) throw Error{RIDG_E_INVALID_ARG, "n_levels_max too large"};
+    const ridg::Geometry geo = ridg::build_geometry(mesh->m);
+    const ridg::Levels lv = ridg::assign_levels(mesh->m, geo, N, c, cfl, nlm);
+    const std::vector<int32_t> part = ridg::partition_mesh(mesh->m, lv, n_parts);
+    std::copy(part.begin(), part.end(), part_out);
+  });
+}
+
+int ridg_group_create(const ridg_mesh* mesh, int N, const double* c, const double* rho, const ridg_options* opt,
+                      const int32_t* part, int32_t n_parts, const int32_t* devices, ridg_group** out) {
+  return guarded([&] {
+    if (!out) throw Error{RIDG_E_INVALID_ARG, "out is null"};
+    *out = nullptr;
+    if (!mesh || !c || !rho || !part) throw Error{RIDG_E_INVALID_ARG, "null mesh, c, rho or part"};
+    ridg_options o{};
+    if (opt) o = *opt;
+    if (o.dtype != RIDG_F32 && o.dtype != RIDG_F64) throw Error{RIDG_E_INVALID_ARG, "dtype must be RIDG_F32 or RIDG_F64"};
+    if (N < 1 || N > 6) throw Error{RIDG_E_INVALID_ARG, "order N must be in 1..6"};
+    if (o.dtype == RIDG_F32)
+      *out = new ridg::Group<float>(mesh->m, N, c, rho, o, part, n_parts, devices);
+    else
+      *out = new ridg::Group<double>(mesh->m, N, c, rho, o, part, n_parts, devices);
+  });
+}
+
+int ridg_group_rtm_shot(ridg_group* g, const ridg_source* src, const double* rec_xyz, int64_t nrec, double t_final,
+                        double t_image_start, const double* observed, double* traces_out, double* image_p,
+                        double* image_q, const double* e_up) {
+  return guarded([&] {
+    if (!g || !src) throw Error{RIDG_E_INVALID_ARG, "null group or source"};
+    g->shot(*src, rec_xyz, nrec, t_final, t_image_start, observed, traces_out, image_p, image_q, e_up);
+  });
+}
+
+int ridg_group_info_get(const ridg_group* g, ridg_group_info* out) {
+  return guarded([&] {
+    if (!g || !out) throw Error{RIDG_E_INVALID_ARG, "null group or out"};
+    g->info(out);
+  });
+}
+
+int64_t ridg_group_trace_len(const ridg_group* g, double t_final, int32_t* np_out) {
+  return g ? g->trace_len(t_final, np_out) : -1;
+}
+
+void ridg_group_destroy(ridg_group* g) { delete g; }
 
 }  // extern "C"

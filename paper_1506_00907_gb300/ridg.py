@@ -30,7 +30,10 @@ EXPORTED = [
     "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc", "ridg_server_create", "ridg_server_create_slots", "ridg_server_submit",
     "ridg_server_wait", "ridg_server_destroy", "ridg_forward", "ridg_set_state_device", "ridg_get_state_device",
     "ridg_set_velocity", "ridg_eval_adjoint_rhs", "ridg_misfit_forward", "ridg_misfit_backward", "ridg_mesh_locate",
+    "ridg_partition", "ridg_group_create", "ridg_group_rtm_shot", "ridg_group_info_get", "ridg_group_trace_len",
+    "ridg_group_destroy",
 ]
+MAX_PARTS = 64
 
 
 class RidgError(RuntimeError):
@@ -86,6 +89,12 @@ class ShotRequest(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class GroupInfo(C.Structure):
+    _fields_ = [("n_parts", C.c_int32), ("reserved", C.c_int32), ("elements", C.c_int64 * 64),
+                ("ghosts", C.c_int64 * 64), ("interface_faces", C.c_int64 * 64), ("dof_updates", C.c_int64),
+                ("transfer_steps", C.c_int64), ("silent_steps", C.c_int64), ("transfer_bytes", C.c_int64)]
+
+
 class RequestTiming(C.Structure):
     _fields_ = [("queued_s", C.c_double), ("run_s", C.c_double), ("total_s", C.c_double), ("start_s", C.c_double),
                 ("end_s", C.c_double), ("slot", C.c_int64)]
@@ -133,6 +142,12 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_server_submit": (C.c_int, [P, P, C.POINTER(C.c_int64)]),
         "ridg_server_wait": (C.c_int, [P, C.c_int64, C.c_double, P]),
         "ridg_server_destroy": (C.c_int, [P]),
+        "ridg_partition": (C.c_int, [P, C.c_int, P, P, C.c_int32, P]),
+        "ridg_group_create": (C.c_int, [P, C.c_int, P, P, P, P, C.c_int32, P, C.POINTER(P)]),
+        "ridg_group_rtm_shot": (C.c_int, [P, P, P, C.c_int64, C.c_double, C.c_double, P, P, P, P, P]),
+        "ridg_group_info_get": (C.c_int, [P, P]),
+        "ridg_group_trace_len": (C.c_int64, [P, C.c_double, P]),
+        "ridg_group_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -367,6 +382,68 @@ class Solver:
         st = ShotStats()
         _check(lib().ridg_last_shot_stats(self._h, C.byref(st)))
         return st
+
+
+def partition(mesh: Mesh, N: int, c, n_parts: int, cfl=0.15, n_levels_max=3):
+    """Part of each element (int32 [K]) for n_parts parts: weights 2^(l-1), finest-level lumping,
+    weighted recursive coordinate bisection (ridg_partition; host only)."""
+    c = _f64(c)
+    opt = Options(F32, float(cfl), int(n_levels_max), IMAGE_P | IMAGE_Q, 1.0, CONTRACT_TENSOR)
+    out = np.zeros(mesh.K, dtype=np.int32)
+    _check(lib().ridg_partition(mesh._h, int(N), _ptr(c), C.byref(opt), int(n_parts), _ptr(out)))
+    return out
+
+
+class Group:
+    """One shot over a partitioned mesh, one solver per part (ridg_group_*); part i on CUDA device
+    devices[i] (default: all on the current device)."""
+
+    def __init__(self, mesh: Mesh, N: int, c, rho, part, dtype="f32", cfl=0.15, n_levels_max=3, devices=None,
+                 tau_scale=1.0, image_mask=IMAGE_P | IMAGE_Q, contraction=CONTRACT_TENSOR):
+        self.mesh = mesh
+        c, rho = _f64(c), _f64(rho)
+        self.part = np.ascontiguousarray(part, dtype=np.int32)
+        self.n_parts = int(self.part.max()) + 1 if self.part.size else 0
+        dev = None if devices is None else np.ascontiguousarray(devices, dtype=np.int32)
+        opt = Options(F64 if dtype == "f64" else F32, float(cfl), int(n_levels_max), int(image_mask),
+                      float(tau_scale), int(contraction))
+        h = C.c_void_p()
+        _check(lib().ridg_group_create(mesh._h, int(N), _ptr(c), _ptr(rho), C.byref(opt), _ptr(self.part),
+                                       self.n_parts, _ptr(dev), C.byref(h)))
+        self._h = h
+        self.K = mesh.K
+
+    def close(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.ridg_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def trace_len(self, t_final):
+        return int(lib().ridg_group_trace_len(self._h, float(t_final), None))
+
+    def info(self) -> GroupInfo:
+        out = GroupInfo()
+        _check(lib().ridg_group_info_get(self._h, C.byref(out)))
+        return out
+
+    def rtm_shot(self, source_xyz, f0, t_peak, amplitude, rec_xyz, t_final, t_image_start=0.0, observed=None,
+                 e_up=(0.0, 0.0, -1.0), wavelet=None, wavelet_dt=None):
+        """Host-buffer shot over all parts: (traces [nrec, n_t], image_p [K, Np], image_q [K, Np])."""
+        src, _keep = _source(source_xyz, f0, t_peak, amplitude, wavelet, wavelet_dt)
+        rec = _f64(np.atleast_2d(rec_xyz)) if len(rec_xyz) else np.zeros((0, 3))
+        np_ = C.c_int32()
+        n_t = int(lib().ridg_group_trace_len(self._h, float(t_final), C.byref(np_)))
+        traces = np.zeros((rec.shape[0], n_t))
+        ip = np.zeros((self.K, np_.value))
+        iq = np.zeros((self.K, np_.value))
+        obs = None if observed is None else _f64(observed, (rec.shape[0], n_t))
+        eu = _f64(e_up)
+        _check(lib().ridg_group_rtm_shot(self._h, C.byref(src), _ptr(rec), rec.shape[0], float(t_final),
+                                         float(t_image_start), _ptr(obs), _ptr(traces), _ptr(ip), _ptr(iq), _ptr(eu)))
+        return traces, ip, iq
 
 
 class Server:

@@ -165,3 +165,17 @@ def test_shot_parallel_images_are_the_sum_of_the_shots_two_ranks():
         p, q = out[r]
         assert np.allclose(p, exp_p, rtol=1e-13, atol=0) and np.allclose(q, exp_q, rtol=1e-13, atol=0)
         assert np.abs(p).max() > 0
+
+
+def test_library_partition_equals_the_oracle_partition():
+    """ridg_partition (host code of the library, its own implementation) gives the oracle's parts."""
+    from paper_1506_00907_gb300 import ridg
+
+    for name in ("inclusions", "tiny"):
+        w, prob = _problem(name)
+        m = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+        for n_parts in (1, 2, 3, 4, 7):
+            lib_part = ridg.partition(m, w.N, w.c, n_parts, cfl=w.cfl, n_levels_max=w.n_levels_max)
+            assert np.array_equal(lib_part, partition(prob.geo, prob.levels, prob.n_levels, n_parts))
+    with pytest.raises(ridg.RidgError):
+        ridg.partition(m, w.N, w.c, 0)
