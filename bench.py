@@ -517,8 +517,9 @@ def precision_sweep(orders, t_final=0.01):
         out = {"order": N, "elements": int(w.K), "record_s": t_final}
         res = {}
         for name, dtype, contraction in (("f64", "f64", ridg.CONTRACT_TENSOR),
-                                         ("f32_tensor_tf32x3", "f32", ridg.CONTRACT_TENSOR),
+                                         ("f32_tensor_tf32x3", "f32", ridg.CONTRACT_TENSOR_TF32),
                                          ("f32_tensor_bf16x3", "f32", ridg.CONTRACT_TENSOR_BF16),
+                                         ("f32_tensor_fp16x3", "f32", ridg.CONTRACT_TENSOR_FP16),
                                          ("f32_cuda_cores", "f32", ridg.CONTRACT_CUDA_CORES)):
             try:
                 s = ridg.Solver(mesh, N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=w.n_levels_max,
@@ -538,7 +539,7 @@ def precision_sweep(orders, t_final=0.01):
                          "backward_full_launch_ms": st.prof_backward_ms / max(1, st.prof_backward_launches)}
             s.close()
         if "f64" in res:
-            for name in ("f32_tensor_tf32x3", "f32_tensor_bf16x3", "f32_cuda_cores"):
+            for name in ("f32_tensor_tf32x3", "f32_tensor_bf16x3", "f32_tensor_fp16x3", "f32_cuda_cores"):
                 if name in res:
                     out[name].update({k: rel(a, b) for k, a, b in zip(("traces_rel_l2", "image_p_rel_l2",
                                                                       "image_q_rel_l2"), res[name], res["f64"])})

@@ -106,15 +106,22 @@ typedef struct ridg_options {
   double tau_scale;     /* multiplies the penalty parameters tau_p = 1/Zbar, tau_v = Zbar of the
                            upwind fluxes (Sec. 3.1, Eqs. weakFormP/V); <= 0 selects 1 (upwind) */
   int32_t contraction;  /* RIDG_F32 only: RIDG_CONTRACT_TENSOR (0, default) runs the D_r/D_s/D_t and
-                           LIFT products on tensor cores (three-term TF32 split, FP32 accumulation);
+                           LIFT products on tensor cores with FP32 accumulation: the three-term TF32
+                           split up to N = 4, the FP16 split below from N = 5 (faster there and more
+                           accurate); RIDG_CONTRACT_TENSOR_TF32 the TF32 split at every order;
                            RIDG_CONTRACT_CUDA_CORES runs them as plain FP32 FMAs;
                            RIDG_CONTRACT_TENSOR_BF16 on tensor cores as a BF16 hi + lo split (three
-                           m16n8k16 products, FP32 accumulation: about 2^-16 relative per product) */
+                           m16n8k16 products, FP32 accumulation: about 2^-16 relative per product);
+                           RIDG_CONTRACT_TENSOR_FP16 as an FP16 hi + lo split (about 2^-22), each
+                           element column of each operand tile scaled by a power of two into FP16's
+                           range before the split and the scale removed from the FP32 sums */
   int32_t reserved[3];
 } ridg_options;
 #define RIDG_CONTRACT_TENSOR 0
 #define RIDG_CONTRACT_CUDA_CORES 1
 #define RIDG_CONTRACT_TENSOR_BF16 2
+#define RIDG_CONTRACT_TENSOR_FP16 3
+#define RIDG_CONTRACT_TENSOR_TF32 4
 
 #define RIDG_IMAGE_P 1 /* classical image, Eq. imageP */
 #define RIDG_IMAGE_Q 2 /* characteristic image, Eq. imageQ */

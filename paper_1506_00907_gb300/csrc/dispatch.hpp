@@ -57,6 +57,7 @@ struct AdjMrArgs {
   const real* Lt;
   int NPa;
   const int* fmask;
+  const int* inv_fmask;  // [Np][3]: f * 32 + jf of each face node that is node m, in (f, jf) order, or -1
   const int* nbr;
   const uint8_t* finfo;
   const int* perm;

@@ -14,7 +14,7 @@ namespace ridg {
 // FP32 on tensor cores with the split format KIND
 template <int N, int W, int KIND>
 static cudaError_t launch_step_tc(const StepArgs<float>& a, int64_t blocks, cudaStream_t st) {
-  constexpr size_t smem = SmemTc<N, W>::bytes;
+  constexpr size_t smem = SmemTc<N, W, KIND>::bytes;
   static PerDeviceSetup setup;
   const cudaError_t configured = setup.run([] {
     return cudaFuncSetAttribute(dg_step_kernel_tc<N, W, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
@@ -31,6 +31,7 @@ static cudaError_t launch_step_w(const StepArgs<real>& a, cudaStream_t st) {
   if constexpr (std::is_same<real, float>::value) {
     if (a.contraction == RIDG_CONTRACT_TENSOR) return launch_step_tc<N, W, kSplitTf32>(a, blocks, st);
     if (a.contraction == RIDG_CONTRACT_TENSOR_BF16) return launch_step_tc<N, W, kSplitBf16>(a, blocks, st);
+    if (a.contraction == RIDG_CONTRACT_TENSOR_FP16) return launch_step_tc<N, W, kSplitFp16>(a, blocks, st);
   }
   // FP64, or FP32 on CUDA cores
   constexpr size_t smem = step_smem_bytes<N, real, W>();
@@ -134,17 +135,21 @@ cudaError_t Launch<N, real>::adjml_step(const AdjMrArgs<real>& a, cudaStream_t s
   const int64_t blocks = (a.n_slots - a.slot_lo) / 32;
   if (blocks <= 0) return cudaSuccess;
   constexpr size_t sm_t = adjml_traces_smem<N, real>(), sm_r = adjml_rhs_smem<N, real>();
-  static_assert(sm_t <= 227 * 1024 && sm_r <= 227 * 1024, "multi-rate adjoint kernels exceed the shared memory");
+  constexpr size_t sm_p = adjml_pull_smem<N, real>();
+  static_assert(sm_t <= 227 * 1024 && sm_r <= 227 * 1024 && sm_p <= 200 * 1024,
+                "multi-rate adjoint kernels exceed the shared memory");
   static PerDeviceSetup setup;
   const cudaError_t configured = setup.run([] {
     cudaError_t e =
         cudaFuncSetAttribute(adjml_traces_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_t));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(adjml_rhs_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_r));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(adjml_pull_kernel<N, real>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(sm_p));
     return e;
   });
   if (configured != cudaSuccess) return configured;
-  adjml_pull_kernel<N, real><<<unsigned(blocks), 256, 0, st>>>(a);
+  adjml_pull_kernel<N, real><<<unsigned(blocks), 256, sm_p, st>>>(a);
   adjml_traces_kernel<N, real><<<unsigned(blocks), 256, sm_t, st>>>(a);
   adjml_rhs_kernel<N, real><<<unsigned(blocks), 256, sm_r, st>>>(a);
   return cudaGetLastError();

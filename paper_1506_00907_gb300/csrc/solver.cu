@@ -1,5 +1,6 @@
 // Host engine and C ABI: uploads the discretisation, schedules the fused step kernel per step of
 // the finest level (Algorithm 1), and drives one RTM shot (Sec. 2, Sec. 4.3).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -256,9 +257,15 @@ class Engine final : public ridg_solver {
     int nlm = opt.n_levels_max > 0 ? opt.n_levels_max : 3;
     tau_scale_ = opt.tau_scale > 0 ? opt.tau_scale : 1.0;
     if (opt.contraction != RIDG_CONTRACT_TENSOR && opt.contraction != RIDG_CONTRACT_CUDA_CORES &&
-        opt.contraction != RIDG_CONTRACT_TENSOR_BF16)
-      throw Error{RIDG_E_INVALID_ARG, "contraction must be one of RIDG_CONTRACT_TENSOR, _CUDA_CORES, _TENSOR_BF16"};
+        opt.contraction != RIDG_CONTRACT_TENSOR_BF16 && opt.contraction != RIDG_CONTRACT_TENSOR_FP16 &&
+        opt.contraction != RIDG_CONTRACT_TENSOR_TF32)
+      throw Error{RIDG_E_INVALID_ARG,
+                  "contraction must be one of RIDG_CONTRACT_TENSOR, _CUDA_CORES, _TENSOR_BF16, _TENSOR_FP16, _TENSOR_TF32"};
+    // RIDG_CONTRACT_TENSOR: the TF32 split up to N = 4, the FP16 split with column scales from N = 5
+    // (measured faster there, and more accurate at every order)
     contraction_ = std::is_same<real, float>::value ? opt.contraction : RIDG_CONTRACT_CUDA_CORES;
+    if (contraction_ == RIDG_CONTRACT_TENSOR && N >= 5) contraction_ = RIDG_CONTRACT_TENSOR_FP16;
+    if (contraction_ == RIDG_CONTRACT_TENSOR_TF32) contraction_ = RIDG_CONTRACT_TENSOR;
     image_mode_ = ((opt.image_mask & RIDG_IMAGE_P) || !(opt.image_mask & 3) ? kModeImageP : 0) |
                   ((opt.image_mask & RIDG_IMAGE_Q) || !(opt.image_mask & 3) ? kModeImageQ : 0);
     if (nlm > kMaxLevels) throw Error{RIDG_E_INVALID_ARG, "n_levels_max too large"};
@@ -743,6 +750,7 @@ class Engine final : public ridg_solver {
     a.Lt = dptr<const real>(Lt_d_);
     a.NPa = NPa_;
     a.fmask = dptr<const int>(fmask_d_);
+    a.inv_fmask = dptr<const int>(inv_fmask_d_);
     a.nbr = dptr<const int>(nbr_d_);
     a.finfo = dptr<const uint8_t>(finfo_d_);
     a.perm = dptr<const int>(perm_d_);
@@ -1080,7 +1088,8 @@ class Engine final : public ridg_solver {
     size_t need = dispatch_order(N_, [&](auto NC) {
       constexpr int NN = decltype(NC)::value;
       if constexpr (std::is_same<real, float>::value)
-        if (contraction_ != RIDG_CONTRACT_CUDA_CORES) return std::max(SmemTc<NN, 1>::bytes, SmemTc<NN, 2>::bytes);
+        if (contraction_ != RIDG_CONTRACT_CUDA_CORES)
+          return std::max(SmemTc<NN, 1, kSplitFp16>::bytes, SmemTc<NN, 2, kSplitFp16>::bytes);
       return std::max(step_smem_bytes<NN, real, 1>(), step_smem_bytes<NN, real, 2>());
     });
     if (need > size_t(optin))
@@ -1171,14 +1180,25 @@ class Engine final : public ridg_solver {
     upload(Dt_d_, Dt, st_);
     upload(Dt4_d_, Dt4, st_);
     upload(Lt_d_, Lt, st_);
-    if (contraction_ == RIDG_CONTRACT_TENSOR || contraction_ == RIDG_CONTRACT_TENSOR_BF16)
-      upload(afrag_d_, operator_fragments(contraction_ == RIDG_CONTRACT_TENSOR_BF16), st_);
+    if (contraction_ != RIDG_CONTRACT_CUDA_CORES)
+      upload(afrag_d_, operator_fragments(contraction_), st_);
     std::vector<int> fm(128, 0), pm(192, 0);
     for (int f = 0; f < 4; ++f)
       for (int j = 0; j < Nfp_; ++j) fm[f * 32 + j] = ref_.fmask[f][j];
     for (int c = 0; c < 6; ++c)
       for (int j = 0; j < Nfp_; ++j) pm[c * 32 + j] = ref_.perm[c][j];
     upload(fmask_d_, fm, st_);
+    {
+      // the face nodes (f * 32 + jf, in (f, jf) order) that are node m, three at most, -1 after them
+      std::vector<int> inv(size_t(Np_) * 3, -1);
+      for (int m = 0; m < Np_; ++m) {
+        int cnt = 0;
+        for (int f = 0; f < 4; ++f)
+          for (int j = 0; j < Nfp_; ++j)
+            if (ref_.fmask[f][j] == m && cnt < 3) inv[m * 3 + cnt++] = f * 32 + j;
+      }
+      upload(inv_fmask_d_, inv, st_);
+    }
     upload(perm_d_, pm, st_);
     upload(M_d_, ref_.M.a, st_);
     upload(pos_d_, pos_of_, st_);
@@ -1274,7 +1294,20 @@ class Engine final : public ridg_solver {
   //  2t, 2t+1 (register 0/1) and 2t+8, 2t+9 (register 2/3), two values per register, lower column
   //  in the low half; fragment columns 2t, 2t+1, 2t+8, 2t+9 are the step's nodes t, t+4, t+8, t+12
   //  (the kernel loads B in the same order).
-  std::vector<uint32_t> operator_fragments(bool bf16) const {
+  // FP16 rounding (round to nearest even) of an FP32 value, as its 16 bits
+  static uint32_t fp16_bits(float x) {
+    const __half_raw r = __half(__float2half_rn(x));
+    return r.x;
+  }
+  static float fp16_value(uint32_t bits) {
+    __half_raw r;
+    r.x = uint16_t(bits);
+    return __half2float(__half(r));
+  }
+
+  std::vector<uint32_t> operator_fragments(int contraction) const {
+    const bool bf16 = contraction != RIDG_CONTRACT_TENSOR;  // a 16-bit split: BF16 or FP16
+    const bool fp16 = contraction == RIDG_CONTRACT_TENSOR_FP16;
     const int KS = bf16 ? 16 : 8;
     const int MT = (Np_ + 15) / 16, KSD = (Np_ + KS - 1) / KS, KSF = (Nfp_ + KS - 1) / KS;
     const int NSTEP = 3 * KSD + 4 * KSF;
@@ -1299,6 +1332,11 @@ class Engine final : public ridg_solver {
             uint32_t h2[2], l2[2];
             const double v2[2] = {val(r, c0), val(r, c1)};
             for (int i = 0; i < 2; ++i) {
+              if (fp16) {
+                h2[i] = fp16_bits(float(v2[i]));
+                l2[i] = fp16_bits(float(v2[i] - double(fp16_value(h2[i]))));
+                continue;
+              }
               h2[i] = bf16_bits(float(v2[i]));
               const uint32_t hb = h2[i] << 16;
               float hv;
@@ -1543,7 +1581,7 @@ class Engine final : public ridg_solver {
   std::vector<int> bface_host_;
   std::vector<int64_t> level_count_;
   DBuf geo_d_, J_d_, mat_d_, nbr_d_, finfo_d_, bface_d_, meta_d_, Dt_d_, Dt4_d_, Lt_d_, fmask_d_, perm_d_, M_d_, slot_of_d_;
-  DBuf afrag_d_, gtab_d_[2], pos_d_;
+  DBuf afrag_d_, gtab_d_[2], pos_d_, inv_fmask_d_;
   double tau_scale_ = 1.0;
   double cfl_ = 0.15;
   static constexpr double kVelocityCflMargin = 4.0 / 3.0;

@@ -19,20 +19,24 @@
 // 32 (or 2 x 16) consecutive columns.
 #pragma once
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "step_kernel.cuh"
 
 namespace ridg {
 // Split formats of the tensor-core products: TF32 hi + lo with m16n8k8 (k-steps of 8 nodes), or
-// BF16 hi + lo with m16n8k16 (k-steps of 16 nodes, half the instructions, 16 significand bits).
-constexpr int kSplitTf32 = 0, kSplitBf16 = 1;
+// BF16 hi + lo with m16n8k16 (k-steps of 16 nodes, half the instructions, 16 significand bits), or
+// FP16 hi + lo with m16n8k16 (22 significand bits; FP16's range holds the fields only after a
+// per-column power-of-two scale, applied to each operand tile before the split and removed from the
+// FP32 accumulators).
+constexpr int kSplitTf32 = 0, kSplitBf16 = 1, kSplitFp16 = 2;
 
 template <int N, int KIND = kSplitTf32>
 struct TcOrder {
   using O = Order<N>;
   static constexpr int Np = O::Np, Nfp = O::Nfp;
   static constexpr int MT = (Np + 15) / 16;  // 16-node tiles
-  static constexpr int KS = KIND == kSplitBf16 ? 16 : 8;  // nodes per k-step
+  static constexpr int KS = KIND == kSplitTf32 ? 8 : 16;  // nodes per k-step
   static constexpr int KSD = (Np + KS - 1) / KS;   // k-steps over the nodes
   static constexpr int KSF = (Nfp + KS - 1) / KS;  // k-steps over the nodes of one face
   static constexpr int NWARP = 2 * MT;
@@ -96,18 +100,53 @@ __device__ __forceinline__ void split_bf16x2(float x0, float x1, uint32_t& hi, u
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-// B fragment of a BF16 k-step (16 x 8, column major).  The k index is permuted inside the step so
+// m16n8k16 FP16 product with FP32 accumulation (A 16 x 16 row major, B 16 x 8 column major).
+__device__ __forceinline__ void mma_f16(float c[4], const uint32_t a[4], const uint32_t b[2]) {
+  asm(
+      "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Two values as FP16 hi + lo pairs (round to nearest even): hi = fp16(x), lo = fp16(x - hi).
+__device__ __forceinline__ void split_f16x2(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const __half2 l = __floats2half2_rn(x0 - __low2float(h), x1 - __high2float(h));
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// B fragment of a 16-bit k-step (16 x 8, column major).  The k index is permuted inside the step so
 // that lane (g, t) reads rows t, t + 4, t + 8, t + 12 (the conflict-free rows of the TF32 loads):
 // fragment positions 2t, 2t+1, 2t+8, 2t+9 hold rows t, t+4, t+8, t+12; the host orders the operator
-// columns of each step the same way, so the product is unchanged.
-template <int CS>
+// columns of each step the same way, so the product is unchanged.  FP16 values are scaled by sc (the
+// power of two of their column and operand) before the split.
+template <int CS, int KIND>
 __device__ __forceinline__ void load_b16(const float* X, int row0, int kvalid_rel, int t, int col, uint32_t bh[2],
-                                         uint32_t bl[2]) {
+                                         uint32_t bl[2], float sc) {
   float x[4];
 #pragma unroll
   for (int i = 0; i < 4; ++i) x[i] = (t + 4 * i < kvalid_rel) ? X[(row0 + t + 4 * i) * CS + col] : 0.f;
-  split_bf16x2(x[0], x[1], bh[0], bl[0]);
-  split_bf16x2(x[2], x[3], bh[1], bl[1]);
+  if constexpr (KIND == kSplitFp16) {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) x[i] *= sc;
+    split_f16x2(x[0], x[1], bh[0], bl[0]);
+    split_f16x2(x[2], x[3], bh[1], bl[1]);
+  } else {
+    split_bf16x2(x[0], x[1], bh[0], bl[0]);
+    split_bf16x2(x[2], x[3], bh[1], bl[1]);
+  }
+}
+
+// The power of two that brings a column's largest magnitude m into [2^13, 2^14) (1 for m = 0), and its
+// inverse; both exact.
+__device__ __forceinline__ float2 fp16_column_scale(float m) {
+  if (!(m > 0.f) || !isfinite(m)) return make_float2(1.f, 1.f);
+  const int e = int((__float_as_uint(m) >> 23) & 0xff) - 127;  // m in [2^e, 2^(e+1)) (normal m)
+  int k = 13 - e;
+  k = k > 126 ? 126 : (k < -126 ? -126 : k);
+  return make_float2(__uint_as_float(uint32_t(127 + k) << 23), __uint_as_float(uint32_t(127 - k) << 23));
 }
 
 __device__ __forceinline__ void load_a(const uint32_t* frag, int lane, FragA& a) {
@@ -123,7 +162,7 @@ __device__ __forceinline__ void load_a(const uint32_t* frag, int lane, FragA& a)
   a.l[3] = l.w;
 }
 
-template <int N, int W>
+template <int N, int W, int KIND = kSplitTf32>
 struct SmemTc {
   using O = Order<N>;
   static constexpr int Np = O::Np, Nfp = O::Nfp;
@@ -138,8 +177,9 @@ struct SmemTc {
   static constexpr int G = EPB * GS + 4;  // coefficients [EPB][GS], rows 16.. shifted by 4 words (see grow)
   static constexpr int IMG = (W == 2) ? 2 * 2 * Np * EPB : 0;  // two FP64 image tiles, in floats
   static constexpr int INTS = 4 * EPB + EPB + EPB + EPB + 128 + 192 + 4 * EPB;  // nbr, finfo bytes, bface, meta, ...
+  static constexpr int SC = KIND == kSplitFp16 ? 6 * 32 : 0;  // FP16: column scales (p, r, s) and inverses
   static constexpr size_t bytes_with(bool ring) {
-    return (size_t(Q) * (ring ? 3 : 1) + 2 * size_t(ST) + UX + G + IMG) * sizeof(float) + INTS * sizeof(int);
+    return (size_t(Q) * (ring ? 3 : 1) + 2 * size_t(ST) + UX + G + IMG + SC) * sizeof(float) + INTS * sizeof(int);
   }
   // the history is staged in shared memory only where that still leaves room for MINB blocks
   static constexpr bool ring_in_smem = TcOrder<N>::MINB * (bytes_with(true) + 1024) <= 228 * 1024;
@@ -153,19 +193,21 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   using T = TcOrder<N, KIND>;
   constexpr int KS = T::KS;
   // one k-step of the split product: B pieces from shared memory, and the MMA of the split format
-  auto load_bk = [](const float* X, int row0, int kv, int t, int col, uint32_t bh[2], uint32_t bl[2]) {
-    if constexpr (KIND == kSplitBf16)
-      load_b16<SmemTc<N, W>::CS>(X, row0, kv, t, col, bh, bl);
+  auto load_bk = [](const float* X, int row0, int kv, int t, int col, uint32_t bh[2], uint32_t bl[2], float sc) {
+    if constexpr (KIND == kSplitTf32)
+      load_b<SmemTc<N, W, KIND>::CS>(X, row0, kv, t, col, bh, bl);
     else
-      load_b<SmemTc<N, W>::CS>(X, row0, kv, t, col, bh, bl);
+      load_b16<SmemTc<N, W, KIND>::CS, KIND>(X, row0, kv, t, col, bh, bl, sc);
   };
   auto mma = [](float c[4], const uint32_t a[4], const uint32_t b[2]) {
     if constexpr (KIND == kSplitBf16)
       mma_bf16(c, a, b);
+    else if constexpr (KIND == kSplitFp16)
+      mma_f16(c, a, b);
     else
       mma_tf32(c, a, b);
   };
-  using SM = SmemTc<N, W>;
+  using SM = SmemTc<N, W, KIND>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NT = T::NT, NFPP = O::NFPP;
   constexpr int CS = SM::CS, EPB = SM::EPB, GS = SM::GS;
   constexpr bool RING = SM::ring_in_smem;
@@ -191,6 +233,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   int* sFm = sMeta + EPB;                                   // [4][32]
   int* sPerm = sFm + 128;                                   // [6][32]
   int2* sInj = reinterpret_cast<int2*>(sPerm + 192);        // [2][EPB] injection ranges per wavefield
+  float* sSc = reinterpret_cast<float*>(sInj + 2 * EPB);   // FP16: [3][32] column scales, [3][32] inverses
   float* sRhs = sS;  // [4][Np][CS] right-hand sides after the products, then the half-step fields
 
   const int tid = threadIdx.x;
@@ -420,6 +463,35 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     sU[(2 * Np + m) * CS + c] = g0.z * vx + g1.y * vy + g8 * vz;
   }
   __syncthreads();
+  // FP16 split: per-column power-of-two scales of the product operands, from their largest magnitudes:
+  // p (the derivatives D_j p, one accumulator each), U_j with the penalty traces t (both accumulate
+  // into r_p), and s (each L_f s_f its own accumulator).  sSc[0..2][c] scales, sSc[3..5][c] inverses.
+  if constexpr (KIND == kSplitFp16) {
+    for (int task = tid; task < 6 * 32; task += NT) {
+      const int c = task & 31, part = task >> 5;
+      const float* X = part == 0 ? sQ : (part <= 3 ? sU + (part - 1) * Np * CS : (part == 4 ? sT : sS));
+      const int rows = part <= 3 ? Np : 4 * Nfp;
+      float m = 0.f;
+      for (int r = 0; r < rows; ++r) m = fmaxf(m, fabsf(X[r * CS + c]));
+      sSc[task] = m;
+    }
+    __syncthreads();
+    if (tid < 32) {
+      float mx[6];
+#pragma unroll
+      for (int part = 0; part < 6; ++part) mx[part] = sSc[part * 32 + tid];
+      const float2 sp = fp16_column_scale(mx[0]);
+      const float2 sr = fp16_column_scale(fmaxf(fmaxf(mx[1], mx[2]), fmaxf(mx[3], mx[4])));
+      const float2 ss = fp16_column_scale(mx[5]);
+      sSc[0 * 32 + tid] = sp.x;
+      sSc[1 * 32 + tid] = sr.x;
+      sSc[2 * 32 + tid] = ss.x;
+      sSc[3 * 32 + tid] = sp.y;
+      sSc[4 * 32 + tid] = sr.y;
+      sSc[5 * 32 + tid] = ss.y;
+    }
+    __syncthreads();
+  }
 
 // ---------------------------------------------------------------- phase 3: tensor-core products
   const int lane = tid & 31, wid = tid >> 5;
@@ -431,6 +503,23 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   // takes blocks pair and pair + 2.
   auto bcol = [](int beta, int n) { return 4 * beta + (n & 3) + 16 * (n >> 2); };
   const int colb[2] = {bcol(pair, g), bcol(pair + 2, g)};  // B-fragment columns of the two blocks
+  // FP16: the operand scales of the B-fragment columns (p, r, s), 1 for the other split formats
+  float scp[2] = {1.f, 1.f}, scr[2] = {1.f, 1.f}, scs[2] = {1.f, 1.f};
+  if constexpr (KIND == kSplitFp16) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      scp[b] = sSc[0 * 32 + colb[b]];
+      scr[b] = sSc[1 * 32 + colb[b]];
+      scs[b] = sSc[2 * 32 + colb[b]];
+    }
+  }
+  // FP16: the inverse scale of accumulator column (b, k) of operand family fam (0 p, 1 r, 2 s)
+  auto inv_sc = [&](int fam, int b, int k) {
+    if constexpr (KIND == kSplitFp16)
+      return sSc[(3 + fam) * 32 + bcol(pair + 2 * b, 2 * t4 + k)];
+    else
+      return 1.f;
+  };
   // accumulator entry q = 2 hn + k of block b: node mt*16 + g + 8 hn, column bcol(pair + 2b, 2 t4 + k).
   // r_p = sum_j D_j U_j + sum_f L_f t_f (Eq. dgLocalSchemeP) accumulates in rp; each D_j p and each
   // L_f s_f is folded into r_v = -(1/rho) grad p - sum_f n_f (L_f s_f) (Eq. dgLocalSchemeU) as soon
@@ -487,8 +576,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
         uint32_t ph[2][2], pl[2][2], uh[2][2], ul[2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          load_bk(sQ, kb * KS, kv, t4, colb[b], ph[b], pl[b]);
-          load_bk(Ub, kb * KS, kv, t4, colb[b], uh[b], ul[b]);
+          load_bk(sQ, kb * KS, kv, t4, colb[b], ph[b], pl[b], scp[b]);
+          load_bk(Ub, kb * KS, kv, t4, colb[b], uh[b], ul[b], scr[b]);
         }
         // the three split terms of four independent accumulators, interleaved
 #pragma unroll
@@ -514,13 +603,15 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
 #pragma unroll
       for (int b = 0; b < 2; ++b)
 #pragma unroll
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < 2; ++k) {
+          const float iv = inv_sc(0, b, k);
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
-            const float gvk = gcoef(kGtV + 3 * d + jd, ecol[b][k]);
+            const float gvk = gcoef(kGtV + 3 * d + jd, ecol[b][k]) * iv;
             rv[d][b][k] += gvk * acc[b][k];
             rv[d][b][2 + k] += gvk * acc[b][2 + k];
           }
+        }
     }
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
@@ -536,8 +627,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
         uint32_t th[2][2], tl[2][2], sh[2][2], sl[2][2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-          load_bk(sT, f * Nfp + kb * KS, kv, t4, colb[b], th[b], tl[b]);
-          load_bk(sS, f * Nfp + kb * KS, kv, t4, colb[b], sh[b], sl[b]);
+          load_bk(sT, f * Nfp + kb * KS, kv, t4, colb[b], th[b], tl[b], scr[b]);
+          load_bk(sS, f * Nfp + kb * KS, kv, t4, colb[b], sh[b], sl[b], scs[b]);
         }
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
@@ -564,7 +655,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
           const float4 nf = gcoef4(kGtN + 4 * f, ecol[b][k]);
-          const float nfd[3] = {nf.x, nf.y, nf.z};
+          const float iv = inv_sc(2, b, k);
+          const float nfd[3] = {nf.x * iv, nf.y * iv, nf.z * iv};
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
             rv[d][b][k] -= nfd[d] * acc[b][k];
@@ -583,7 +675,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       const int n = mt * 16 + g + 8 * (q >> 1);
       if (n >= Np) continue;
       const int cb = bcol(pair + 2 * b, 2 * t4 + (q & 1));
-      sRhs[(0 * Np + n) * CS + cb] = rp[b][q];
+      sRhs[(0 * Np + n) * CS + cb] = rp[b][q] * inv_sc(1, b, q & 1);
 #pragma unroll
       for (int d = 0; d < 3; ++d) sRhs[((1 + d) * Np + n) * CS + cb] = rv[d][b][q];
     }

@@ -48,7 +48,7 @@ class Options(C.Structure):
 
 
 IMAGE_P, IMAGE_Q = 1, 2
-CONTRACT_TENSOR, CONTRACT_CUDA_CORES, CONTRACT_TENSOR_BF16 = 0, 1, 2
+CONTRACT_TENSOR, CONTRACT_CUDA_CORES, CONTRACT_TENSOR_BF16, CONTRACT_TENSOR_FP16, CONTRACT_TENSOR_TF32 = 0, 1, 2, 3, 4
 SRC_RICKER, SRC_SAMPLED = 0, 1
 
 

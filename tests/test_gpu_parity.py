@@ -369,3 +369,42 @@ def test_rtm_shot_parity_bf16_split():
     assert rel_l2(tr, ref.traces) < TOL_BF16
     assert rel_l2(ip, ref.image_p) < TOL_BF16
     assert rel_l2(iq, ref.image_q) < TOL_BF16
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_rhs_parity_fp16_split(N):
+    """FP32 with the element products as an FP16 hi + lo split (m16n8k16), each column of each operand
+    tile scaled by a power of two into FP16's range: right-hand side with every boundary condition,
+    several blocks and a ragged tail, at the FP32 tolerance; the fields are scaled by 1e-12 as well,
+    far below FP16's range, which only the column scales bring back."""
+    w = tiny_layered_rtm(N=N)
+    fb = mixed_bc(w)
+    prob = _oracle_problem(w, face_bc=fb)
+    s = _gpu(w, "f32", face_bc=fb, contraction=ridg.CONTRACT_TENSOR_FP16)
+    g = prob.geo
+    for scale in (1.0, 1e-12):
+        q = scale * random_state(w.K, s.Np, seed=11)
+        r_ref = rhs(np.arange(g.K), q, traces(q, g), g)
+        assert rel_l2(s.eval_rhs(q), r_ref) < TOL["f32"]
+
+
+def test_rtm_shot_parity_fp16_split():
+    w, ref = _oracle_shot(4)
+    s = _gpu(w, "f32", contraction=ridg.CONTRACT_TENSOR_FP16)
+    tr, ip, iq = s.rtm_shot(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, w.t_image_start)
+    assert rel_l2(tr, ref.traces) < TOL["f32"]
+    assert rel_l2(ip, ref.image_p) < TOL["f32"]
+    assert rel_l2(iq, ref.image_q) < TOL["f32"]
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6])
+def test_rhs_parity_tf32_split_at_every_order(N):
+    """The TF32 three-term split forced at every order (the default tensor-core mode runs it up to N = 4
+    and the FP16 split from N = 5)."""
+    w = tiny_layered_rtm(N=N)
+    fb = mixed_bc(w)
+    prob = _oracle_problem(w, face_bc=fb)
+    s = _gpu(w, "f32", face_bc=fb, contraction=ridg.CONTRACT_TENSOR_TF32)
+    q = random_state(w.K, s.Np, seed=11)
+    g = prob.geo
+    assert rel_l2(s.eval_rhs(q), rhs(np.arange(g.K), q, traces(q, g), g)) < TOL["f32"]
