@@ -44,25 +44,36 @@ __device__ __forceinline__ int adjml_level(const AdjMrArgs<real>& A, int64_t slo
   return lev;
 }
 
-// faces holding each node: sInv[m * 3 + i] = f * 32 + jf (or -1)
+// faces holding each node: sInv[m * 3 + i] = f * 32 + jf (or -1), from the table built on the host
 template <int N>
-__device__ __forceinline__ void adjml_inverse_fmask(const int* __restrict__ fmask, int* sInv) {
-  using O = Order<N>;
-  for (int m = threadIdx.x; m < O::Np; m += blockDim.x) {
-    int cnt = 0;
-    for (int f = 0; f < 4; ++f)
-      for (int jf = 0; jf < O::Nfp; ++jf)
-        if (fmask[f * 32 + jf] == m && cnt < 3) sInv[m * 3 + cnt++] = f * 32 + jf;
-    for (; cnt < 3; ++cnt) sInv[m * 3 + cnt] = -1;
-  }
+__device__ __forceinline__ void adjml_inverse_fmask(const int* __restrict__ inv_fmask, int* sInv) {
+  for (int i = threadIdx.x; i < Order<N>::Np * 3; i += blockDim.x) sInv[i] = inv_fmask[i];
 }
 
-// Reverse of the trace pushes and of the update: thread per (node, column) of the block's slots.
+// Reverse of the trace pushes and of the update.  First the adjoints of the traces this block's
+// elements pushed are taken (and cleared) from the neighbours' inbox adjoints: a half-warp per
+// (column, face) reads the face's contiguous row, lanes over the face nodes, into shared memory;
+// the per-column normals and flags are staged once.  Then a thread per (node, column) sums, per
+// node, the entries of the faces that hold it (in face order) and updates mu and the ring adjoints.
+template <int N, typename real>
+constexpr size_t adjml_pull_smem() {
+  return size_t(2) * 32 * 4 * 2 * Order<N>::Nfp * sizeof(real);
+}
+
 template <int N, typename real>
 __global__ void adjml_pull_kernel(AdjMrArgs<real> A) {
   using O = Order<N>;
-  constexpr int Np = O::Np, NFPP = O::NFPP;
+  constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
   __shared__ int sInv[Np * 3];
+  __shared__ real sN[12][32];  // outward normals per column
+  __shared__ int sMeta[32];
+  __shared__ uint8_t sInfo[32 * 4];
+  // full (set 0) and half-step (set 1) trace adjoints per column, face, (p, v) and face node
+  extern __shared__ __align__(16) unsigned char smem_pull[];
+  real* sG = reinterpret_cast<real*>(smem_pull);
+  auto G = [&](int set, int c, int f, int comp, int jf) -> real& {
+    return sG[(((set * 32 + c) * 4 + f) * 2 + comp) * Nfp + jf];
+  };
   const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * 32;
   const int64_t blk = slot0 >> 5;
   const int lev = adjml_level(A, slot0);
@@ -74,49 +85,91 @@ __global__ void adjml_pull_kernel(AdjMrArgs<real> A) {
   real* r2 = A.mu_ring + A.ring_old2[lev] * qsize;
   real* xfull = A.mu_in + A.slot_full[lev] * tsz;
   real* xhalf = A.mu_in + A.slot_half[lev] * tsz;
-  adjml_inverse_fmask<N>(A.fmask, sInv);
+  adjml_inverse_fmask<N>(A.inv_fmask, sInv);
+  for (int i = threadIdx.x; i < 32; i += blockDim.x) sMeta[i] = A.meta[slot0 + i];
+  for (int i = threadIdx.x; i < 32 * 4; i += blockDim.x) sInfo[i] = A.finfo[slot0 * 4 + i];
+  for (int i = threadIdx.x; i < 12 * 32; i += blockDim.x) {
+    const int k = i >> 5, c = i & 31;
+    sN[k][c] = real(A.geo[(slot0 + c) * kGeo + 9 + k]);
+  }
+  __syncthreads();
+  {
+    const int hw = threadIdx.x >> 4, j = threadIdx.x & 15, nhw = blockDim.x >> 4;
+    for (int item = hw; item < 128; item += nhw) {
+      const int c = item & 31, f = item >> 5;
+      const int64_t s = slot0 + c;
+      const int meta = sMeta[c];
+      const uint8_t info = sInfo[c * 4 + f];
+      // boundary faces push nothing; invalid slots have nothing to take
+      const bool take = (meta & kMetaValid) && finfo_bc(info) == 0;
+      const bool half = take && (meta & kMetaHalf);
+      const int64_t at = take ? int64_t(A.nbr[s * 4 + f]) * (8 * NFPP) + finfo_face(info) * 2 * NFPP : 0;
+      for (int jf = j; jf < Nfp; jf += 16) {
+        real gp = 0, gv = 0, hp = 0, hv = 0;
+        if (take) {
+          const int j2 = A.perm[finfo_perm(info) * 32 + jf];
+          gp = xfull[at + j2];
+          gv = xfull[at + NFPP + j2];
+          xfull[at + j2] = real(0);
+          xfull[at + NFPP + j2] = real(0);
+          if (half) {
+            hp = xhalf[at + j2];
+            hv = xhalf[at + NFPP + j2];
+            xhalf[at + j2] = real(0);
+            xhalf[at + NFPP + j2] = real(0);
+          }
+        }
+        G(0, c, f, 0, jf) = gp;
+        G(0, c, f, 1, jf) = gv;
+        G(1, c, f, 0, jf) = hp;
+        G(1, c, f, 1, jf) = hv;
+      }
+    }
+  }
   __syncthreads();
   for (int item = threadIdx.x; item < Np * 32; item += blockDim.x) {
     const int m = item >> 5, c = item & 31;
-    const int64_t s = slot0 + c;
-    const int meta = A.meta[s];
+    const int meta = sMeta[c];
     if (!(meta & kMetaValid)) continue;
     const bool half = (meta & kMetaHalf) != 0;
-    const double* g = A.geo + s * kGeo;
+    const int64_t s = slot0 + c;
     real gq[4] = {0, 0, 0, 0}, hq[4] = {0, 0, 0, 0};
     for (int k = 0; k < 3; ++k) {
       const int e = sInv[m * 3 + k];
       if (e < 0) break;
       const int f = e >> 5, jf = e & 31;
-      const uint8_t info = A.finfo[s * 4 + f];
-      if (finfo_bc(info) != 0) continue;  // boundary faces push nothing
-      const int64_t s2 = A.nbr[s * 4 + f];
-      const int j2 = A.perm[finfo_perm(info) * 32 + jf];
-      const int64_t at = s2 * (8 * NFPP) + finfo_face(info) * 2 * NFPP;
+      if (finfo_bc(sInfo[c * 4 + f]) != 0) continue;  // boundary faces push nothing
       // the pushed pair is (p, -n.v) in this element's normal: its adjoint goes to p and to v
-      const real gp = xfull[at + j2], gv = xfull[at + NFPP + j2];
-      xfull[at + j2] = real(0);
-      xfull[at + NFPP + j2] = real(0);
+      const real gp = G(0, c, f, 0, jf), gv = G(0, c, f, 1, jf);
       gq[0] += gp;
 #pragma unroll
-      for (int i = 0; i < 3; ++i) gq[1 + i] -= real(g[9 + 3 * f + i]) * gv;
+      for (int i = 0; i < 3; ++i) gq[1 + i] -= sN[3 * f + i][c] * gv;
       if (half) {
-        const real hp = xhalf[at + j2], hv = xhalf[at + NFPP + j2];
-        xhalf[at + j2] = real(0);
-        xhalf[at + NFPP + j2] = real(0);
+        const real hp = G(1, c, f, 0, jf), hv = G(1, c, f, 1, jf);
         hq[0] += hp;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) hq[1 + i] -= real(g[9 + 3 * f + i]) * hv;
+        for (int i = 0; i < 3; ++i) hq[1 + i] -= sN[3 * f + i][c] * hv;
       }
+    }
+    // every value is read before any is written (the arrays may alias as far as the compiler knows),
+    // so the sixteen loads are in flight together
+    real vm[4], vn[4], v1[4], v2[4];
+#pragma unroll
+    for (int fld = 0; fld < 4; ++fld) {
+      const int64_t at = ((blk * 4 + fld) * Np + m) * 32 + c;
+      vm[fld] = A.mu[at];
+      vn[fld] = rn[at];
+      v1[fld] = r1[at];
+      v2[fld] = r2[at];
     }
 #pragma unroll
     for (int fld = 0; fld < 4; ++fld) {
       const int64_t at = ((blk * 4 + fld) * Np + m) * 32 + c;
-      const real mq = A.mu[at] + gq[fld], mh = hq[fld];
+      const real mq = vm[fld] + gq[fld], mh = hq[fld];
       A.mu[at] = mq + mh;
-      rn[at] += h * (real(AB::a1) * mq + real(AB::b1) * mh);
-      r1[at] += h * (real(AB::a2) * mq + real(AB::b2) * mh);
-      r2[at] += h * (real(AB::a3) * mq + real(AB::b3) * mh);
+      rn[at] = vn[fld] + h * (real(AB::a1) * mq + real(AB::b1) * mh);
+      r1[at] = v1[fld] + h * (real(AB::a2) * mq + real(AB::b2) * mh);
+      r2[at] = v2[fld] + h * (real(AB::a3) * mq + real(AB::b3) * mh);
     }
   }
 }
@@ -221,7 +274,7 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
     sC[i] = k < 21 ? real(A.geo[s * kGeo + k]) : A.mat[s * kMat + (k - 21)];
   }
   for (int i = threadIdx.x; i < 32; i += blockDim.x) sValid[i] = (A.meta[slot0 + i] & kMetaValid) != 0;
-  adjml_inverse_fmask<N>(A.fmask, sInv);
+  adjml_inverse_fmask<N>(A.inv_fmask, sInv);
   cp_async_wait_all();
   __syncthreads();
   for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) rnew[i] = real(0);
