@@ -23,6 +23,7 @@ from .workloads import (  # noqa: F401
     Workload,
     config1_cube,
     config2_layered_rtm,
+    config3_crop,
     small_layered_rtm,
     tiny_layered_rtm,
     adjoint_box,

@@ -98,6 +98,26 @@ def config2_layered_rtm() -> Workload:
                     t_peak=0.1127 * 12.0 / 10.0, receivers=rec, t_final=1.5, t_image_start=0.0)
 
 
+def config3_crop(N=5, f0=50.0, t_final=0.04) -> Workload:
+    """The 1/8-volume crop [500, 1500]^2 x [250, 750] m of the layered bench model (its elements whose
+    centroids lie inside, transparent faces on the cut; it holds the interface at 500 m and the
+    refined bands), order N (5 or 6), source at (1000, 1000, 250) m on the crop's top, 50 receivers on
+    z = 260 m along y = 1000 m; a Ricker pulse of f0 (50 Hz by default, t_peak = 0.1127 * 12 / f0) so
+    that the whole pulse lies inside a short record."""
+    w = config2_layered_rtm()
+    cen = w.xyz[w.tets].mean(axis=1)
+    keep = ((cen[:, 0] > 500.0) & (cen[:, 0] < 1500.0) & (cen[:, 1] > 500.0) & (cen[:, 1] < 1500.0)
+            & (cen[:, 2] > 250.0) & (cen[:, 2] < 750.0))
+    tets = w.tets[keep]
+    used = np.unique(tets)
+    remap = np.full(w.xyz.shape[0], -1, dtype=np.int64)
+    remap[used] = np.arange(used.size)
+    rec = np.stack([np.arange(510.0, 1490.0 + 1e-9, 20.0), np.full(50, 1000.0), np.full(50, 260.0)], axis=1)
+    return Workload(f"layered_crop_N{N}", w.xyz[used], remap[tets], w.c[keep], w.rho[keep], N=N,
+                    default_bc=BC_TRANSPARENT, cfl=0.15, n_levels_max=3, dtype="f32", source_xyz=(1000.0, 1000.0, 250.0),
+                    f0=f0, t_peak=0.1127 * 12.0 / f0, receivers=rec, t_final=t_final)
+
+
 def small_layered_rtm(N=3, t_final=0.12) -> Workload:
     """A 400 x 400 x 200 m version of the layered RTM recipe for oracle-sized checks."""
     lx, ly, lz, h = 400.0, 400.0, 200.0, 50.0

@@ -1,0 +1,152 @@
+"""Precision of the FP32 product modes against the FP64 oracle on the 1/8-volume crop of the layered
+bench model (the survey's mixed-precision configuration) at N = 5 and 6: the TF32 split, the BF16
+and FP16 splits (the FP16 split is the default tensor-core mode at these orders) and plain FP32 on
+CUDA cores, relative L2 of the receiver traces and both
+images of a whole shot; the library's FP64 mode as well.
+
+The oracle shot of the crop (34,848 elements, three rate levels, hundreds of global steps) takes
+minutes even on every host core, so it runs as the partitioned oracle (Sec. 4.2) over one gloo rank
+per core (the ranks' union is the unpartitioned oracle bit for bit, tests/test_oracle_partition.py).
+Opt-in: RIDG_CONFIG3=1; RIDG_CONFIG3_OUT names a file that receives one JSON line per order."""
+
+import json
+import os
+import socket
+import time
+
+import numpy as np
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+from oracle.partition import PartMRAB, partition
+from oracle.rtm import make_problem, rtm_shot
+from paper_1506_00907_gb300 import ridg
+from synth import config3_crop
+from tests.parity_cases import TOL, rel_l2
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not os.environ.get("RIDG_CONFIG3"),
+                                 reason="opt-in (RIDG_CONFIG3=1): minutes of oracle time on every host core")]
+
+F0, T_FINAL = 60.0, 0.03
+BYTES_PER_RANK = {5: 2.0e9, 6: 3.0e9}  # peak memory of one oracle rank of the crop (estimate with margin)
+
+
+def _workload(N):
+    return config3_crop(N, f0=F0, t_final=T_FINAL)
+
+
+class _Comm:
+    def exchange(self, sends, recv_shapes):
+        reqs, got = [], {}
+        for r in sorted(recv_shapes):
+            t = torch.empty(recv_shapes[r], dtype=torch.float64)
+            reqs.append(dist.irecv(t, src=r))
+            got[r] = t
+        for r in sorted(sends):
+            reqs.append(dist.isend(torch.from_numpy(np.ascontiguousarray(sends[r])), dst=r))
+        for q in reqs:
+            q.wait()
+        return {r: t.numpy() for r, t in got.items()}
+
+
+def _worker(rank, world, port, N, path):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    torch.set_num_threads(1)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = _workload(N)
+        prob = make_problem(w.xyz, w.tets, w.c, w.rho, N, default_bc=w.default_bc, cfl=w.cfl,
+                            n_levels_max=w.n_levels_max)
+        part = partition(prob.geo, prob.levels, prob.n_levels, world)
+
+        def stepper(*a, **k):
+            return PartMRAB(*a, **k, part=part, rank=rank, comm=_Comm())
+
+        res = rtm_shot(prob, w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final, stepper=stepper)
+        own = part == rank
+        rec_own = np.array([part[prob.geo.locate(x)[0]] == rank for x in w.receivers])
+        out = [np.where(rec_own[:, None], res.traces, 0.0), np.where(own[:, None], res.image_p, 0.0),
+               np.where(own[:, None], res.image_q, 0.0)]
+        tens = [torch.from_numpy(np.ascontiguousarray(a)) for a in out]
+        for t in tens:  # the parts are disjoint: the sum is their union
+            dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        if rank == 0:
+            np.savez(path, traces=tens[0].numpy(), image_p=tens[1].numpy(), image_q=tens[2].numpy())
+    finally:
+        dist.destroy_process_group()
+
+
+def _ranks(N):
+    n = os.cpu_count() or 2
+    try:
+        avail = [int(l.split()[1]) * 1024 for l in open("/proc/meminfo") if l.startswith("MemAvailable:")][0]
+        n = min(n, int(0.5 * avail // BYTES_PER_RANK[N]))
+    except (OSError, IndexError, ValueError):
+        n = 2
+    return max(2, n)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+_LAST_ORACLE_S = [0.0]
+
+
+def run_oracle_ranks(world, N, path):
+    """The partitioned oracle shot of the crop over world spawned ranks, one thread each (the ranks
+    inherit the thread limits set here); its union is written to path."""
+    saved = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for v in saved:
+        os.environ[v] = "1"
+    t0 = time.perf_counter()
+    try:
+        mp.start_processes(_worker, args=(world, _free_port(), N, path), nprocs=world, start_method="spawn")
+    finally:
+        for v, val in saved.items():
+            if val is None:
+                os.environ.pop(v, None)
+            else:
+                os.environ[v] = val
+    _LAST_ORACLE_S[0] = time.perf_counter() - t0
+
+
+@pytest.mark.parametrize("N", [5, 6])
+def test_config3_precision_against_the_oracle_on_the_crop(N, tmp_path):
+    world = _ranks(N)
+    path = str(tmp_path / f"oracle_N{N}.npz")
+    run_oracle_ranks(world, N, path)
+    oracle_s = _LAST_ORACLE_S[0]
+    ref = np.load(path)
+    w = _workload(N)
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    args = (w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
+    line = {"order": N, "elements": int(w.K), "record_s": w.t_final, "f0_hz": w.f0, "receivers": len(w.receivers),
+            "oracle": f"partitioned FP64 oracle over {world} gloo ranks on the host cores, {oracle_s:.0f} s"}
+    modes = (("f64", "f64", ridg.CONTRACT_TENSOR), ("f32_tensor_tf32x3", "f32", ridg.CONTRACT_TENSOR_TF32),
+             ("f32_tensor_bf16x3", "f32", ridg.CONTRACT_TENSOR_BF16),
+             ("f32_tensor_fp16x3", "f32", ridg.CONTRACT_TENSOR_FP16),
+             ("f32_cuda_cores", "f32", ridg.CONTRACT_CUDA_CORES))
+    for name, dtype, ctr in modes:
+        s = ridg.Solver(mesh, N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=w.n_levels_max, contraction=ctr)
+        if name == "f64":
+            line["levels"] = [int(x) for x in s.info.level_count[:s.info.n_levels]]
+        tr, ip, iq = s.rtm_shot(*args)
+        line[name] = {"traces_rel_l2": rel_l2(tr, ref["traces"]), "image_p_rel_l2": rel_l2(ip, ref["image_p"]),
+                      "image_q_rel_l2": rel_l2(iq, ref["image_q"])}
+        s.close()
+    out = os.environ.get("RIDG_CONFIG3_OUT")
+    if out:
+        with open(out, "a") as f:
+            f.write(json.dumps(line) + "\n")
+    assert np.abs(ref["image_p"]).max() > 0 and np.abs(ref["traces"]).max() > 0
+    assert max(line["f64"].values()) < TOL["f64"]
+    for name in ("f32_tensor_tf32x3", "f32_tensor_fp16x3", "f32_cuda_cores"):
+        assert max(line[name].values()) < TOL["f32"], (name, line[name])
+    assert max(line["f32_tensor_bf16x3"].values()) < 1e-4
