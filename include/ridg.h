@@ -426,6 +426,18 @@ int ridg_group_info_get(const ridg_group* g, ridg_group_info* out);
 int64_t ridg_group_trace_len(const ridg_group* g, double t_final, int32_t* np_out);
 void ridg_group_destroy(ridg_group* g);
 
+/* ------------------------------------------------------------------ failure injection (tests)
+ * A host-side failure point that fires once, through the same error path as the failure it stands
+ * for, after `after` passes (0: the next one); nothing touches the GPU.  Points: "alloc" (a device
+ * allocation: RIDG_E_OOM), "arena" (the boundary-trace arena of a shot: RIDG_E_OOM), "admission" (the
+ * shot server's memory admission refuses a request: RIDG_E_OOM), "exchange" (a part group's interface
+ * transfer: RIDG_E_CUDA from ridg_group_rtm_shot, every other part released), "none" (disarm).  The
+ * environment variable RIDG_FAULT=<point>[:<after>] arms one when the library loads.  The calls
+ * after a fired failure work as before.  No counterpart in the paper.  Errors: RIDG_E_INVALID_ARG. */
+int ridg_inject_fault(const char* point, int64_t after);
+/* The armed point (0 none, 1 alloc, 2 arena, 3 admission, 4 exchange). */
+int ridg_fault_armed(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,10 +4,12 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <array>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -51,6 +53,51 @@ static auto dispatch_order(int N, F&& f) {
   }
 }
 
+// ---- host-side fault injection (tests): one armed failure point fires once, after a number of
+// passes, through the same error path as the failure it stands for; nothing touches the GPU.
+// Armed by RIDG_FAULT=<point>[:<passes before it fires>] in the environment (read when the library
+// loads) or by ridg_inject_fault.
+enum FaultPoint { kFaultNone = 0, kFaultAlloc, kFaultArena, kFaultAdmission, kFaultExchange };
+struct FaultState {
+  std::atomic<int> point{kFaultNone};
+  std::atomic<int64_t> after{0};
+};
+static FaultState g_fault;
+
+static int fault_point_of(const std::string& name) {
+  if (name == "alloc") return kFaultAlloc;
+  if (name == "arena") return kFaultArena;
+  if (name == "admission") return kFaultAdmission;
+  if (name == "exchange") return kFaultExchange;
+  if (name == "none") return kFaultNone;
+  return -1;
+}
+
+// true once, when the armed point k is passed for the (after + 1)-th time; then disarmed
+static bool fault_fires(int k) {
+  if (g_fault.point.load() != k) return false;
+  if (g_fault.after.fetch_sub(1) > 0) return false;
+  int expected = k;
+  return g_fault.point.compare_exchange_strong(expected, kFaultNone);
+}
+
+static const bool g_fault_from_env = [] {
+  const char* v = std::getenv("RIDG_FAULT");
+  if (!v) return false;
+  std::string spec(v), name = spec;
+  int64_t after = 0;
+  const size_t colon = spec.find(':');
+  if (colon != std::string::npos) {
+    name = spec.substr(0, colon);
+    after = std::atoll(spec.c_str() + colon + 1);
+  }
+  const int k = fault_point_of(name);
+  if (k <= 0) return false;
+  g_fault.after.store(after);
+  g_fault.point.store(k);
+  return true;
+}();
+
 // Owning device allocation.
 struct DBuf {
   void* p = nullptr;
@@ -73,6 +120,8 @@ struct DBuf {
     if (n == bytes && p) return;
     release();
     if (n == 0) return;
+    if (fault_fires(kFaultAlloc))
+      throw Error{RIDG_E_OOM, "cudaMalloc of " + std::to_string(n) + " bytes failed (injected failure)"};
     cudaError_t e = cudaMalloc(&p, n);
     if (e != cudaSuccess) {
       p = nullptr;
@@ -933,6 +982,8 @@ class Engine final : public ridg_solver {
     std::vector<int64_t> arena_base(tau_f + 2, 0);
     for (int64_t t = 0; t <= tau_f; ++t) arena_base[t + 1] = arena_base[t] + (n_bfaces_ - bface_first(slot_lo(t)));
     size_t arena_bytes = size_t(arena_base[tau_f + 1]) * 2 * NFPP_ * sizeof(real);
+    if (fault_fires(kFaultArena))
+      throw Error{RIDG_E_OOM, "boundary-trace arena of " + std::to_string(arena_bytes) + " bytes (injected failure)"};
     arena_.reserve(std::max<size_t>(arena_bytes, 16));
     stats_.boundary_trace_bytes = int64_t(arena_bytes);
     q_snap_.alloc(qsize() * sizeof(real));
@@ -1772,6 +1823,7 @@ class Group final : public ridg_group, public PartHook<real> {
   // ---- PartHook (called from the part's own thread, its device current)
   void exchange(Engine<real>& e, int l0, int waves) override {
     Part& P = parts_[e.rank_];
+    if (fault_fires(kFaultExchange)) throw Error{RIDG_E_CUDA, "interface transfer failed (injected failure)"};
     if (!any_[l0]) {
       ++P.silent_steps;  // nothing pushed across an interface (finest level only, lumping held)
       return;
@@ -2061,6 +2113,8 @@ struct ridg_server {
     } done{this, s};
     for (;;) {
       const size_t need = s->solver->shot_extra_device_bytes(q->r.t_final);
+      if (ridg::fault_fires(ridg::kFaultAdmission))
+        throw Error{RIDG_E_OOM, "shot needs " + std::to_string(need) + " more device bytes (injected admission refusal)"};
       size_t free_b = 0, total_b = 0;
       RIDG_CUDA(cudaMemGetInfo(&free_b, &total_b));
       if (need + margin <= free_b) return;
@@ -2615,5 +2669,18 @@ int64_t ridg_group_trace_len(const ridg_group* g, double t_final, int32_t* np_ou
 }
 
 void ridg_group_destroy(ridg_group* g) { delete g; }
+
+int ridg_inject_fault(const char* point, int64_t after) {
+  return guarded([&] {
+    const int k = point ? ridg::fault_point_of(point) : -1;
+    if (k < 0) throw Error{RIDG_E_INVALID_ARG, "unknown failure point"};
+    if (after < 0) throw Error{RIDG_E_INVALID_ARG, "after must be >= 0"};
+    ridg::g_fault.point.store(ridg::kFaultNone);
+    ridg::g_fault.after.store(after);
+    ridg::g_fault.point.store(k);
+  });
+}
+
+int ridg_fault_armed(void) { return ridg::g_fault.point.load(); }
 
 }  // extern "C"

@@ -31,7 +31,7 @@ EXPORTED = [
     "ridg_server_wait", "ridg_server_destroy", "ridg_forward", "ridg_set_state_device", "ridg_get_state_device",
     "ridg_set_velocity", "ridg_eval_adjoint_rhs", "ridg_misfit_forward", "ridg_misfit_backward", "ridg_mesh_locate",
     "ridg_partition", "ridg_group_create", "ridg_group_rtm_shot", "ridg_group_info_get", "ridg_group_trace_len",
-    "ridg_group_destroy",
+    "ridg_group_destroy", "ridg_inject_fault", "ridg_fault_armed",
 ]
 MAX_PARTS = 64
 
@@ -148,6 +148,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_group_info_get": (C.c_int, [P, P]),
         "ridg_group_trace_len": (C.c_int64, [P, C.c_double, P]),
         "ridg_group_destroy": (None, [P]),
+        "ridg_inject_fault": (C.c_int, [C.c_char_p, C.c_int64]),
+        "ridg_fault_armed": (C.c_int, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -382,6 +384,16 @@ class Solver:
         st = ShotStats()
         _check(lib().ridg_last_shot_stats(self._h, C.byref(st)))
         return st
+
+
+def inject_fault(point: str, after: int = 0):
+    """Arms a host-side failure point ("alloc", "arena", "admission", "exchange"; "none" disarms) that
+    fires once after `after` passes (ridg_inject_fault)."""
+    _check(lib().ridg_inject_fault(point.encode(), int(after)))
+
+
+def fault_armed() -> int:
+    return int(lib().ridg_fault_armed())
 
 
 def partition(mesh: Mesh, N: int, c, n_parts: int, cfl=0.15, n_levels_max=3):

@@ -2,6 +2,7 @@
 host-side setup (reference operators, mesh checks, error codes) agrees with the oracle.  No
 kernel runs here."""
 
+import os
 import re
 
 import numpy as np
@@ -10,6 +11,8 @@ import pytest
 from oracle.reference_element import ReferenceElement
 from paper_1506_00907_gb300 import ridg
 from synth import tiny_layered_rtm, unit_cube_mesh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
@@ -104,3 +107,24 @@ def test_point_location_matches_the_oracle():
         assert k == k_ref
         if k >= 0:
             assert np.allclose(r, r_ref, atol=1e-10)
+
+
+def test_fault_points_arm_and_disarm():
+    """Host-side failure points: armed by ridg_inject_fault or by RIDG_FAULT when the library loads,
+    disarmed by "none"; unknown names and negative counts are refused (no GPU involved)."""
+    import subprocess
+    import sys
+
+    ridg.inject_fault("arena", 3)
+    assert ridg.fault_armed() == 2
+    ridg.inject_fault("none")
+    assert ridg.fault_armed() == 0
+    with pytest.raises(ridg.RidgError):
+        ridg.inject_fault("disk")
+    with pytest.raises(ridg.RidgError):
+        ridg.inject_fault("alloc", -1)
+    code = ("from paper_1506_00907_gb300 import ridg; print(ridg.fault_armed())")
+    env = dict(os.environ, RIDG_FAULT="exchange:5")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, env=env, capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.strip() == "4"
