@@ -53,9 +53,12 @@ def test_full_size_global_step_parity(workload, solver):
     st.set_history(r1, r2)
     st.global_step()
     assert rel_l2(q_gpu, st.q) < TOL["f32"]
-    # element by element: no element (first, last, padded block tails, level boundaries) is off
-    per = np.linalg.norm((q_gpu - st.q).reshape(w.K, -1), axis=1) / np.linalg.norm(st.q.reshape(w.K, -1), axis=1)
-    assert per.max() < 100 * TOL["f32"]
+    # element by element: no element (first, last, padded block tails, level boundaries) is off, against
+    # its own norm (loose) and with the largest element error against the largest element norm
+    err_k = np.linalg.norm((q_gpu - st.q).reshape(w.K, -1), axis=1)
+    ref_k = np.linalg.norm(st.q.reshape(w.K, -1), axis=1)
+    assert (err_k / ref_k).max() < 100 * TOL["f32"]
+    assert err_k.max() / ref_k.max() < 10 * TOL["f32"]
 
 
 def test_full_size_shot_is_linear(workload, solver):

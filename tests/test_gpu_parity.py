@@ -57,9 +57,12 @@ def test_rhs_parity_mixed_boundaries(dtype, N):
     g = prob.geo
     r_ref = rhs(np.arange(g.K), q, traces(q, g), g)
     assert rel_l2(r_gpu, r_ref) < TOL[dtype]
-    # element by element as well (every element's relative error bounded)
-    per = np.linalg.norm((r_gpu - r_ref).reshape(w.K, -1), axis=1) / np.linalg.norm(r_ref.reshape(w.K, -1), axis=1)
-    assert per.max() < 100 * TOL[dtype]
+    # element by element as well: every element's error against its own norm (loose: some elements'
+    # right-hand sides nearly cancel), and the largest element error against the largest element norm
+    err_k = np.linalg.norm((r_gpu - r_ref).reshape(w.K, -1), axis=1)
+    ref_k = np.linalg.norm(r_ref.reshape(w.K, -1), axis=1)
+    assert (err_k / ref_k).max() < 100 * TOL[dtype]
+    assert err_k.max() / ref_k.max() < 10 * TOL[dtype]
 
 
 def test_config1_standing_mode_fp64():
