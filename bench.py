@@ -669,6 +669,39 @@ def gradient_bench(dtype="f64", n_checkpoints=16, model="box"):
     return 0
 
 
+def group_bench(n_parts, t_final=0.01):
+    """Domain decomposition on one device: the bench model's shot over a short record with the mesh
+    split into n_parts (the library's partition; each part its own solver and stream, interface traces
+    copied after every fine step) against the single solver; wall times, the transfer counts and bytes,
+    and whether the results are bit for bit the single solver's.  One JSON line."""
+    from paper_1506_00907_gb300 import ridg
+
+    w = _workload()
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    args = (w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, t_final)
+    s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max)
+    s.rtm_shot(*args)  # buffers in place
+    t0 = time.perf_counter()
+    ref = s.rtm_shot(*args)
+    t_single = time.perf_counter() - t0
+    s.close()
+    part = ridg.partition(mesh, w.N, w.c, n_parts, cfl=w.cfl, n_levels_max=w.n_levels_max)
+    g = ridg.Group(mesh, w.N, w.c, w.rho, part, cfl=w.cfl, n_levels_max=w.n_levels_max)
+    g.rtm_shot(*args)
+    t0 = time.perf_counter()
+    out = g.rtm_shot(*args)
+    t_group = time.perf_counter() - t0
+    info = g.info()
+    print(json.dumps({"workload": f"bench mesh {w.K} tets N={w.N} FP32, {t_final} s record, {n_parts} parts on one device",
+                      "single_s": t_single, "group_s": t_group, "group_vs_single": t_single / t_group,
+                      "elements": list(info.elements[:n_parts]), "ghosts": list(info.ghosts[:n_parts]),
+                      "interface_faces": list(info.interface_faces[:n_parts]), "transfer_steps": info.transfer_steps,
+                      "silent_steps": info.silent_steps, "transfer_bytes": info.transfer_bytes,
+                      "bitwise_equal": bool(all(np.array_equal(a, b) for a, b in zip(out, ref)))}), flush=True)
+    g.close()
+    return 0
+
+
 def _kernel_hash():
     import hashlib
 
@@ -696,9 +729,17 @@ def main():
     ap.add_argument("--serving-sizes", default="50k,200k,800k", help="serving models (subset of 50k,200k,800k)")
     ap.add_argument("--serving-slots", default="1,2", help="slots per model to compare")
     ap.add_argument("--serving-contraction", default="tf32", choices=["tf32", "bf16"])
+    ap.add_argument("--serving-record", type=float, default=0.01, help="record length (s) of each served shot")
     ap.add_argument("--gradient", default="", nargs="?", const="box", choices=["", "box", "bench", "bench3"],
                     help="time the misfit gradient (on the adjoint box, or on the bench mesh with one or three levels) and exit")
+    ap.add_argument("--group-parts", type=int, default=0,
+                    help="time the bench shot with the mesh split into this many parts on one device and exit")
     args = ap.parse_args()
+    if args.group_parts > 0:
+        from paper_1506_00907_gb300.build import build
+
+        build()
+        return group_bench(args.group_parts)
     if args.gradient:
         from paper_1506_00907_gb300.build import build
 
@@ -708,7 +749,7 @@ def main():
         from paper_1506_00907_gb300.build import build
 
         build()
-        return serving_stream(args.serving_stream, sizes=tuple(args.serving_sizes.split(",")),
+        return serving_stream(args.serving_stream, t_rec=args.serving_record, sizes=tuple(args.serving_sizes.split(",")),
                               slot_counts=tuple(int(x) for x in args.serving_slots.split(",")),
                               contraction=args.serving_contraction)
     if args.precision_sweep:

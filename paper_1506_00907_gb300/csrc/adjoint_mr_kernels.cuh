@@ -178,20 +178,28 @@ __global__ void adjml_pull_kernel(AdjMrArgs<real> A) {
 // weights of the jumps, w_p = -tau_p at + bt and w_v = at - tau_v bt with at = alpha_f L_f^T mu_r,p
 // and bt = beta_f L_f^T (n_f . mu_r,v).  The neighbour's traces receive (w_p, w_v) in the element's
 // inbox adjoint; the element's own traces receive minus them, with the boundary ghosts folded in,
-// in the scratch rows (thread per (face, node, column)).
+// in the scratch rows (a half-warp per face and four columns, LIFT^T staged where it fits).
 template <int N, typename real>
 __global__ void adjml_traces_kernel(AdjMrArgs<real> A) {
   using O = Order<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
+  constexpr bool STAGE_LT = adj_traces_stage_lt<N, real>();
   extern __shared__ __align__(16) unsigned char smem_adjml[];
   real* sL = reinterpret_cast<real*>(smem_adjml);  // [4][Np][32]
-  real* sC = sL + 4 * Np * 32;                     // [kAdjMlTc][32]: normals, alpha_f, beta_f, tau_p, tau_v
-  int* sI = reinterpret_cast<int*>(sC + kAdjMlTc * 32);  // [4][32] boundary kinds, then [32] valid flags
+  real* sV = sL + 4 * Np * 32;                     // [4 faces][Np][32]: n_f . mu_r,v
+  real* sC = sV + 4 * Np * 32;                     // [kAdjMlTc][32]: normals, alpha_f, beta_f, tau_p, tau_v
+  real* sLt = sC + kAdjMlTc * 32;                  // [Np][4 Nfp] (if staged): LIFT^T, lanes read consecutive entries
+  int* sI = reinterpret_cast<int*>(sLt + (STAGE_LT ? Np * 4 * Nfp : 0));  // [4][32] boundary kinds, [32] valid
   const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * 32;
   const int64_t blk = slot0 >> 5;
   const int lev = adjml_level(A, slot0);
   const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
   load_lambda_tile<N, real>(A.mu_ring + A.ring_new[lev] * qsize, sL, blk);
+  if constexpr (STAGE_LT)
+    for (int i = threadIdx.x; i < 4 * Nfp * Np; i += blockDim.x) {
+      const int fj = i / Np, n = i - fj * Np;
+      cp_async_small<sizeof(real)>(sLt + n * (4 * Nfp) + fj, A.Lt + int64_t(fj) * A.NPa + n);
+    }
   cp_async_commit();
   for (int i = threadIdx.x; i < kAdjMlTc * 32; i += blockDim.x) {
     const int k = i >> 5, c = i & 31;
@@ -205,46 +213,74 @@ __global__ void adjml_traces_kernel(AdjMrArgs<real> A) {
                     : int((A.meta[slot0 + (i & 31)] & kMetaValid) != 0);
   cp_async_wait_all();
   __syncthreads();
+  for (int i = threadIdx.x; i < 4 * Np * 32; i += blockDim.x) {
+    const int f = i / (Np * 32), r = i - f * (Np * 32), n = r >> 5, c = r & 31;
+    const real* nf = sC + 3 * f * 32 + c;
+    sV[i] = nf[0] * sL[(1 * Np + n) * 32 + c] + nf[32] * sL[(2 * Np + n) * 32 + c] + nf[64] * sL[(3 * Np + n) * 32 + c];
+  }
+  __syncthreads();
+  // half-warp per (face, group of four columns), lanes over the face's nodes: each LIFT^T entry serves
+  // four columns, whose mu_r values come in one vector load per node.  Per face node the weights of the
+  // jumps, w_p = -tau_p at + bt and w_v = at - tau_v bt (at = alpha_f L_f^T mu_r,p, bt = beta_f L_f^T
+  // (n_f . mu_r,v)); the neighbour's traces receive them in the element's inbox adjoint, the element's
+  // own traces minus them, with the boundary ghosts folded in, in its scratch rows.
   real* xin = A.mu_in + int64_t(A.slot_read) * A.n_slots * (8 * NFPP);
-  for (int item = threadIdx.x; item < 4 * Nfp * 32; item += blockDim.x) {
-    const int c = item & 31, fj = item >> 5, f = fj / Nfp, j = fj - f * Nfp;
-    const int64_t s = slot0 + c;
-    real* ow = A.own + s * (8 * NFPP) + f * 2 * NFPP;
-    if (!sI[128 + c]) {
-      ow[j] = real(0);
-      ow[NFPP + j] = real(0);
-      continue;
+  constexpr int NJ = (Nfp + 15) / 16;
+  const int hw = threadIdx.x >> 4, lane16 = threadIdx.x & 15, nhw = blockDim.x >> 4;
+  for (int item = hw; item < 4 * 8; item += nhw) {
+    const int f = item >> 3, c0 = (item & 7) * 4;
+    const real* vf = sV + f * Np * 32;
+#pragma unroll
+    for (int t = 0; t < NJ; ++t) {
+      const int j = lane16 + 16 * t;
+      if (j >= Nfp) continue;
+      real ap[4] = {0, 0, 0, 0}, av[4] = {0, 0, 0, 0};
+#pragma unroll 4
+      for (int n = 0; n < Np; ++n) {
+        const real l = STAGE_LT ? sLt[n * (4 * Nfp) + f * Nfp + j] : A.Lt[int64_t(f * Nfp + j) * A.NPa + n];
+        real lp[4], lv[4];
+        load4(sL + n * 32 + c0, lp);
+        load4(vf + n * 32 + c0, lv);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ap[u] += l * lp[u];
+          av[u] += l * lv[u];
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u;
+        const int64_t s = slot0 + c;
+        real* ow = A.own + s * (8 * NFPP) + f * 2 * NFPP;
+        if (!sI[128 + c]) {
+          ow[j] = real(0);
+          ow[NFPP + j] = real(0);
+          continue;
+        }
+        const real* cc = sC + c;  // coefficient k of this column at cc[32 k]
+        const real a = cc[32 * (12 + f)] * ap[u], b = cc[32 * (16 + f)] * av[u];
+        const real taup = cc[32 * (20 + f)], tauv = cc[32 * (24 + f)];
+        const real wp = -taup * a + b, wv = a - tauv * b;
+        const int bc = sI[f * 32 + c];
+        real op = 0, ov = 0;
+        if (bc == 0) {
+          op = -wp;
+          ov = -wv;
+          real* x = xin + s * (8 * NFPP) + f * 2 * NFPP;
+          x[j] += wp;
+          x[NFPP + j] += wv;
+        } else if (bc == 1) {  // free surface: jp = -2 p-, jv = 0
+          op = real(-2) * wp;
+        } else if (bc == 2) {  // transparent: jp = -p-, jv = -vn-
+          op = -wp;
+          ov = -wv;
+        } else {  // rigid wall: jp = 0, jv = -2 vn-
+          ov = real(-2) * wv;
+        }
+        ow[j] = op;
+        ow[NFPP + j] = ov;
+      }
     }
-    const real* cc = sC + c;  // coefficient k of this column at cc[32 k]
-    const real* row = A.Lt + int64_t(fj) * A.NPa;
-    const real n0 = cc[32 * (3 * f)], n1 = cc[32 * (3 * f + 1)], n2 = cc[32 * (3 * f + 2)];
-    real ap = 0, av = 0;
-    for (int n = 0; n < Np; ++n) {
-      const real l = row[n];
-      ap += l * sL[(0 * Np + n) * 32 + c];
-      av += l * (n0 * sL[(1 * Np + n) * 32 + c] + n1 * sL[(2 * Np + n) * 32 + c] + n2 * sL[(3 * Np + n) * 32 + c]);
-    }
-    const real a = cc[32 * (12 + f)] * ap, b = cc[32 * (16 + f)] * av;
-    const real taup = cc[32 * (20 + f)], tauv = cc[32 * (24 + f)];
-    const real wp = -taup * a + b, wv = a - tauv * b;
-    const int bc = sI[f * 32 + c];
-    real op = 0, ov = 0;
-    if (bc == 0) {
-      op = -wp;
-      ov = -wv;
-      real* x = xin + s * (8 * NFPP) + f * 2 * NFPP;
-      x[j] += wp;
-      x[NFPP + j] += wv;
-    } else if (bc == 1) {  // free surface: jp = -2 p-, jv = 0
-      op = real(-2) * wp;
-    } else if (bc == 2) {  // transparent: jp = -p-, jv = -vn-
-      op = -wp;
-      ov = -wv;
-    } else {  // rigid wall: jp = 0, jv = -2 vn-
-      ov = real(-2) * wv;
-    }
-    ow[j] = op;
-    ow[NFPP + j] = ov;
   }
 }
 
@@ -338,7 +374,10 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
 
 template <int N, typename real>
 constexpr size_t adjml_traces_smem() {
-  return (size_t(4) * Order<N>::Np * 32 + size_t(kAdjMlTc) * 32) * sizeof(real) + size_t(5) * 32 * sizeof(int);
+  return (size_t(8) * Order<N>::Np * 32 + size_t(kAdjMlTc) * 32 +
+          (adj_traces_stage_lt<N, real>() ? size_t(4) * Order<N>::Nfp * Order<N>::Np : 0)) *
+             sizeof(real) +
+         size_t(5) * 32 * sizeof(int);
 }
 template <int N, typename real>
 constexpr size_t adjml_rhs_smem() {
