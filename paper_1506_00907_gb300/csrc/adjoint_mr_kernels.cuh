@@ -51,28 +51,40 @@ __device__ __forceinline__ void adjml_inverse_fmask(const int* __restrict__ inv_
 }
 
 // Reverse of the trace pushes and of the update.  First the adjoints of the traces this block's
-// elements pushed are taken (and cleared) from the neighbours' inbox adjoints: a half-warp per
-// (column, face) reads the face's contiguous row, lanes over the face nodes, into shared memory;
-// the per-column normals and flags are staged once.  Then a thread per (node, column) sums, per
+// elements pushed are taken (and cleared) from the neighbours' inbox adjoints into shared memory, a
+// fixed set of (column, face, face node) entries per thread with the neighbour and face-node tables
+// staged, so that a thread's loads are all in flight together; the per-column normals and flags are
+// staged once.  Then a thread per (node, column) sums, per
 // node, the entries of the faces that hold it (in face order) and updates mu and the ring adjoints.
 template <int N, typename real>
 constexpr size_t adjml_pull_smem() {
-  return size_t(2) * 32 * 4 * 2 * Order<N>::Nfp * sizeof(real);
+  return size_t(2) * 4 * 2 * Order<N>::Nfp * 33 * sizeof(real);
+}
+
+// blocks per SM the pull kernel's registers are held to: three at low orders in FP32 (its loads are in
+// flight together, so more resident warps hide more latency), the compiler's choice otherwise
+template <int N, typename real>
+constexpr int adjml_pull_min_blocks() {
+  return (sizeof(real) == 4 && N <= 4) ? 3 : 1;
 }
 
 template <int N, typename real>
-__global__ void adjml_pull_kernel(AdjMrArgs<real> A) {
+__global__ void __launch_bounds__(256, adjml_pull_min_blocks<N, real>()) adjml_pull_kernel(AdjMrArgs<real> A) {
   using O = Order<N>;
   constexpr int Np = O::Np, Nfp = O::Nfp, NFPP = O::NFPP;
   __shared__ int sInv[Np * 3];
   __shared__ real sN[12][32];  // outward normals per column
   __shared__ int sMeta[32];
   __shared__ uint8_t sInfo[32 * 4];
-  // full (set 0) and half-step (set 1) trace adjoints per column, face, (p, v) and face node
+  __shared__ int sNbr[32 * 4];
+  __shared__ int sPerm[6 * 32];
+  // full (set 0) and half-step (set 1) trace adjoints per face, (p, v), face node and column; columns
+  // innermost with a stride of 33 per face node, so that neither lanes over columns nor lanes over
+  // face nodes meet in a bank
   extern __shared__ __align__(16) unsigned char smem_pull[];
   real* sG = reinterpret_cast<real*>(smem_pull);
   auto G = [&](int set, int c, int f, int comp, int jf) -> real& {
-    return sG[(((set * 32 + c) * 4 + f) * 2 + comp) * Nfp + jf];
+    return sG[(((set * 4 + f) * 2 + comp) * Nfp + jf) * 33 + c];
   };
   const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * 32;
   const int64_t blk = slot0 >> 5;
@@ -87,42 +99,59 @@ __global__ void adjml_pull_kernel(AdjMrArgs<real> A) {
   real* xhalf = A.mu_in + A.slot_half[lev] * tsz;
   adjml_inverse_fmask<N>(A.inv_fmask, sInv);
   for (int i = threadIdx.x; i < 32; i += blockDim.x) sMeta[i] = A.meta[slot0 + i];
-  for (int i = threadIdx.x; i < 32 * 4; i += blockDim.x) sInfo[i] = A.finfo[slot0 * 4 + i];
+  for (int i = threadIdx.x; i < 32 * 4; i += blockDim.x) {
+    sInfo[i] = A.finfo[slot0 * 4 + i];
+    sNbr[i] = A.nbr[slot0 * 4 + i];
+  }
+  for (int i = threadIdx.x; i < 6 * 32; i += blockDim.x) sPerm[i] = A.perm[i];
   for (int i = threadIdx.x; i < 12 * 32; i += blockDim.x) {
     const int k = i >> 5, c = i & 31;
     sN[k][c] = real(A.geo[(slot0 + c) * kGeo + 9 + k]);
   }
   __syncthreads();
   {
-    const int hw = threadIdx.x >> 4, j = threadIdx.x & 15, nhw = blockDim.x >> 4;
-    for (int item = hw; item < 128; item += nhw) {
-      const int c = item & 31, f = item >> 5;
-      const int64_t s = slot0 + c;
+    // thread per (column, face, face node) entry, a fixed number per thread: every entry's neighbour
+    // row and permuted index come from shared memory, so all of a thread's loads are issued before any
+    // of its clearing stores
+    constexpr int NE = 32 * 4 * Nfp;
+    constexpr int PER = (NE + 255) / 256;  // launched with 256 threads
+    real gp[PER], gv[PER], hp[PER], hv[PER];
+    int64_t at[PER];
+    bool take[PER], half[PER];
+    // entry e = (c * 4 + f) * Nfp + jf: lanes run over a face's nodes, whose row is contiguous
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      const int ee = e < NE ? e : 0;
+      const int c = ee / (4 * Nfp), fj = ee - c * (4 * Nfp), f = fj / Nfp, jf = fj - f * Nfp;
       const int meta = sMeta[c];
       const uint8_t info = sInfo[c * 4 + f];
-      // boundary faces push nothing; invalid slots have nothing to take
-      const bool take = (meta & kMetaValid) && finfo_bc(info) == 0;
-      const bool half = take && (meta & kMetaHalf);
-      const int64_t at = take ? int64_t(A.nbr[s * 4 + f]) * (8 * NFPP) + finfo_face(info) * 2 * NFPP : 0;
-      for (int jf = j; jf < Nfp; jf += 16) {
-        real gp = 0, gv = 0, hp = 0, hv = 0;
-        if (take) {
-          const int j2 = A.perm[finfo_perm(info) * 32 + jf];
-          gp = xfull[at + j2];
-          gv = xfull[at + NFPP + j2];
-          xfull[at + j2] = real(0);
-          xfull[at + NFPP + j2] = real(0);
-          if (half) {
-            hp = xhalf[at + j2];
-            hv = xhalf[at + NFPP + j2];
-            xhalf[at + j2] = real(0);
-            xhalf[at + NFPP + j2] = real(0);
-          }
-        }
-        G(0, c, f, 0, jf) = gp;
-        G(0, c, f, 1, jf) = gv;
-        G(1, c, f, 0, jf) = hp;
-        G(1, c, f, 1, jf) = hv;
+      take[u] = e < NE && (meta & kMetaValid) && finfo_bc(info) == 0;  // boundary faces push nothing
+      half[u] = take[u] && (meta & kMetaHalf);
+      at[u] = take[u] ? int64_t(sNbr[c * 4 + f]) * (8 * NFPP) + finfo_face(info) * 2 * NFPP +
+                            sPerm[finfo_perm(info) * 32 + jf]
+                      : 0;
+      gp[u] = take[u] ? xfull[at[u]] : real(0);
+      gv[u] = take[u] ? xfull[at[u] + NFPP] : real(0);
+      hp[u] = half[u] ? xhalf[at[u]] : real(0);
+      hv[u] = half[u] ? xhalf[at[u] + NFPP] : real(0);
+    }
+#pragma unroll
+    for (int u = 0; u < PER; ++u) {
+      const int e = threadIdx.x + 256 * u;
+      if (e >= NE) continue;
+      const int c = e / (4 * Nfp), fj = e - c * (4 * Nfp), f = fj / Nfp, jf = fj - f * Nfp;
+      G(0, c, f, 0, jf) = gp[u];
+      G(0, c, f, 1, jf) = gv[u];
+      G(1, c, f, 0, jf) = hp[u];
+      G(1, c, f, 1, jf) = hv[u];
+      if (take[u]) {
+        xfull[at[u]] = real(0);
+        xfull[at[u] + NFPP] = real(0);
+      }
+      if (half[u]) {
+        xhalf[at[u]] = real(0);
+        xhalf[at[u] + NFPP] = real(0);
       }
     }
   }
