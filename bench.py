@@ -702,6 +702,37 @@ def group_bench(n_parts, t_final=0.01):
     return 0
 
 
+def tier_bench(budget_gb, t_final=0.2):
+    """Boundary-trace records beyond a device budget on the bench model: the same shot (FP32, a
+    shorter record) with every record on the device and with budget_gb of device memory for them
+    (the rest in pinned host memory, moved in chunks on a second stream); wall times, chunks, bytes
+    and whether the results are bit for bit the same.  One JSON line."""
+    from paper_1506_00907_gb300 import ridg
+
+    w = _workload()
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    args = (w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, t_final)
+    s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max)
+    s.rtm_shot(*args)  # buffers in place
+    t0 = time.perf_counter()
+    ref = s.rtm_shot(*args)
+    t_dev = time.perf_counter() - t0
+    full = s.shot_stats().boundary_trace_bytes
+    s.set_trace_budget(int(budget_gb * 1e9))
+    s.rtm_shot(*args)  # host memory in place
+    t0 = time.perf_counter()
+    out = s.rtm_shot(*args)
+    t_tier = time.perf_counter() - t0
+    st = s.shot_stats()
+    print(json.dumps({"workload": f"bench mesh {w.K} tets N={w.N} FP32, {t_final} s record",
+                      "record_bytes": full, "device_budget_bytes": int(budget_gb * 1e9),
+                      "chunks": st.trace_chunks, "host_bytes_each_way": st.host_trace_bytes,
+                      "all_device_s": t_dev, "tiered_s": t_tier, "tiered_vs_all_device": t_tier / t_dev,
+                      "bitwise_equal": bool(all(np.array_equal(a, b) for a, b in zip(out, ref)))}), flush=True)
+    s.close()
+    return 0
+
+
 def _kernel_hash():
     import hashlib
 
@@ -732,9 +763,16 @@ def main():
     ap.add_argument("--serving-record", type=float, default=0.01, help="record length (s) of each served shot")
     ap.add_argument("--gradient", default="", nargs="?", const="box", choices=["", "box", "bench", "bench3"],
                     help="time the misfit gradient (on the adjoint box, or on the bench mesh with one or three levels) and exit")
+    ap.add_argument("--trace-budget", type=float, default=0.0,
+                    help="time the bench shot (0.2 s record) with this many GB of device memory for its boundary-trace records and exit")
     ap.add_argument("--group-parts", type=int, default=0,
                     help="time the bench shot with the mesh split into this many parts on one device and exit")
     args = ap.parse_args()
+    if args.trace_budget > 0:
+        from paper_1506_00907_gb300.build import build
+
+        build()
+        return tier_bench(args.trace_budget)
     if args.group_parts > 0:
         from paper_1506_00907_gb300.build import build
 

@@ -43,6 +43,7 @@ extern "C" {
 #define RIDG_E_TIMEOUT -6     /* a bounded wait gave up (ridg_server_wait's timeout) */
 #define RIDG_E_NOT_FOUND -7   /* a source or receiver lies outside the mesh */
 #define RIDG_E_BUSY -8        /* a shot server's queue is full */
+#define RIDG_E_INTERNAL -9    /* a consistency check of the solver's tables failed (RIDG_DEBUG=1) */
 
 /* boundary-condition codes per local face (Sec. 2): 0 = automatic (interior where a neighbour
  * exists, else the default code), 1 = free surface p = 0, 2 = transparent p - rho c n.v = 0
@@ -259,9 +260,27 @@ typedef struct ridg_shot_stats {
    * every element (all levels active), forward (one wavefield) and backward (two wavefields) */
   double prof_forward_ms, prof_backward_ms;
   int64_t prof_forward_launches, prof_backward_launches;
+  /* boundary-trace records beyond the device budget (ridg_set_trace_budget): the chunks they were
+   * moved in (1: all on the device) and the bytes copied to host memory (the backward run copies
+   * the ones it reads back) */
+  int64_t trace_chunks, host_trace_bytes;
 } ridg_shot_stats;
 /* Synchronises the solver's stream, then returns the counters of the last shot. */
 int ridg_last_shot_stats(const ridg_solver* s, ridg_shot_stats* stats);
+
+/* Device memory for the boundary-trace records of a shot (Sec. 4.3; the forward run records the
+ * traces of every boundary face of every active element at every fine step, the backward source run
+ * replays them).  device_bytes = 0 (the default) keeps every record on the device.  With
+ * device_bytes > 0 and a shot whose records need more, the records of consecutive fine steps are
+ * grouped into chunks of at most device_bytes / 2: during the forward run each full chunk except the
+ * last two is copied to pinned host memory (allocated by the solver, the size of all records, kept
+ * for later shots) on a second stream while the next chunk fills the other half of the device
+ * buffer, and the backward run copies them back, one chunk ahead, in reverse order.  Results are
+ * bit for bit those of the shot with every record on the device.  A shot fails with
+ * RIDG_E_INVALID_ARG when device_bytes / 2 cannot hold the records of one fine step, and with
+ * RIDG_E_OOM when the host memory cannot be allocated.  device_bytes < 0: RIDG_E_INVALID_ARG.
+ * Admission by device memory (ridg_server_*) counts at most device_bytes for the records. */
+int ridg_set_trace_budget(ridg_solver* s, int64_t device_bytes);
 
 /* Profiling: when every > 0, every every-th global step the fused launch that covers all elements
  * is bracketed by CUDA events on the solver's stream; 0 turns it off (default). */

@@ -262,7 +262,16 @@ __global__ void adjml_traces_kernel(AdjMrArgs<real> A) {
 #pragma unroll
     for (int t = 0; t < NJ; ++t) {
       const int j = lane16 + 16 * t;
-      if (j >= Nfp) continue;
+      if (j >= Nfp) {
+        if (j < NFPP)  // pad words of the own rows: their 32-byte sectors are written whole
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            real* ow = A.own + (slot0 + c0 + u) * (8 * NFPP) + f * 2 * NFPP;
+            ow[j] = real(0);
+            ow[NFPP + j] = real(0);
+          }
+        continue;
+      }
       real ap[4] = {0, 0, 0, 0}, av[4] = {0, 0, 0, 0};
 #pragma unroll 4
       for (int n = 0; n < Np; ++n) {
@@ -317,12 +326,23 @@ __global__ void adjml_traces_kernel(AdjMrArgs<real> A) {
 // this step's right-hand side is cleared (thread per (node, column); with 256 threads a thread
 // keeps one column).  acc[slot] += sum_m mu_r,p (r_p - F w)_m, the source-free right-hand side,
 // summed in a fixed order (eight warp partial sums, added in FP64).
+// the interleaved derivative rows (D_0, D_1, D_2, 0)[n][m] are staged in shared memory where they
+// take at most 24 KB (FP32 up to N = 4, FP64 up to N = 3): every thread of a warp reads the same
+// entry, a broadcast from shared memory instead of an L1 lookup per entry
+template <int N, typename real>
+constexpr bool adjml_rhs_stage_d() {
+  return size_t(Order<N>::Np) * Order<N>::Np * 4 * sizeof(real) <= 24 * 1024;
+}
+
 template <int N, typename real>
 __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
   using O = Order<N>;
   constexpr int Np = O::Np, NFPP = O::NFPP;
+  constexpr bool STAGE_D = adjml_rhs_stage_d<N, real>();
+  constexpr int DS = STAGE_D ? Np * Np * 4 : 0;
   extern __shared__ __align__(16) unsigned char smem_adjml[];
-  real* sL = reinterpret_cast<real*>(smem_adjml);  // [4][Np][32]
+  real* sD = reinterpret_cast<real*>(smem_adjml);  // [Np][Np][4] (if staged)
+  real* sL = sD + DS;                              // [4][Np][32]
   real* sC = sL + 4 * Np * 32;                     // [kAdjMlRc][32]: rx, normals, rho c^2, 1/rho
   int* sInv = reinterpret_cast<int*>(sC + kAdjMlRc * 32);  // [Np][3]
   int* sValid = sInv + Np * 3;                             // [32]
@@ -332,6 +352,12 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
   const int64_t qsize = (A.n_slots >> 5) * 4 * Np * 32;
   real* rnew = A.mu_ring + A.ring_new[lev] * qsize + blk * 4 * Np * 32;
   load_lambda_tile<N, real>(A.mu_ring + A.ring_new[lev] * qsize, sL, blk);
+  if constexpr (STAGE_D) {
+    constexpr int CH = DS * int(sizeof(real)) / 16;
+    const char* src = reinterpret_cast<const char*>(A.Dt4);
+    char* dst = reinterpret_cast<char*>(sD);
+    for (int i = threadIdx.x; i < CH; i += blockDim.x) cp_async_bytes16(dst + 16 * i, src + 16 * i);
+  }
   cp_async_commit();
   for (int i = threadIdx.x; i < kAdjMlRc * 32; i += blockDim.x) {
     const int k = i >> 5, c = i & 31;
@@ -356,10 +382,12 @@ __global__ void __launch_bounds__(256) adjml_rhs_kernel(AdjMrArgs<real> A) {
     }
     const real* cc = sC + c;  // coefficient k of this column at cc[32 k]
     real dp[3] = {0, 0, 0}, dv[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
-    const real* dm = A.Dt4 + int64_t(m) * Np * 4;
     for (int n = 0; n < Np; ++n) {
       real d[3];
-      load_d3(dm + 4 * n, d);
+      if constexpr (STAGE_D)
+        load_d3(sD + (m * Np + n) * 4, d);
+      else
+        load_d3(A.Dt4 + (int64_t(m) * Np + n) * 4, d);
       const real lp = sL[(0 * Np + n) * 32 + c];
       const real lv[3] = {sL[(1 * Np + n) * 32 + c], sL[(2 * Np + n) * 32 + c], sL[(3 * Np + n) * 32 + c]};
 #pragma unroll
@@ -410,7 +438,9 @@ constexpr size_t adjml_traces_smem() {
 }
 template <int N, typename real>
 constexpr size_t adjml_rhs_smem() {
-  return (size_t(4) * Order<N>::Np * 32 + size_t(kAdjMlRc) * 32) * sizeof(real) +
+  return (size_t(4) * Order<N>::Np * 32 + size_t(kAdjMlRc) * 32 +
+          (adjml_rhs_stage_d<N, real>() ? size_t(Order<N>::Np) * Order<N>::Np * 4 : 0)) *
+             sizeof(real) +
          (size_t(Order<N>::Np) * 3 + 32) * sizeof(int);
 }
 

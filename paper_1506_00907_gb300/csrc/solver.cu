@@ -2,6 +2,7 @@
 // the finest level (Algorithm 1), and drives one RTM shot (Sec. 2, Sec. 4.3).
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <atomic>
@@ -16,6 +17,8 @@
 #include <memory>
 #include <mutex>
 #include <thread>
+#include <tuple>
+#include <utility>
 #include <stdexcept>
 #include <string>
 #include <type_traits>
@@ -98,6 +101,26 @@ static const bool g_fault_from_env = [] {
   return true;
 }();
 
+// NVTX range for the lifetime of the object (shot phases, fine steps by their first active level):
+// seen by ncu's --nvtx filters and by timeline tools, a few tens of nanoseconds without one.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Environment switches read when a solver is created: RIDG_PROFILE=<every> turns on the CUDA-event
+// profiling of ridg_set_profiling; RIDG_DEBUG=1 checks the solver's tables on the host before they
+// are uploaded (a failed check is RIDG_E_INTERNAL, naming the entry).
+static int env_int(const char* name, int fallback) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return fallback;
+  char* end = nullptr;
+  long x = std::strtol(v, &end, 10);
+  return (end && *end == '\0') ? int(x) : fallback;
+}
+
 // Owning device allocation.
 struct DBuf {
   void* p = nullptr;
@@ -132,6 +155,34 @@ struct DBuf {
   }
 };
 
+// Owning pinned host allocation (grow-only), for boundary-trace records kept in host memory.
+struct HBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  HBuf() = default;
+  HBuf(const HBuf&) = delete;
+  HBuf& operator=(const HBuf&) = delete;
+  ~HBuf() { release(); }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void reserve(size_t n) {
+    if (p && bytes >= n) return;
+    release();
+    if (fault_fires(kFaultAlloc))
+      throw Error{RIDG_E_OOM, "cudaHostAlloc of " + std::to_string(n) + " bytes failed (injected failure)"};
+    cudaError_t e = cudaHostAlloc(&p, n, cudaHostAllocDefault);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      cudaGetLastError();
+      throw Error{RIDG_E_OOM, "cudaHostAlloc of " + std::to_string(n) + " bytes failed: " + cudaGetErrorString(e)};
+    }
+    bytes = n;
+  }
+};
+
 template <typename T>
 static T* dptr(const DBuf& b) {
   return static_cast<T*>(b.p);
@@ -144,6 +195,137 @@ static void upload(DBuf& b, const std::vector<T>& v, cudaStream_t st) {
   b.reserve(v.size() * sizeof(T));
   if (!v.empty()) RIDG_CUDA(cudaMemcpyAsync(b.p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st));
 }
+
+// Boundary-trace records of a shot beyond a device budget (Sec. 4.3: the paper moves them from the
+// device to a host deque).  The records of consecutive fine steps form chunks of at most half the
+// budget.  The forward run fills one half of the device buffer while a copy stream moves the chunk
+// before it to pinned host memory; the backward run reads the chunks in reverse order, one half
+// while the copy stream brings the next chunk back into the other.  The last two chunks never leave
+// the device (a tiered shot has at least three: two chunks of half the budget would hold every
+// record).  Events order the compute and copy streams; no kernel waits on a copy.
+class TraceTier {
+ public:
+  TraceTier() = default;
+  TraceTier(const TraceTier&) = delete;
+  TraceTier& operator=(const TraceTier&) = delete;
+  ~TraceTier() {
+    if (cs_) cudaStreamSynchronize(cs_);
+    for (cudaEvent_t e : ev_)
+      if (e) cudaEventDestroy(e);
+    if (cs_) cudaStreamDestroy(cs_);
+  }
+  // rec_base[t] is the first record of step t (t = 0 .. n_steps, the last entry the total), each
+  // record rec_bytes long.  Returns false when the budget is 0 or holds every record (no tier);
+  // throws when half the budget cannot hold the records of the largest step.
+  bool plan(const std::vector<int64_t>& rec_base, size_t rec_bytes, size_t budget) {
+    const int64_t n_steps = int64_t(rec_base.size()) - 1;
+    const int64_t total = rec_base.back();
+    active_ = false;
+    if (budget == 0 || size_t(total) * rec_bytes <= budget) return false;
+    const int64_t cap = int64_t(budget / 2 / rec_bytes);
+    int64_t largest = 0;
+    for (int64_t t = 0; t < n_steps; ++t) largest = std::max(largest, rec_base[t + 1] - rec_base[t]);
+    if (largest > cap)
+      throw Error{RIDG_E_INVALID_ARG, "boundary-trace budget of " + std::to_string(budget) +
+                                          " bytes is below twice the records of one step (" +
+                                          std::to_string(2 * largest * int64_t(rec_bytes)) + " bytes)"};
+    rec_bytes_ = rec_bytes;
+    cap_ = cap;
+    first_step_.assign(1, 0);
+    chunk_of_.assign(size_t(n_steps), 0);
+    for (int64_t t = 0; t < n_steps; ++t) {
+      if (rec_base[t + 1] - rec_base[first_step_.back()] > cap) first_step_.push_back(t);
+      chunk_of_[size_t(t)] = int(first_step_.size()) - 1;
+    }
+    first_step_.push_back(n_steps);
+    first_rec_.resize(first_step_.size());
+    for (size_t k = 0; k < first_step_.size(); ++k) first_rec_[k] = rec_base[size_t(first_step_[k])];
+    if (!cs_) {
+      RIDG_CUDA(cudaStreamCreateWithFlags(&cs_, cudaStreamNonBlocking));
+      for (cudaEvent_t& e : ev_) RIDG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    active_ = true;
+    return true;
+  }
+  bool active() const { return active_; }
+  int n_chunks() const { return int(first_step_.size()) - 1; }
+  size_t device_bytes() const { return size_t(2 * cap_) * rec_bytes_; }
+  int chunk_of(int64_t t) const { return chunk_of_[size_t(t)]; }
+  int64_t first_record(int k) const { return first_rec_[size_t(k)]; }
+  int64_t host_bytes() const { return host_bytes_; }
+
+  // before the forward run: the copy stream's earlier work (a previous shot) is done first
+  void begin_forward(cudaStream_t st) {
+    after_copies(st);
+    cur_ = -1;
+    drained_[0] = drained_[1] = false;
+    host_bytes_ = 0;
+  }
+  // device address of chunk k for a forward step that records into it (chunks in ascending order)
+  char* forward_chunk(int k, char* dev, char* host, cudaStream_t st) {
+    if (k != cur_) {
+      if (cur_ >= 0 && cur_ < n_chunks() - 2) {  // the last two chunks stay on the device
+        const size_t n = size_t(first_rec_[cur_ + 1] - first_rec_[cur_]) * rec_bytes_;
+        RIDG_CUDA(cudaEventRecord(ev_[kFilled], st));
+        RIDG_CUDA(cudaStreamWaitEvent(cs_, ev_[kFilled], 0));
+        RIDG_CUDA(cudaMemcpyAsync(host + size_t(first_rec_[cur_]) * rec_bytes_, half(dev, cur_), n,
+                                  cudaMemcpyDeviceToHost, cs_));
+        RIDG_CUDA(cudaEventRecord(ev_[kDrained + (cur_ & 1)], cs_));
+        drained_[cur_ & 1] = true;
+        host_bytes_ += int64_t(n);
+      }
+      if (drained_[k & 1]) RIDG_CUDA(cudaStreamWaitEvent(st, ev_[kDrained + (k & 1)], 0));
+      drained_[k & 1] = false;
+      cur_ = k;
+    }
+    return half(dev, k);
+  }
+  // before the backward run, which reads the steps down to lowest_step
+  void begin_backward(int64_t lowest_step) {
+    cur_ = n_chunks();
+    const int64_t last = int64_t(chunk_of_.size()) - 1;
+    lowest_ = chunk_of(std::min(std::max<int64_t>(lowest_step, 0), last));
+  }
+  // device address of chunk k for a backward step that reads it (chunks in descending order)
+  char* backward_chunk(int k, char* dev, char* host, cudaStream_t st) {
+    if (k != cur_) {
+      const int K = n_chunks();
+      if (k < K - 2) RIDG_CUDA(cudaStreamWaitEvent(st, ev_[kReady + (k & 1)], 0));
+      const int next = k - 1;
+      if (next >= lowest_ && next < K - 2) {
+        // into the other half, whose chunk (k + 1) the steps launched so far have read
+        const size_t n = size_t(first_rec_[next + 1] - first_rec_[next]) * rec_bytes_;
+        RIDG_CUDA(cudaEventRecord(ev_[kUsed], st));
+        RIDG_CUDA(cudaStreamWaitEvent(cs_, ev_[kUsed], 0));
+        RIDG_CUDA(cudaMemcpyAsync(half(dev, next), host + size_t(first_rec_[next]) * rec_bytes_, n,
+                                  cudaMemcpyHostToDevice, cs_));
+        RIDG_CUDA(cudaEventRecord(ev_[kReady + (next & 1)], cs_));
+      }
+      cur_ = k;
+    }
+    return half(dev, k);
+  }
+  // the compute stream waits for every copy issued so far
+  void after_copies(cudaStream_t st) {
+    if (!cs_) return;
+    RIDG_CUDA(cudaEventRecord(ev_[kTail], cs_));
+    RIDG_CUDA(cudaStreamWaitEvent(st, ev_[kTail], 0));
+  }
+
+ private:
+  enum { kFilled = 0, kDrained = 1, kReady = 3, kUsed = 5, kTail = 6, kEvents = 7 };
+  char* half(char* dev, int k) const { return dev + size_t(k & 1) * size_t(cap_) * rec_bytes_; }
+  bool active_ = false;
+  size_t rec_bytes_ = 0;
+  int64_t cap_ = 0;
+  std::vector<int64_t> first_step_, first_rec_;
+  std::vector<int> chunk_of_;
+  int cur_ = -1, lowest_ = 0;
+  bool drained_[2] = {false, false};
+  int64_t host_bytes_ = 0;
+  cudaStream_t cs_ = nullptr;
+  cudaEvent_t ev_[kEvents] = {};
+};
 
 static int mod3(int64_t x) { return int(((x % 3) + 3) % 3); }
 
@@ -219,6 +401,7 @@ struct ridg_solver {
   virtual cudaStream_t stream() const = 0;
   virtual const ridg_shot_stats& stats() = 0;
   virtual void set_profiling(int every) = 0;
+  virtual void set_trace_budget(int64_t device_bytes) = 0;
   // device bytes a shot of this record length would still allocate (arena growth, first-shot buffers)
   virtual size_t shot_extra_device_bytes(double t_final) const = 0;
   // frees the device buffers only a shot uses (the next shot allocates them again); returns their bytes
@@ -330,6 +513,8 @@ class Engine final : public ridg_solver {
     check_shared_memory();
     build_nodes();
     check_face_nodes();
+    debug_ = env_int("RIDG_DEBUG", 0) > 0;
+    prof_every_ = std::max(0, env_int("RIDG_PROFILE", 0));
     build_tables();
     alloc_wave(w_[0]);
     reset_time();
@@ -359,6 +544,10 @@ class Engine final : public ridg_solver {
     return stats_;
   }
   void set_profiling(int every) override { prof_every_ = std::max(0, every); }
+  void set_trace_budget(int64_t device_bytes) override {
+    if (device_bytes < 0) throw Error{RIDG_E_INVALID_ARG, "boundary-trace budget must be >= 0"};
+    trace_budget_ = size_t(device_bytes);
+  }
 
   ~Engine() override {
     for (auto e : prof_ev_) cudaEventDestroy(e);
@@ -492,6 +681,7 @@ class Engine final : public ridg_solver {
   // sampled at every global step into traces_dev [nrec][n_t].
   void forward(const ridg_source& src, const double* rec, int64_t nrec, double t_final,
                double* traces_dev) override {
+    NvtxRange nv("ridg forward");
     if (!(t_final > 0.0)) throw Error{RIDG_E_INVALID_ARG, "t_final must be > 0"};
     if (nrec < 0 || (nrec > 0 && (!rec || !traces_dev))) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
     const Wavelet wav = Wavelet::of(src);
@@ -601,6 +791,7 @@ class Engine final : public ridg_solver {
 
   double misfit_forward(const ridg_source& src, const double* rec, int64_t nrec, double t_final,
                         const double* observed, int n_ckpt, double* traces_host) override {
+    NvtxRange nv("ridg misfit forward");
     if (!(t_final > 0.0)) throw Error{RIDG_E_INVALID_ARG, "t_final must be > 0"};
     if (nrec < 1 || !rec || !observed) throw Error{RIDG_E_INVALID_ARG, "receivers and observed traces are required"};
     adj_.ready = false;
@@ -703,6 +894,7 @@ class Engine final : public ridg_solver {
   }
 
   void misfit_backward(double* grad) override {
+    NvtxRange nv("ridg misfit backward");
     if (!adj_.ready) throw Error{RIDG_E_INVALID_ARG, "no misfit forward run to differentiate (or the velocity changed)"};
     if (!grad) throw Error{RIDG_E_INVALID_ARG, "grad is null"};
     if (L_ > 1) return misfit_backward_levels(grad);
@@ -873,7 +1065,8 @@ class Engine final : public ridg_solver {
     const int64_t tau_f = int64_t(std::ceil(t_final / dtg - 1e-9)) * NL_;
     int64_t recs = 0;
     for (int64_t t = 0; t <= tau_f; ++t) recs += n_bfaces_ - bface_first(slot_lo(t));
-    const size_t arena = std::max<size_t>(size_t(recs) * 2 * NFPP_ * sizeof(real), 16);
+    size_t arena = std::max<size_t>(size_t(recs) * 2 * NFPP_ * sizeof(real), 16);
+    if (trace_budget_ > 0 && arena > trace_budget_) arena = trace_budget_;  // at most the budget (TraceTier)
     size_t extra = arena > arena_.bytes ? arena - arena_.bytes : 0;
     if (!q_snap_.p) extra += 4 * qsize() * sizeof(real) + 2 * size_t(n_slots_) * Np_ * sizeof(double);
     if (!w_[1].q.p) extra += 4 * qsize() * sizeof(real) + 3 * trace_slot_elems() * sizeof(real);
@@ -897,6 +1090,7 @@ class Engine final : public ridg_solver {
   // ------------------------------------------------------------------ one shot
   void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i, const double* obs_dev,
             double* traces_dev, double* imgp_dev, double* imgq_dev, const double* e_up) override {
+    NvtxRange nv_shot("ridg shot");
     if (!(t_final > 0.0) || !(t_i >= 0.0) || t_i > t_final + lv_.dt_local * double(NL_))
       throw Error{RIDG_E_INVALID_ARG, "bad time span"};
     if (nrec < 0 || (nrec > 0 && !rec)) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
@@ -981,11 +1175,28 @@ class Engine final : public ridg_solver {
     // ---- boundary-trace arena: one record per boundary face of every active element per step
     std::vector<int64_t> arena_base(tau_f + 2, 0);
     for (int64_t t = 0; t <= tau_f; ++t) arena_base[t + 1] = arena_base[t] + (n_bfaces_ - bface_first(slot_lo(t)));
-    size_t arena_bytes = size_t(arena_base[tau_f + 1]) * 2 * NFPP_ * sizeof(real);
+    const size_t rec_bytes = 2 * NFPP_ * sizeof(real);
+    size_t arena_bytes = size_t(arena_base[tau_f + 1]) * rec_bytes;
     if (fault_fires(kFaultArena))
       throw Error{RIDG_E_OOM, "boundary-trace arena of " + std::to_string(arena_bytes) + " bytes (injected failure)"};
-    arena_.reserve(std::max<size_t>(arena_bytes, 16));
+    // beyond the device budget the records go to pinned host memory in chunks (TraceTier)
+    const bool tiered = tier_.plan(arena_base, rec_bytes, trace_budget_);
+    arena_.reserve(std::max<size_t>(tiered ? tier_.device_bytes() : arena_bytes, 16));
+    if (tiered && tier_.n_chunks() > 2) host_arena_.reserve(arena_bytes);
     stats_.boundary_trace_bytes = int64_t(arena_bytes);
+    stats_.trace_chunks = tiered ? tier_.n_chunks() : 1;
+    // device address and record offset of step t's records (the first record of its chunk at the start)
+    auto arena_at = [&](int64_t t, int sigma, int64_t slot_lo) {
+      char* base = static_cast<char*>(arena_.p);
+      int64_t first = 0;
+      if (tiered) {
+        const int k = tier_.chunk_of(t);
+        char* host = static_cast<char*>(host_arena_.p);
+        base = sigma > 0 ? tier_.forward_chunk(k, base, host, st_) : tier_.backward_chunk(k, base, host, st_);
+        first = tier_.first_record(k);
+      }
+      return std::make_pair(reinterpret_cast<real*>(base), arena_base[t] - first - bface_first(slot_lo));
+    };
     q_snap_.alloc(qsize() * sizeof(real));
     ring_snap_.alloc(3 * qsize() * sizeof(real));
     img_p_.alloc(size_t(n_slots_) * Np_ * sizeof(double));
@@ -1001,13 +1212,16 @@ class Engine final : public ridg_solver {
       a.wave[0] = wave_args(w_[0]);
       a.wave[0].amp_mode = 1;
       a.wave[0].amp = real(wav(double(tau_) * dtl));
-      a.arena_write = dptr<real>(arena_);
-      a.arena_offset = arena_base[std::min<int64_t>(tau_, tau_f)] - bface_first(a.slot_lo);
+      std::tie(a.arena_write, a.arena_offset) = arena_at(std::min<int64_t>(tau_, tau_f), +1, a.slot_lo);
       launch_fine(a, +1, 1);
     };
-    for (int64_t g = 0; g < n_global; ++g) {
-      for (int64_t s = 0; s < NL_; ++s) forward_step(kModeRecord);
-      sample(traces, n_t, g + 1, nrec);
+    if (tiered) tier_.begin_forward(st_);
+    {
+      NvtxRange nv("forward source run");
+      for (int64_t g = 0; g < n_global; ++g) {
+        for (int64_t s = 0; s < NL_; ++s) forward_step(kModeRecord);
+        sample(traces, n_t, g + 1, nrec);
+      }
     }
     stats_.dof_updates_forward = dof_;
     RIDG_CUDA(cudaMemcpyAsync(q_snap_.p, w_[0].q.p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
@@ -1049,6 +1263,8 @@ class Engine final : public ridg_solver {
       dscale_inv = dptr<const double>(scale_d_) + 2;
     }
     int64_t dof_before = dof_;
+    if (tiered) tier_.begin_backward(tau_i + 1);
+    NvtxRange nv_back("backward source and receiver runs");
     while (tau_ > tau_i) {
       StepArgs<real> a = fine_args(-1, 2, kModeReplay | image_mode_);
       a.wave[0] = wave_args(w_[0]);
@@ -1069,8 +1285,7 @@ class Engine final : public ridg_solver {
           if (j != i) li *= (u - xs[j]) / (xs[i] - xs[j]);
         a.interp_w[i] = li;
       }
-      a.arena_read = dptr<real>(arena_);
-      a.arena_offset = arena_base[tau_] - bface_first(a.slot_lo);
+      std::tie(a.arena_read, a.arena_offset) = arena_at(tau_, -1, a.slot_lo);
       a.image_p = dptr<double>(img_p_);
       a.image_q = dptr<double>(img_q_);
       double eu[3] = {0.0, 0.0, -1.0};
@@ -1079,6 +1294,12 @@ class Engine final : public ridg_solver {
       launch_fine(a, -1, 2);
     }
     stats_.dof_updates_backward = dof_ - dof_before;
+    if (tiered) {
+      tier_.after_copies(st_);
+      stats_.host_trace_bytes = tier_.host_bytes();
+    } else {
+      stats_.host_trace_bytes = 0;
+    }
     if (imgp_dev) image_out(dptr<double>(img_p_), dscale_inv, imgp_dev);
     if (imgq_dev) image_out(dptr<double>(img_q_), dscale_inv, imgq_dev);
     RIDG_CUDA(cudaGetLastError());
@@ -1211,6 +1432,7 @@ class Engine final : public ridg_solver {
     }
     n_bfaces_ = nb;
     bface_host_ = bface;
+    if (debug_) check_tables(nbr, finfo, bface, meta);
     upload(geo_d_, geo, st_);
     upload(J_d_, J, st_);
     upload_material();
@@ -1257,6 +1479,50 @@ class Engine final : public ridg_solver {
     level_count_.assign(L_, 0);
     for (int64_t k = 0; k < mesh_.K; ++k)
       if (owned(k)) level_count_[lv_.level[k] - 1]++;
+  }
+
+  // RIDG_DEBUG: every index the kernels follow stays in its array and the connectivity is symmetric
+  // (a face's neighbour names it back through the recorded face), the slot maps are inverse to each
+  // other, the boundary-face numbering counts the boundary faces in slot order, and the face-node
+  // tables are permutations of the face's nodes.
+  void check_tables(const std::vector<int>& nbr, const std::vector<uint8_t>& finfo, const std::vector<int>& bface,
+                    const std::vector<int>& meta) const {
+    auto fail = [](const std::string& what) { throw Error{RIDG_E_INTERNAL, "table check: " + what}; };
+    const int64_t S = n_slots_;
+    for (int64_t k = 0; k < mesh_.K; ++k) {
+      const int64_t s = ord_.slot_of[k];
+      if (s >= S || (s >= 0 && ord_.elem_of[s] != k)) fail("slot_of/elem_of of element " + std::to_string(k));
+    }
+    int64_t nb = 0;
+    for (int64_t s = 0; s < S; ++s) {
+      if (bface[s] != nb) fail("boundary-face start of slot " + std::to_string(s));
+      if (!(meta[s] & kMetaValid)) continue;
+      for (int f = 0; f < 4; ++f) {
+        const int n2 = nbr[s * 4 + f];
+        const int nf = finfo_face(finfo[s * 4 + f]), pc = finfo_perm(finfo[s * 4 + f]);
+        const int bc = finfo_bc(finfo[s * 4 + f]);
+        const std::string at = "slot " + std::to_string(s) + " face " + std::to_string(f);
+        if (n2 < -1 || n2 >= S) fail("neighbour slot out of range at " + at);
+        if ((n2 < 0) != (bc != 0)) fail("boundary code and neighbour disagree at " + at);
+        if (pc > 5 || bc > 3) fail("face code out of range at " + at);
+        if (n2 < 0) {
+          ++nb;
+          continue;
+        }
+        if ((meta[n2] & kMetaValid) && nbr[int64_t(n2) * 4 + nf] != int(s)) fail("asymmetric neighbours at " + at);
+      }
+    }
+    if (nb != n_bfaces_) fail("boundary-face count");
+    for (int c = 0; c < 6; ++c) {
+      std::vector<int> seen(Nfp_, 0);
+      for (int j = 0; j < Nfp_; ++j) {
+        const int q = ref_.perm[c][j];
+        if (q < 0 || q >= Nfp_ || seen[q]++) fail("face-node permutation " + std::to_string(c));
+      }
+    }
+    for (int f = 0; f < 4; ++f)
+      for (int j = 0; j < Nfp_; ++j)
+        if (ref_.fmask[f][j] < 0 || ref_.fmask[f][j] >= Np_) fail("face node " + std::to_string(j) + " of face " + std::to_string(f));
   }
 
   // Per-element coefficients of the FP32 tensor-core kernel for penalty sign `sigma` (Eq. penaltyFlux
@@ -1513,6 +1779,10 @@ class Engine final : public ridg_solver {
 
   void launch_fine(const StepArgs<real>& a, int sigma, int W) {
     int l0 = first_active_level(tau_);
+    static const char* const kStepNames[kMaxLevels] = {
+        "fine step, levels 1+", "fine step, levels 2+", "fine step, levels 3+", "fine step, levels 4+",
+        "fine step, levels 5+", "fine step, levels 6+", "fine step, levels 7+", "fine step, levels 8+"};
+    NvtxRange nv(kStepNames[std::min(std::max(l0, 1), kMaxLevels) - 1]);
     bool prof = prof_every_ > 0 && l0 == 1 && ((tau_ / NL_) % prof_every_) == 0;
     if (prof) {
       if (prof_used_ >= prof_w_.size()) {
@@ -1640,6 +1910,10 @@ class Engine final : public ridg_solver {
   int image_mode_ = kModeImage;
   std::vector<int> pos_of_;  // device position of each reference node
   DBuf q_snap_, ring_snap_, img_p_, img_q_, arena_, rec_slot_, rec_row_, traces_tmp_, scale_d_;
+  HBuf host_arena_;
+  bool debug_ = false;       // RIDG_DEBUG: host checks of the tables
+  size_t trace_budget_ = 0;  // device bytes for boundary-trace records (0: no limit)
+  TraceTier tier_;           // after the buffers it copies between: destroyed (and drained) first
   Wave<real> w_[2];
   int64_t tau_ = 0, dof_ = 0;
   std::vector<int> ring_count_;
@@ -2424,6 +2698,13 @@ int ridg_set_profiling(ridg_solver* s, int32_t every) {
   return guarded([&] {
     RIDG_NEED(s);
     s->set_profiling(every);
+  });
+}
+
+int ridg_set_trace_budget(ridg_solver* s, int64_t device_bytes) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->set_trace_budget(device_bytes);
   });
 }
 

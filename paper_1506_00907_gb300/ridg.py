@@ -31,7 +31,7 @@ EXPORTED = [
     "ridg_server_wait", "ridg_server_destroy", "ridg_forward", "ridg_set_state_device", "ridg_get_state_device",
     "ridg_set_velocity", "ridg_eval_adjoint_rhs", "ridg_misfit_forward", "ridg_misfit_backward", "ridg_mesh_locate",
     "ridg_partition", "ridg_group_create", "ridg_group_rtm_shot", "ridg_group_info_get", "ridg_group_trace_len",
-    "ridg_group_destroy", "ridg_inject_fault", "ridg_fault_armed",
+    "ridg_group_destroy", "ridg_inject_fault", "ridg_fault_armed", "ridg_set_trace_budget",
 ]
 MAX_PARTS = 64
 
@@ -79,7 +79,8 @@ class ShotStats(C.Structure):
                 ("fused_launches", C.c_int64), ("kernel_launches", C.c_int64), ("n_global", C.c_int64),
                 ("boundary_trace_bytes", C.c_int64), ("prof_forward_ms", C.c_double),
                 ("prof_backward_ms", C.c_double), ("prof_forward_launches", C.c_int64),
-                ("prof_backward_launches", C.c_int64)]
+                ("prof_backward_launches", C.c_int64), ("trace_chunks", C.c_int64),
+                ("host_trace_bytes", C.c_int64)]
 
 
 class ShotRequest(C.Structure):
@@ -128,6 +129,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_rtm_shot_device": (C.c_int, [P, P, P, C.c_int64, C.c_double, C.c_double, P, P, P, P, P]),
         "ridg_last_shot_stats": (C.c_int, [P, P]),
         "ridg_set_profiling": (C.c_int, [P, C.c_int32]),
+        "ridg_set_trace_budget": (C.c_int, [P, C.c_int64]),
         "ridg_energy_noalloc": (C.c_int, [P, P]),
         "ridg_forward": (C.c_int, [P, P, P, C.c_int64, C.c_double, P]),
         "ridg_set_state_device": (C.c_int, [P, P]),
@@ -379,6 +381,11 @@ class Solver:
 
     def set_profiling(self, every: int):
         _check(lib().ridg_set_profiling(self._h, int(every)))
+
+    def set_trace_budget(self, device_bytes: int):
+        """Device bytes for a shot's boundary-trace records; beyond them the records live in pinned
+        host memory (ridg_set_trace_budget).  0: all on the device."""
+        _check(lib().ridg_set_trace_budget(self._h, int(device_bytes)))
 
     def shot_stats(self) -> ShotStats:
         st = ShotStats()
