@@ -250,6 +250,39 @@ int ridg_rtm_shot_device(ridg_solver* s, const ridg_source* src, const double* r
                          double t_final, double t_image_start, const double* observed_dev, double* traces_dev,
                          double* image_p_dev, double* image_q_dev, const double* e_up);
 
+/* ------------------------------------------------------------------ several shots in lockstep
+ * n_shots (1 .. RIDG_MAX_BATCH) shots of this solver's model, each as ridg_rtm_shot (its own source,
+ * wavelet, receivers, observed traces and outputs; Sec. 2 per shot), over one record length t_final,
+ * one image window [t_image_start, t_final] and one e_up.  The shots advance in lockstep: every fine
+ * step is a single launch of the fused step kernel over the active elements of all of them (FP32
+ * tensor-core contractions; with FP64 or CUDA-core FP32 the shots are stepped one after the other
+ * within each fine step), so the finest-level steps, which cover few elements, fill more of the GPU
+ * and the element tables are read once per step.  Every shot's results are those of the same shot
+ * run alone by ridg_rtm_shot, bit for bit.  The solver keeps device state for each shot of its
+ * largest batch (fields, histories, traces, boundary records, images) until it is destroyed (a shot
+ * server gives it back from idle slots when it needs the memory).  ridg_last_shot_stats then counts
+ * the whole batch.  A solver with a trace budget (ridg_set_trace_budget) runs batches of one shot
+ * only.  The paper runs one shot at a time.
+ *   shots[i].observed, .traces_out, .image_p, .image_q: as the arguments of ridg_rtm_shot (host
+ *   buffers) or of ridg_rtm_shot_device (device buffers, for ridg_rtm_shots_device); rec_xyz is a
+ *   host array either way.
+ * Errors: as ridg_rtm_shot; RIDG_E_INVALID_ARG for n_shots outside 1 .. RIDG_MAX_BATCH. */
+#define RIDG_MAX_BATCH 4
+typedef struct ridg_shot_io {
+  ridg_source source;
+  const double* rec_xyz; /* [nrec][3] host */
+  int64_t nrec;
+  const double* observed; /* [nrec][n_t] or NULL (re-inject the modelled traces) */
+  double* traces_out;     /* [nrec][n_t] or NULL */
+  double* image_p;        /* [K][Np] or NULL */
+  double* image_q;        /* [K][Np] or NULL */
+} ridg_shot_io;
+int ridg_rtm_shots(ridg_solver* s, int32_t n_shots, const ridg_shot_io* shots, double t_final,
+                   double t_image_start, const double* e_up);
+/* Device-buffer form: returns after the work is enqueued on the solver's stream. */
+int ridg_rtm_shots_device(ridg_solver* s, int32_t n_shots, const ridg_shot_io* shots, double t_final,
+                          double t_image_start, const double* e_up);
+
 /* Counters of the last shot: DOF updates (elements updated x 4 x Np, both wavefields counted in
  * the backward phase), fused-kernel launches and total kernel launches. */
 typedef struct ridg_shot_stats {
@@ -381,6 +414,12 @@ int ridg_server_create_slots(ridg_solver* const* solvers, const int32_t* models,
  * RIDG_E_INVALID_ARG for a malformed request or a model no slot serves (checked again, with the
  * solver, when it runs). */
 int ridg_server_submit(ridg_server* sv, const ridg_shot_request* req, int64_t* ticket);
+/* A slot that takes a request also takes up to max_batch - 1 later waiting requests of its model
+ * with the same t_final, t_image_start and e_up, and runs them together as one lockstep batch
+ * (ridg_rtm_shots: one merged launch per fine step); each request's results are those it gets
+ * alone.  max_batch in 1 .. RIDG_MAX_BATCH; 1 (the default) runs one shot at a time.  Admission
+ * counts the memory of the whole batch.  Errors: RIDG_E_INVALID_ARG. */
+int ridg_server_set_batch(ridg_server* sv, int32_t max_batch);
 /* Waits at most timeout_s seconds (< 0: without limit) for a request.  When it has completed,
  * releases the ticket, fills timing (may be NULL) and returns the request's own status (0, or the
  * error it ran into, with its message in ridg_last_error); RIDG_E_TIMEOUT if it has not completed

@@ -72,7 +72,10 @@ struct AdjMrArgs {
 
 template <int N, typename real>
 struct Launch {
-  static cudaError_t step(const StepArgs<real>& a, int W, cudaStream_t st);
+  // batch != null: a merged launch of n_shots shots (FP32 tensor-core contractions only), the grid
+  // n_shots x batch->shot_blocks blocks
+  static cudaError_t step(const StepArgs<real>& a, int W, cudaStream_t st, const BatchArgs<real>* batch = nullptr,
+                          int n_shots = 1);
   static cudaError_t init_traces(const real* q, real* trace, int slot, int64_t n_slots, const double* geo,
                                  const int* meta, const int* fmask, const int* nbr, const uint8_t* finfo,
                                  const int* perm, cudaStream_t st);

@@ -11,29 +11,48 @@
 
 namespace ridg {
 
-// FP32 on tensor cores with the split format KIND
-template <int N, int W, int KIND>
-static cudaError_t launch_step_tc(const StepArgs<float>& a, int64_t blocks, cudaStream_t st) {
+// FP32 on tensor cores with the split format KIND; BATCH: n_shots shots of one solver in one launch
+template <int N, int W, int KIND, bool BATCH>
+static cudaError_t launch_step_tc(const StepArgs<float>& a, const BatchArgs<float>* batch, int n_shots, int64_t blocks,
+                                  cudaStream_t st) {
   constexpr size_t smem = SmemTc<N, W, KIND>::bytes;
   static PerDeviceSetup setup;
   const cudaError_t configured = setup.run([] {
-    return cudaFuncSetAttribute(dg_step_kernel_tc<N, W, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    return cudaFuncSetAttribute(dg_step_kernel_tc<N, W, KIND, BATCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                int(smem));
   });
   if (configured != cudaSuccess) return configured;
-  dg_step_kernel_tc<N, W, KIND><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a);
+  if constexpr (BATCH) {
+    dg_step_kernel_tc<N, W, KIND, true><<<dim3(unsigned(blocks * n_shots)), TcOrder<N>::NT, smem, st>>>(a, *batch);
+  } else {
+    (void)batch;
+    (void)n_shots;
+    dg_step_kernel_tc<N, W, KIND, false><<<dim3(unsigned(blocks)), TcOrder<N>::NT, smem, st>>>(a, NoBatch{0});
+  }
   return cudaGetLastError();
 }
 
+template <int N, int W, int KIND>
+static cudaError_t launch_step_tc_any(const StepArgs<float>& a, const BatchArgs<float>* batch, int n_shots,
+                                      int64_t blocks, cudaStream_t st) {
+  if (batch) return launch_step_tc<N, W, KIND, true>(a, batch, n_shots, blocks, st);
+  return launch_step_tc<N, W, KIND, false>(a, nullptr, 1, blocks, st);
+}
+
 template <int N, typename real, int W>
-static cudaError_t launch_step_w(const StepArgs<real>& a, cudaStream_t st) {
+static cudaError_t launch_step_w(const StepArgs<real>& a, const BatchArgs<real>* batch, int n_shots, cudaStream_t st) {
   int64_t blocks = (a.slot_hi - a.slot_lo) / (32 / W);
   if (blocks <= 0) return cudaSuccess;
+  if (batch && (n_shots < 1 || n_shots > kMaxBatch || batch->shot_blocks != blocks)) return cudaErrorInvalidValue;
   if constexpr (std::is_same<real, float>::value) {
-    if (a.contraction == RIDG_CONTRACT_TENSOR) return launch_step_tc<N, W, kSplitTf32>(a, blocks, st);
-    if (a.contraction == RIDG_CONTRACT_TENSOR_BF16) return launch_step_tc<N, W, kSplitBf16>(a, blocks, st);
-    if (a.contraction == RIDG_CONTRACT_TENSOR_FP16) return launch_step_tc<N, W, kSplitFp16>(a, blocks, st);
+    if (a.contraction == RIDG_CONTRACT_TENSOR) return launch_step_tc_any<N, W, kSplitTf32>(a, batch, n_shots, blocks, st);
+    if (a.contraction == RIDG_CONTRACT_TENSOR_BF16)
+      return launch_step_tc_any<N, W, kSplitBf16>(a, batch, n_shots, blocks, st);
+    if (a.contraction == RIDG_CONTRACT_TENSOR_FP16)
+      return launch_step_tc_any<N, W, kSplitFp16>(a, batch, n_shots, blocks, st);
   }
-  // FP64, or FP32 on CUDA cores
+  // FP64, or FP32 on CUDA cores: one shot per launch (the engine launches a batch shot by shot)
+  if (batch) return cudaErrorInvalidValue;
   constexpr size_t smem = step_smem_bytes<N, real, W>();
   static PerDeviceSetup setup;
   const cudaError_t configured = setup.run([] {
@@ -45,8 +64,9 @@ static cudaError_t launch_step_w(const StepArgs<real>& a, cudaStream_t st) {
 }
 
 template <int N, typename real>
-cudaError_t Launch<N, real>::step(const StepArgs<real>& a, int W, cudaStream_t st) {
-  return W == 1 ? launch_step_w<N, real, 1>(a, st) : launch_step_w<N, real, 2>(a, st);
+cudaError_t Launch<N, real>::step(const StepArgs<real>& a, int W, cudaStream_t st, const BatchArgs<real>* batch,
+                                  int n_shots) {
+  return W == 1 ? launch_step_w<N, real, 1>(a, batch, n_shots, st) : launch_step_w<N, real, 2>(a, batch, n_shots, st);
 }
 
 template <int N, typename real>

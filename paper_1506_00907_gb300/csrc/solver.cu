@@ -398,12 +398,16 @@ struct ridg_solver {
   virtual void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i,
                     const double* obs_dev, double* traces_dev, double* imgp_dev, double* imgq_dev,
                     const double* e_up) = 0;
+  // n shots in lockstep, device buffers (ridg_rtm_shots_device)
+  virtual void shots(int32_t n, const ridg_shot_io* io, double t_final, double t_i, const double* e_up) = 0;
   virtual cudaStream_t stream() const = 0;
   virtual const ridg_shot_stats& stats() = 0;
   virtual void set_profiling(int every) = 0;
   virtual void set_trace_budget(int64_t device_bytes) = 0;
   // device bytes a shot of this record length would still allocate (arena growth, first-shot buffers)
   virtual size_t shot_extra_device_bytes(double t_final) const = 0;
+  // the same for a batch of n shots in lockstep
+  virtual size_t shots_extra_device_bytes(double t_final, int32_t n) const = 0;
   // frees the device buffers only a shot uses (the next shot allocates them again); returns their bytes
   virtual size_t release_shot_buffers() = 0;
   virtual void forward(const ridg_source& src, const double* rec, int64_t nrec, double t_final,
@@ -1072,6 +1076,28 @@ class Engine final : public ridg_solver {
     if (!w_[1].q.p) extra += 4 * qsize() * sizeof(real) + 3 * trace_slot_elems() * sizeof(real);
     return extra;
   }
+  size_t shots_extra_device_bytes(double t_final, int32_t n) const override {
+    size_t extra = shot_extra_device_bytes(t_final);
+    if (n <= 1 || !(t_final > 0.0)) return extra;
+    // shots 1.. of the batch: their own arena, snapshots, images and two wavefields
+    const double dtg = lv_.dt_local * double(NL_);
+    const int64_t tau_f = int64_t(std::ceil(t_final / dtg - 1e-9)) * NL_;
+    int64_t recs = 0;
+    for (int64_t t = 0; t <= tau_f; ++t) recs += n_bfaces_ - bface_first(slot_lo(t));
+    const size_t arena = std::max<size_t>(size_t(recs) * 2 * NFPP_ * sizeof(real), 16);
+    const size_t wave = 4 * qsize() * sizeof(real) + 3 * trace_slot_elems() * sizeof(real);
+    const size_t per = arena + 4 * qsize() * sizeof(real) + 2 * size_t(n_slots_) * Np_ * sizeof(double) + 2 * wave;
+    for (int32_t b = 1; b < n; ++b) {
+      const ShotState* x = size_t(b - 1) < extra_shots_.size() ? extra_shots_[size_t(b - 1)].get() : nullptr;
+      size_t have = 0;
+      if (x) {
+        have = x->arena.bytes + x->q_snap.bytes + x->ring_snap.bytes + x->img_p.bytes + x->img_q.bytes;
+        for (const Wave<real>& w : x->w) have += w.q.bytes + w.ring.bytes + w.trace.bytes;
+      }
+      extra += per > have ? per - have : 0;
+    }
+    return extra;
+  }
   size_t release_shot_buffers() override {
     RIDG_CUDA(cudaStreamSynchronize(st_));
     size_t bytes = 0;
@@ -1080,6 +1106,14 @@ class Engine final : public ridg_solver {
       bytes += d->bytes;
       d->release();
     }
+    for (auto& x : extra_shots_) {
+      for (DBuf* d : {&x->rec_slot, &x->rec_row, &x->traces_tmp, &x->arena, &x->q_snap, &x->ring_snap, &x->img_p,
+                      &x->img_q, &x->scale})
+        bytes += d->bytes;
+      for (Wave<real>& w : x->w)
+        for (DBuf* d : {&w.q, &w.ring, &w.trace, &w.inj_range, &w.inj_w, &w.inj_row}) bytes += d->bytes;
+    }
+    extra_shots_.clear();
     return bytes;
   }
   int64_t trace_len(double t_final) const override {
@@ -1087,13 +1121,37 @@ class Engine final : public ridg_solver {
     return int64_t(std::ceil(t_final / dtg - 1e-9)) + 1;
   }
 
-  // ------------------------------------------------------------------ one shot
+  // ------------------------------------------------------------------ RTM shots
   void shot(const ridg_source& src, const double* rec, int64_t nrec, double t_final, double t_i, const double* obs_dev,
             double* traces_dev, double* imgp_dev, double* imgq_dev, const double* e_up) override {
-    NvtxRange nv_shot("ridg shot");
+    ridg_shot_io io{};
+    io.source = src;
+    io.rec_xyz = rec;
+    io.nrec = nrec;
+    io.observed = obs_dev;
+    io.traces_out = traces_dev;
+    io.image_p = imgp_dev;
+    io.image_q = imgq_dev;
+    shots(1, &io, t_final, t_i, e_up);
+  }
+
+  // n shots of this solver's model in lockstep (one record length and image window): every fine step
+  // is one merged launch over the active slots of all of them (FP32 tensor-core contractions; the
+  // other kernels step the shots one after the other).  Shot 0 keeps its device state in the
+  // solver's own buffers, shots 1.. in extra_shots_.
+  void shots(int32_t n, const ridg_shot_io* io, double t_final, double t_i, const double* e_up) override {
+    NvtxRange nv_shot(n == 1 ? "ridg shot" : "ridg merged shots");
+    if (n < 1 || n > kMaxBatch || !io)
+      throw Error{RIDG_E_INVALID_ARG, "a batch holds 1 to " + std::to_string(kMaxBatch) + " shots"};
+    if (n > 1 && hook_) throw Error{RIDG_E_INVALID_ARG, "the parts of a group run one shot at a time"};
+    if (n > 1 && trace_budget_ > 0)
+      throw Error{RIDG_E_INVALID_ARG, "a batch of shots keeps its boundary records on the device (no trace budget)"};
     if (!(t_final > 0.0) || !(t_i >= 0.0) || t_i > t_final + lv_.dt_local * double(NL_))
       throw Error{RIDG_E_INVALID_ARG, "bad time span"};
-    if (nrec < 0 || (nrec > 0 && !rec)) throw Error{RIDG_E_INVALID_ARG, "bad receiver list"};
+    for (int b = 0; b < n; ++b)
+      if (io[b].nrec < 0 || (io[b].nrec > 0 && !io[b].rec_xyz))
+        throw Error{RIDG_E_INVALID_ARG, "bad receiver list of shot " + std::to_string(b)};
+    while (int(extra_shots_.size()) < n - 1) extra_shots_.push_back(std::make_unique<ShotState>());
     std::memset(&stats_, 0, sizeof(stats_));
     prof_used_ = 0;
     const double dtl = lv_.dt_local, dtg = dtl * double(NL_);
@@ -1103,91 +1161,104 @@ class Engine final : public ridg_solver {
     n_i = std::min(n_i, n_global);
     const int64_t tau_f = n_global * NL_, tau_i = n_i * NL_;
     stats_.n_global = n_global;
-    // ---- source and receivers
-    double rst[3];
-    int64_t ks = locate_point(mesh_, loc_, src.xyz, rst);
-    if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
-    std::vector<real> w_src = projected_dirac(ks, rst);
-    const Wavelet wav = Wavelet::of(src);
-    const bool src_here = owned(ks);
-    struct Rec {
-      int64_t slot;
-      std::vector<real> row, w;
-      int idx;
-    };
-    std::vector<Rec> recs(nrec);
-    for (int64_t r = 0; r < nrec; ++r) {
-      int64_t kr = locate_point(mesh_, loc_, rec + 3 * r, rst);
-      if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
-      recs[r].slot = owned(kr) ? ord_.slot_of[kr] : -1;  // -1: another part samples and injects it
-      std::array<double, 3> p = {rst[0], rst[1], rst[2]};
-      std::vector<double> l = ref_.lagrange_at(p);
-      recs[r].row.assign(l.begin(), l.end());
-      recs[r].w = projected_dirac(kr, rst);
-      recs[r].idx = int(r);
-    }
-    // source injection table (wavefield 0)
-    {
-      std::vector<int2> range(n_slots_, make_int2(0, 0));
-      if (src_here) range[ord_.slot_of[ks]] = make_int2(0, 1);
-      upload(w_[0].inj_range, range, st_);
-      upload(w_[0].inj_w, w_src, st_);
-      upload(w_[0].inj_row, std::vector<int>{0}, st_);
-    }
-    alloc_wave(w_[1]);
-    {
-      // receiver injections grouped by slot (wavefield 1)
-      std::vector<Rec> sorted;
-      for (const Rec& r : recs)
-        if (r.slot >= 0) sorted.push_back(r);
-      std::stable_sort(sorted.begin(), sorted.end(), [](const Rec& a, const Rec& b) { return a.slot < b.slot; });
-      std::vector<int2> range(n_slots_, make_int2(0, 0));
-      std::vector<real> wv;
-      std::vector<int> rows;
-      for (size_t i = 0; i < sorted.size(); ++i) {
-        int2& rg = range[sorted[i].slot];
-        if (rg.y == 0) rg.x = int(i);
-        rg.y += 1;
-        wv.insert(wv.end(), sorted[i].w.begin(), sorted[i].w.end());
-        rows.push_back(sorted[i].idx);
-      }
-      if (rows.empty()) {
-        rows.push_back(0);
-        wv.assign(Np_, real(0));
-      }
-      upload(w_[1].inj_range, range, st_);
-      upload(w_[1].inj_w, wv, st_);
-      upload(w_[1].inj_row, rows, st_);
-      std::vector<int64_t> rslot(std::max<int64_t>(nrec, 1), 0);
-      std::vector<real> rrow(std::max<int64_t>(nrec, 1) * Np_, real(0));
+    std::vector<ShotRef> S(n);
+    for (int b = 0; b < n; ++b) S[b] = shot_ref(b);
+    // ---- sources and receivers of every shot
+    std::vector<Wavelet> wav(n);
+    for (int b = 0; b < n; ++b) {
+      const ridg_source& src = io[b].source;
+      const int64_t nrec = io[b].nrec;
+      const double* rec = io[b].rec_xyz;
+      double rst[3];
+      int64_t ks = locate_point(mesh_, loc_, src.xyz, rst);
+      if (ks < 0) throw Error{RIDG_E_NOT_FOUND, "source lies outside the mesh"};
+      std::vector<real> w_src = projected_dirac(ks, rst);
+      wav[b] = Wavelet::of(src);
+      const bool src_here = owned(ks);
+      struct Rec {
+        int64_t slot;
+        std::vector<real> row, w;
+        int idx;
+      };
+      std::vector<Rec> recs(nrec);
       for (int64_t r = 0; r < nrec; ++r) {
-        rslot[r] = recs[r].slot;
-        for (int m = 0; m < Np_; ++m) rrow[r * Np_ + m] = recs[r].row[m];
+        int64_t kr = locate_point(mesh_, loc_, rec + 3 * r, rst);
+        if (kr < 0) throw Error{RIDG_E_NOT_FOUND, "receiver " + std::to_string(r) + " lies outside the mesh"};
+        recs[r].slot = owned(kr) ? ord_.slot_of[kr] : -1;  // -1: another part samples and injects it
+        std::array<double, 3> p = {rst[0], rst[1], rst[2]};
+        std::vector<double> l = ref_.lagrange_at(p);
+        recs[r].row.assign(l.begin(), l.end());
+        recs[r].w = projected_dirac(kr, rst);
+        recs[r].idx = int(r);
       }
-      upload(rec_slot_, rslot, st_);
-      upload(rec_row_, rrow, st_);
+      Wave<real>* w = S[b].w;
+      alloc_wave(w[0]);
+      // source injection table (wavefield 0)
+      {
+        std::vector<int2> range(n_slots_, make_int2(0, 0));
+        if (src_here) range[ord_.slot_of[ks]] = make_int2(0, 1);
+        upload(w[0].inj_range, range, st_);
+        upload(w[0].inj_w, w_src, st_);
+        upload(w[0].inj_row, std::vector<int>{0}, st_);
+      }
+      alloc_wave(w[1]);
+      {
+        // receiver injections grouped by slot (wavefield 1)
+        std::vector<Rec> sorted;
+        for (const Rec& r : recs)
+          if (r.slot >= 0) sorted.push_back(r);
+        std::stable_sort(sorted.begin(), sorted.end(), [](const Rec& a, const Rec& c) { return a.slot < c.slot; });
+        std::vector<int2> range(n_slots_, make_int2(0, 0));
+        std::vector<real> wv;
+        std::vector<int> rows;
+        for (size_t i = 0; i < sorted.size(); ++i) {
+          int2& rg = range[sorted[i].slot];
+          if (rg.y == 0) rg.x = int(i);
+          rg.y += 1;
+          wv.insert(wv.end(), sorted[i].w.begin(), sorted[i].w.end());
+          rows.push_back(sorted[i].idx);
+        }
+        if (rows.empty()) {
+          rows.push_back(0);
+          wv.assign(Np_, real(0));
+        }
+        upload(w[1].inj_range, range, st_);
+        upload(w[1].inj_w, wv, st_);
+        upload(w[1].inj_row, rows, st_);
+        std::vector<int64_t> rslot(std::max<int64_t>(nrec, 1), 0);
+        std::vector<real> rrow(std::max<int64_t>(nrec, 1) * Np_, real(0));
+        for (int64_t r = 0; r < nrec; ++r) {
+          rslot[r] = recs[r].slot;
+          for (int m = 0; m < Np_; ++m) rrow[r * Np_ + m] = recs[r].row[m];
+        }
+        upload(*S[b].rec_slot, rslot, st_);
+        upload(*S[b].rec_row, rrow, st_);
+      }
     }
-    double* traces = traces_dev;
-    if (!traces) {
-      traces_tmp_.alloc(size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double));
-      traces = dptr<double>(traces_tmp_);
+    std::vector<double*> traces(n);
+    for (int b = 0; b < n; ++b) {
+      traces[b] = io[b].traces_out;
+      if (!traces[b]) {
+        S[b].traces_tmp->alloc(size_t(std::max<int64_t>(io[b].nrec, 1)) * n_t * sizeof(double));
+        traces[b] = dptr<double>(*S[b].traces_tmp);
+      }
     }
-    // ---- boundary-trace arena: one record per boundary face of every active element per step
+    // ---- boundary-trace arenas: one record per boundary face of every active element per step
     std::vector<int64_t> arena_base(tau_f + 2, 0);
     for (int64_t t = 0; t <= tau_f; ++t) arena_base[t + 1] = arena_base[t] + (n_bfaces_ - bface_first(slot_lo(t)));
     const size_t rec_bytes = 2 * NFPP_ * sizeof(real);
     size_t arena_bytes = size_t(arena_base[tau_f + 1]) * rec_bytes;
     if (fault_fires(kFaultArena))
       throw Error{RIDG_E_OOM, "boundary-trace arena of " + std::to_string(arena_bytes) + " bytes (injected failure)"};
-    // beyond the device budget the records go to pinned host memory in chunks (TraceTier)
+    // beyond the device budget the records go to pinned host memory in chunks (TraceTier; one shot)
     const bool tiered = tier_.plan(arena_base, rec_bytes, trace_budget_);
-    arena_.reserve(std::max<size_t>(tiered ? tier_.device_bytes() : arena_bytes, 16));
+    for (int b = 0; b < n; ++b) S[b].arena->reserve(std::max<size_t>(tiered ? tier_.device_bytes() : arena_bytes, 16));
     if (tiered && tier_.n_chunks() > 2) host_arena_.reserve(arena_bytes);
-    stats_.boundary_trace_bytes = int64_t(arena_bytes);
+    stats_.boundary_trace_bytes = int64_t(arena_bytes) * n;
     stats_.trace_chunks = tiered ? tier_.n_chunks() : 1;
     // device address and record offset of step t's records (the first record of its chunk at the start)
-    auto arena_at = [&](int64_t t, int sigma, int64_t slot_lo) {
-      char* base = static_cast<char*>(arena_.p);
+    auto arena_at = [&](int b, int64_t t, int sigma, int64_t slot_lo) {
+      char* base = static_cast<char*>(S[b].arena->p);
       int64_t first = 0;
       if (tiered) {
         const int k = tier_.chunk_of(t);
@@ -1197,34 +1268,48 @@ class Engine final : public ridg_solver {
       }
       return std::make_pair(reinterpret_cast<real*>(base), arena_base[t] - first - bface_first(slot_lo));
     };
-    q_snap_.alloc(qsize() * sizeof(real));
-    ring_snap_.alloc(3 * qsize() * sizeof(real));
-    img_p_.alloc(size_t(n_slots_) * Np_ * sizeof(double));
-    img_q_.alloc(size_t(n_slots_) * Np_ * sizeof(double));
+    for (int b = 0; b < n; ++b) {
+      S[b].q_snap->alloc(qsize() * sizeof(real));
+      S[b].ring_snap->alloc(3 * qsize() * sizeof(real));
+      S[b].img_p->alloc(size_t(n_slots_) * Np_ * sizeof(double));
+      S[b].img_q->alloc(size_t(n_slots_) * Np_ * sizeof(double));
+    }
+    BatchArgs<real> batch{};
+    const bool merged = n > 1;
 
-    // ---- forward source run
-    zero_wave(w_[0]);
+    // ---- forward source runs
+    for (int b = 0; b < n; ++b) zero_wave(S[b].w[0]);
     reset_time();
-    RIDG_CUDA(cudaMemsetAsync(traces, 0, size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double), st_));
-    sample(traces, n_t, 0, nrec);
+    for (int b = 0; b < n; ++b) {
+      RIDG_CUDA(cudaMemsetAsync(traces[b], 0, size_t(std::max<int64_t>(io[b].nrec, 1)) * n_t * sizeof(double), st_));
+      sample(S[b], traces[b], n_t, 0, io[b].nrec);
+    }
     auto forward_step = [&](int mode) {
       StepArgs<real> a = fine_args(+1, 1, mode);
-      a.wave[0] = wave_args(w_[0]);
-      a.wave[0].amp_mode = 1;
-      a.wave[0].amp = real(wav(double(tau_) * dtl));
-      std::tie(a.arena_write, a.arena_offset) = arena_at(std::min<int64_t>(tau_, tau_f), +1, a.slot_lo);
-      launch_fine(a, +1, 1);
+      const int64_t t_rec = std::min<int64_t>(tau_, tau_f);
+      for (int b = 0; b < n; ++b) {
+        ShotArgs<real>& sa = batch.shot[b];
+        sa = ShotArgs<real>{};
+        sa.wave[0] = wave_args(S[b].w[0]);
+        sa.wave[0].amp_mode = 1;
+        sa.wave[0].amp = real(wav[b](double(tau_) * dtl));
+        std::tie(sa.arena_write, a.arena_offset) = arena_at(b, t_rec, +1, a.slot_lo);
+      }
+      a.wave[0] = batch.shot[0].wave[0];
+      a.arena_write = batch.shot[0].arena_write;
+      launch_fine(a, +1, 1, merged ? &batch : nullptr, n);
     };
     if (tiered) tier_.begin_forward(st_);
     {
       NvtxRange nv("forward source run");
       for (int64_t g = 0; g < n_global; ++g) {
         for (int64_t s = 0; s < NL_; ++s) forward_step(kModeRecord);
-        sample(traces, n_t, g + 1, nrec);
+        for (int b = 0; b < n; ++b) sample(S[b], traces[b], n_t, g + 1, io[b].nrec);
       }
     }
     stats_.dof_updates_forward = dof_;
-    RIDG_CUDA(cudaMemcpyAsync(q_snap_.p, w_[0].q.p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
+    for (int b = 0; b < n; ++b)
+      RIDG_CUDA(cudaMemcpyAsync(S[b].q_snap->p, S[b].w[0].q.p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
     // two more global steps (and the first right-hand side of a third) give, per level l, the
     // right-hand sides at t_f + Delta t_l and t_f + 2 Delta t_l that start the backward run
     for (int64_t i = 0; i <= 2 * NL_; ++i) {
@@ -1233,48 +1318,50 @@ class Engine final : public ridg_solver {
       forward_step(t_now == tau_f ? kModeRecord : 0);
       for (int l = 1; l <= L_; ++l) {
         int64_t d = int64_t(1) << (L_ - l);
-        if (t_now == tau_f + 2 * d) snapshot_history(l, before[l - 1]);
+        if (t_now == tau_f + 2 * d)
+          for (int b = 0; b < n; ++b) snapshot_history(S[b], l, before[l - 1]);
       }
     }
     // ---- backward: source (replayed boundary) and receiver wavefields in lockstep
-    RIDG_CUDA(cudaMemcpyAsync(w_[0].q.p, q_snap_.p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
-    RIDG_CUDA(cudaMemcpyAsync(w_[0].ring.p, ring_snap_.p, 3 * qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
-    zero_wave(w_[1]);
-    RIDG_CUDA(cudaMemsetAsync(img_p_.p, 0, img_p_.bytes, st_));
-    RIDG_CUDA(cudaMemsetAsync(img_q_.p, 0, img_q_.bytes, st_));
+    for (int b = 0; b < n; ++b) {
+      RIDG_CUDA(cudaMemcpyAsync(S[b].w[0].q.p, S[b].q_snap->p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
+      RIDG_CUDA(cudaMemcpyAsync(S[b].w[0].ring.p, S[b].ring_snap->p, 3 * qsize() * sizeof(real),
+                                cudaMemcpyDeviceToDevice, st_));
+      zero_wave(S[b].w[1]);
+      RIDG_CUDA(cudaMemsetAsync(S[b].img_p->p, 0, S[b].img_p->bytes, st_));
+      RIDG_CUDA(cudaMemsetAsync(S[b].img_q->p, 0, S[b].img_q->bytes, st_));
+    }
     std::fill(ring_count_.begin(), ring_count_.end(), 0);
     tau_ = tau_f;
-    RIDG_CUDA(cudaMemsetAsync(w_[0].trace.p, 0, w_[0].trace.bytes, st_));
-    init_traces(w_[0], mod3(tau_));
+    for (int b = 0; b < n; ++b) {
+      RIDG_CUDA(cudaMemsetAsync(S[b].w[0].trace.p, 0, S[b].w[0].trace.bytes, st_));
+      init_traces(S[b].w[0], mod3(tau_));
+    }
     if (hook_) hook_->exchange(*this, 1, 1);
-    const double* data = obs_dev ? obs_dev : traces;
     // the receiver run injects the data times a power of two that brings max |data| into [1, 2), so
     // that the image products of small-amplitude shots stay inside the FP32 range; the images are
     // divided by it on the way out (both steps exact)
-    const double* dscale = nullptr;
-    const double* dscale_inv = nullptr;
-    if (nrec > 0) {
-      scale_d_.reserve(kDataScaleWorkBytes);
-      cudaError_t e = data_scale(data, nrec * n_t, scale_d_.p, st_);
-      if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("data scale: ") + cudaGetErrorString(e)};
-      if (hook_) hook_->combine_data_scale(*this, scale_d_.p);
-      stats_.kernel_launches += 2;
-      dscale = dptr<const double>(scale_d_) + 1;
-      dscale_inv = dptr<const double>(scale_d_) + 2;
+    std::vector<const double*> data(n), dscale(n, nullptr), dscale_inv(n, nullptr);
+    for (int b = 0; b < n; ++b) {
+      data[b] = io[b].observed ? io[b].observed : traces[b];
+      const int64_t nrec = io[b].nrec;
+      if (nrec > 0) {
+        S[b].scale->reserve(kDataScaleWorkBytes);
+        cudaError_t e = data_scale(data[b], nrec * n_t, S[b].scale->p, st_);
+        if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("data scale: ") + cudaGetErrorString(e)};
+        if (hook_) hook_->combine_data_scale(*this, S[b].scale->p);
+        stats_.kernel_launches += 2;
+        dscale[b] = dptr<const double>(*S[b].scale) + 1;
+        dscale_inv[b] = dptr<const double>(*S[b].scale) + 2;
+      }
     }
+    double eu[3] = {0.0, 0.0, -1.0};
+    if (e_up) std::memcpy(eu, e_up, sizeof(eu));
     int64_t dof_before = dof_;
     if (tiered) tier_.begin_backward(tau_i + 1);
     NvtxRange nv_back("backward source and receiver runs");
     while (tau_ > tau_i) {
       StepArgs<real> a = fine_args(-1, 2, kModeReplay | image_mode_);
-      a.wave[0] = wave_args(w_[0]);
-      a.wave[0].amp_mode = 1;
-      a.wave[0].amp = real(wav(double(tau_) * dtl));
-      a.wave[1] = wave_args(w_[1]);
-      a.wave[1].amp_mode = nrec > 0 ? 2 : 0;
-      a.wave[1].data = data;
-      a.wave[1].data_scale = dscale;
-      a.wave[1].n_time = int(n_t);
       int64_t n_lo = tau_ / NL_;
       double u = double(tau_ - n_lo * NL_) / double(NL_);
       a.interp_n0 = int(n_lo - 1);
@@ -1285,13 +1372,28 @@ class Engine final : public ridg_solver {
           if (j != i) li *= (u - xs[j]) / (xs[i] - xs[j]);
         a.interp_w[i] = li;
       }
-      std::tie(a.arena_read, a.arena_offset) = arena_at(tau_, -1, a.slot_lo);
-      a.image_p = dptr<double>(img_p_);
-      a.image_q = dptr<double>(img_q_);
-      double eu[3] = {0.0, 0.0, -1.0};
-      if (e_up) std::memcpy(eu, e_up, sizeof(eu));
       for (int d = 0; d < 3; ++d) a.e_up[d] = real(eu[d]);
-      launch_fine(a, -1, 2);
+      for (int b = 0; b < n; ++b) {
+        ShotArgs<real>& sa = batch.shot[b];
+        sa = ShotArgs<real>{};
+        sa.wave[0] = wave_args(S[b].w[0]);
+        sa.wave[0].amp_mode = 1;
+        sa.wave[0].amp = real(wav[b](double(tau_) * dtl));
+        sa.wave[1] = wave_args(S[b].w[1]);
+        sa.wave[1].amp_mode = io[b].nrec > 0 ? 2 : 0;
+        sa.wave[1].data = data[b];
+        sa.wave[1].data_scale = dscale[b];
+        sa.wave[1].n_time = int(n_t);
+        std::tie(sa.arena_read, a.arena_offset) = arena_at(b, tau_, -1, a.slot_lo);
+        sa.image_p = dptr<double>(*S[b].img_p);
+        sa.image_q = dptr<double>(*S[b].img_q);
+      }
+      a.wave[0] = batch.shot[0].wave[0];
+      a.wave[1] = batch.shot[0].wave[1];
+      a.arena_read = batch.shot[0].arena_read;
+      a.image_p = batch.shot[0].image_p;
+      a.image_q = batch.shot[0].image_q;
+      launch_fine(a, -1, 2, merged ? &batch : nullptr, n);
     }
     stats_.dof_updates_backward = dof_ - dof_before;
     if (tiered) {
@@ -1300,13 +1402,25 @@ class Engine final : public ridg_solver {
     } else {
       stats_.host_trace_bytes = 0;
     }
-    if (imgp_dev) image_out(dptr<double>(img_p_), dscale_inv, imgp_dev);
-    if (imgq_dev) image_out(dptr<double>(img_q_), dscale_inv, imgq_dev);
+    for (int b = 0; b < n; ++b) {
+      if (io[b].image_p) image_out(dptr<double>(*S[b].img_p), dscale_inv[b], io[b].image_p);
+      if (io[b].image_q) image_out(dptr<double>(*S[b].img_q), dscale_inv[b], io[b].image_q);
+    }
     RIDG_CUDA(cudaGetLastError());
   }
 
  private:
   // ------------------------------------------------------------------ helpers
+  // the device buffers of shot b of a batch
+  struct ShotRef {
+    Wave<real>* w;
+    DBuf *rec_slot, *rec_row, *traces_tmp, *arena, *q_snap, *ring_snap, *img_p, *img_q, *scale;
+  };
+  ShotRef shot_ref(int b) {
+    if (b == 0) return ShotRef{w_, &rec_slot_, &rec_row_, &traces_tmp_, &arena_, &q_snap_, &ring_snap_, &img_p_, &img_q_, &scale_d_};
+    ShotState& x = *extra_shots_[size_t(b - 1)];
+    return ShotRef{x.w, &x.rec_slot, &x.rec_row, &x.traces_tmp, &x.arena, &x.q_snap, &x.ring_snap, &x.img_p, &x.img_q, &x.scale};
+  }
   size_t qsize() const { return size_t(n_slots_) * 4 * Np_; }
   size_t trace_slot_elems() const { return size_t(n_slots_) * 8 * NFPP_; }
   size_t device_bytes() const {
@@ -1316,6 +1430,10 @@ class Engine final : public ridg_solver {
                          &afrag_d_, &gtab_d_[0], &gtab_d_[1]};
     for (auto* x : all) b += x->bytes;
     for (auto& w : w_) b += w.q.bytes + w.ring.bytes + w.trace.bytes;
+    for (const auto& x : extra_shots_) {
+      b += x->arena.bytes + x->q_snap.bytes + x->ring_snap.bytes + x->img_p.bytes + x->img_q.bytes;
+      for (const Wave<real>& w : x->w) b += w.q.bytes + w.ring.bytes + w.trace.bytes;
+    }
     return b;
   }
   int64_t bface_first(int64_t slot) const { return slot >= n_slots_ ? n_bfaces_ : bface_host_[slot]; }
@@ -1768,16 +1886,40 @@ class Engine final : public ridg_solver {
     return a;
   }
 
-  void launch(const StepArgs<real>& a0, int W) {
+  // batch != null: n shots in lockstep, one merged launch where the kernel supports it (FP32 tensor-core
+  // contractions), else one launch per shot with its arguments in the step's own
+  void launch(const StepArgs<real>& a0, int W, const BatchArgs<real>* batch = nullptr, int n = 1) {
     StepArgs<real> a = a0;
     a.gtab = dptr<const float>(gtab_d_[a.tau_sign > real(0) ? 0 : 1]);
-    cudaError_t e = dispatch_order(N_, [&](auto NC) { return Launch<decltype(NC)::value, real>::step(a, W, st_); });
-    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("step kernel launch: ") + cudaGetErrorString(e)};
-    ++stats_.kernel_launches;
-    ++stats_.fused_launches;
+    const bool merges = std::is_same<real, float>::value && contraction_ != RIDG_CONTRACT_CUDA_CORES;
+    auto one = [&](const StepArgs<real>& x, const BatchArgs<real>* bt) {
+      cudaError_t e = dispatch_order(N_, [&](auto NC) {
+        return Launch<decltype(NC)::value, real>::step(x, W, st_, bt, bt ? n : 1);
+      });
+      if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("step kernel launch: ") + cudaGetErrorString(e)};
+      ++stats_.kernel_launches;
+      ++stats_.fused_launches;
+    };
+    if (!batch) return one(a, nullptr);
+    if (merges) {
+      BatchArgs<real> bt = *batch;
+      bt.shot_blocks = int((a.slot_hi - a.slot_lo) / (32 / W));
+      return one(a, &bt);
+    }
+    for (int b = 0; b < n; ++b) {
+      StepArgs<real> x = a;
+      const ShotArgs<real>& sa = batch->shot[b];
+      x.wave[0] = sa.wave[0];
+      x.wave[1] = sa.wave[1];
+      x.arena_write = sa.arena_write;
+      x.arena_read = sa.arena_read;
+      x.image_p = sa.image_p;
+      x.image_q = sa.image_q;
+      one(x, nullptr);
+    }
   }
 
-  void launch_fine(const StepArgs<real>& a, int sigma, int W) {
+  void launch_fine(const StepArgs<real>& a, int sigma, int W, const BatchArgs<real>* batch = nullptr, int n = 1) {
     int l0 = first_active_level(tau_);
     static const char* const kStepNames[kMaxLevels] = {
         "fine step, levels 1+", "fine step, levels 2+", "fine step, levels 3+", "fine step, levels 4+",
@@ -1796,7 +1938,7 @@ class Engine final : public ridg_solver {
       prof_w_[prof_used_] = W;
       RIDG_CUDA(cudaEventRecord(prof_ev_[2 * prof_used_], st_));
     }
-    launch(a, W);
+    launch(a, W, batch, n);
     if (prof) {
       RIDG_CUDA(cudaEventRecord(prof_ev_[2 * prof_used_ + 1], st_));
       ++prof_used_;
@@ -1804,7 +1946,7 @@ class Engine final : public ridg_solver {
     if (hook_) hook_->exchange(*this, l0, W == 2 ? 3 : 1);
     for (int l = l0; l <= L_; ++l) {
       ring_count_[l - 1] += 1;
-      dof_ += level_count_[l - 1] * 4 * Np_ * W;
+      dof_ += level_count_[l - 1] * 4 * Np_ * W * (batch ? n : 1);
     }
     tau_ += sigma;
   }
@@ -1820,17 +1962,19 @@ class Engine final : public ridg_solver {
   }
   void init_traces(Wave<real>& w, int slot) { init_traces_into(dptr<real>(w.q), dptr<real>(w.trace), slot); }
 
-  void sample(double* traces, int64_t n_t, int64_t col, int64_t nrec) {
+  void sample(double* traces, int64_t n_t, int64_t col, int64_t nrec) { sample(shot_ref(0), traces, n_t, col, nrec); }
+  // receiver traces of shot S's source wavefield at column col
+  void sample(const ShotRef& S, double* traces, int64_t n_t, int64_t col, int64_t nrec) {
     if (nrec <= 0) return;
     cudaError_t e = dispatch_order(N_, [&](auto NC) {
-      return Launch<decltype(NC)::value, real>::sample(dptr<real>(w_[0].q), dptr<const int64_t>(rec_slot_),
-                                                        dptr<const real>(rec_row_), int(nrec), traces, n_t, col, st_);
+      return Launch<decltype(NC)::value, real>::sample(dptr<real>(S.w[0].q), dptr<const int64_t>(*S.rec_slot),
+                                                        dptr<const real>(*S.rec_row), int(nrec), traces, n_t, col, st_);
     });
     if (e != cudaSuccess) throw Error{RIDG_E_CUDA, cudaGetErrorString(e)};
     ++stats_.kernel_launches;
   }
 
-  void snapshot_history(int l, int count_before) {
+  void snapshot_history(const ShotRef& S, int l, int count_before) {
     // the step that just ran wrote r(t_f + 2 dt_l) into ring slot count_before % 3; the one before
     // it, r(t_f + dt_l), sits in (count_before + 2) % 3.  The backward run starts with counter 0,
     // whose older slots are 2 (one step back: t_f + dt_l) and 1 (two steps back: t_f + 2 dt_l).
@@ -1838,8 +1982,8 @@ class Engine final : public ridg_solver {
     size_t off = size_t(ord_.level_begin[l - 1] / 32) * per;
     size_t len = size_t((ord_.level_begin[l] - ord_.level_begin[l - 1]) / 32) * per * sizeof(real);
     if (len == 0) return;
-    const char* ring = static_cast<const char*>(w_[0].ring.p);
-    char* snap = static_cast<char*>(ring_snap_.p);
+    const char* ring = static_cast<const char*>(S.w[0].ring.p);
+    char* snap = static_cast<char*>(S.ring_snap->p);
     size_t qb = qsize() * sizeof(real);
     int newest = count_before % 3, prev = (count_before + 2) % 3;
     RIDG_CUDA(cudaMemcpyAsync(snap + 1 * qb + off * sizeof(real), ring + newest * qb + off * sizeof(real), len,
@@ -1915,6 +2059,12 @@ class Engine final : public ridg_solver {
   size_t trace_budget_ = 0;  // device bytes for boundary-trace records (0: no limit)
   TraceTier tier_;           // after the buffers it copies between: destroyed (and drained) first
   Wave<real> w_[2];
+  // device state of shots 1.. of a merged batch (shot 0 uses the buffers above)
+  struct ShotState {
+    Wave<real> w[2];
+    DBuf rec_slot, rec_row, traces_tmp, arena, q_snap, ring_snap, img_p, img_q, scale;
+  };
+  std::vector<std::unique_ptr<ShotState>> extra_shots_;
   int64_t tau_ = 0, dof_ = 0;
   std::vector<int> ring_count_;
   ridg_shot_stats stats_{};
@@ -2322,6 +2472,50 @@ static void run_host_shot(ridg_solver* s, const ridg_source& src, const double* 
       if (!std::isfinite(image_p[i])) throw Error{RIDG_E_UNSTABLE, "non-finite image value"};
 }
 
+// n shots in lockstep with host buffers: the observed traces of each in, the batch on the solver's
+// stream, every shot's traces and images out, then one wait.
+static void run_host_shots(ridg_solver* s, int32_t n, const ridg_shot_io* io, double t_final, double t_image_start,
+                           const double* e_up, HostShotBuffers* b) {
+  if (n < 1 || n > kMaxBatch || !io) throw Error{RIDG_E_INVALID_ARG, "a batch holds 1 to " + std::to_string(kMaxBatch) + " shots"};
+  ridg_info inf;
+  s->info(&inf);
+  const int64_t n_t = s->trace_len(t_final);
+  const size_t ib = size_t(inf.K) * inf.Np * sizeof(double);
+  cudaStream_t st = s->stream();
+  std::vector<ridg_shot_io> dev(io, io + n);
+  for (int i = 0; i < n; ++i) {
+    const int64_t nrec = io[i].nrec;
+    if (nrec < 0) throw Error{RIDG_E_INVALID_ARG, "bad receiver list of shot " + std::to_string(i)};
+    const size_t tb = size_t(std::max<int64_t>(nrec, 1)) * n_t * sizeof(double);
+    if (io[i].observed) {
+      b[i].obs.reserve(tb);
+      RIDG_CUDA(cudaMemcpyAsync(b[i].obs.p, io[i].observed, size_t(nrec) * n_t * sizeof(double), cudaMemcpyHostToDevice, st));
+      dev[i].observed = dptr<double>(b[i].obs);
+    }
+    b[i].tr.reserve(tb);
+    dev[i].traces_out = dptr<double>(b[i].tr);
+    if (io[i].image_p) b[i].ip.reserve(ib);
+    if (io[i].image_q) b[i].iq.reserve(ib);
+    dev[i].image_p = io[i].image_p ? dptr<double>(b[i].ip) : nullptr;
+    dev[i].image_q = io[i].image_q ? dptr<double>(b[i].iq) : nullptr;
+  }
+  s->shots(n, dev.data(), t_final, t_image_start, e_up);
+  for (int i = 0; i < n; ++i) {
+    const int64_t nrec = io[i].nrec;
+    if (io[i].traces_out && nrec > 0)
+      RIDG_CUDA(cudaMemcpyAsync(io[i].traces_out, b[i].tr.p, size_t(nrec) * n_t * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (io[i].image_p) RIDG_CUDA(cudaMemcpyAsync(io[i].image_p, b[i].ip.p, ib, cudaMemcpyDeviceToHost, st));
+    if (io[i].image_q) RIDG_CUDA(cudaMemcpyAsync(io[i].image_q, b[i].iq.p, ib, cudaMemcpyDeviceToHost, st));
+  }
+  RIDG_CUDA(cudaStreamSynchronize(st));
+  for (int i = 0; i < n; ++i)
+    if (io[i].image_p)
+      for (size_t k = 0; k < ib / sizeof(double); ++k)
+        if (!std::isfinite(io[i].image_p[k])) throw Error{RIDG_E_UNSTABLE, "non-finite image value"};
+}
+
+static_assert(kMaxBatch == RIDG_MAX_BATCH, "the merged launch holds as many shots as the ABI allows");
+
 }  // namespace ridg
 
 // Shot server: requests queued in arrival order, served by slots (one solver and one worker thread
@@ -2343,11 +2537,12 @@ struct ridg_server {
     bool busy = false;     // running a request, or its buffers being released
     bool waiting = false;  // its request waits for device memory (counts as not running)
     std::thread worker;
-    ridg::HostShotBuffers buffers;
+    ridg::HostShotBuffers buffers[ridg::kMaxBatch];  // one per shot of a lockstep batch
   };
   std::vector<std::unique_ptr<Slot>> slots;
   int device = 0;
   int64_t max_queued = 1;
+  int32_t max_batch = 1;  // waiting requests a slot starts together as one lockstep batch
   clock::time_point created = clock::now();
   std::mutex mu;
   std::condition_variable work_cv, done_cv;
@@ -2372,7 +2567,7 @@ struct ridg_server {
 
   // Device memory for the shot slot s is about to run: free it from idle slots, or wait for
   // running ones, or give up with RIDG_E_OOM.
-  void admit(Slot* s, const Request* q) {
+  void admit(Slot* s, const Request* q, int32_t n_shots) {
     const size_t margin = size_t(256) << 20;
     struct Done {
       ridg_server* sv;
@@ -2386,7 +2581,7 @@ struct ridg_server {
       }
     } done{this, s};
     for (;;) {
-      const size_t need = s->solver->shot_extra_device_bytes(q->r.t_final);
+      const size_t need = s->solver->shots_extra_device_bytes(q->r.t_final, n_shots);
       if (ridg::fault_fires(ridg::kFaultAdmission))
         throw Error{RIDG_E_OOM, "shot needs " + std::to_string(need) + " more device bytes (injected admission refusal)"};
       size_t free_b = 0, total_b = 0;
@@ -2413,18 +2608,20 @@ struct ridg_server {
       size_t released = 0;
       for (Slot* o : idle) {
         released += o->solver->release_shot_buffers();
-        for (ridg::DBuf* d : {&o->buffers.obs, &o->buffers.tr, &o->buffers.ip, &o->buffers.iq}) {
-          released += d->bytes;
-          d->release();
-        }
+        for (ridg::HostShotBuffers& hb : o->buffers)
+          for (ridg::DBuf* d : {&hb.obs, &hb.tr, &hb.ip, &hb.iq}) {
+            released += d->bytes;
+            d->release();
+          }
       }
       released += [&] {
         // this slot's own host-shot buffers are re-reserved by the shot
         size_t b = 0;
-        for (ridg::DBuf* d : {&s->buffers.obs, &s->buffers.tr, &s->buffers.ip, &s->buffers.iq}) {
-          b += d->bytes;
-          d->release();
-        }
+        for (ridg::HostShotBuffers& hb : s->buffers)
+          for (ridg::DBuf* d : {&hb.obs, &hb.tr, &hb.ip, &hb.iq}) {
+            b += d->bytes;
+            d->release();
+          }
         return b;
       }();
       {
@@ -2440,30 +2637,63 @@ struct ridg_server {
     }
   }
 
+  // a waiting request r may join q's lockstep batch: same record length, image window and e_up
+  static bool joins(const Request* q, const Request* r) {
+    return r->r.model == q->r.model && r->r.t_final == q->r.t_final && r->r.t_image_start == q->r.t_image_start &&
+           r->eup == q->eup;
+  }
+
   void run(Slot* s, int64_t index) {
     cudaSetDevice(device);
     for (;;) {
-      Request* q = nullptr;
+      std::vector<Request*> batch;
       {
         std::unique_lock<std::mutex> lk(mu);
         work_cv.wait(lk, [&] { return stop || (!memory_wait && !s->busy && next_of(s->model) != queue.end()); });
         if (stop) return;
         auto it = next_of(s->model);
-        q = requests[*it].get();
+        batch.push_back(requests[*it].get());
         queue.erase(it);
+        // later requests of the model that share the time span join it, up to max_batch shots
+        for (auto jt = queue.begin(); jt != queue.end() && int32_t(batch.size()) < max_batch;) {
+          Request* r = requests[*jt].get();
+          if (joins(batch[0], r)) {
+            batch.push_back(r);
+            jt = queue.erase(jt);
+          } else {
+            ++jt;
+          }
+        }
         s->busy = true;
-        q->started = clock::now();
-        q->slot = index;
+        const auto now = clock::now();
+        for (Request* r : batch) {
+          r->started = now;
+          r->slot = index;
+        }
       }
+      Request* q = batch[0];
+      const int32_t n = int32_t(batch.size());
       int status = RIDG_OK;
       std::string error;
       try {
-        admit(s, q);
+        admit(s, q, n);
         work_cv.notify_all();
-        ridg::run_host_shot(s->solver, q->r.source, q->rec.empty() ? nullptr : q->rec.data(), q->r.nrec,
-                            q->r.t_final, q->r.t_image_start, q->obs.empty() ? nullptr : q->obs.data(),
-                            q->r.traces_out, q->r.image_p, q->r.image_q, q->eup.empty() ? nullptr : q->eup.data(),
-                            s->buffers);
+        if (n == 1) {
+          ridg::run_host_shot(s->solver, q->r.source, q->rec.empty() ? nullptr : q->rec.data(), q->r.nrec,
+                              q->r.t_final, q->r.t_image_start, q->obs.empty() ? nullptr : q->obs.data(),
+                              q->r.traces_out, q->r.image_p, q->r.image_q, q->eup.empty() ? nullptr : q->eup.data(),
+                              s->buffers[0]);
+        } else {
+          std::vector<ridg_shot_io> io(static_cast<size_t>(n));
+          for (int32_t i = 0; i < n; ++i) {
+            const Request* r = batch[size_t(i)];
+            io[size_t(i)] = ridg_shot_io{r->r.source, r->rec.empty() ? nullptr : r->rec.data(), r->r.nrec,
+                                         r->obs.empty() ? nullptr : r->obs.data(), r->r.traces_out, r->r.image_p,
+                                         r->r.image_q};
+          }
+          ridg::run_host_shots(s->solver, n, io.data(), q->r.t_final, q->r.t_image_start,
+                               q->eup.empty() ? nullptr : q->eup.data(), s->buffers);
+        }
       } catch (const Error& e) {
         status = e.code;
         error = e.msg;
@@ -2476,12 +2706,15 @@ struct ridg_server {
       }
       {
         std::lock_guard<std::mutex> lk(mu);
-        q->status = status;
-        q->error = error;
-        q->finished = clock::now();
-        q->done = true;
+        const auto now = clock::now();
+        for (Request* r : batch) {
+          r->status = status;
+          r->error = error;
+          r->finished = now;
+          r->done = true;
+        }
         s->busy = false;
-        ++finished_shots;
+        finished_shots += n;
       }
       done_cv.notify_all();
       work_cv.notify_all();
@@ -2686,6 +2919,27 @@ int ridg_rtm_shot(ridg_solver* s, const ridg_source* src, const double* rec_xyz,
   });
 }
 
+int ridg_rtm_shots_device(ridg_solver* s, int32_t n_shots, const ridg_shot_io* shots, double t_final,
+                          double t_image_start, const double* e_up) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (n_shots < 1 || n_shots > RIDG_MAX_BATCH || !shots)
+      throw Error{RIDG_E_INVALID_ARG, "n_shots must be in 1.." + std::to_string(RIDG_MAX_BATCH)};
+    s->shots(n_shots, shots, t_final, t_image_start, e_up);
+  });
+}
+
+int ridg_rtm_shots(ridg_solver* s, int32_t n_shots, const ridg_shot_io* shots, double t_final, double t_image_start,
+                   const double* e_up) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    if (n_shots < 1 || n_shots > RIDG_MAX_BATCH || !shots)
+      throw Error{RIDG_E_INVALID_ARG, "n_shots must be in 1.." + std::to_string(RIDG_MAX_BATCH)};
+    std::vector<ridg::HostShotBuffers> b(static_cast<size_t>(n_shots));
+    ridg::run_host_shots(s, n_shots, shots, t_final, t_image_start, e_up, b.data());
+  });
+}
+
 int ridg_last_shot_stats(const ridg_solver* s, ridg_shot_stats* stats) {
   return guarded([&] {
     RIDG_NEED(s);
@@ -2837,6 +3091,19 @@ int ridg_server_submit(ridg_server* sv, const ridg_shot_request* req, int64_t* t
       sv->requests[t] = std::move(q);
       sv->queue.push_back(t);
       *ticket = t;
+    }
+    sv->work_cv.notify_all();
+  });
+}
+
+int ridg_server_set_batch(ridg_server* sv, int32_t max_batch) {
+  return guarded([&] {
+    if (!sv) throw Error{RIDG_E_INVALID_ARG, "server handle is null"};
+    if (max_batch < 1 || max_batch > RIDG_MAX_BATCH)
+      throw Error{RIDG_E_INVALID_ARG, "max_batch must be in 1.." + std::to_string(RIDG_MAX_BATCH)};
+    {
+      std::lock_guard<std::mutex> lk(sv->mu);
+      sv->max_batch = max_batch;
     }
     sv->work_cv.notify_all();
   });

@@ -119,6 +119,28 @@ struct StepArgs {
   int contraction;       // FP32 element products: RIDG_CONTRACT_TENSOR / _CUDA_CORES / _TENSOR_BF16
 };
 
+// Merged launch of several shots of one solver (same mesh, tables and fine-step schedule, run in
+// lockstep; the serving form): blocks [b * shot_blocks, (b + 1) * shot_blocks) step shot b, whose
+// wavefields, boundary-record arena and images are shot[b]; everything else is the step's StepArgs.
+constexpr int kMaxBatch = 4;
+template <typename real>
+struct ShotArgs {
+  WaveArgs<real> wave[2];
+  real* arena_write;
+  const real* arena_read;
+  double* image_p;
+  double* image_q;
+};
+template <typename real>
+struct BatchArgs {
+  int shot_blocks;  // blocks of one shot in this launch
+  ShotArgs<real> shot[kMaxBatch];
+};
+// the merged-launch argument of a kernel built for one shot: nothing
+struct NoBatch {
+  int unused;
+};
+
 template <int N>
 struct Order {
   static constexpr int Np = (N + 1) * (N + 2) * (N + 3) / 6;

@@ -21,6 +21,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "step_kernel.cuh"
 
 namespace ridg {
@@ -187,8 +189,10 @@ struct SmemTc {
   static_assert(4 * Np * CS <= 2 * ST + UX, "right-hand-side staging must fit in the penalty/U region");
 };
 
-template <int N, int W, int KIND>
-__global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kernel_tc(const StepArgs<float> A) {
+// BATCH: a merged launch of several shots (BatchArgs); otherwise one shot (B unused)
+template <int N, int W, int KIND, bool BATCH = false>
+__global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB)
+    dg_step_kernel_tc(const StepArgs<float> A, const std::conditional_t<BATCH, BatchArgs<float>, NoBatch> B) {
   using O = Order<N>;
   using T = TcOrder<N, KIND>;
   constexpr int KS = T::KS;
@@ -237,7 +241,50 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
   float* sRhs = sS;  // [4][Np][CS] right-hand sides after the products, then the half-step fields
 
   const int tid = threadIdx.x;
-  const int64_t slot0 = A.slot_lo + int64_t(blockIdx.x) * EPB;
+  // merged launch: this block's shot, whose per-shot arguments are staged in shared memory
+  __shared__ std::conditional_t<BATCH, ShotArgs<float>, int> sShot;
+  int64_t bidx = blockIdx.x;
+  if constexpr (BATCH) {
+    const int shot = int(blockIdx.x / unsigned(B.shot_blocks));
+    bidx -= int64_t(shot) * B.shot_blocks;
+    if (tid == 0) {
+#pragma unroll
+      for (int b = 0; b < kMaxBatch; ++b)
+        if (b == shot) sShot = B.shot[b];
+    }
+    __syncthreads();
+  }
+  auto WV = [&](int w) -> const WaveArgs<float>& {
+    if constexpr (BATCH)
+      return sShot.wave[w];
+    else
+      return A.wave[w];
+  };
+  float* const arena_write = [&] {
+    if constexpr (BATCH)
+      return sShot.arena_write;
+    else
+      return A.arena_write;
+  }();
+  const float* const arena_read = [&] {
+    if constexpr (BATCH)
+      return sShot.arena_read;
+    else
+      return A.arena_read;
+  }();
+  double* const image_p = [&] {
+    if constexpr (BATCH)
+      return sShot.image_p;
+    else
+      return A.image_p;
+  }();
+  double* const image_q = [&] {
+    if constexpr (BATCH)
+      return sShot.image_q;
+    else
+      return A.image_q;
+  }();
+  const int64_t slot0 = A.slot_lo + bidx * EPB;
   if (slot0 >= A.slot_hi) return;
   const int64_t blk = slot0 >> 5;
   const int lane0 = int(slot0 & 31);
@@ -278,8 +325,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     copy_bytes(sPerm, A.perm, 192 * 4);
 #pragma unroll
     for (int w = 0; w < 2; ++w) {
-      if (w < W && A.wave[w].amp_mode != 0) {
-        copy_bytes(sInj + w * EPB, A.wave[w].inj_range + slot0, EPB * 8);
+      if (w < W && WV(w).amp_mode != 0) {
+        copy_bytes(sInj + w * EPB, WV(w).inj_range + slot0, EPB * 8);
       } else {
         for (int i = tid; i < EPB; i += NT) sInj[w * EPB + i] = make_int2(0, 0);
       }
@@ -293,19 +340,19 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
     for (int i = tid; i < PER; i += NT) {
       const int row = i >> 3, sub = i & 7;  // sub = w * CPR + ch
       const int w = sub / CPR, ch = sub - w * CPR;
-      cp_async_bytes16(sQ + row * CS + sub * 4, A.wave[w].q + fbase + row * 32 + ch * 4);
+      cp_async_bytes16(sQ + row * CS + sub * 4, WV(w).q + fbase + row * 32 + ch * 4);
     }
     constexpr int CHW = EPB * 8 * NFPP / 4;  // 16-byte chunks of one wavefield's inboxes
     for (int i = tid; i < W * CHW; i += NT) {
       const int w = i / CHW, ch = i - w * CHW;
       cp_async_bytes16(sX + w * (EPB * 8 * NFPP) + ch * 4,
-                       A.wave[w].trace + (int64_t(A.trace_read) * A.n_slots + slot0) * (8 * NFPP) + ch * 4);
+                       WV(w).trace + (int64_t(A.trace_read) * A.n_slots + slot0) * (8 * NFPP) + ch * 4);
     }
     cp_async_commit();
     // the history slices this block reads from global memory in the update: into L2 now
     if (!RING && !rhs_only && tid < 2 * W) {
       const int w = tid >> 1, ring = (tid & 1) ? r2i : r1i;
-      const float* src = A.wave[w].ring + ring * qsize + blk * 4 * Np * 32;
+      const float* src = WV(w).ring + ring * qsize + blk * 4 * Np * 32;
       asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(src), "r"(4 * Np * 32 * 4) : "memory");
     }
   }
@@ -328,7 +375,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
         int b = sBf[e];
         for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
         cp_async_bytes16(sX + e * (8 * NFPP) + f * 2 * NFPP + ch * 4,
-                         A.arena_read + (A.arena_offset + b) * (2 * NFPP) + ch * 4);
+                         arena_read + (A.arena_offset + b) * (2 * NFPP) + ch * 4);
       }
     }
   }
@@ -342,7 +389,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       for (int i = tid; i < PER; i += NT) {
         const int row = i >> 3, sub = i & 7;
         const int w = sub / CPR, ch = sub - w * CPR;
-        cp_async_bytes16(dbase + row * CS + sub * 4, A.wave[w].ring + ring * qsize + fbase + row * 32 + ch * 4);
+        cp_async_bytes16(dbase + row * CS + sub * 4, WV(w).ring + ring * qsize + fbase + row * 32 + ch * 4);
       }
     }
   }
@@ -352,7 +399,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       const int im = i / (Np * CPN), rem = i - im * Np * CPN;
       if (!(A.mode & (im == 0 ? kModeImageP : kModeImageQ))) continue;
       const int n = rem / CPN, ch = rem - n * CPN;
-      const double* src = (im == 0 ? A.image_p : A.image_q) + (blk * Np + n) * 32 + lane0 + ch * 2;
+      const double* src = (im == 0 ? image_p : image_q) + (blk * Np + n) * 32 + lane0 + ch * 2;
       cp_async_bytes16(sImg + (im * Np + n) * EPB + ch * 2, src);
     }
   }
@@ -432,7 +479,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
         const int e = col_e(c);
         int b = sBf[e];
         for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
-        rec = A.arena_write + (A.arena_offset + b) * (2 * NFPP);
+        rec = arena_write + (A.arena_offset + b) * (2 * NFPP);
       }
 #pragma unroll
       for (int t = 0; t < NJ; ++t) {
@@ -714,7 +761,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
         q0[w][fld] = sQ[sidx];
       }
       // point injections (source wavelet or receiver traces)
-      const WaveArgs<float>& wa = A.wave[w];
+      const WaveArgs<float>& wa = WV(w);
       const int2 ir = sInj[w * EPB + e];
       if (ir.y > 0 && ok) {
         for (int qq = ir.x; qq < ir.x + ir.y; ++qq) {
@@ -750,8 +797,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
           r1[w][fld] = sR1[sidx];
           r2[w][fld] = sR2[sidx];
         } else {
-          r1[w][fld] = A.wave[w].ring[r1i * qsize + gofs + fld * Np * 32];
-          r2[w][fld] = A.wave[w].ring[r2i * qsize + gofs + fld * Np * 32];
+          r1[w][fld] = WV(w).ring[r1i * qsize + gofs + fld * Np * 32];
+          r2[w][fld] = WV(w).ring[r2i * qsize + gofs + fld * Np * 32];
         }
       }
     // images from the fields and histories at t_start, before the update
@@ -785,13 +832,13 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       const float incP = h * (xS * xR + h * (t2p + h * t3p));
       const float incQ = h * (qS * qR + h * (t2q + h * t3q));
       const int64_t io = (blk * Np + n) * 32 + lane0 + e;
-      if (A.mode & kModeImageP) A.image_p[io] = sImg[(0 * Np + n) * EPB + e] - double(incP);
-      if (A.mode & kModeImageQ) A.image_q[io] = sImg[(1 * Np + n) * EPB + e] - double(incQ);
+      if (A.mode & kModeImageP) image_p[io] = sImg[(0 * Np + n) * EPB + e] - double(incP);
+      if (A.mode & kModeImageQ) image_q[io] = sImg[(1 * Np + n) * EPB + e] - double(incQ);
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) {
-      float* qg = A.wave[w].q + gofs;
-      float* rg = A.wave[w].ring + rn * qsize + gofs;
+      float* qg = WV(w).q + gofs;
+      float* rg = WV(w).ring + rn * qsize + gofs;
 #pragma unroll
       for (int fld = 0; fld < 4; ++fld) {
         const float rr = r[w][fld];
@@ -832,8 +879,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB) dg_step_kern
       const int64_t s2 = sNbr[e * 4 + f];
       const int* pm = sPerm + finfo_perm(uint8_t(info)) * 32;
       const int64_t fo = s2 * (8 * NFPP) + finfo_face(uint8_t(info)) * 2 * NFPP;
-      float* tw = A.wave[w].trace + int64_t(ws) * A.n_slots * (8 * NFPP) + fo;
-      float* th = A.wave[w].trace + int64_t(hs) * A.n_slots * (8 * NFPP) + fo;
+      float* tw = WV(w).trace + int64_t(ws) * A.n_slots * (8 * NFPP) + fo;
+      float* th = WV(w).trace + int64_t(hs) * A.n_slots * (8 * NFPP) + fo;
       for (int jj = j; jj < Nfp; jj += 16) {
         const int n = sFm[f * 32 + jj];
         const int j2 = pm[jj];

@@ -26,6 +26,7 @@ EXPORTED = [
     "ridg_last_error", "ridg_version", "ridg_mesh_create", "ridg_mesh_destroy", "ridg_mesh_counts",
     "ridg_reference_operators", "ridg_solver_create", "ridg_solver_destroy", "ridg_solver_info",
     "ridg_solver_levels", "ridg_solver_nodes", "ridg_set_state", "ridg_set_history", "ridg_eval_rhs", "ridg_step",
+    "ridg_rtm_shots", "ridg_rtm_shots_device", "ridg_server_set_batch",
     "ridg_get_state", "ridg_energy", "ridg_trace_len", "ridg_rtm_shot", "ridg_rtm_shot_device",
     "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc", "ridg_server_create", "ridg_server_create_slots", "ridg_server_submit",
     "ridg_server_wait", "ridg_server_destroy", "ridg_forward", "ridg_set_state_device", "ridg_get_state_device",
@@ -72,6 +73,14 @@ def _source(source_xyz, f0, t_peak, amplitude, wavelet=None, wavelet_dt=None):
     w = _f64(wavelet).reshape(-1)
     return Source((C.c_double * 3)(*source_xyz), 0.0, 0.0, amplitude, SRC_SAMPLED, 0, float(wavelet_dt), w.size,
                   _ptr(w)), w
+
+
+class ShotIO(C.Structure):
+    _fields_ = [("source", Source), ("rec_xyz", C.c_void_p), ("nrec", C.c_int64), ("observed", C.c_void_p),
+                ("traces_out", C.c_void_p), ("image_p", C.c_void_p), ("image_q", C.c_void_p)]
+
+
+MAX_BATCH = 4  # RIDG_MAX_BATCH: shots of one lockstep batch
 
 
 class ShotStats(C.Structure):
@@ -127,6 +136,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_trace_len": (C.c_int64, [P, C.c_double]),
         "ridg_rtm_shot": (C.c_int, [P, P, P, C.c_int64, C.c_double, C.c_double, P, P, P, P, P]),
         "ridg_rtm_shot_device": (C.c_int, [P, P, P, C.c_int64, C.c_double, C.c_double, P, P, P, P, P]),
+        "ridg_rtm_shots": (C.c_int, [P, C.c_int32, P, C.c_double, C.c_double, P]),
+        "ridg_rtm_shots_device": (C.c_int, [P, C.c_int32, P, C.c_double, C.c_double, P]),
         "ridg_last_shot_stats": (C.c_int, [P, P]),
         "ridg_set_profiling": (C.c_int, [P, C.c_int32]),
         "ridg_set_trace_budget": (C.c_int, [P, C.c_int64]),
@@ -144,6 +155,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_server_submit": (C.c_int, [P, P, C.POINTER(C.c_int64)]),
         "ridg_server_wait": (C.c_int, [P, C.c_int64, C.c_double, P]),
         "ridg_server_destroy": (C.c_int, [P]),
+        "ridg_server_set_batch": (C.c_int, [P, C.c_int32]),
         "ridg_partition": (C.c_int, [P, C.c_int, P, P, C.c_int32, P]),
         "ridg_group_create": (C.c_int, [P, C.c_int, P, P, P, P, C.c_int32, P, C.POINTER(P)]),
         "ridg_group_rtm_shot": (C.c_int, [P, P, P, C.c_int64, C.c_double, C.c_double, P, P, P, P, P]),
@@ -379,6 +391,46 @@ class Solver:
                                           float(t_image_start), _ptr(observed), _ptr(traces), _ptr(image_p),
                                           _ptr(image_q), _ptr(eu)))
 
+    def _shot_ios(self, shots, host, t_final, want_images=True):
+        """ShotIO array (and the arrays it points to) of a lockstep batch; host: numpy outputs."""
+        n = len(shots)
+        ios = (ShotIO * max(n, 1))()  # the library rejects n outside 1 .. MAX_BATCH
+        keep, outs = [], []
+        n_t = self.trace_len(t_final)
+        for i, sh in enumerate(shots):
+            src, w = _source(sh["source_xyz"], sh.get("f0", 10.0), sh.get("t_peak", 0.0), sh.get("amplitude", 1.0),
+                             sh.get("wavelet"), sh.get("wavelet_dt"))
+            rx = sh.get("rec_xyz", ())
+            rec = _f64(np.atleast_2d(rx)) if len(rx) else np.zeros((0, 3))
+            keep += [w, rec]
+            if host:
+                obs = None if sh.get("observed") is None else _f64(sh["observed"], (rec.shape[0], n_t))
+                tr = np.zeros((rec.shape[0], n_t))
+                ip = np.zeros((self.K, self.Np)) if want_images else None
+                iq = np.zeros((self.K, self.Np)) if want_images else None
+                keep.append(obs)
+                outs.append((tr, ip, iq))
+            else:
+                obs, tr, ip, iq = sh.get("observed"), sh.get("traces"), sh.get("image_p"), sh.get("image_q")
+            ios[i] = ShotIO(src, _ptr(rec), rec.shape[0], _ptr(obs), _ptr(tr), _ptr(ip), _ptr(iq))
+        return ios, keep, outs
+
+    def rtm_shots(self, shots, t_final, t_image_start=0.0, e_up=(0.0, 0.0, -1.0), want_images=True):
+        """Several shots of this model in lockstep, one merged launch per fine step (ridg_rtm_shots).
+        ``shots``: dicts with the arguments of rtm_shot (source_xyz, f0, t_peak, amplitude, rec_xyz,
+        observed, wavelet, wavelet_dt); returns [(traces, image_p, image_q)] in their order."""
+        ios, _keep, outs = self._shot_ios(shots, True, t_final, want_images)
+        eu = _f64(e_up)
+        _check(lib().ridg_rtm_shots(self._h, len(shots), ios, float(t_final), float(t_image_start), _ptr(eu)))
+        return outs
+
+    def rtm_shots_device(self, shots, t_final, t_image_start=0.0, e_up=(0.0, 0.0, -1.0)):
+        """Device-buffer batch (ridg_rtm_shots_device): each dict may hold torch CUDA float64 tensors
+        observed, traces, image_p, image_q; returns after enqueueing."""
+        ios, _keep, _ = self._shot_ios(shots, False, t_final)
+        eu = _f64(e_up)
+        _check(lib().ridg_rtm_shots_device(self._h, len(shots), ios, float(t_final), float(t_image_start), _ptr(eu)))
+
     def set_profiling(self, every: int):
         _check(lib().ridg_set_profiling(self._h, int(every)))
 
@@ -469,10 +521,11 @@ class Server:
     """Shot server (``ridg_server_*``) over one solver or several slots.  ``solvers`` is a Solver or a
     list of them; ``models[i]`` is the model number of ``solvers[i]`` (default: all 0).  An idle slot
     takes the oldest waiting request of its model, so shots on different slots run concurrently
-    (give those solvers different CUDA streams).  The solvers must not be used directly while the
-    server exists."""
+    (give those solvers different CUDA streams).  With ``max_batch`` > 1 a slot starts up to that many
+    waiting requests of its model with the same time span together, as one lockstep batch (one merged
+    launch per fine step).  The solvers must not be used directly while the server exists."""
 
-    def __init__(self, solvers, max_queued: int = 8, models=None):
+    def __init__(self, solvers, max_queued: int = 8, models=None, max_batch: int = 1):
         solvers = list(solvers) if isinstance(solvers, (list, tuple)) else [solvers]
         models = [0] * len(solvers) if models is None else [int(m) for m in models]
         if len(models) != len(solvers):
@@ -485,6 +538,11 @@ class Server:
         _check(lib().ridg_server_create_slots(hs, ms, len(solvers), int(max_queued), C.byref(h)))
         self._h = h
         self._pending = {}
+        if max_batch != 1:
+            self.set_batch(max_batch)
+
+    def set_batch(self, max_batch: int):
+        _check(lib().ridg_server_set_batch(self._h, int(max_batch)))
 
     @property
     def solver(self):
