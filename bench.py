@@ -550,12 +550,15 @@ def precision_sweep(orders, t_final=0.01):
     return 0
 
 
-def serving_stream(n_req, t_rec=0.01, sizes=("50k", "200k", "800k"), slot_counts=(1, 2), contraction="tf32"):
+def serving_stream(n_req, t_rec=0.01, sizes=("50k", "200k", "800k"), slot_counts=(1, 2), contraction="tf32",
+                   batch_sizes=(1,)):
     """Shot-serving stream over the serving models (about 5e4 / 2e5 / 8e5 elements at N = 3 / 4 / 5,
     three layers, three rate levels; ``sizes`` picks a subset): n_req requests (model, surface
     source, 101-401 receivers; seed 5) with Poisson arrivals (seed 5) at 0.8x and 1.5x the measured
-    sequential rate, served with each number of slots per model in ``slot_counts``; FP32 with the
-    TF32 or BF16 split.  Prints one JSON line."""
+    sequential rate, served with each number of slots per model in ``slot_counts`` and, for each
+    size in ``batch_sizes``, slots that start up to that many waiting requests of their model as one
+    lockstep batch (the same arrival times for every setting; the sequential rate is that of one shot
+    at a time); FP32 with the TF32 or BF16 split.  Prints one JSON line."""
     import torch
 
     from paper_1506_00907_gb300 import ridg
@@ -575,7 +578,7 @@ def serving_stream(n_req, t_rec=0.01, sizes=("50k", "200k", "800k"), slot_counts
             slots[m].append(ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max,
                                         stream=st.cuda_stream, contraction=ctr))
     reqs = [(m % nm, src, rec) for m, src, rec in serving_requests(n_req)]
-    out = {"requests": n_req, "record_s": t_rec, "contraction": contraction,
+    out = {"requests": n_req, "record_s": t_rec, "contraction": contraction, "batch_sizes": list(batch_sizes),
            "models": [{"elements": int(w.K), "order": w.N, "levels": s[0].info.n_levels} for w, s in
                       zip(models, slots.values())],
            "arrivals": "Poisson (seed 5) at 0.8x and 1.5x the sequential rate; model, source and receiver count "
@@ -586,38 +589,89 @@ def serving_stream(n_req, t_rec=0.01, sizes=("50k", "200k", "800k"), slot_counts
         w = models[m]
         return sv.submit(src, w.f0, w.t_peak, 1.0, rec, t_rec, model=m)
 
-    def server(k):
+    def server(k, batch=1):
         sl = [slots[m][i] for m in range(nm) for i in range(k)]
-        return ridg.Server(sl, max_queued=n_req, models=[m for m in range(nm) for _ in range(k)])
+        return ridg.Server(sl, max_queued=n_req, models=[m for m in range(nm) for _ in range(k)], max_batch=batch)
 
     with server(kmax) as sv:  # buffers of every slot in place
         for t in [submit(sv, (m, (1000.0, 1000.0, 8.0), reqs[0][2])) for m in range(nm) for _ in range(kmax)]:
             sv.wait(t)
-    n_seq = min(n_req, 24)
+    n_seq = min(n_req, 48)
     with server(1) as sv:
         t0 = time.perf_counter()
         for r in reqs[:n_seq]:
             sv.wait(submit(sv, r))
         seq = n_seq / (time.perf_counter() - t0)
     out["sequential_shots_per_s"] = seq
-    for k in slot_counts:
-        for factor in (0.8, 1.5):
-            gaps = np.random.default_rng(5).exponential(1.0 / (factor * seq), n_req)
-            with server(k) as sv:
-                t0 = time.perf_counter()
-                arrive, tickets = 0.0, []
-                for i, r in enumerate(reqs):
-                    arrive += gaps[i]
-                    time.sleep(max(0.0, arrive - (time.perf_counter() - t0)))
-                    tickets.append(submit(sv, r))
-                lat = [sv.wait(t)[3]["total_s"] for t in tickets]
-                span = time.perf_counter() - t0 - gaps[0]
-            out[f"rate{factor}x_slots{k}"] = {"p50_s": float(np.percentile(lat, 50)),
-                                              "p99_s": float(np.percentile(lat, 99)), "shots_per_s": n_req / span,
-                                              "vs_sequential": n_req / span / seq}
+    for k, bsz, factor in [(k, b, f) for k in slot_counts for b in batch_sizes for f in (0.8, 1.5)]:
+        gaps = np.random.default_rng(5).exponential(1.0 / (factor * seq), n_req)
+        with server(k, bsz) as sv:
+            t0 = time.perf_counter()
+            arrive, tickets = 0.0, []
+            for i, r in enumerate(reqs):
+                arrive += gaps[i]
+                time.sleep(max(0.0, arrive - (time.perf_counter() - t0)))
+                tickets.append(submit(sv, r))
+            lat = [sv.wait(t)[3]["total_s"] for t in tickets]
+            span = time.perf_counter() - t0 - gaps[0]
+        key = f"rate{factor}x_slots{k}" + ("" if bsz == 1 else f"_batch{bsz}")
+        out[key] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                    "shots_per_s": n_req / span, "vs_sequential": n_req / span / seq}
     for ss in slots.values():
         for x in ss:
             x.close()
+    print(json.dumps(out), flush=True)
+    return 0
+
+
+def batch_bench(sizes=("50k", "200k"), t_rec=0.01, batches=(1, 2, 4), reps=3, contraction="tf32"):
+    """Lockstep shot batches (ridg_rtm_shots_device: one merged launch per fine step over every shot of
+    the batch) against the same shots one after another, on the serving models (surface sources and
+    receiver lines of the serving stream, seed 5), FP32 with the TF32 or BF16 split: shots/s and
+    DOF-updates/s, CUDA events around ``reps`` back-to-back batches of each size (device buffers, so
+    the host copies are left out).  Prints one JSON line."""
+    import torch
+
+    from paper_1506_00907_gb300 import ridg
+    from synth import serving_model, serving_requests
+
+    ctr = ridg.CONTRACT_TENSOR_BF16 if contraction == "bf16" else ridg.CONTRACT_TENSOR
+    reqs = serving_requests(4 * max(batches))
+    out = {"record_s": t_rec, "contraction": contraction, "reps": reps, "models": []}
+    for sz in sizes:
+        w = serving_model(sz)
+        mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+        st = torch.cuda.Stream()
+        s = ridg.Solver(mesh, w.N, w.c, w.rho, dtype="f32", cfl=w.cfl, n_levels_max=w.n_levels_max,
+                        stream=st.cuda_stream, contraction=ctr)
+        n_t = s.trace_len(t_rec)
+        shots = []
+        for _, src, rec in reqs[:max(batches)]:
+            shots.append(dict(source_xyz=src, f0=w.f0, t_peak=w.t_peak, amplitude=1.0, rec_xyz=rec,
+                              traces=torch.zeros((len(rec), n_t), dtype=torch.float64, device="cuda"),
+                              image_p=torch.zeros((w.K, s.Np), dtype=torch.float64, device="cuda"),
+                              image_q=torch.zeros((w.K, s.Np), dtype=torch.float64, device="cuda")))
+        row = {"elements": int(w.K), "order": w.N, "levels": s.info.n_levels}
+        s.rtm_shots_device(shots, t_rec)  # every shot's buffers in place
+        torch.cuda.synchronize()
+        for b in batches:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.rtm_shots_device(shots[:b], t_rec)
+            e0.record(st)
+            for _ in range(reps):
+                s.rtm_shots_device(shots[:b], t_rec)
+            e1.record(st)
+            torch.cuda.synchronize()
+            sec = e0.elapsed_time(e1) / 1e3
+            stt = s.shot_stats()
+            dof = (stt.dof_updates_forward + stt.dof_updates_backward) * reps
+            row[f"batch{b}"] = {"shots_per_s": reps * b / sec, "dof_updates_per_s": dof / sec,
+                                "ms_per_batch": 1e3 * sec / reps}
+        base = row[f"batch{batches[0]}"]["shots_per_s"]
+        for b in batches:
+            row[f"batch{b}"][f"vs_batch{batches[0]}"] = row[f"batch{b}"]["shots_per_s"] / base
+        out["models"].append(row)
+        s.close()
     print(json.dumps(out), flush=True)
     return 0
 
@@ -760,6 +814,9 @@ def main():
     ap.add_argument("--serving-sizes", default="50k,200k,800k", help="serving models (subset of 50k,200k,800k)")
     ap.add_argument("--serving-slots", default="1,2", help="slots per model to compare")
     ap.add_argument("--serving-contraction", default="tf32", choices=["tf32", "bf16"])
+    ap.add_argument("--serving-batch", default="1",
+                    help="batch sizes to compare: waiting requests of a model a slot starts together (1..4)")
+    ap.add_argument("--batch-bench", default="", help="lockstep batch throughput on these serving models (e.g. 50k,200k)")
     ap.add_argument("--serving-record", type=float, default=0.01, help="record length (s) of each served shot")
     ap.add_argument("--gradient", default="", nargs="?", const="box", choices=["", "box", "bench", "bench3"],
                     help="time the misfit gradient (on the adjoint box, or on the bench mesh with one or three levels) and exit")
@@ -789,7 +846,14 @@ def main():
         build()
         return serving_stream(args.serving_stream, t_rec=args.serving_record, sizes=tuple(args.serving_sizes.split(",")),
                               slot_counts=tuple(int(x) for x in args.serving_slots.split(",")),
-                              contraction=args.serving_contraction)
+                              contraction=args.serving_contraction,
+                              batch_sizes=tuple(int(x) for x in args.serving_batch.split(",")))
+    if args.batch_bench:
+        from paper_1506_00907_gb300.build import build
+
+        build()
+        return batch_bench(tuple(args.batch_bench.split(",")), t_rec=args.serving_record,
+                           contraction=args.serving_contraction)
     if args.precision_sweep:
         from paper_1506_00907_gb300.build import build
 
