@@ -260,30 +260,31 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB)
     else
       return A.wave[w];
   };
-  float* const arena_write = [&] {
+  // per-shot pointers, read where they are used (kernel parameters stay in the constant bank)
+  auto arena_write = [&]() -> float* {
     if constexpr (BATCH)
       return sShot.arena_write;
     else
       return A.arena_write;
-  }();
-  const float* const arena_read = [&] {
+  };
+  auto arena_read = [&]() -> const float* {
     if constexpr (BATCH)
       return sShot.arena_read;
     else
       return A.arena_read;
-  }();
-  double* const image_p = [&] {
+  };
+  auto image_p = [&]() -> double* {
     if constexpr (BATCH)
       return sShot.image_p;
     else
       return A.image_p;
-  }();
-  double* const image_q = [&] {
+  };
+  auto image_q = [&]() -> double* {
     if constexpr (BATCH)
       return sShot.image_q;
     else
       return A.image_q;
-  }();
+  };
   const int64_t slot0 = A.slot_lo + bidx * EPB;
   if (slot0 >= A.slot_hi) return;
   const int64_t blk = slot0 >> 5;
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB)
         int b = sBf[e];
         for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
         cp_async_bytes16(sX + e * (8 * NFPP) + f * 2 * NFPP + ch * 4,
-                         arena_read + (A.arena_offset + b) * (2 * NFPP) + ch * 4);
+                         arena_read() + (A.arena_offset + b) * (2 * NFPP) + ch * 4);
       }
     }
   }
@@ -399,7 +400,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB)
       const int im = i / (Np * CPN), rem = i - im * Np * CPN;
       if (!(A.mode & (im == 0 ? kModeImageP : kModeImageQ))) continue;
       const int n = rem / CPN, ch = rem - n * CPN;
-      const double* src = (im == 0 ? image_p : image_q) + (blk * Np + n) * 32 + lane0 + ch * 2;
+      const double* src = (im == 0 ? image_p() : image_q()) + (blk * Np + n) * 32 + lane0 + ch * 2;
       cp_async_bytes16(sImg + (im * Np + n) * EPB + ch * 2, src);
     }
   }
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB)
         const int e = col_e(c);
         int b = sBf[e];
         for (int ff = 0; ff < f; ++ff) b += (finfo_bc(sInfo[e * 4 + ff]) != 0);
-        rec = arena_write + (A.arena_offset + b) * (2 * NFPP);
+        rec = arena_write() + (A.arena_offset + b) * (2 * NFPP);
       }
 #pragma unroll
       for (int t = 0; t < NJ; ++t) {
@@ -832,8 +833,8 @@ __global__ void __launch_bounds__(TcOrder<N>::NT, TcOrder<N>::MINB)
       const float incP = h * (xS * xR + h * (t2p + h * t3p));
       const float incQ = h * (qS * qR + h * (t2q + h * t3q));
       const int64_t io = (blk * Np + n) * 32 + lane0 + e;
-      if (A.mode & kModeImageP) image_p[io] = sImg[(0 * Np + n) * EPB + e] - double(incP);
-      if (A.mode & kModeImageQ) image_q[io] = sImg[(1 * Np + n) * EPB + e] - double(incQ);
+      if (A.mode & kModeImageP) image_p()[io] = sImg[(0 * Np + n) * EPB + e] - double(incP);
+      if (A.mode & kModeImageQ) image_q()[io] = sImg[(1 * Np + n) * EPB + e] - double(incQ);
     }
 #pragma unroll
     for (int w = 0; w < W; ++w) {
