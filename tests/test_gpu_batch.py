@@ -126,6 +126,13 @@ def test_batch_device_buffers_and_limits():
     s.set_trace_budget(0)
     out = s.rtm_shots(shots[:1], w.t_final)
     assert np.array_equal(out[0][0], host[0][0]) and np.array_equal(out[0][1], host[0][1])
+    # a shot without receivers (no receiver run data) beside one with them
+    silent = dict(shots[0], rec_xyz=np.zeros((0, 3)))
+    mixed = s.rtm_shots([silent, shots[2]], w.t_final)
+    alone = _alone(s, silent, w.t_final, 0.0)
+    assert mixed[0][0].shape == (0, n_t)
+    assert np.array_equal(mixed[0][1], alone[1]) and np.array_equal(mixed[0][2], alone[2])
+    assert np.array_equal(mixed[1][0], host[2][0]) and np.array_equal(mixed[1][1], host[2][1])
 
 
 def test_server_batches_waiting_requests():
