@@ -418,7 +418,9 @@ int ridg_server_submit(ridg_server* sv, const ridg_shot_request* req, int64_t* t
  * with the same t_final, t_image_start and e_up, and runs them together as one lockstep batch
  * (ridg_rtm_shots: one merged launch per fine step); each request's results are those it gets
  * alone.  max_batch in 1 .. RIDG_MAX_BATCH; 1 (the default) runs one shot at a time.  Admission
- * counts the memory of the whole batch.  Errors: RIDG_E_INVALID_ARG. */
+ * counts the memory of the whole batch; a batch that fails (a request the library rejects, or too
+ * little memory for all of them) runs its requests one by one, each completing with its own status.
+ * Errors: RIDG_E_INVALID_ARG. */
 int ridg_server_set_batch(ridg_server* sv, int32_t max_batch);
 /* Waits at most timeout_s seconds (< 0: without limit) for a request.  When it has completed,
  * releases the ticket, fills timing (may be NULL) and returns the request's own status (0, or the

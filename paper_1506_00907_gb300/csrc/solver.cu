@@ -2673,43 +2673,69 @@ struct ridg_server {
       }
       Request* q = batch[0];
       const int32_t n = int32_t(batch.size());
-      int status = RIDG_OK;
-      std::string error;
-      try {
-        admit(s, q, n);
+      // runs fn, recording its error as the status of the requests it served
+      auto attempt = [](auto&& fn, int& status, std::string& error) {
+        status = RIDG_OK;
+        error.clear();
+        try {
+          fn();
+        } catch (const Error& e) {
+          status = e.code;
+          error = e.msg;
+        } catch (const std::bad_alloc&) {
+          status = RIDG_E_OOM;
+          error = "host allocation failed";
+        } catch (const std::exception& e) {
+          status = RIDG_E_INVALID_ARG;
+          error = e.what();
+        }
+      };
+      auto alone = [&](Request* r) {
+        ridg::run_host_shot(s->solver, r->r.source, r->rec.empty() ? nullptr : r->rec.data(), r->r.nrec,
+                            r->r.t_final, r->r.t_image_start, r->obs.empty() ? nullptr : r->obs.data(),
+                            r->r.traces_out, r->r.image_p, r->r.image_q, r->eup.empty() ? nullptr : r->eup.data(),
+                            s->buffers[0]);
+      };
+      std::vector<int> status(static_cast<size_t>(n), RIDG_OK);
+      std::vector<std::string> error(static_cast<size_t>(n));
+      auto admitted = [&](Request* r, int32_t shots) {
+        admit(s, r, shots);
         work_cv.notify_all();
-        if (n == 1) {
-          ridg::run_host_shot(s->solver, q->r.source, q->rec.empty() ? nullptr : q->rec.data(), q->r.nrec,
-                              q->r.t_final, q->r.t_image_start, q->obs.empty() ? nullptr : q->obs.data(),
-                              q->r.traces_out, q->r.image_p, q->r.image_q, q->eup.empty() ? nullptr : q->eup.data(),
-                              s->buffers[0]);
-        } else {
-          std::vector<ridg_shot_io> io(static_cast<size_t>(n));
-          for (int32_t i = 0; i < n; ++i) {
-            const Request* r = batch[size_t(i)];
-            io[size_t(i)] = ridg_shot_io{r->r.source, r->rec.empty() ? nullptr : r->rec.data(), r->r.nrec,
-                                         r->obs.empty() ? nullptr : r->obs.data(), r->r.traces_out, r->r.image_p,
-                                         r->r.image_q};
-          }
+      };
+      if (n == 1) {
+        attempt([&] {
+          admitted(q, 1);
+          alone(q);
+        }, status[0], error[0]);
+      } else {
+        std::vector<ridg_shot_io> io(static_cast<size_t>(n));
+        for (int32_t i = 0; i < n; ++i) {
+          const Request* r = batch[size_t(i)];
+          io[size_t(i)] = ridg_shot_io{r->r.source, r->rec.empty() ? nullptr : r->rec.data(), r->r.nrec,
+                                       r->obs.empty() ? nullptr : r->obs.data(), r->r.traces_out, r->r.image_p,
+                                       r->r.image_q};
+        }
+        attempt([&] {
+          admitted(q, n);
           ridg::run_host_shots(s->solver, n, io.data(), q->r.t_final, q->r.t_image_start,
                                q->eup.empty() ? nullptr : q->eup.data(), s->buffers);
-        }
-      } catch (const Error& e) {
-        status = e.code;
-        error = e.msg;
-      } catch (const std::bad_alloc&) {
-        status = RIDG_E_OOM;
-        error = "host allocation failed";
-      } catch (const std::exception& e) {
-        status = RIDG_E_INVALID_ARG;
-        error = e.what();
+        }, status[0], error[0]);
+        // a batch that failed (one bad request, or too little memory for all of them) runs its requests
+        // one by one, so that each gets its own result and status
+        if (status[0] != RIDG_OK)
+          for (int32_t i = 0; i < n; ++i)
+            attempt([&] {
+              admitted(batch[size_t(i)], 1);
+              alone(batch[size_t(i)]);
+            }, status[size_t(i)], error[size_t(i)]);
       }
       {
         std::lock_guard<std::mutex> lk(mu);
         const auto now = clock::now();
-        for (Request* r : batch) {
-          r->status = status;
-          r->error = error;
+        for (int32_t i = 0; i < n; ++i) {
+          Request* r = batch[size_t(i)];
+          r->status = status[size_t(i)];
+          r->error = error[size_t(i)];
           r->finished = now;
           r->done = true;
         }

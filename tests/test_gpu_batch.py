@@ -159,3 +159,28 @@ def test_server_batches_waiting_requests():
     # requests 0, 1, 3 (same record) form the first batch; 2 (shorter record) and 4 follow
     assert start[0] == start[1] == start[3]
     assert start[2] != start[0] and start[4] != start[0]
+
+
+def test_server_batch_with_a_failing_request():
+    """A request whose source lies outside the mesh, batched with good ones: it completes with its own
+    error (RIDG_E_NOT_FOUND) and the others with the results they give alone."""
+    w = tiny_layered_rtm(N=3, t_final=0.004)
+    s = _solver(w, "f32")
+    shots = _shots(w, s.trace_len(w.t_final))
+    alone = [_alone(s, sh, w.t_final, 0.0) for sh in shots[:2]]
+    with ridg.Server(s, max_queued=8, max_batch=4) as sv:
+        first = sv.submit(w.source_xyz, w.f0, w.t_peak, 1.0, w.receivers, 0.3, want_images=False)  # keeps it busy
+        time.sleep(0.2)
+        good0 = sv.submit(shots[0]["source_xyz"], shots[0]["f0"], shots[0]["t_peak"], 1.0, shots[0]["rec_xyz"],
+                          w.t_final)
+        bad = sv.submit((1e6, 0.0, 0.0), w.f0, w.t_peak, 1.0, w.receivers, w.t_final)
+        good1 = sv.submit(shots[1]["source_xyz"], shots[1]["f0"], shots[1]["t_peak"], shots[1]["amplitude"],
+                          shots[1]["rec_xyz"], w.t_final, observed=shots[1]["observed"])
+        sv.wait(first, timeout=300)
+        r0 = sv.wait(good0, timeout=300)
+        with pytest.raises(ridg.RidgError) as e:
+            sv.wait(bad, timeout=300)
+        assert e.value.code == -7  # RIDG_E_NOT_FOUND
+        r1 = sv.wait(good1, timeout=300)
+    for (tr, ip, iq), got in zip(alone, (r0, r1)):
+        assert np.array_equal(tr, got[0]) and np.array_equal(ip, got[1]) and np.array_equal(iq, got[2])
