@@ -297,9 +297,25 @@ typedef struct ridg_shot_stats {
    * moved in (1: all on the device) and the bytes copied to host memory (the backward run copies
    * the ones it reads back) */
   int64_t trace_chunks, host_trace_bytes;
+  /* 1 when the shot's time stepping ran as one CUDA-graph launch (ridg_set_graph_replay) */
+  int64_t graph_replay;
 } ridg_shot_stats;
 /* Synchronises the solver's stream, then returns the counters of the last shot. */
 int ridg_last_shot_stats(const ridg_solver* s, ridg_shot_stats* stats);
+
+/* CUDA-graph replay of the time stepping of repeated shots (on != 0; off by default).  A shot or
+ * lockstep batch (ridg_rtm_shot_device, ridg_rtm_shots_device, and the shots of a server's slots,
+ * whose buffers stay in place) whose launches would take exactly the arguments of the previous one
+ * -- the same number of shots, record length, image window, e_up and image mask, per shot the same
+ * wavelet, receiver count and device buffers (observed, traces, images) -- captures its stream work
+ * (every kernel launch, memset and device copy from the start of the forward run to the images)
+ * into a CUDA graph the second time, and launches that graph the times after: one launch instead of
+ * one per fine step.  Source and receiver positions and the observed data may differ, since the
+ * kernels read them from device tables uploaded before the stepping.  The results are those of the
+ * launches it replaces, bit for bit.  Profiling (ridg_set_profiling), a trace budget, the parts of
+ * a group and solvers on the default stream (which cannot be captured) run without graphs.  The paper has no counterpart.  Errors: RIDG_E_INVALID_ARG,
+ * RIDG_E_CUDA (the capture or instantiation failed). */
+int ridg_set_graph_replay(ridg_solver* s, int32_t on);
 
 /* Device memory for the boundary-trace records of a shot (Sec. 4.3; the forward run records the
  * traces of every boundary face of every active element at every fine step, the backward source run

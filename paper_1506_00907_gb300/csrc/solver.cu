@@ -404,6 +404,8 @@ struct ridg_solver {
   virtual const ridg_shot_stats& stats() = 0;
   virtual void set_profiling(int every) = 0;
   virtual void set_trace_budget(int64_t device_bytes) = 0;
+  // CUDA-graph replay of repeated shots with the same launch arguments (ridg_set_graph_replay)
+  virtual void set_graph_replay(bool on) = 0;
   // device bytes a shot of this record length would still allocate (arena growth, first-shot buffers)
   virtual size_t shot_extra_device_bytes(double t_final) const = 0;
   // the same for a batch of n shots in lockstep
@@ -555,6 +557,12 @@ class Engine final : public ridg_solver {
 
   ~Engine() override {
     for (auto e : prof_ev_) cudaEventDestroy(e);
+    drop_graph();
+  }
+  void set_graph_replay(bool on) override {
+    RIDG_CUDA(cudaStreamSynchronize(st_));
+    graph_on_ = on;
+    drop_graph();
   }
 
   void info(ridg_info* out) const override {
@@ -1274,9 +1282,15 @@ class Engine final : public ridg_solver {
       S[b].img_p->alloc(size_t(n_slots_) * Np_ * sizeof(double));
       S[b].img_q->alloc(size_t(n_slots_) * Np_ * sizeof(double));
     }
+    for (int b = 0; b < n; ++b)
+      if (io[b].nrec > 0) S[b].scale->reserve(kDataScaleWorkBytes);
     BatchArgs<real> batch{};
     const bool merged = n > 1;
+    double eu[3] = {0.0, 0.0, -1.0};
+    if (e_up) std::memcpy(eu, e_up, sizeof(eu));
 
+    // the time stepping: only work enqueued on the solver's stream (capturable as a CUDA graph)
+    auto steps = [&] {
     // ---- forward source runs
     for (int b = 0; b < n; ++b) zero_wave(S[b].w[0]);
     reset_time();
@@ -1346,7 +1360,6 @@ class Engine final : public ridg_solver {
       data[b] = io[b].observed ? io[b].observed : traces[b];
       const int64_t nrec = io[b].nrec;
       if (nrec > 0) {
-        S[b].scale->reserve(kDataScaleWorkBytes);
         cudaError_t e = data_scale(data[b], nrec * n_t, S[b].scale->p, st_);
         if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("data scale: ") + cudaGetErrorString(e)};
         if (hook_) hook_->combine_data_scale(*this, S[b].scale->p);
@@ -1355,8 +1368,6 @@ class Engine final : public ridg_solver {
         dscale_inv[b] = dptr<const double>(*S[b].scale) + 2;
       }
     }
-    double eu[3] = {0.0, 0.0, -1.0};
-    if (e_up) std::memcpy(eu, e_up, sizeof(eu));
     int64_t dof_before = dof_;
     if (tiered) tier_.begin_backward(tau_i + 1);
     NvtxRange nv_back("backward source and receiver runs");
@@ -1406,6 +1417,13 @@ class Engine final : public ridg_solver {
       if (io[b].image_p) image_out(dptr<double>(*S[b].img_p), dscale_inv[b], io[b].image_p);
       if (io[b].image_q) image_out(dptr<double>(*S[b].img_q), dscale_inv[b], io[b].image_q);
     }
+    };  // steps
+    // (the legacy default stream cannot be captured)
+    if (!graph_on_ || tiered || hook_ || prof_every_ > 0 || st_ == nullptr || st_ == cudaStreamLegacy) {
+      steps();
+    } else {
+      run_graphed(steps, graph_key(n, io, t_final, t_i, eu, S, traces));
+    }
     RIDG_CUDA(cudaGetLastError());
   }
 
@@ -1421,6 +1439,107 @@ class Engine final : public ridg_solver {
     ShotState& x = *extra_shots_[size_t(b - 1)];
     return ShotRef{x.w, &x.rec_slot, &x.rec_row, &x.traces_tmp, &x.arena, &x.q_snap, &x.ring_snap, &x.img_p, &x.img_q, &x.scale};
   }
+  // ---- CUDA-graph replay of a batch's time stepping
+  // Every argument the time stepping bakes into its launches: the batch's time span, e_up and image
+  // mode, per shot the wavelet (its values at every step are kernel arguments), the receiver count
+  // and the device address of every buffer it touches.  Source and receiver positions and the data
+  // values are read from device memory, uploaded before the stepping, so they may differ.
+  std::vector<uint64_t> graph_key(int32_t n, const ridg_shot_io* io, double t_final, double t_i, const double* eu,
+                                  const std::vector<ShotRef>& S, const std::vector<double*>& traces) const {
+    std::vector<uint64_t> k;
+    auto bits = [](double x) {
+      uint64_t u;
+      std::memcpy(&u, &x, sizeof(u));
+      return u;
+    };
+    auto ptr = [](const void* p) { return uint64_t(reinterpret_cast<uintptr_t>(p)); };
+    k.push_back(uint64_t(n));
+    k.push_back(bits(t_final));
+    k.push_back(bits(t_i));
+    for (int d = 0; d < 3; ++d) k.push_back(bits(eu[d]));
+    k.push_back(uint64_t(image_mode_));
+    k.push_back(uint64_t(contraction_));
+    for (int b = 0; b < n; ++b) {
+      const ridg_source& src = io[b].source;
+      k.push_back(uint64_t(src.kind));
+      for (double x : {src.f0, src.t_peak, src.amplitude, src.sample_dt}) k.push_back(bits(x));
+      k.push_back(uint64_t(src.n_samples));
+      uint64_t h = 1469598103934665603ull;  // FNV-1a over the samples
+      if (src.kind == RIDG_SRC_SAMPLED && src.samples)
+        for (int64_t i = 0; i < src.n_samples; ++i) {
+          const uint64_t u = bits(src.samples[i]);
+          for (int byte = 0; byte < 8; ++byte) h = (h ^ ((u >> (8 * byte)) & 0xffu)) * 1099511628211ull;
+        }
+      k.push_back(h);
+      k.push_back(uint64_t(io[b].nrec));
+      for (const void* p : {static_cast<const void*>(io[b].observed), static_cast<const void*>(traces[b]),
+                            static_cast<const void*>(io[b].image_p), static_cast<const void*>(io[b].image_q)})
+        k.push_back(ptr(p));
+      for (int w = 0; w < 2; ++w) {
+        const Wave<real>& wv = S[b].w[w];
+        const DBuf* wbufs[] = {&wv.q, &wv.ring, &wv.trace, &wv.inj_range, &wv.inj_w, &wv.inj_row};
+        for (const DBuf* d : wbufs) k.push_back(ptr(d->p));
+      }
+      const DBuf* sbufs[] = {S[b].rec_slot, S[b].rec_row, S[b].arena, S[b].q_snap,
+                             S[b].ring_snap, S[b].img_p, S[b].img_q, S[b].scale};
+      for (const DBuf* d : sbufs) k.push_back(ptr(d->p));
+    }
+    return k;
+  }
+
+  // The first run of a key runs directly; the second captures its stream work into a graph, which
+  // later runs of the same key launch instead of the individual kernels (with the host-side counters
+  // and time state of the captured run restored).
+  template <typename F>
+  void run_graphed(F&& steps, std::vector<uint64_t> key) {
+    if (graph_exec_ && key == graph_exec_key_) {
+      RIDG_CUDA(cudaGraphLaunch(graph_exec_, st_));
+      stats_ = graph_stats_;
+      tau_ = graph_tau_;
+      dof_ = graph_dof_;
+      ring_count_ = graph_ring_;
+      stats_.graph_replay = 1;
+      return;
+    }
+    if (!(graph_seen_ && key == graph_key_)) {
+      steps();
+      graph_key_ = std::move(key);
+      graph_seen_ = true;
+      return;
+    }
+    drop_graph();
+    RIDG_CUDA(cudaStreamBeginCapture(st_, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t g = nullptr;
+    try {
+      steps();
+    } catch (...) {
+      cudaStreamEndCapture(st_, &g);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      throw;
+    }
+    RIDG_CUDA(cudaStreamEndCapture(st_, &g));
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("graph instantiation: ") + cudaGetErrorString(e)};
+    graph_exec_ = ex;
+    graph_exec_key_ = std::move(key);
+    graph_stats_ = stats_;
+    graph_tau_ = tau_;
+    graph_dof_ = dof_;
+    graph_ring_ = ring_count_;
+    RIDG_CUDA(cudaGraphLaunch(graph_exec_, st_));
+    stats_.graph_replay = 1;
+  }
+  void drop_graph() {
+    if (graph_exec_) cudaGraphExecDestroy(graph_exec_);
+    graph_exec_ = nullptr;
+    graph_exec_key_.clear();
+    graph_key_.clear();
+    graph_seen_ = false;
+  }
+
   size_t qsize() const { return size_t(n_slots_) * 4 * Np_; }
   size_t trace_slot_elems() const { return size_t(n_slots_) * 8 * NFPP_; }
   size_t device_bytes() const {
@@ -2065,6 +2184,13 @@ class Engine final : public ridg_solver {
     DBuf rec_slot, rec_row, traces_tmp, arena, q_snap, ring_snap, img_p, img_q, scale;
   };
   std::vector<std::unique_ptr<ShotState>> extra_shots_;
+  // CUDA-graph replay (ridg_set_graph_replay): the key of the last direct run and the captured graph
+  bool graph_on_ = false, graph_seen_ = false;
+  std::vector<uint64_t> graph_key_, graph_exec_key_;
+  cudaGraphExec_t graph_exec_ = nullptr;
+  ridg_shot_stats graph_stats_{};
+  int64_t graph_tau_ = 0, graph_dof_ = 0;
+  std::vector<int> graph_ring_;
   int64_t tau_ = 0, dof_ = 0;
   std::vector<int> ring_count_;
   ridg_shot_stats stats_{};
@@ -2971,6 +3097,13 @@ int ridg_last_shot_stats(const ridg_solver* s, ridg_shot_stats* stats) {
     RIDG_NEED(s);
     if (!stats) throw Error{RIDG_E_INVALID_ARG, "stats is null"};
     *stats = const_cast<ridg_solver*>(s)->stats();
+  });
+}
+
+int ridg_set_graph_replay(ridg_solver* s, int32_t on) {
+  return guarded([&] {
+    RIDG_NEED(s);
+    s->set_graph_replay(on != 0);
   });
 }
 

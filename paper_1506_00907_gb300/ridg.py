@@ -26,7 +26,7 @@ EXPORTED = [
     "ridg_last_error", "ridg_version", "ridg_mesh_create", "ridg_mesh_destroy", "ridg_mesh_counts",
     "ridg_reference_operators", "ridg_solver_create", "ridg_solver_destroy", "ridg_solver_info",
     "ridg_solver_levels", "ridg_solver_nodes", "ridg_set_state", "ridg_set_history", "ridg_eval_rhs", "ridg_step",
-    "ridg_rtm_shots", "ridg_rtm_shots_device", "ridg_server_set_batch",
+    "ridg_rtm_shots", "ridg_rtm_shots_device", "ridg_server_set_batch", "ridg_set_graph_replay",
     "ridg_get_state", "ridg_energy", "ridg_trace_len", "ridg_rtm_shot", "ridg_rtm_shot_device",
     "ridg_last_shot_stats", "ridg_set_profiling", "ridg_energy_noalloc", "ridg_server_create", "ridg_server_create_slots", "ridg_server_submit",
     "ridg_server_wait", "ridg_server_destroy", "ridg_forward", "ridg_set_state_device", "ridg_get_state_device",
@@ -89,7 +89,7 @@ class ShotStats(C.Structure):
                 ("boundary_trace_bytes", C.c_int64), ("prof_forward_ms", C.c_double),
                 ("prof_backward_ms", C.c_double), ("prof_forward_launches", C.c_int64),
                 ("prof_backward_launches", C.c_int64), ("trace_chunks", C.c_int64),
-                ("host_trace_bytes", C.c_int64)]
+                ("host_trace_bytes", C.c_int64), ("graph_replay", C.c_int64)]
 
 
 class ShotRequest(C.Structure):
@@ -140,6 +140,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "ridg_rtm_shots_device": (C.c_int, [P, C.c_int32, P, C.c_double, C.c_double, P]),
         "ridg_last_shot_stats": (C.c_int, [P, P]),
         "ridg_set_profiling": (C.c_int, [P, C.c_int32]),
+        "ridg_set_graph_replay": (C.c_int, [P, C.c_int32]),
         "ridg_set_trace_budget": (C.c_int, [P, C.c_int64]),
         "ridg_energy_noalloc": (C.c_int, [P, P]),
         "ridg_forward": (C.c_int, [P, P, P, C.c_int64, C.c_double, P]),
@@ -433,6 +434,11 @@ class Solver:
 
     def set_profiling(self, every: int):
         _check(lib().ridg_set_profiling(self._h, int(every)))
+
+    def set_graph_replay(self, on: bool = True):
+        """Repeated shots with the same launch arguments run their time stepping as one CUDA-graph launch
+        (ridg_set_graph_replay)."""
+        _check(lib().ridg_set_graph_replay(self._h, 1 if on else 0))
 
     def set_trace_budget(self, device_bytes: int):
         """Device bytes for a shot's boundary-trace records; beyond them the records live in pinned
