@@ -629,7 +629,8 @@ def batch_bench(sizes=("50k", "200k"), t_rec=0.01, batches=(1, 2, 4), reps=3, co
     the batch) against the same shots one after another, on the serving models (surface sources and
     receiver lines of the serving stream, seed 5), FP32 with the TF32 or BF16 split: shots/s and
     DOF-updates/s, CUDA events around ``reps`` back-to-back batches of each size (device buffers, so
-    the host copies are left out).  Prints one JSON line."""
+    the host copies are left out), launched kernel by kernel and replayed as CUDA graphs.  Prints one
+    JSON line."""
     import torch
 
     from paper_1506_00907_gb300 import ridg
@@ -654,22 +655,27 @@ def batch_bench(sizes=("50k", "200k"), t_rec=0.01, batches=(1, 2, 4), reps=3, co
         row = {"elements": int(w.K), "order": w.N, "levels": s.info.n_levels}
         s.rtm_shots_device(shots, t_rec)  # every shot's buffers in place
         torch.cuda.synchronize()
-        for b in batches:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.rtm_shots_device(shots[:b], t_rec)
-            e0.record(st)
-            for _ in range(reps):
-                s.rtm_shots_device(shots[:b], t_rec)
-            e1.record(st)
-            torch.cuda.synchronize()
-            sec = e0.elapsed_time(e1) / 1e3
-            stt = s.shot_stats()
-            dof = (stt.dof_updates_forward + stt.dof_updates_backward) * reps
-            row[f"batch{b}"] = {"shots_per_s": reps * b / sec, "dof_updates_per_s": dof / sec,
-                                "ms_per_batch": 1e3 * sec / reps}
+        for graph in (False, True):
+            s.set_graph_replay(graph)
+            for b in batches:
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                for _ in range(2 if graph else 1):  # with graphs: the direct run and the capture
+                    s.rtm_shots_device(shots[:b], t_rec)
+                e0.record(st)
+                for _ in range(reps):
+                    s.rtm_shots_device(shots[:b], t_rec)
+                e1.record(st)
+                torch.cuda.synchronize()
+                sec = e0.elapsed_time(e1) / 1e3
+                stt = s.shot_stats()
+                dof = (stt.dof_updates_forward + stt.dof_updates_backward) * reps
+                row[f"batch{b}" + ("_graph" if graph else "")] = {
+                    "shots_per_s": reps * b / sec, "dof_updates_per_s": dof / sec, "ms_per_batch": 1e3 * sec / reps,
+                    "graph_replay": int(stt.graph_replay)}
+        s.set_graph_replay(False)
         base = row[f"batch{batches[0]}"]["shots_per_s"]
-        for b in batches:
-            row[f"batch{b}"][f"vs_batch{batches[0]}"] = row[f"batch{b}"]["shots_per_s"] / base
+        for key in [k for k in row if k.startswith("batch")]:
+            row[key][f"vs_batch{batches[0]}"] = row[key]["shots_per_s"] / base
         out["models"].append(row)
         s.close()
     print(json.dumps(out), flush=True)
