@@ -1459,6 +1459,9 @@ class Engine final : public ridg_solver {
     for (int d = 0; d < 3; ++d) k.push_back(bits(eu[d]));
     k.push_back(uint64_t(image_mode_));
     k.push_back(uint64_t(contraction_));
+    const DBuf* tables[] = {&geo_d_, &mat_d_, &nbr_d_, &finfo_d_, &bface_d_, &meta_d_, &Dt_d_, &Lt_d_, &fmask_d_,
+                            &perm_d_, &afrag_d_, &gtab_d_[0], &gtab_d_[1], &slot_of_d_, &pos_d_};
+    for (const DBuf* d : tables) k.push_back(ptr(d->p));
     for (int b = 0; b < n; ++b) {
       const ridg_source& src = io[b].source;
       k.push_back(uint64_t(src.kind));
