@@ -114,3 +114,30 @@ def test_server_slot_with_graph_replay():
         assert np.array_equal(tr, tr2) and np.array_equal(ip, ip2) and np.array_equal(iq, iq2)
     assert replays == 1
     torch.cuda.synchronize()
+
+
+def test_graph_replay_stays_off_with_profiling_or_a_trace_budget():
+    """Profiling events and the host-memory record tier need the shot launched step by step: with
+    either, repeated shots with fixed device buffers run directly (and give the same results)."""
+    w = tiny_layered_rtm(N=3, t_final=0.003)
+    (direct, _), (graphed, _) = _solvers(w, "f32")
+    n_t = direct.trace_len(w.t_final)
+    sh = [dict(source_xyz=w.source_xyz, f0=w.f0, t_peak=w.t_peak, amplitude=1.0, rec_xyz=w.receivers)]
+    bd = [_buffers(direct, w, len(w.receivers), n_t)]
+    bg = [_buffers(graphed, w, len(w.receivers), n_t)]
+    ref, _ = _run(direct, bd, sh, w)
+    total = direct.shot_stats().boundary_trace_bytes
+    graphed.set_profiling(1)
+    for _ in range(3):
+        got, rg = _run(graphed, bg, sh, w)
+        assert rg == 0
+        assert all(np.array_equal(a, b) for a, b in zip(ref[0], got[0]))
+    graphed.set_profiling(0)
+    graphed.set_trace_budget(max(total // 4, 1 << 16))
+    for _ in range(3):
+        got, rg = _run(graphed, bg, sh, w)
+        assert rg == 0 and graphed.shot_stats().trace_chunks > 1
+        assert all(np.array_equal(a, b) for a, b in zip(ref[0], got[0]))
+    graphed.set_trace_budget(0)  # all records on the device again: the graphs come back
+    modes = [_run(graphed, bg, sh, w)[1] for _ in range(3)]
+    assert modes == [0, 1, 1]
