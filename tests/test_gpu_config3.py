@@ -1,6 +1,6 @@
 """Precision of the FP32 product modes against the FP64 oracle on the 1/8-volume crop of the layered
-bench model (the survey's mixed-precision configuration) at N = 5 and 6: the TF32 split, the BF16
-and FP16 splits (the FP16 split is the default tensor-core mode at these orders) and plain FP32 on
+bench model (the mixed-precision sweep: source at 250 m depth, receivers at 260 m) at N = 5 and 6:
+the TF32 split, the BF16 and FP16 splits (the FP16 split is the default tensor-core mode at these orders) and plain FP32 on
 CUDA cores, relative L2 of the receiver traces and both
 images of a whole shot; the library's FP64 mode as well.
 
