@@ -1291,133 +1291,135 @@ class Engine final : public ridg_solver {
 
     // the time stepping: only work enqueued on the solver's stream (capturable as a CUDA graph)
     auto steps = [&] {
-    // ---- forward source runs
-    for (int b = 0; b < n; ++b) zero_wave(S[b].w[0]);
-    reset_time();
-    for (int b = 0; b < n; ++b) {
-      RIDG_CUDA(cudaMemsetAsync(traces[b], 0, size_t(std::max<int64_t>(io[b].nrec, 1)) * n_t * sizeof(double), st_));
-      sample(S[b], traces[b], n_t, 0, io[b].nrec);
-    }
-    auto forward_step = [&](int mode) {
-      StepArgs<real> a = fine_args(+1, 1, mode);
-      const int64_t t_rec = std::min<int64_t>(tau_, tau_f);
+      // ---- forward source runs
+      for (int b = 0; b < n; ++b) zero_wave(S[b].w[0]);
+      reset_time();
       for (int b = 0; b < n; ++b) {
-        ShotArgs<real>& sa = batch.shot[b];
-        sa = ShotArgs<real>{};
-        sa.wave[0] = wave_args(S[b].w[0]);
-        sa.wave[0].amp_mode = 1;
-        sa.wave[0].amp = real(wav[b](double(tau_) * dtl));
-        std::tie(sa.arena_write, a.arena_offset) = arena_at(b, t_rec, +1, a.slot_lo);
+        RIDG_CUDA(cudaMemsetAsync(traces[b], 0, size_t(std::max<int64_t>(io[b].nrec, 1)) * n_t * sizeof(double), st_));
+        sample(S[b], traces[b], n_t, 0, io[b].nrec);
       }
-      a.wave[0] = batch.shot[0].wave[0];
-      a.arena_write = batch.shot[0].arena_write;
-      launch_fine(a, +1, 1, merged ? &batch : nullptr, n);
+      auto forward_step = [&](int mode) {
+        StepArgs<real> a = fine_args(+1, 1, mode);
+        const int64_t t_rec = std::min<int64_t>(tau_, tau_f);
+        for (int b = 0; b < n; ++b) {
+          ShotArgs<real>& sa = batch.shot[b];
+          sa = ShotArgs<real>{};
+          sa.wave[0] = wave_args(S[b].w[0]);
+          sa.wave[0].amp_mode = 1;
+          sa.wave[0].amp = real(wav[b](double(tau_) * dtl));
+          std::tie(sa.arena_write, a.arena_offset) = arena_at(b, t_rec, +1, a.slot_lo);
+        }
+        a.wave[0] = batch.shot[0].wave[0];
+        a.arena_write = batch.shot[0].arena_write;
+        launch_fine(a, +1, 1, merged ? &batch : nullptr, n);
+      };
+      if (tiered) tier_.begin_forward(st_);
+      {
+        NvtxRange nv("forward source run");
+        for (int64_t g = 0; g < n_global; ++g) {
+          for (int64_t s = 0; s < NL_; ++s) forward_step(kModeRecord);
+          for (int b = 0; b < n; ++b) sample(S[b], traces[b], n_t, g + 1, io[b].nrec);
+        }
+      }
+      stats_.dof_updates_forward = dof_;
+      for (int b = 0; b < n; ++b)
+        RIDG_CUDA(cudaMemcpyAsync(S[b].q_snap->p, S[b].w[0].q.p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice,
+                                  st_));
+      // two more global steps (and the first right-hand side of a third) give, per level l, the
+      // right-hand sides at t_f + Delta t_l and t_f + 2 Delta t_l that start the backward run
+      for (int64_t i = 0; i <= 2 * NL_; ++i) {
+        int64_t t_now = tau_;
+        std::vector<int> before = ring_count_;
+        forward_step(t_now == tau_f ? kModeRecord : 0);
+        for (int l = 1; l <= L_; ++l) {
+          int64_t d = int64_t(1) << (L_ - l);
+          if (t_now == tau_f + 2 * d)
+            for (int b = 0; b < n; ++b) snapshot_history(S[b], l, before[l - 1]);
+        }
+      }
+      // ---- backward: source (replayed boundary) and receiver wavefields in lockstep
+      for (int b = 0; b < n; ++b) {
+        RIDG_CUDA(cudaMemcpyAsync(S[b].w[0].q.p, S[b].q_snap->p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice,
+                                  st_));
+        RIDG_CUDA(cudaMemcpyAsync(S[b].w[0].ring.p, S[b].ring_snap->p, 3 * qsize() * sizeof(real),
+                                  cudaMemcpyDeviceToDevice, st_));
+        zero_wave(S[b].w[1]);
+        RIDG_CUDA(cudaMemsetAsync(S[b].img_p->p, 0, S[b].img_p->bytes, st_));
+        RIDG_CUDA(cudaMemsetAsync(S[b].img_q->p, 0, S[b].img_q->bytes, st_));
+      }
+      std::fill(ring_count_.begin(), ring_count_.end(), 0);
+      tau_ = tau_f;
+      for (int b = 0; b < n; ++b) {
+        RIDG_CUDA(cudaMemsetAsync(S[b].w[0].trace.p, 0, S[b].w[0].trace.bytes, st_));
+        init_traces(S[b].w[0], mod3(tau_));
+      }
+      if (hook_) hook_->exchange(*this, 1, 1);
+      // the receiver run injects the data times a power of two that brings max |data| into [1, 2), so
+      // that the image products of small-amplitude shots stay inside the FP32 range; the images are
+      // divided by it on the way out (both steps exact)
+      std::vector<const double*> data(n), dscale(n, nullptr), dscale_inv(n, nullptr);
+      for (int b = 0; b < n; ++b) {
+        data[b] = io[b].observed ? io[b].observed : traces[b];
+        const int64_t nrec = io[b].nrec;
+        if (nrec > 0) {
+          cudaError_t e = data_scale(data[b], nrec * n_t, S[b].scale->p, st_);
+          if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("data scale: ") + cudaGetErrorString(e)};
+          if (hook_) hook_->combine_data_scale(*this, S[b].scale->p);
+          stats_.kernel_launches += 2;
+          dscale[b] = dptr<const double>(*S[b].scale) + 1;
+          dscale_inv[b] = dptr<const double>(*S[b].scale) + 2;
+        }
+      }
+      int64_t dof_before = dof_;
+      if (tiered) tier_.begin_backward(tau_i + 1);
+      NvtxRange nv_back("backward source and receiver runs");
+      while (tau_ > tau_i) {
+        StepArgs<real> a = fine_args(-1, 2, kModeReplay | image_mode_);
+        int64_t n_lo = tau_ / NL_;
+        double u = double(tau_ - n_lo * NL_) / double(NL_);
+        a.interp_n0 = int(n_lo - 1);
+        const double xs[4] = {-1.0, 0.0, 1.0, 2.0};
+        for (int i = 0; i < 4; ++i) {
+          double li = 1.0;
+          for (int j = 0; j < 4; ++j)
+            if (j != i) li *= (u - xs[j]) / (xs[i] - xs[j]);
+          a.interp_w[i] = li;
+        }
+        for (int d = 0; d < 3; ++d) a.e_up[d] = real(eu[d]);
+        for (int b = 0; b < n; ++b) {
+          ShotArgs<real>& sa = batch.shot[b];
+          sa = ShotArgs<real>{};
+          sa.wave[0] = wave_args(S[b].w[0]);
+          sa.wave[0].amp_mode = 1;
+          sa.wave[0].amp = real(wav[b](double(tau_) * dtl));
+          sa.wave[1] = wave_args(S[b].w[1]);
+          sa.wave[1].amp_mode = io[b].nrec > 0 ? 2 : 0;
+          sa.wave[1].data = data[b];
+          sa.wave[1].data_scale = dscale[b];
+          sa.wave[1].n_time = int(n_t);
+          std::tie(sa.arena_read, a.arena_offset) = arena_at(b, tau_, -1, a.slot_lo);
+          sa.image_p = dptr<double>(*S[b].img_p);
+          sa.image_q = dptr<double>(*S[b].img_q);
+        }
+        a.wave[0] = batch.shot[0].wave[0];
+        a.wave[1] = batch.shot[0].wave[1];
+        a.arena_read = batch.shot[0].arena_read;
+        a.image_p = batch.shot[0].image_p;
+        a.image_q = batch.shot[0].image_q;
+        launch_fine(a, -1, 2, merged ? &batch : nullptr, n);
+      }
+      stats_.dof_updates_backward = dof_ - dof_before;
+      if (tiered) {
+        tier_.after_copies(st_);
+        stats_.host_trace_bytes = tier_.host_bytes();
+      } else {
+        stats_.host_trace_bytes = 0;
+      }
+      for (int b = 0; b < n; ++b) {
+        if (io[b].image_p) image_out(dptr<double>(*S[b].img_p), dscale_inv[b], io[b].image_p);
+        if (io[b].image_q) image_out(dptr<double>(*S[b].img_q), dscale_inv[b], io[b].image_q);
+      }
     };
-    if (tiered) tier_.begin_forward(st_);
-    {
-      NvtxRange nv("forward source run");
-      for (int64_t g = 0; g < n_global; ++g) {
-        for (int64_t s = 0; s < NL_; ++s) forward_step(kModeRecord);
-        for (int b = 0; b < n; ++b) sample(S[b], traces[b], n_t, g + 1, io[b].nrec);
-      }
-    }
-    stats_.dof_updates_forward = dof_;
-    for (int b = 0; b < n; ++b)
-      RIDG_CUDA(cudaMemcpyAsync(S[b].q_snap->p, S[b].w[0].q.p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
-    // two more global steps (and the first right-hand side of a third) give, per level l, the
-    // right-hand sides at t_f + Delta t_l and t_f + 2 Delta t_l that start the backward run
-    for (int64_t i = 0; i <= 2 * NL_; ++i) {
-      int64_t t_now = tau_;
-      std::vector<int> before = ring_count_;
-      forward_step(t_now == tau_f ? kModeRecord : 0);
-      for (int l = 1; l <= L_; ++l) {
-        int64_t d = int64_t(1) << (L_ - l);
-        if (t_now == tau_f + 2 * d)
-          for (int b = 0; b < n; ++b) snapshot_history(S[b], l, before[l - 1]);
-      }
-    }
-    // ---- backward: source (replayed boundary) and receiver wavefields in lockstep
-    for (int b = 0; b < n; ++b) {
-      RIDG_CUDA(cudaMemcpyAsync(S[b].w[0].q.p, S[b].q_snap->p, qsize() * sizeof(real), cudaMemcpyDeviceToDevice, st_));
-      RIDG_CUDA(cudaMemcpyAsync(S[b].w[0].ring.p, S[b].ring_snap->p, 3 * qsize() * sizeof(real),
-                                cudaMemcpyDeviceToDevice, st_));
-      zero_wave(S[b].w[1]);
-      RIDG_CUDA(cudaMemsetAsync(S[b].img_p->p, 0, S[b].img_p->bytes, st_));
-      RIDG_CUDA(cudaMemsetAsync(S[b].img_q->p, 0, S[b].img_q->bytes, st_));
-    }
-    std::fill(ring_count_.begin(), ring_count_.end(), 0);
-    tau_ = tau_f;
-    for (int b = 0; b < n; ++b) {
-      RIDG_CUDA(cudaMemsetAsync(S[b].w[0].trace.p, 0, S[b].w[0].trace.bytes, st_));
-      init_traces(S[b].w[0], mod3(tau_));
-    }
-    if (hook_) hook_->exchange(*this, 1, 1);
-    // the receiver run injects the data times a power of two that brings max |data| into [1, 2), so
-    // that the image products of small-amplitude shots stay inside the FP32 range; the images are
-    // divided by it on the way out (both steps exact)
-    std::vector<const double*> data(n), dscale(n, nullptr), dscale_inv(n, nullptr);
-    for (int b = 0; b < n; ++b) {
-      data[b] = io[b].observed ? io[b].observed : traces[b];
-      const int64_t nrec = io[b].nrec;
-      if (nrec > 0) {
-        cudaError_t e = data_scale(data[b], nrec * n_t, S[b].scale->p, st_);
-        if (e != cudaSuccess) throw Error{RIDG_E_CUDA, std::string("data scale: ") + cudaGetErrorString(e)};
-        if (hook_) hook_->combine_data_scale(*this, S[b].scale->p);
-        stats_.kernel_launches += 2;
-        dscale[b] = dptr<const double>(*S[b].scale) + 1;
-        dscale_inv[b] = dptr<const double>(*S[b].scale) + 2;
-      }
-    }
-    int64_t dof_before = dof_;
-    if (tiered) tier_.begin_backward(tau_i + 1);
-    NvtxRange nv_back("backward source and receiver runs");
-    while (tau_ > tau_i) {
-      StepArgs<real> a = fine_args(-1, 2, kModeReplay | image_mode_);
-      int64_t n_lo = tau_ / NL_;
-      double u = double(tau_ - n_lo * NL_) / double(NL_);
-      a.interp_n0 = int(n_lo - 1);
-      const double xs[4] = {-1.0, 0.0, 1.0, 2.0};
-      for (int i = 0; i < 4; ++i) {
-        double li = 1.0;
-        for (int j = 0; j < 4; ++j)
-          if (j != i) li *= (u - xs[j]) / (xs[i] - xs[j]);
-        a.interp_w[i] = li;
-      }
-      for (int d = 0; d < 3; ++d) a.e_up[d] = real(eu[d]);
-      for (int b = 0; b < n; ++b) {
-        ShotArgs<real>& sa = batch.shot[b];
-        sa = ShotArgs<real>{};
-        sa.wave[0] = wave_args(S[b].w[0]);
-        sa.wave[0].amp_mode = 1;
-        sa.wave[0].amp = real(wav[b](double(tau_) * dtl));
-        sa.wave[1] = wave_args(S[b].w[1]);
-        sa.wave[1].amp_mode = io[b].nrec > 0 ? 2 : 0;
-        sa.wave[1].data = data[b];
-        sa.wave[1].data_scale = dscale[b];
-        sa.wave[1].n_time = int(n_t);
-        std::tie(sa.arena_read, a.arena_offset) = arena_at(b, tau_, -1, a.slot_lo);
-        sa.image_p = dptr<double>(*S[b].img_p);
-        sa.image_q = dptr<double>(*S[b].img_q);
-      }
-      a.wave[0] = batch.shot[0].wave[0];
-      a.wave[1] = batch.shot[0].wave[1];
-      a.arena_read = batch.shot[0].arena_read;
-      a.image_p = batch.shot[0].image_p;
-      a.image_q = batch.shot[0].image_q;
-      launch_fine(a, -1, 2, merged ? &batch : nullptr, n);
-    }
-    stats_.dof_updates_backward = dof_ - dof_before;
-    if (tiered) {
-      tier_.after_copies(st_);
-      stats_.host_trace_bytes = tier_.host_bytes();
-    } else {
-      stats_.host_trace_bytes = 0;
-    }
-    for (int b = 0; b < n; ++b) {
-      if (io[b].image_p) image_out(dptr<double>(*S[b].img_p), dscale_inv[b], io[b].image_p);
-      if (io[b].image_q) image_out(dptr<double>(*S[b].img_q), dscale_inv[b], io[b].image_q);
-    }
-    };  // steps
     // (the legacy default stream cannot be captured)
     if (!graph_on_ || tiered || hook_ || prof_every_ > 0 || st_ == nullptr || st_ == cudaStreamLegacy) {
       steps();
@@ -1435,9 +1437,12 @@ class Engine final : public ridg_solver {
     DBuf *rec_slot, *rec_row, *traces_tmp, *arena, *q_snap, *ring_snap, *img_p, *img_q, *scale;
   };
   ShotRef shot_ref(int b) {
-    if (b == 0) return ShotRef{w_, &rec_slot_, &rec_row_, &traces_tmp_, &arena_, &q_snap_, &ring_snap_, &img_p_, &img_q_, &scale_d_};
+    if (b == 0)
+      return ShotRef{w_, &rec_slot_, &rec_row_, &traces_tmp_, &arena_, &q_snap_, &ring_snap_, &img_p_, &img_q_,
+                     &scale_d_};
     ShotState& x = *extra_shots_[size_t(b - 1)];
-    return ShotRef{x.w, &x.rec_slot, &x.rec_row, &x.traces_tmp, &x.arena, &x.q_snap, &x.ring_snap, &x.img_p, &x.img_q, &x.scale};
+    return ShotRef{x.w,      &x.rec_slot,  &x.rec_row, &x.traces_tmp, &x.arena,
+                   &x.q_snap, &x.ring_snap, &x.img_p,   &x.img_q,      &x.scale};
   }
   // ---- CUDA-graph replay of a batch's time stepping
   // Every argument the time stepping bakes into its launches: the batch's time span, e_up and image
