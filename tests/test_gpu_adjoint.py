@@ -32,21 +32,41 @@ def _solver(w, dtype="f64", face_bc=None, N=None, n_levels_max=1):
     return ridg.Solver(mesh, w.N if N is None else N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=n_levels_max)
 
 
-@pytest.mark.parametrize("N", [2, 3])
-def test_adjoint_rhs_is_the_transpose_of_the_oracle_operator(N):
+@pytest.mark.parametrize("dtype,N", [("f64", 2), ("f64", 3), ("f32", 2), ("f32", 3), ("f32", 4)])
+def test_adjoint_rhs_is_the_transpose_of_the_oracle_operator(dtype, N):
+    """A^T against the transpose of the oracle's assembled operator, in both precisions."""
     w = adjoint_box_small()
     fb = mixed_bc(w)
     c = w.c_observed  # a velocity other than the reference one: tau stays that of w.c
     prob = make_problem(w.xyz, w.tets, w.c, w.rho, N, face_bc=fb, default_bc=w.default_bc, cfl=w.cfl, n_levels_max=1)
     AT = assemble_operator(frozen_geometry(prob.geo, c)).T.tocsr()
-    s = _solver(w, face_bc=fb, N=N)
+    s = _solver(w, dtype=dtype, face_bc=fb, N=N)
     s.set_velocity(c)
     lam = random_state(w.K, s.Np, seed=41)
+    if dtype == "f32":
+        lam = lam.astype(np.float32).astype(np.float64)  # the FP32 solver's own input
     ref = (AT @ lam.reshape(-1)).reshape(lam.shape)
     out = s.eval_adjoint_rhs(lam)
-    assert rel_l2(out, ref) < TOL["f64"]
+    assert rel_l2(out, ref) < TOL[dtype]
     per = np.linalg.norm((out - ref).reshape(w.K, -1), axis=1) / np.linalg.norm(ref.reshape(w.K, -1), axis=1)
-    assert per.max() < 100 * TOL["f64"]
+    assert per.max() < 100 * TOL[dtype]
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_adjoint_rhs_fp32_on_the_box(N):
+    """FP32 A^T on the 648-element box (21 blocks of element slots, a ragged last one) against the
+    FP64 library operator, element by element."""
+    w = adjoint_box()
+    mesh = ridg.Mesh(w.xyz, w.tets, default_bc=w.default_bc)
+    lam = random_state(w.K, (N + 1) * (N + 2) * (N + 3) // 6, seed=43).astype(np.float32).astype(np.float64)
+    outs = {}
+    for dtype in ("f32", "f64"):
+        sv = ridg.Solver(mesh, N, w.c, w.rho, dtype=dtype, cfl=w.cfl, n_levels_max=1)
+        outs[dtype] = sv.eval_adjoint_rhs(lam)
+    assert rel_l2(outs["f32"], outs["f64"]) < TOL["f32"]
+    per = np.linalg.norm((outs["f32"] - outs["f64"]).reshape(w.K, -1), axis=1) / np.linalg.norm(
+        outs["f64"].reshape(w.K, -1), axis=1)
+    assert per.max() < 100 * TOL["f32"]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
